@@ -1,0 +1,26 @@
+"""FP64 CPU oracle for the per-iteration hot path of the DTT/FFT displacement solver.
+
+TEST INFRASTRUCTURE.  This package is a plain, slow, obviously-correct
+restatement of the paper's method (arXiv 2607.05929, "A robust and versatile
+parallel FFT-based mechanical solver for general non-periodic and periodic
+boundary conditions") in NumPy/SciPy, in FP64.  It shares no code with the
+CUDA path.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import it; the product path never does.
+
+Modules and what they restate:
+
+* ``bc``          BC -> symmetry -> per-axis transform kind (Sec. 2.2, Eq. GeneralBCtobesolved; Table 1)
+* ``transforms``  the five forward DTs of Table 1 and their inverses (Sec. 2.4, Sec. 2.7.2)
+* ``stencils``    HEX1 / TETRA2 gradient and divergence with ghost voxels (Sec. 2.5, Remark 1)
+* ``green``       B0 and 2mu0 discrete Green operators (Sec. 2.6.2-2.6.3, Eqs. NSGO1_*, NSGO2_*)
+* ``laws``        small-strain constitutive laws (Sec. 3.1; cubic elasticity as in Sec. 3.3)
+* ``anderson``    Anderson acceleration on p (Sec. 2.3, Algorithm 1)
+* ``solver``      Algorithm 1, one load step
+* ``direct``      the same discrete problem assembled as a sparse matrix and solved directly
+
+Parity status of each part is stated in the module headers; Anderson's
+acceleration step has no closed form to pin it against beyond its own
+definition (parity unpinned beyond self-consistency: its decisions are fixed
+by the stated rule and the fixed point it reaches is pinned by the direct
+solve and the laminate closed forms).
+"""

@@ -1,0 +1,152 @@
+"""Algorithm 1 (Sec. 2.4): one load step of the accelerated displacement fixed point.
+
+Per iteration m, in the order of Algorithm 1:
+
+  a1  G = grad_d u^f + grad_d u*                      (voxel points)
+  a2  P = F(G, committed state)                        (the behaviour law)
+  a3  D = div_d P  (+ D*, zero for traction-free faces)
+  a4  err = h1 sqrt(S_D / S_P) vs eps  (Eq. equilibrium_condition; S_D = sum of D^2
+      over the transformed node components, S_P = sum over voxel points of
+      ||P||_F^2 / n_ppv: squared L2 norms, which makes err dimensionless)
+      p  = div_d (R0 : grad_d u^f) - D                (Eq. div_pol)
+  a5  Anderson on p                                    (anderson.py)
+  a6  forward DT of each component of p                (Table 1, x then y then z)
+  a7  B0 / 2mu0 Green operator                         (Eqs. NSGO1_*, NSGO2_*)
+  a8  inverse DT -> u^f                                (dismissed nodes = 0)
+
+On convergence the committed state is updated from the converged strain (a9).
+"""
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import anderson as anderson_mod
+from .bc import Grid
+from .green import green_factor
+from .laws import b0_apply, phase_groups, stress
+from .stencils import div, full_nodes, grad, grad_full, n_points
+from .transforms import dt3d_forward, dt3d_inverse
+
+
+@dataclass
+class Report:
+    iterations: int
+    converged: bool
+    err: list = field(default_factory=list)
+    accelerated: list = field(default_factory=list)
+    mean_P: np.ndarray = None
+    mean_G: np.ndarray = None
+
+
+class Problem:
+    """Plain-data problem built from a synthetic.Workload."""
+
+    def __init__(self, wl, fast=None):
+        self.wl = wl
+        self.grid = Grid(wl.n, wl.bc, wl.h)
+        self.scheme = wl.scheme
+        self.npp = n_points(wl.scheme)
+        self.lambda0 = 0.0 if wl.green == "MU0" else float(wl.lambda0)
+        self.mu0 = float(wl.mu0)
+        self.groups = phase_groups(wl.phase, len(wl.materials))
+        self.fast = fast
+        self.masks = [self.grid.dof_mask(q) for q in range(3)]
+        self.factors = [green_factor(self.grid, q, wl.scheme, self.lambda0, self.mu0) for q in range(3)]
+        has_j2 = any(m.law == 2 for m in wl.materials)
+        self.state = None
+        if has_j2:
+            shp = (self.npp,) + self.grid.n
+            self.state = {"ep": np.zeros((self.npp, 3, 3) + self.grid.n), "p": np.zeros(shp)}
+        self.uf = np.zeros(self.grid.node_shape)
+
+    # --- a0: prescribed displacement and its discrete gradient ------------------------
+    def ustar_full(self, A=None, b=None):
+        """u* on the full (n+1)^3 node grid (affine: u*_q = A[q] . x + b[q])."""
+        A = self.wl.A if A is None else A
+        b = self.wl.b if b is None else b
+        n, h = self.grid.n, self.grid.h
+        x = [np.arange(n[a] + 1) * h[a] for a in range(3)]
+        X = np.meshgrid(*x, indexing="ij")
+        return np.stack([A[q, 0] * X[0] + A[q, 1] * X[1] + A[q, 2] * X[2] + b[q] for q in range(3)])
+
+    def grad_ustar(self, A=None, b=None):
+        return grad_full(self.ustar_full(A, b), self.grid, self.scheme)
+
+    # --- pieces of one iteration ------------------------------------------------------
+    def residual(self, uf, Gs):
+        """a1-a4 and p: returns (p, D, P, G, S_D, S_P)."""
+        Gf = grad(uf, self.grid, self.scheme)
+        G = Gf + Gs
+        P, _ = stress(G, self.wl.materials, self.groups, self.state)
+        D = div(P, self.grid, self.scheme)
+        for q in range(3):
+            D[q][~self.masks[q]] = 0.0
+        S_D = float(np.sum(D * D))
+        S_P = float(np.sum(P * P)) / self.npp
+        p = div(b0_apply(Gf, self.lambda0, self.mu0), self.grid, self.scheme) - D
+        for q in range(3):
+            p[q][~self.masks[q]] = 0.0
+        return p, D, P, G, S_D, S_P
+
+    def error(self, S_D, S_P):
+        if S_P > 0.0:
+            return self.grid.h[0] * np.sqrt(S_D / S_P)
+        return 0.0 if S_D == 0.0 else np.inf
+
+    def green_update(self, q_field):
+        """a6-a8: u^f = iDT(DGO(DT(q)))."""
+        g = self.grid
+        out = np.zeros(g.node_shape)
+        for q in range(3):
+            spec = dt3d_forward(q_field[q], g.kind[q], g.n, fast=self.fast)
+            spec = spec * self.factors[q]
+            out[q] = dt3d_inverse(spec, g.kind[q], g.n, g.N, fast=self.fast)
+        return out
+
+    # --- Algorithm 1, one load step -----------------------------------------------------
+    def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True):
+        wl = self.wl
+        tol = wl.tol if tol is None else tol
+        max_iter = wl.max_iter if max_iter is None else max_iter
+        Gs = self.grad_ustar(A, b)
+        uf = self.uf.copy() if uf0 is None else np.array(uf0, dtype=np.float64)
+        hist = []  # (q_j, g_j) couples
+        q_prev = None
+        rep = Report(iterations=0, converged=False)
+        for m in range(max_iter + 1):
+            p, D, P, G, S_D, S_P = self.residual(uf, Gs)
+            err = self.error(S_D, S_P)
+            rep.err.append(err)
+            rep.iterations = m
+            if err < tol:
+                rep.converged = True
+                break
+            if m == max_iter:
+                break
+            if not np.isfinite(err):
+                break
+            if q_prev is not None:
+                hist.append((q_prev, p))
+                if len(hist) > wl.anderson_depth:
+                    hist.pop(0)
+            q = p
+            if anderson and anderson_mod.accelerate_now(m, wl.anderson_period, len(hist), wl.anderson_depth):
+                c = anderson_mod.coefficients([g_ - q_ for q_, g_ in hist])
+                if c is not None:
+                    q = sum(cj * g_ for cj, (_, g_) in zip(c, hist))
+                    rep.accelerated.append(m)
+            q_prev = q
+            uf = self.green_update(q)
+        self.uf = uf
+        rep.mean_P = P.mean(axis=(0, 3, 4, 5))
+        rep.mean_G = G.mean(axis=(0, 3, 4, 5))
+        if self.state is not None and rep.converged:
+            _, self.state = stress(G, wl.materials, self.groups, self.state)
+        self.last = {"P": P, "G": G, "D": D}
+        return uf, rep
+
+
+def node_field_full(problem, uf):
+    """Total displacement u = u^f + u* on the full node grid (for reporting)."""
+    return full_nodes(uf, problem.grid) + problem.ustar_full()
