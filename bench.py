@@ -1,0 +1,469 @@
+#!/usr/bin/env python
+"""Benchmark of the fixed-point solver's hot path: voxel-iterations per second.
+
+Workload (the 256^3 polycrystal of the paper's method at scale): 256^3 voxels,
+Voronoi polycrystal of 500 grains (seeds uniform in the box, seed 2), cubic
+elasticity C11 = 168, C12 = 121, C44 = 75 GPa with orientations uniform on
+SO(3) (seed 3), small strain, double-tetrahedron (TETRA2) scheme, B0 Green
+operator with lambda0 = C12 and mu0 = (C44 + (C11 - C12)/2)/2, Dirichlet on
+the x faces (all components, eps_xx = 1e-3), Neumann y, periodic z,
+equilibrium tolerance 1e-6, Anderson depth 4 every 3 iterations.
+
+One step = one load step of Algorithm 1 from u^f = 0 to convergence (every
+row of the hot path: gradient, law, divergence and norms, Anderson,
+forward DTs, Green operator, inverse DTs).  value = voxels x iterations / time.
+
+The device-resident number (`value`) times the steps with the phase map
+already on the GPU; `e2e` times the same steps through the C ABI with host
+buffers (phase map in, displacement field out, pinned memory).  The oracle
+(CPU, FP64) is timed on a bounded sample beside it (`cpu_baseline`);
+`--impl reference` times only the oracle.
+
+Multi-GPU: each rank solves its own replica (replicas only; no collective on
+the data path); value = all ranks' voxel-iterations / max rank time.
+"""
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "voxel-iterations/s"
+UNIT = "voxel-it/s"
+WORKLOAD_NAME = ("voronoi_polycrystal_256: 256^3 voxels, 500-grain Voronoi, cubic elastic C11/C12/C44="
+                 "168/121/75 GPa, random orientations, TETRA2, B0, x Dirichlet / y Neumann / z periodic, "
+                 "eps_xx=1e-3, tol=1e-6, Anderson 4/3")
+REF_SLAB = 32  # z-planes of the oracle's bounded sample
+
+
+# ----------------------------------------------------------------------------------------
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--grains", type=int, default=500)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed beside (0 = skip)")
+    return ap.parse_args(argv)
+
+
+def workload(n, grains):
+    """The synthetic workload; the phase map is cached in the temp dir (generation is exact and seeded)."""
+    import synthetic as syn
+
+    key = hashlib.sha1(f"voronoi-{n}-{grains}-2-3-v1".encode()).hexdigest()[:16]
+    path = os.path.join(tempfile.gettempdir(), f"fftm_phase_{key}.npy")
+    phase = None
+    if os.path.exists(path):
+        try:
+            phase = np.load(path)
+        except Exception:
+            phase = None
+    if phase is None:
+        phase, _ = syn.voronoi((n, n, n), grains, 2)
+        try:
+            tmp = f"{path}.{os.getpid()}.npy"
+            np.save(tmp, phase)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+    quats = syn.shoemake_quaternions(grains, 3)
+    mats = [syn.Material(1, (168.0, 121.0, 75.0), tuple(q)) for q in quats]
+    A = np.zeros((3, 3))
+    A[0, 0] = 1e-3
+    C11, C12, C44 = 168.0, 121.0, 75.0
+    return syn.Workload(name=f"voronoi_polycrystal_{n}", n=(n, n, n), phase=phase, materials=mats,
+                        bc=[[["D"] * 3] * 2, [["N"] * 3] * 2, [["P"] * 3] * 2], scheme="TETRA2", green="B0",
+                        lambda0=C12, mu0=0.5 * (C44 + 0.5 * (C11 - C12)), tol=1e-6, A=A, max_iter=1000)
+
+
+# ---- distributed harness (replicas) ------------------------------------------------------
+class Dist:
+    def __init__(self, use_cuda):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("nccl" if use_cuda else "gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def reduce(self, value, op):
+        """All-reduce of a float over ranks ('max' or 'sum')."""
+        if not self.pg:
+            return value
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX if op == "max" else self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def timed_steps(step, steps, warmup, dist, sync, start_timer, stop_timer):
+    """W untimed steps, then K steps bracketed by barrier + sync; returns (seconds, units)."""
+    for _ in range(warmup):
+        step()
+    dist.barrier()
+    sync()
+    start_timer()
+    units = 0.0
+    for _ in range(steps):
+        units += step()
+    sync()
+    sec = stop_timer()
+    dist.barrier()
+    return sec, units
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def element_counts(wl):
+    """Stored nodes, and per axis the field elements (all components) one pass over it moves:
+    a component's transform along an axis covers n+1 (Neumann/Neumann), n (periodic, or mixed
+    Neumann/Dirichlet) or n-1 (Dirichlet/Dirichlet) node positions (Table 1)."""
+    N = [wl.n[a] if wl.bc[a][0][0] == "P" else wl.n[a] + 1 for a in range(3)]
+    nodes = N[0] * N[1] * N[2]
+    per_axis = []
+    for a in range(3):
+        tot = 0
+        for q in range(3):
+            l, r = wl.bc[a][0][q], wl.bc[a][1][q]
+            L = wl.n[a] + (0 if l == "P" else (1 if (l, r) == ("N", "N") else (-1 if (l, r) == ("D", "D") else 0)))
+            tot += L * int(np.prod([N[b] for b in range(3) if b != a]))
+        per_axis.append(tot)
+    return nodes, per_axis
+
+
+def traffic_record(kernel):
+    """ncu DRAM bytes per launch recorded in profiles/, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec if h == rec.get("source_sha1") else None
+
+
+# ---- the oracle's bounded sample ------------------------------------------------------------
+def oracle_sample(wl, iterations):
+    """Time `iterations` fixed-point iterations of the FP64 oracle on a 256 x 256 x REF_SLAB z-slab
+    of the workload (same microstructure planes, same per-voxel work); returns voxel-it/s."""
+    import copy
+
+    from oracle.solver import Problem
+
+    w = copy.copy(wl)
+    w.n = (wl.n[0], wl.n[1], min(REF_SLAB, wl.n[2]))
+    w.phase = np.ascontiguousarray(wl.phase[:, :, : w.n[2]])
+    pr = Problem(w)
+    Gs = pr.grad_ustar()
+    u = np.zeros(pr.grid.node_shape)
+    t0 = time.perf_counter()
+    for _ in range(iterations):
+        p, D, P, G, SD, SP = pr.residual(u, Gs)
+        u = pr.green_update(p)
+    sec = time.perf_counter() - t0
+    vox = w.n[0] * w.n[1] * w.n[2]
+    return vox * iterations / sec, sec, f"{iterations} fixed-point iteration(s) of the FP64 oracle on a " \
+        f"{w.n[0]}x{w.n[1]}x{w.n[2]} z-slab of the workload (same phase map planes, same per-voxel work)"
+
+
+def reference_arm(args):
+    dist_rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if dist_rank != 0:
+        return 0
+    wl = workload(args.n, args.grains)
+    for _ in range(args.warmup):
+        oracle_sample(wl, 1)
+    total_vox_it = 0.0
+    total_sec = 0.0
+    sample = None
+    for _ in range(args.steps):
+        v, sec, sample = oracle_sample(wl, 1)
+        total_sec += sec
+        total_vox_it += v * sec
+    value = total_vox_it / total_sec
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "threads_note": "scipy.fft with workers=-1; NumPy elementwise on one thread"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---- the GPU arm ----------------------------------------------------------------------------
+def gpu_arm(args):
+    import torch
+
+    from paper_2607_05929_gb300 import build as libbuild
+    from paper_2607_05929_gb300 import fftm as F
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the GPU arm has no CPU fallback")
+    dist = Dist(True)
+    torch.cuda.set_device(dist.local)
+    if dist.rank == 0:
+        libbuild.build()
+    dist.barrier()
+    F.load_library()
+    wl = workload(args.n, args.grains)
+    stream = torch.cuda.Stream()
+    ctx = F.fftm_ctx_create(dist.local, stream)
+    mats = [(m.law, m.params, m.quat) for m in wl.materials]
+
+    def make(precision):
+        desc, keep = F.make_desc(wl.n, wl.phase, mats, wl.bc, scheme=wl.scheme, green=wl.green,
+                                 lambda0=wl.lambda0, mu0=wl.mu0, precision=precision, tol=wl.tol,
+                                 max_iter=wl.max_iter)
+        p = F.fftm_problem_create(ctx, desc)
+        F.fftm_set_load(p, wl.A)
+        return p
+
+    prob = make(args.precision)
+    nvox = wl.n[0] * wl.n[1] * wl.n[2]
+    last = {}
+
+    def step():
+        F.fftm_reset_state(prob)
+        st, r, _, _ = F.fftm_solve_step(prob)
+        if not r["converged"]:
+            raise RuntimeError(f"solve did not converge: {r}")
+        last.update(r)
+        return float(nvox * r["iterations"])
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dist.local)
+
+    def start_timer():
+        ev0.record(stream)
+        F.fftm_set_profiling(prob, True)
+        L0[0] = F.fftm_kernel_launches(prob)
+        clocks.start()
+
+    def stop_timer():
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / 1000.0
+
+    L0 = [0]
+    sec, units = timed_steps(step, args.steps, args.warmup, dist, torch.cuda.synchronize, start_timer, stop_timer)
+    clk = clocks.stop()
+    launches = F.fftm_kernel_launches(prob) - L0[0]
+    ktimes = F.fftm_kernel_times(prob)
+    F.fftm_set_profiling(prob, False)
+    sec_max = dist.reduce(sec, "max")
+    units_all = dist.reduce(units, "sum")
+    value = units_all / sec_max
+    iters = last["iterations"]
+
+    # ---- roofline of the dominant kernel (algorithmic bytes / CUDA-event time) ----
+    esz = 4 if args.precision == "fp32" else 8
+    lo = 2 if args.precision == "fp32" else 1  # u^f carried as hi + lo in FP32
+    nodes, per_axis = element_counts(wl)
+    it_total = iters * args.steps
+    acc_total = last["n_accelerated"] * args.steps
+    bytes_cat = {
+        "residual": it_total_plus1(args.steps, iters) * (nodes * 3 * esz * (lo + 1) + nvox * 2),
+        "pass_x": it_total * per_axis[0] * esz * (2 + (1 + 2 * lo)),  # fwd r+w, inv r + base r+w
+        "pass_y": it_total * per_axis[1] * esz * 4,
+        "pass_z_fused": it_total * per_axis[2] * esz * 2,
+        # Gram: 4 D reads; combination: 4 D + 4 u reads, work + base writes
+        "anderson": acc_total * nodes * 3 * esz * (4 + 4 + 4 * lo + 1 + lo),
+    }
+    rows = {}
+    for k, b in bytes_cat.items():
+        ms, n = ktimes.get(k, (0.0, 0))
+        if ms > 0:
+            rows[k] = {"ms": ms, "launches": n, "GBps": b / (ms * 1e-3) / 1e9}
+    dom = max(rows, key=lambda k: rows[k]["ms"])
+    peaks, peak_src = measured_peaks()
+    achieved = rows[dom]["GBps"]
+    traffic = traffic_record(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "algorithmic_bytes_per_launch": bytes_cat[dom] / max(1, rows[dom]["launches"]),
+                "per_category": rows}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sec_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "precision": args.precision,
+                       "iterations_per_step": iters, "anderson_steps_per_step": last["n_accelerated"],
+                       "l2": "inputs larger than L2 (working set several GB; no flush needed)",
+                       "parallelism": f"replicas x{dist.world}"},
+            "roofline": roofline, "gpu_launches": launches, "clocks": clk}
+
+    # ---- FP64 path beside it (same workload, device-resident) ----
+    if args.fp64_steps > 0 and args.precision == "fp32":
+        F.fftm_problem_destroy(prob)
+        prob = make("fp64")
+        step()  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u64 = sum(step() for _ in range(args.fp64_steps))
+        e1.record(stream)
+        e1.synchronize()
+        s64 = e0.elapsed_time(e1) / 1000.0
+        line["fp64_path"] = {"value": u64 / s64, "unit": UNIT, "iterations_per_step": last["iterations"],
+                             "steps": args.fp64_steps}
+        F.fftm_problem_destroy(prob)
+        prob = make(args.precision)
+
+    # ---- end to end through the C ABI with host buffers ----
+    if not args.no_e2e:
+        ph_host = torch.empty(nvox * 2, dtype=torch.uint8, pin_memory=True)
+        ph_np = ph_host.numpy().view(np.uint16)
+        ph_np[:] = np.ascontiguousarray(wl.phase.transpose(2, 1, 0)).ravel()
+        ubytes = F.fftm_field_bytes(prob, F.FFTM_FIELD_U)
+        u_host = torch.empty(ubytes, dtype=torch.uint8, pin_memory=True)
+
+        def e2e_step():
+            F.fftm_set_phase_raw(prob, ph_host.data_ptr())
+            F.fftm_set_load(prob, wl.A)
+            F.fftm_reset_state(prob)
+            st, r, _, _ = F.fftm_solve_step(prob)
+            F.fftm_get_field(prob, F.FFTM_FIELD_U, u_host)
+            return float(nvox * r["iterations"])
+
+        t = [0.0]
+        es, eu = timed_steps(e2e_step, args.steps, 1, dist, torch.cuda.synchronize,
+                             lambda: t.__setitem__(0, time.perf_counter()),
+                             lambda: time.perf_counter() - t[0])
+        es = dist.reduce(es, "max")
+        eu = dist.reduce(eu, "sum")
+        line["e2e"] = {"value": eu / es, "unit": UNIT, "h2d_bytes_per_step": nvox * 2 + 96,
+                       "d2h_bytes_per_step": ubytes + 128}
+
+    # ---- CPU baseline (oracle), rank 0 at N = 1 only ----
+    if not args.no_cpu_baseline and dist.world == 1:
+        v, s, sample = oracle_sample(wl, 2)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": sample, "seconds": s,
+                                "threads_note": "scipy.fft with workers=-1; NumPy elementwise on one thread"}
+    F.fftm_problem_destroy(prob)
+    F.fftm_ctx_destroy(ctx)
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.close()
+    return 0
+
+
+def it_total_plus1(steps, iters):
+    """Residual evaluations: one per iteration plus the final converged check, per step."""
+    return steps * (iters + 1)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

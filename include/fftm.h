@@ -1,0 +1,225 @@
+/*
+ * fftm.h -- C ABI of the GB300 (sm_103a) hot path of the displacement-based
+ * DTT/FFT fixed-point mechanical solver of arXiv 2607.05929 ("A robust and
+ * versatile parallel FFT-based mechanical solver for general non-periodic and
+ * periodic boundary conditions").
+ *
+ * One problem = one voxel grid on one GPU.  Per fixed-point iteration the
+ * library runs, on the caller's CUDA stream (Algorithm 1, Sec. 2.4):
+ *   finite-difference gradient -> constitutive law -> divergence and the
+ *   equilibrium norms (Eqs. div_pol, equilibrium_condition) -> Anderson
+ *   acceleration on p -> per-axis forward DCT/DST/DFT (Table 1) -> B0 or 2mu0
+ *   discrete Green operator (Eqs. NSGO1_*, NSGO2_*) -> inverse transforms ->
+ *   fluctuation displacement u^f.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns an int status: 0 = OK, > 0 = a completed,
+ *   non-fatal outcome (FFTM_NOT_CONVERGED), < 0 = an error.  Nothing throws
+ *   across the ABI.  fftm_last_error() returns a thread-local text for the
+ *   last error of the calling thread.
+ * - Pointers are plain host or device pointers; the argument's name says
+ *   which.  The library never keeps a caller pointer after a call returns:
+ *   inputs are copied, outputs are written before the call returns (for
+ *   device outputs: ordered on the problem's stream).
+ * - Node fields are dense, component-major, x fastest:
+ *   index = x + N1*(y + N2*(z + N3*q)), q = displacement component, with
+ *   N_a = n_a + 1 nodes on a non-periodic axis and n_a on a periodic one
+ *   (node n_a of a periodic axis is node 0; Sec. 2.1, Sec. 2.7.1).
+ * - Voxel fields are dense, x fastest, point-major:
+ *   index = x + n1*(y + n2*(z + n3*(c + nc*r))), r = voxel point (HEX1: one
+ *   point; TETRA2: r = 0 tetrahedron T1, r = 1 tetrahedron T2), c = tensor
+ *   component.  Gradients use G[i][q] = D_i u_q (c = 3 i + q); symmetric
+ *   stresses use c = 0..5 for (11, 22, 33, 23, 13, 12).
+ * - Field element type = the problem's precision (double for FFTM_FP64,
+ *   float for FFTM_FP32).
+ */
+#ifndef FFTM_H
+#define FFTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define FFTM_OK 0
+#define FFTM_NOT_CONVERGED 1  /* max_iter reached; fields hold the last iterate */
+#define FFTM_E_INVALID (-1)   /* bad argument or descriptor */
+#define FFTM_E_NOMEM (-2)     /* device allocation failed or workspace too small */
+#define FFTM_E_CUDA (-3)      /* a CUDA runtime call failed */
+#define FFTM_E_DIVERGED (-4)  /* NaN / Inf in the equilibrium norms */
+#define FFTM_E_UNSUPPORTED (-5)
+
+/* ---- enumerations ----------------------------------------------------- */
+enum fftm_bc { FFTM_BC_PERIODIC = 0, FFTM_BC_DIRICHLET = 1, FFTM_BC_NEUMANN = 2 };
+enum fftm_scheme { FFTM_HEX1 = 0, FFTM_TETRA2 = 1 };
+enum fftm_green { FFTM_GREEN_B0 = 0, FFTM_GREEN_MU0 = 1 };
+enum fftm_precision { FFTM_FP64 = 0, FFTM_FP32 = 1 };
+enum fftm_law {
+  FFTM_LAW_ISO_ELASTIC = 0,   /* params: lambda, mu                          */
+  FFTM_LAW_CUBIC_ELASTIC = 1, /* params: C11, C12, C44; quat = orientation     */
+  FFTM_LAW_J2_LINHARD = 2,    /* params: lambda, mu, sigma_y, H  (reserved)    */
+  FFTM_LAW_B0_LINEAR = 3      /* params: lambda, mu: P = 2 mu G + lambda G.*I  */
+};
+
+/* ---- descriptors ------------------------------------------------------ */
+typedef struct fftm_material {
+  int law;           /* enum fftm_law */
+  double params[8];  /* law parameters, see enum fftm_law */
+  double quat[4];    /* unit quaternion (w, x, y, z): crystal frame -> sample
+                        frame; used by FFTM_LAW_CUBIC_ELASTIC */
+} fftm_material;
+
+typedef struct fftm_problem_desc {
+  int n[3];                  /* voxels per axis, each >= 2 (Sec. 2.1)        */
+  double h[3];               /* voxel sizes, > 0                             */
+  const uint16_t* phase;     /* HOST pointer, n1*n2*n3 phase ids, x fastest;
+                                copied, the caller keeps ownership           */
+  int n_phases;              /* number of entries in materials, <= 65535      */
+  const fftm_material* materials; /* HOST pointer, copied                    */
+  int bc[3][2][3];           /* bc[axis][face][component], enum fftm_bc.
+                                face 0 contains the origin.  A periodic axis
+                                must be periodic on both faces, every comp.
+                                Dirichlet -> u^f_q anti-symmetric, Neumann ->
+                                symmetric (Eq. GeneralBCtobesolved).          */
+  int scheme;                /* enum fftm_scheme (Sec. 2.5)                  */
+  int green;                 /* enum fftm_green (Sec. 2.6.2 / 2.6.3)         */
+  double lambda0, mu0;       /* reference material; lambda0 ignored for MU0  */
+  int precision;             /* enum fftm_precision                          */
+  double tol;                /* equilibrium tolerance epsilon, > 0           */
+  int max_iter;              /* I_max, >= 1                                  */
+  int anderson_depth;        /* couples kept, 2..4 (0 disables Anderson)     */
+  int anderson_period;       /* accelerate when m % period == period - 1     */
+} fftm_problem_desc;
+
+/* Affine prescribed displacement u*_q(x) = sum_a A[q][a] x_a + b[q],
+   x = physical node coordinates (node j of axis a at j*h_a).  u* supplies the
+   Dirichlet values (Sec. 2.2); it must not depend on a periodic coordinate. */
+typedef struct fftm_load {
+  double A[3][3];
+  double b[3];
+} fftm_load;
+
+typedef struct fftm_step_report {
+  int iterations;       /* Green applications performed (0 = initial guess converged) */
+  int converged;        /* 1 if err < tol                                     */
+  double err;           /* final equilibrium error (Eq. equilibrium_condition) */
+  int n_accelerated;    /* Anderson steps taken                               */
+  double mean_P[6];     /* volume mean of P over voxel points, (11,22,33,23,13,12) */
+  double mean_G[9];     /* volume mean of the total gradient G[i][q]          */
+} fftm_step_report;
+
+typedef struct fftm_ctx fftm_ctx;
+typedef struct fftm_problem fftm_problem;
+
+/* ---- library ---------------------------------------------------------- */
+const char* fftm_last_error(void);
+int fftm_version(void);
+
+/* Bind to CUDA device `device` (its primary context) and to `cuda_stream`
+   (a cudaStream_t, or NULL for the legacy default stream).  All work of the
+   problems created from this context is ordered on that stream. */
+int fftm_ctx_create(fftm_ctx** out, int device, void* cuda_stream);
+int fftm_ctx_destroy(fftm_ctx* ctx);
+
+/* Device bytes a problem with this descriptor allocates (fields, Anderson
+   history, transform tables, law tables). */
+int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes);
+
+/* Validate the descriptor, derive per-component per-axis transform kinds and
+   node ranges (Table 1; Sec. 2.7.2 "dismissed" points), build the frequency
+   tables and law tables, allocate device memory (cudaMalloc; FFTM_E_NOMEM on
+   failure), upload the phase map.  u^f starts at zero. */
+int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_problem** out);
+int fftm_problem_destroy(fftm_problem* p);
+
+/* Replace the phase map (HOST pointer, n1*n2*n3 ids < n_phases, copied). */
+int fftm_set_phase(fftm_problem* p, const uint16_t* phase);
+
+/* Set the prescribed displacement of the next load steps (Algorithm 1,
+   "update the desired loading"). */
+int fftm_set_load(fftm_problem* p, const fftm_load* load);
+
+/* Run Algorithm 1 for one load step from the current u^f (the previous
+   step's converged field, zero initially).  Blocks until the report is
+   written.  Returns FFTM_OK, FFTM_NOT_CONVERGED, or an error.  `err_history`
+   (HOST, may be NULL) receives up to `history_len` per-iteration errors;
+   `accel_history` (HOST, may be NULL) receives 1/0 per iteration for an
+   Anderson step taken at that iteration. */
+int fftm_solve_step(fftm_problem* p, fftm_step_report* report, double* err_history,
+                    int* accel_history, int history_len);
+
+/* ---- fields ----------------------------------------------------------- */
+enum fftm_field {
+  FFTM_FIELD_U = 0,      /* u^f, node field (3 comps)                           */
+  FFTM_FIELD_WORK = 1,   /* the p / spectral work field, node layout (3 comps)   */
+  FFTM_FIELD_GRAD = 2,   /* total gradient G at voxel points (9 comps)           */
+  FFTM_FIELD_STRESS = 3, /* stress P at voxel points (6 comps)                   */
+  FFTM_FIELD_D = 4       /* residual D = div P at the nodes (3 comps), dismissed
+                            node components 0; written by FFTM_OP_RESIDUAL       */
+};
+
+/* Bytes of a field (dense layout above, problem precision). */
+int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
+
+/* Copy a field out.  dst is a device pointer if dst_is_device, else host.
+   bytes must equal fftm_field_bytes().  GRAD and STRESS are evaluated from
+   the current u^f on demand. */
+int fftm_get_field(fftm_problem* p, int field, void* dst, int dst_is_device, size_t bytes);
+
+/* Copy a field in (FFTM_FIELD_U or FFTM_FIELD_WORK only).  Values at
+   dismissed node components are ignored and stored as zero. */
+int fftm_set_field(fftm_problem* p, int field, const void* src, int src_is_device, size_t bytes);
+
+/* ---- single steps of one iteration (each a row of the hot path) -------- */
+enum fftm_op {
+  FFTM_OP_RESIDUAL = 0,     /* u^f -> WORK = p (Eq. div_pol), D, and norms:
+                               norms[0] = S_D, norms[1] = S_P, norms[2] = err  */
+  FFTM_OP_DT_FORWARD = 1,   /* WORK -> WORK, 3D forward DT (x, y, z; Table 1);
+                               DCT/DST coefficient k of an axis sits at node
+                               position lo + k; a periodic axis is stored in
+                               halfcomplex order (real part of frequency k at
+                               k, imaginary part at n - k)                      */
+  FFTM_OP_GREEN = 2,        /* WORK -> WORK, multiply by the Green factor
+                               -1 / (2 mu0 ||xi||^2 + lambda0 |xi_q|^2)
+                               (0 where the denominator is null)               */
+  FFTM_OP_DT_INVERSE = 3,   /* WORK -> WORK, 3D inverse DT, normalised          */
+  FFTM_OP_GREEN_UPDATE = 4  /* WORK (p) -> u^f: forward DT, Green, inverse DT,
+                               with the z pass fused (the solver's path)        */
+};
+
+/* Run one step on the problem's stream; `norms` (HOST, 3 doubles) is
+   written for FFTM_OP_RESIDUAL and may be NULL otherwise.  Blocks until done. */
+int fftm_apply(fftm_problem* p, int op, double* norms);
+
+/* Number of kernels the library launched on this problem since creation. */
+int fftm_kernel_launches(const fftm_problem* p, long long* count);
+
+/* Zero u^f and the acceleration history (a fresh load sequence). */
+int fftm_reset_state(fftm_problem* p);
+
+/* Per-kernel timing with CUDA events on the problem's stream (off by default).
+   While enabled, every launch of the solver is bracketed by two events; the
+   elapsed times are accumulated per category when the stream is next
+   synchronised by the library.  Categories (FFTM_KCAT_*): */
+enum fftm_kcat {
+  FFTM_KCAT_RESIDUAL = 0,  /* gradient + law + divergence + norm reduction      */
+  FFTM_KCAT_PASS_X = 1,    /* x-axis transform passes (forward and inverse)      */
+  FFTM_KCAT_PASS_Y = 2,    /* y-axis transform passes                            */
+  FFTM_KCAT_PASS_Z = 3,    /* fused z forward + Green + z inverse                */
+  FFTM_KCAT_ANDERSON = 4,  /* Gram, least squares, combination                   */
+  FFTM_KCAT_OTHER = 5,     /* statistics, packing, standalone steps              */
+  FFTM_KCAT_COUNT = 6
+};
+int fftm_set_profiling(fftm_problem* p, int enable);
+/* ms[c] = total milliseconds, launches[c] = launches of category c since the
+   last fftm_set_profiling(p, 1); both HOST arrays of n >= FFTM_KCAT_COUNT. */
+int fftm_kernel_times(const fftm_problem* p, double* ms, long long* launches, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFTM_H */

@@ -12,7 +12,8 @@ formulation; the reading used here (stated in the design notes) is:
   field is q = sum_j c_j g_j with c = argmin || sum_j c_j f_j ||_2 subject to
   sum_j c_j = 1 (least squares on the differences f_j - f_last).
 * The step is skipped (q = p_m) when the 3x3 normal matrix of those
-  differences has a Cholesky pivot below 1e-12 of its diagonal entry.
+  differences has a Cholesky pivot below 1e-8 of its diagonal entry: the
+  residual differences are then too close to collinear for a well-determined mix.
 
 Parity unpinned beyond self-consistency: there is no closed form for the
 accelerated iterates; the fixed point they converge to is pinned elsewhere.
@@ -20,7 +21,7 @@ accelerated iterates; the fixed point they converge to is pinned elsewhere.
 
 import numpy as np
 
-PIVOT_TOL = 1e-12
+PIVOT_TOL = 1e-8
 
 
 def normal_matrix_ok(A, tol=PIVOT_TOL):

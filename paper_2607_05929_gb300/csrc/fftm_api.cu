@@ -1,0 +1,1066 @@
+// C ABI of the fftm library (include/fftm.h): problem setup and the solve
+// loop of Algorithm 1 (Sec. 2.4) on one GPU and one stream.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fftm.h"
+#include "fftm_internal.cuh"
+
+using namespace fftm;
+
+static thread_local std::string g_last_error;
+
+static int set_err(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CU(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return set_err(FFTM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
+  } while (0)
+
+struct fftm_ctx {
+  int device;
+  cudaStream_t stream;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+// BC on a face -> symmetry of u^f_q (Sec. 2.2): +1 symmetric (Neumann), -1 anti-symmetric (Dirichlet).
+int face_sym(int bc) { return bc == FFTM_BC_NEUMANN ? 1 : -1; }
+
+// Pair of face symmetries -> transform kind (Table 1).
+int kind_of(int left, int right, bool periodic) {
+  if (periodic) return K_DFT;
+  if (left > 0 && right > 0) return K_DCT1;
+  if (left > 0 && right < 0) return K_DCT3;
+  if (left < 0 && right < 0) return K_DST1;
+  return K_DST3;
+}
+
+// Node range [lo, lo + L) of a kind (Table 1 index j; the rest is dismissed, Sec. 2.7.2).
+void kind_range(int kind, int n, int* lo, int* L) {
+  switch (kind) {
+    case K_DFT: *lo = 0; *L = n; break;
+    case K_DCT1: *lo = 0; *L = n + 1; break;
+    case K_DCT3: *lo = 0; *L = n; break;
+    case K_DST1: *lo = 1; *L = n - 1; break;
+    default: *lo = 1; *L = n; break;
+  }
+}
+
+// Fundamental frequency of index k (Table 1) and whether it is exactly 0 or pi.
+double kind_xi(int kind, int n, int k, bool* zero, bool* pi) {
+  *zero = false;
+  *pi = false;
+  switch (kind) {
+    case K_DFT: *zero = (k == 0); *pi = (2 * k == n); return 2.0 * kPi * k / n;
+    case K_DCT1: *zero = (k == 0); *pi = (k == n); return kPi * k / n;
+    case K_DST1: return kPi * (k + 1) / n;
+    default: return kPi * (k + 0.5) / n;
+  }
+}
+
+bool factor_radices(int M, std::vector<int>* rad) {
+  rad->clear();
+  int m = M;
+  while (m % 3 == 0) { rad->push_back(3); m /= 3; }
+  while (m % 8 == 0) { rad->push_back(8); m /= 8; }
+  while (m % 4 == 0) { rad->push_back(4); m /= 4; }
+  while (m % 2 == 0) { rad->push_back(2); m /= 2; }
+  return m == 1 && (int)rad->size() <= MAX_STAGES;
+}
+
+struct HostPlan {
+  int kind, n, lo, L, M;
+  std::vector<int> radix;
+  std::vector<int16_t> perm;
+  std::vector<double> tw;  // interleaved re, im
+  std::vector<double> qw;
+};
+
+HostPlan make_plan(int kind, int n) {
+  HostPlan p;
+  p.kind = kind;
+  p.n = n;
+  kind_range(kind, n, &p.lo, &p.L);
+  p.M = (kind == K_DFT) ? n : 2 * n;
+  factor_radices(p.M, &p.radix);
+  const int S = (int)p.radix.size();
+  std::vector<int> Lw(S + 1, 1);  // Lw[s] = R_0 ... R_{s-1}
+  for (int s = 0; s < S; ++s) Lw[s + 1] = Lw[s] * p.radix[s];
+  p.perm.resize(p.M);
+  for (int j = 0; j < p.M; ++j) {
+    int rem = j, pos = 0;
+    for (int s = S - 1; s >= 0; --s) {
+      const int r = rem % p.radix[s];
+      rem /= p.radix[s];
+      pos += r * Lw[s];
+    }
+    p.perm[j] = (int16_t)pos;
+  }
+  p.tw.resize(2 * p.M);
+  for (int t = 0; t < p.M; ++t) {
+    const double a = -2.0 * kPi * t / p.M;
+    p.tw[2 * t] = std::cos(a);
+    p.tw[2 * t + 1] = std::sin(a);
+  }
+  p.qw.resize(2 * (n + 1));
+  for (int j = 0; j <= n; ++j) {
+    const double a = kPi * j / (2.0 * n);
+    p.qw[2 * j] = std::cos(a);
+    p.qw[2 * j + 1] = std::sin(a);
+  }
+  return p;
+}
+
+// Rotation of a unit quaternion (w, v): R = (w^2 - v.v) I + 2 v v^T + 2 w [v]_x.
+void quat_rot(const double q[4], double R[3][3]) {
+  double nrm = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  const double w = q[0] / nrm, v[3] = {q[1] / nrm, q[2] / nrm, q[3] / nrm};
+  const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const double X[3][3] = {{0, -v[2], v[1]}, {v[2], 0, -v[0]}, {-v[1], v[0], 0}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) R[i][j] = (i == j ? w * w - vv : 0.0) + 2.0 * v[i] * v[j] + 2.0 * w * X[i][j];
+}
+
+// Mandel 6x6 of the cubic stiffness (C11, C12, C44) rotated by R (crystal -> sample).
+void cubic_mandel(double C11, double C12, double C44, const double R[3][3], double Cm[6][6]) {
+  double C0[3][3][3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) {
+          double v = 0.0;
+          if (a == b && c == d) v += (a == c) ? C11 : C12;
+          if (a != b && ((a == c && b == d) || (a == d && b == c))) v += C44;
+          C0[a][b][c][d] = v;
+        }
+  static const int I2[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+  for (int I = 0; I < 6; ++I)
+    for (int J = 0; J < 6; ++J) {
+      const int i = I2[I][0], j = I2[I][1], k = I2[J][0], l = I2[J][1];
+      double s = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          for (int c = 0; c < 3; ++c)
+            for (int d = 0; d < 3; ++d)
+              if (C0[a][b][c][d] != 0.0) s += R[i][a] * R[j][b] * R[k][c] * R[l][d] * C0[a][b][c][d];
+      const double f = (I >= 3 ? std::sqrt(2.0) : 1.0) * (J >= 3 ? std::sqrt(2.0) : 1.0);
+      Cm[I][J] = f * s;
+    }
+}
+
+}  // namespace
+
+struct fftm_problem {
+  fftm_ctx* ctx = nullptr;
+  fftm_problem_desc desc;
+  std::vector<fftm_material> mats;
+  int prec = FFTM_FP64;
+  int tetra = 0;
+  int n[3], N[3], periodic[3];
+  double h[3];
+  long long PX, sy, sz, comp_stride, nvox;
+  int kind[3][3], lo[3][3], hi[3][3], sgn[3][3][2];
+  HostPlan plans[3][3];  // [q][axis]
+  fftm_load load;
+  long long launches = 0;
+
+  // device memory (type-erased; element size esz)
+  size_t esz = 8;
+  void* fields = nullptr;  // 11 sets x 3 comps
+  void* Dbuf = nullptr;    // 3 comps, allocated on first FFTM_OP_RESIDUAL
+  void* tables = nullptr;  // plans + green tables
+  uint16_t* phase = nullptr;
+  int* law_id = nullptr;
+  void* law_c = nullptr;
+  double* partial = nullptr;
+  size_t partial_len = 0;
+  double* dscal = nullptr;  // [0..1] norms, [2..9] anderson coef, [16..] stats
+  int* dint = nullptr;      // accepted flags per iteration
+  int dint_len = 0;
+  double* hpin = nullptr;   // pinned host scalars
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  // device table offsets (bytes) inside `tables`
+  size_t off_perm[3][3], off_tw[3][3], off_qw[3][3], off_S2[3][3], off_C2[3][3];
+  int maxM[3], maxL[3];
+  int cur = 0;  // ring slot holding the current u^f
+  // per-kernel timing (fftm_set_profiling)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_free;
+  struct Pending { int cat, a, b; };
+  std::vector<Pending> pending;
+  double prof_ms[FFTM_KCAT_COUNT] = {0, 0, 0, 0, 0, 0};
+  long long prof_cnt[FFTM_KCAT_COUNT] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+// Field sets (3 component arrays each).  u^f lives in a ring of NSLOT slots so
+// that the last Anderson couples (u^k, D^k) stay in place without copies:
+// iteration m reads u^m from slot (cur0 + m) % NSLOT, writes D^m to the D slot
+// of the same index and u^{m+1} to the next slot.  In FP32 each u slot has a
+// low part (set SET_UL) holding what the FP32 high part drops.
+constexpr int NSLOT = 5;
+enum { SET_UH = 0, SET_D = 5, SET_WORK = 10, SET_BH = 11, SET_UL = 12, SET_BL = 17 };
+inline int nsets(bool lo) { return lo ? 18 : 12; }
+
+template <typename T>
+T* field_ptr(fftm_problem* p, int set, int q) {
+  return reinterpret_cast<T*>(p->fields) + ((long long)set * 3 + q) * p->comp_stride;
+}
+template <typename T>
+void set_ptrs(fftm_problem* p, int set, T* out[3]) {
+  for (int q = 0; q < 3; ++q) out[q] = field_ptr<T>(p, set, q);
+}
+
+int ev_get(fftm_problem* p) {
+  if (p->ev_free.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    p->ev.push_back(e);
+    return (int)p->ev.size() - 1;
+  }
+  const int i = p->ev_free.back();
+  p->ev_free.pop_back();
+  return i;
+}
+
+// Brackets the launches of one category with two events when profiling is on.
+struct ProfScope {
+  fftm_problem* p;
+  int cat, a = -1;
+  ProfScope(fftm_problem* p_, int c) : p(p_), cat(c) {
+    if (p->prof && (a = ev_get(p)) >= 0) cudaEventRecord(p->ev[a], p->ctx->stream);
+  }
+  ~ProfScope() {
+    if (a < 0) return;
+    const int b = ev_get(p);
+    if (b < 0) return;
+    cudaEventRecord(p->ev[b], p->ctx->stream);
+    p->pending.push_back({cat, a, b});
+  }
+};
+
+// Accumulate the elapsed times of completed event pairs (call after a stream sync).
+void prof_flush(fftm_problem* p) {
+  for (const auto& e : p->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p->ev[e.a], p->ev[e.b]) == cudaSuccess) {
+      p->prof_ms[e.cat] += ms;
+      p->prof_cnt[e.cat] += 1;
+    }
+    p->ev_free.push_back(e.a);
+    p->ev_free.push_back(e.b);
+  }
+  p->pending.clear();
+}
+
+template <typename T>
+const typename V2<T>::t* tptr_v2(fftm_problem* p, size_t off) {
+  return reinterpret_cast<const typename V2<T>::t*>(reinterpret_cast<char*>(p->tables) + off);
+}
+template <typename T>
+const T* tptr(fftm_problem* p, size_t off) {
+  return reinterpret_cast<const T*>(reinterpret_cast<char*>(p->tables) + off);
+}
+
+template <typename T>
+AxisPlan<T> dev_plan(fftm_problem* p, int q, int a) {
+  const HostPlan& h = p->plans[q][a];
+  AxisPlan<T> d;
+  d.kind = h.kind;
+  d.n = h.n;
+  d.lo = h.lo;
+  d.L = h.L;
+  d.M = h.M;
+  d.nst = (int)h.radix.size();
+  for (int s = 0; s < MAX_STAGES; ++s) d.radix[s] = s < d.nst ? h.radix[s] : 1;
+  d.perm = reinterpret_cast<const int16_t*>(reinterpret_cast<char*>(p->tables) + p->off_perm[q][a]);
+  d.tw = tptr_v2<T>(p, p->off_tw[q][a]);
+  d.qw = tptr_v2<T>(p, p->off_qw[q][a]);
+  return d;
+}
+
+double axis_norm(fftm_problem* p, int q, int a) {
+  const int k = p->kind[q][a];
+  return (k == K_DFT ? 1.0 : 2.0) * p->n[a];
+}
+
+template <typename T>
+PassParams<T> pass_params(fftm_problem* p, int axis, int inverse, int fused, int in_set, int out_set) {
+  PassParams<T> P;
+  std::memset(&P, 0, sizeof(P));
+  for (int q = 0; q < 3; ++q) {
+    P.in[q] = field_ptr<T>(p, in_set, q);
+    P.out[q] = field_ptr<T>(p, out_set, q);
+    P.plan[q] = dev_plan<T>(p, q, axis);
+    P.scale[q] = T(1);
+  }
+  P.axis = axis;
+  for (int a = 0; a < 3; ++a) P.N[a] = p->N[a];
+  P.stride[0] = 1;
+  P.stride[1] = p->sy;
+  P.stride[2] = p->sz;
+  P.inverse = inverse;
+  P.fused = fused;
+  for (int q = 0; q < 3; ++q)
+    for (int a = 0; a < 3; ++a) {
+      P.S2[q][a] = tptr<T>(p, p->off_S2[q][a]);
+      P.C2[q][a] = tptr<T>(p, p->off_C2[q][a]);
+      P.flo[q][a] = p->plans[q][a].lo;
+      P.fL[q][a] = p->plans[q][a].L;
+    }
+  for (int a = 0; a < 3; ++a) P.hf[a] = T(4.0 / (p->h[a] * p->h[a]));
+  const double lam0 = p->desc.green == FFTM_GREEN_MU0 ? 0.0 : p->desc.lambda0;
+  P.two_mu0 = T(2.0 * p->desc.mu0);
+  P.lam0 = T(lam0);
+  P.tetra = p->tetra;
+  for (int q = 0; q < 3; ++q) P.gscale[q] = T(1.0 / (axis_norm(p, q, 0) * axis_norm(p, q, 1) * axis_norm(p, q, 2)));
+  return P;
+}
+
+template <typename T>
+int launch_pp(fftm_problem* p, const PassParams<T>& P, int axis) {
+  ProfScope ps(p, axis == 0 ? FFTM_KCAT_PASS_X : (axis == 1 ? FFTM_KCAT_PASS_Y : FFTM_KCAT_PASS_Z));
+  CU(launch_pass<T>(P, p->maxM[axis], p->maxL[axis], p->n[axis], p->ctx->stream));
+  p->launches++;
+  return FFTM_OK;
+}
+
+template <typename T>
+int run_pass(fftm_problem* p, int axis, int inverse, int fused, int in_set, int out_set, bool normalise) {
+  PassParams<T> P = pass_params<T>(p, axis, inverse, fused, in_set, out_set);
+  if (normalise)
+    for (int q = 0; q < 3; ++q) P.scale[q] = T(1.0 / axis_norm(p, q, axis));
+  return launch_pp<T>(p, P, axis);
+}
+
+template <typename T>
+ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
+  ResParams<T> R;
+  std::memset(&R, 0, sizeof(R));
+  const bool lo = p->esz == 4;
+  for (int q = 0; q < 3; ++q) {
+    R.u[q] = field_ptr<T>(p, SET_UH + slot, q);
+    R.ulo[q] = lo ? field_ptr<T>(p, SET_UL + slot, q) : nullptr;
+    R.D[q] = D_base ? D_base + q * p->comp_stride : field_ptr<T>(p, SET_D + slot, q);
+    R.p[q] = p_base ? p_base + q * p->comp_stride : nullptr;
+  }
+  R.phase = p->phase;
+  R.law_id = p->law_id;
+  R.law_c = reinterpret_cast<const T*>(p->law_c);
+  for (int a = 0; a < 3; ++a) {
+    R.n[a] = p->n[a];
+    R.N[a] = p->N[a];
+    R.periodic[a] = p->periodic[a];
+    R.wdiv[a] = T(0.25 / p->h[a]);
+    R.wgrad[a] = T((p->tetra ? 0.5 : 0.25) / p->h[a]);
+  }
+  R.sy = p->sy;
+  R.sz = p->sz;
+  R.vy = p->n[0];
+  R.vz = (long long)p->n[0] * p->n[1];
+  for (int i = 0; i < 3; ++i)
+    for (int q = 0; q < 3; ++q) R.Gs[i * 3 + q] = T(p->load.A[q][i]);  // G*_iq = d u*_q / d x_i
+  const double lam0 = p->desc.green == FFTM_GREEN_MU0 ? 0.0 : p->desc.lambda0;
+  R.lam0 = T(lam0);
+  R.two_mu0 = T(2.0 * p->desc.mu0);
+  for (int q = 0; q < 3; ++q)
+    for (int a = 0; a < 3; ++a) {
+      R.sgn[q][a][0] = p->sgn[q][a][0];
+      R.sgn[q][a][1] = p->sgn[q][a][1];
+      R.lo[q][a] = p->lo[q][a];
+      R.hi[q][a] = p->hi[q][a];
+    }
+  R.partial = p->partial;
+  return R;
+}
+
+// a1-a4: D (into the D slot of `slot`, or the test buffers) and the two norms.
+template <typename T>
+int run_residual(fftm_problem* p, int slot, bool test_outputs) {
+  T* D = nullptr;
+  T* pp = nullptr;
+  if (test_outputs) {
+    if (!p->Dbuf) {
+      CU(cudaMalloc(&p->Dbuf, 3 * p->comp_stride * sizeof(T)));
+      CU(cudaMemsetAsync(p->Dbuf, 0, 3 * p->comp_stride * sizeof(T), p->ctx->stream));
+    }
+    D = reinterpret_cast<T*>(p->Dbuf);
+    pp = field_ptr<T>(p, SET_WORK, 0);
+  }
+  ResParams<T> R = res_params<T>(p, slot, D, pp);
+  int blocks = 0;
+  ProfScope ps(p, test_outputs ? FFTM_KCAT_OTHER : FFTM_KCAT_RESIDUAL);
+  CU(launch_residual<T>(R, p->tetra, test_outputs, p->ctx->stream, &blocks));
+  CU(launch_reduce_norms(p->partial, blocks, 2, p->dscal, p->ctx->stream));
+  p->launches += 2;
+  return FFTM_OK;
+}
+
+// a6-a8: out = base - Gamma(in) (base may be absent: out = Gamma(in)).  The
+// first pass reads `in_set`, the rest work in place on WORK; the z pass runs
+// forward z, the Green factor and inverse z in one kernel.
+template <typename T>
+int green_apply(fftm_problem* p, int in_set, int base_set, int base_lo_set, int out_set, int out_lo_set,
+                bool negate) {
+  int rc;
+  if ((rc = run_pass<T>(p, 0, 0, 0, in_set, SET_WORK, false))) return rc;
+  if ((rc = run_pass<T>(p, 1, 0, 0, SET_WORK, SET_WORK, false))) return rc;
+  {
+    PassParams<T> P = pass_params<T>(p, 2, 0, 1, SET_WORK, SET_WORK);
+    if (negate)
+      for (int q = 0; q < 3; ++q) P.gscale[q] = -P.gscale[q];
+    if ((rc = launch_pp<T>(p, P, 2))) return rc;
+  }
+  if ((rc = run_pass<T>(p, 1, 1, 0, SET_WORK, SET_WORK, false))) return rc;
+  PassParams<T> P = pass_params<T>(p, 0, 1, 0, SET_WORK, out_set);
+  if (base_set >= 0)
+    for (int q = 0; q < 3; ++q) {
+      P.base[q] = field_ptr<T>(p, base_set, q);
+      P.base_lo[q] = base_lo_set >= 0 ? field_ptr<T>(p, base_lo_set, q) : nullptr;
+      P.out_lo[q] = out_lo_set >= 0 ? field_ptr<T>(p, out_lo_set, q) : nullptr;
+    }
+  return launch_pp<T>(p, P, 0);
+}
+
+double error_of(fftm_problem* p, double SD, double SP) {
+  if (SP > 0.0) return p->h[0] * std::sqrt(SD / SP);
+  return SD == 0.0 ? 0.0 : INFINITY;
+}
+
+// Algorithm 1 for one load step.  The update of iteration m is
+//   u^{m+1} = u^m - Gamma(D^m)                                 (plain step)
+//   u^{m+1} = sum_k c_k u^k - Gamma(sum_k c_k D^k)             (Anderson step)
+// which equals the paper's u^{m+1} = Gamma(p^m), p^m = div(R0 : grad u^m) - D^m,
+// because Gamma inverts div(R0 : grad .) exactly on the transformed fields.
+template <typename T>
+int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* acc_hist, int hist_len) {
+  cudaStream_t s = p->ctx->stream;
+  const bool lo = p->esz == 4;
+  const int depth = p->desc.anderson_depth, period = p->desc.anderson_period;
+  const int max_iter = p->desc.max_iter;
+  const long long cnt = p->comp_stride;
+  if (p->dint_len < max_iter + 1) {
+    if (p->dint) cudaFree(p->dint);
+    p->dint = nullptr;
+    CU(cudaMalloc(&p->dint, (max_iter + 1) * sizeof(int)));
+    p->dint_len = max_iter + 1;
+  }
+  CU(cudaMemsetAsync(p->dint, 0, (max_iter + 1) * sizeof(int), s));
+  const int cur0 = p->cur;
+  int m = 0, converged = 0;
+  double err = 0.0;
+  for (m = 0;; ++m) {
+    const int sm = (cur0 + m) % NSLOT;
+    int rc = run_residual<T>(p, sm, false);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(p->hpin, p->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    prof_flush(p);
+    err = error_of(p, p->hpin[0], p->hpin[1]);
+    if (err_hist && m < hist_len) err_hist[m] = err;
+    p->cur = sm;
+    if (!std::isfinite(err)) return set_err(FFTM_E_DIVERGED, "non-finite equilibrium norm");
+    if (err < p->desc.tol) {
+      converged = 1;
+      break;
+    }
+    if (m >= max_iter) break;
+    const int sn = (cur0 + m + 1) % NSLOT;
+    // couples k = m - depth + 1 .. m (k >= 1) are in slots (cur0 + k) % NSLOT
+    const int have = std::min(m, depth);
+    const bool accel = depth > 0 && (m % period == period - 1) && have == depth;
+    if (accel) {
+      const T* Ds[4][3];
+      const T* uh[4][3];
+      const T* ul[4][3];
+      for (int j = 0; j < 4; ++j) {
+        const int k = m - depth + 1 + std::min(j, depth - 1);
+        const int sk = (cur0 + k) % NSLOT;
+        for (int q = 0; q < 3; ++q) {
+          Ds[j][q] = field_ptr<T>(p, SET_D + sk, q);
+          uh[j][q] = field_ptr<T>(p, SET_UH + sk, q);
+          ul[j][q] = lo ? field_ptr<T>(p, SET_UL + sk, q) : nullptr;
+        }
+      }
+      {
+      const int gb = gram_blocks(cnt);
+      ProfScope ps(p, FFTM_KCAT_ANDERSON);
+      CU(launch_gram<T>(Ds, depth, cnt, p->partial, gb, s));
+      CU(launch_anderson_solve(p->partial, gb, depth, 1e-8, p->dscal + 2, p->dint + m, s));
+      T* work[3];
+      T* bh[3];
+      T* bl[3];
+      set_ptrs<T>(p, SET_WORK, work);
+      set_ptrs<T>(p, SET_BH, bh);
+      if (lo) set_ptrs<T>(p, SET_BL, bl);
+      CU(launch_combine<T>(work, bh, lo ? bl : nullptr, Ds, uh, ul, depth, p->dscal + 2, cnt, s));
+      p->launches += 3;
+      }
+      rc = green_apply<T>(p, SET_WORK, SET_BH, lo ? SET_BL : -1, SET_UH + sn, lo ? SET_UL + sn : -1, true);
+    } else {
+      rc = green_apply<T>(p, SET_D + sm, SET_UH + sm, lo ? SET_UL + sm : -1, SET_UH + sn, lo ? SET_UL + sn : -1,
+                          true);
+    }
+    if (rc) return rc;
+  }
+  // report
+  std::vector<int> acc(m + 1, 0);
+  CU(cudaMemcpyAsync(acc.data(), p->dint, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  const int sb = 152 * 2;
+  {
+    ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
+    ProfScope ps(p, FFTM_KCAT_OTHER);
+    CU(launch_stats<T>(R, p->tetra, p->partial, sb, s));
+    CU(launch_reduce_norms(p->partial, sb, 18, p->dscal + 16, s));
+    p->launches += 2;
+  }
+  CU(cudaMemcpyAsync(p->hpin + 16, p->dscal + 16, 18 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  prof_flush(p);
+  std::memset(rep, 0, sizeof(*rep));
+  rep->iterations = m;
+  rep->converged = converged;
+  rep->err = err;
+  int nacc = 0;
+  for (int i = 0; i <= m; ++i) {
+    if (acc_hist && i < hist_len) acc_hist[i] = acc[i];
+    nacc += acc[i];
+  }
+  rep->n_accelerated = nacc;
+  const double npts = (double)p->nvox * (p->tetra ? 2 : 1);
+  static const int map6[6] = {0, 4, 8, 5, 2, 1};
+  for (int c = 0; c < 6; ++c) rep->mean_P[c] = p->hpin[16 + map6[c]] / npts;
+  for (int c = 0; c < 9; ++c) rep->mean_G[c] = p->hpin[16 + 9 + c] / npts;
+  return converged ? FFTM_OK : FFTM_NOT_CONVERGED;
+}
+
+int validate(const fftm_problem_desc* d) {
+  if (!d) return set_err(FFTM_E_INVALID, "null descriptor");
+  for (int a = 0; a < 3; ++a) {
+    if (d->n[a] < 2 || d->n[a] > 8192) return set_err(FFTM_E_INVALID, "n must be in [2, 8192]");
+    if (!(d->h[a] > 0.0)) return set_err(FFTM_E_INVALID, "h must be > 0");
+  }
+  if (!d->phase) return set_err(FFTM_E_INVALID, "phase map is null");
+  if (d->n_phases < 1 || d->n_phases > 65535 || !d->materials)
+    return set_err(FFTM_E_INVALID, "n_phases must be in [1, 65535] with a materials array");
+  for (int i = 0; i < d->n_phases; ++i) {
+    const int law = d->materials[i].law;
+    if (law == FFTM_LAW_J2_LINHARD) return set_err(FFTM_E_UNSUPPORTED, "J2 law not available in this build");
+    if (law != FFTM_LAW_ISO_ELASTIC && law != FFTM_LAW_CUBIC_ELASTIC && law != FFTM_LAW_B0_LINEAR)
+      return set_err(FFTM_E_INVALID, "unknown law");
+  }
+  for (int a = 0; a < 3; ++a) {
+    int np = 0;
+    for (int f = 0; f < 2; ++f)
+      for (int q = 0; q < 3; ++q) {
+        const int b = d->bc[a][f][q];
+        if (b != FFTM_BC_PERIODIC && b != FFTM_BC_DIRICHLET && b != FFTM_BC_NEUMANN)
+          return set_err(FFTM_E_INVALID, "bad bc value");
+        np += (b == FFTM_BC_PERIODIC);
+      }
+    if (np != 0 && np != 6)
+      return set_err(FFTM_E_INVALID, "a periodic axis must be periodic on both faces for every component");
+  }
+  if (d->scheme != FFTM_HEX1 && d->scheme != FFTM_TETRA2) return set_err(FFTM_E_INVALID, "bad scheme");
+  if (d->green != FFTM_GREEN_B0 && d->green != FFTM_GREEN_MU0) return set_err(FFTM_E_INVALID, "bad green");
+  if (!(d->mu0 > 0.0) || !(d->lambda0 >= 0.0)) return set_err(FFTM_E_INVALID, "need mu0 > 0, lambda0 >= 0");
+  if (d->precision != FFTM_FP64 && d->precision != FFTM_FP32) return set_err(FFTM_E_INVALID, "bad precision");
+  if (!(d->tol > 0.0) || d->max_iter < 1) return set_err(FFTM_E_INVALID, "need tol > 0 and max_iter >= 1");
+  if (d->anderson_depth != 0 && (d->anderson_depth < 2 || d->anderson_depth > 4))
+    return set_err(FFTM_E_INVALID, "anderson_depth must be 0 or 2..4");
+  if (d->anderson_depth != 0 && d->anderson_period < 1) return set_err(FFTM_E_INVALID, "anderson_period >= 1");
+  for (int a = 0; a < 3; ++a) {
+    const bool per = d->bc[a][0][0] == FFTM_BC_PERIODIC;
+    const int M = per ? d->n[a] : 2 * d->n[a];
+    std::vector<int> r;
+    if (!factor_radices(M, &r)) return set_err(FFTM_E_UNSUPPORTED, "grid sizes must be 2^a 3^b");
+    if (M > 2048) return set_err(FFTM_E_UNSUPPORTED, "transform length above 2048");
+  }
+  return FFTM_OK;
+}
+
+struct Sizes {
+  long long PX, comp_stride;
+  size_t fields, tables, lawc, partial;
+};
+
+Sizes sizes_of(const fftm_problem_desc* d) {
+  Sizes s;
+  const size_t esz = d->precision == FFTM_FP64 ? 8 : 4;
+  int N[3];
+  for (int a = 0; a < 3; ++a) N[a] = d->bc[a][0][0] == FFTM_BC_PERIODIC ? d->n[a] : d->n[a] + 1;
+  s.PX = (N[0] + 7) / 8 * 8;
+  s.comp_stride = (s.PX * N[1] * N[2] + 63) / 64 * 64;
+  s.fields = (size_t)nsets(esz == 4) * 3 * s.comp_stride * esz;
+  size_t t = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int M = 2 * d->n[a] + 2;
+    t += 3 * ((size_t)M * 2 + 16 + (size_t)M * 2 * esz + 16 + (size_t)(d->n[a] + 2) * 2 * esz + 16 +
+              2 * ((size_t)(d->n[a] + 2) * esz + 16));
+  }
+  s.tables = t + 4096;
+  s.lawc = (size_t)d->n_phases * LAWC * esz;
+  s.partial = (size_t)(4 * 152 * 64) * 20 * sizeof(double);
+  return s;
+}
+
+}  // namespace
+
+// ======================================================================================
+extern "C" {
+
+const char* fftm_last_error(void) { return g_last_error.c_str(); }
+int fftm_version(void) { return 1; }
+
+int fftm_ctx_create(fftm_ctx** out, int device, void* cuda_stream) {
+  if (!out) return set_err(FFTM_E_INVALID, "null out");
+  int count = 0;
+  CU(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return set_err(FFTM_E_INVALID, "bad device index");
+  CU(cudaSetDevice(device));
+  fftm_ctx* c = new (std::nothrow) fftm_ctx;
+  if (!c) return set_err(FFTM_E_NOMEM, "host allocation");
+  c->device = device;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  *out = c;
+  return FFTM_OK;
+}
+
+int fftm_ctx_destroy(fftm_ctx* ctx) {
+  delete ctx;
+  return FFTM_OK;
+}
+
+int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
+  int rc = validate(desc);
+  if (rc) return rc;
+  if (!bytes) return set_err(FFTM_E_INVALID, "null bytes");
+  Sizes s = sizes_of(desc);
+  const long long nvox = (long long)desc->n[0] * desc->n[1] * desc->n[2];
+  *bytes = s.fields + s.tables + s.lawc + s.partial + nvox * sizeof(uint16_t) + desc->n_phases * sizeof(int);
+  return FFTM_OK;
+}
+
+int fftm_problem_destroy(fftm_problem* p) {
+  if (!p) return FFTM_OK;
+  if (p->ctx) cudaSetDevice(p->ctx->device);
+  cudaFree(p->fields);
+  cudaFree(p->Dbuf);
+  cudaFree(p->tables);
+  cudaFree(p->phase);
+  cudaFree(p->law_id);
+  cudaFree(p->law_c);
+  cudaFree(p->partial);
+  cudaFree(p->dscal);
+  cudaFree(p->dint);
+  cudaFree(p->scratch);
+  if (p->hpin) cudaFreeHost(p->hpin);
+  for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  delete p;
+  return FFTM_OK;
+}
+
+int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_problem** out) {
+  if (!ctx || !out) return set_err(FFTM_E_INVALID, "null ctx or out");
+  int rc = validate(desc);
+  if (rc) return rc;
+  CU(cudaSetDevice(ctx->device));
+  std::unique_ptr<fftm_problem> p(new (std::nothrow) fftm_problem);
+  if (!p) return set_err(FFTM_E_NOMEM, "host allocation");
+  p->ctx = ctx;
+  p->desc = *desc;
+  p->mats.assign(desc->materials, desc->materials + desc->n_phases);
+  p->desc.materials = nullptr;
+  p->desc.phase = nullptr;
+  p->prec = desc->precision;
+  p->esz = desc->precision == FFTM_FP64 ? 8 : 4;
+  p->tetra = desc->scheme == FFTM_TETRA2;
+  std::memset(&p->load, 0, sizeof(p->load));
+  for (int a = 0; a < 3; ++a) {
+    p->n[a] = desc->n[a];
+    p->h[a] = desc->h[a];
+    p->periodic[a] = desc->bc[a][0][0] == FFTM_BC_PERIODIC;
+    p->N[a] = p->periodic[a] ? p->n[a] : p->n[a] + 1;
+  }
+  Sizes sz = sizes_of(desc);
+  p->PX = sz.PX;
+  p->sy = sz.PX;
+  p->sz = sz.PX * p->N[1];
+  p->comp_stride = sz.comp_stride;
+  p->nvox = (long long)p->n[0] * p->n[1] * p->n[2];
+  for (int q = 0; q < 3; ++q)
+    for (int a = 0; a < 3; ++a) {
+      const int sl = face_sym(desc->bc[a][0][q]), sr = face_sym(desc->bc[a][1][q]);
+      p->sgn[q][a][0] = p->periodic[a] ? 1 : sl;
+      p->sgn[q][a][1] = p->periodic[a] ? 1 : sr;
+      p->kind[q][a] = kind_of(sl, sr, p->periodic[a]);
+      int lo, L;
+      kind_range(p->kind[q][a], p->n[a], &lo, &L);
+      p->lo[q][a] = lo;
+      p->hi[q][a] = lo + L;
+      p->plans[q][a] = make_plan(p->kind[q][a], p->n[a]);
+    }
+  for (int a = 0; a < 3; ++a) {
+    p->maxM[a] = 0;
+    p->maxL[a] = 0;
+    for (int q = 0; q < 3; ++q) {
+      p->maxM[a] = std::max(p->maxM[a], p->plans[q][a].M);
+      p->maxL[a] = std::max(p->maxL[a], p->plans[q][a].L);
+    }
+  }
+  // ---- device allocations ----
+  const cudaStream_t s = ctx->stream;
+  if (cudaMalloc(&p->fields, sz.fields) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(FFTM_E_NOMEM, "device allocation of the fields failed");
+  }
+  CU(cudaMemsetAsync(p->fields, 0, sz.fields, s));
+  CU(cudaMalloc(&p->phase, p->nvox * sizeof(uint16_t)));
+  CU(cudaMemcpyAsync(p->phase, desc->phase, p->nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
+  CU(cudaMalloc(&p->partial, sz.partial));
+  p->partial_len = sz.partial / sizeof(double);
+  CU(cudaMalloc(&p->dscal, 64 * sizeof(double)));
+  CU(cudaMemsetAsync(p->dscal, 0, 64 * sizeof(double), s));
+  CU(cudaMallocHost(&p->hpin, 64 * sizeof(double)));
+  // ---- tables: plans and Green half-angle tables ----
+  std::vector<unsigned char> tab;
+  auto put = [&](const void* src, size_t bytes) {
+    size_t off = (tab.size() + 15) & ~(size_t)15;
+    tab.resize(off + bytes);
+    std::memcpy(tab.data() + off, src, bytes);
+    return off;
+  };
+  for (int q = 0; q < 3; ++q)
+    for (int a = 0; a < 3; ++a) {
+      const HostPlan& h = p->plans[q][a];
+      p->off_perm[q][a] = put(h.perm.data(), h.perm.size() * sizeof(int16_t));
+      std::vector<double> s2(h.L), c2(h.L);
+      for (int k = 0; k < h.L; ++k) {
+        bool z, pi;
+        const double xi = kind_xi(h.kind, h.n, k, &z, &pi);
+        const double sv = z ? 0.0 : std::sin(0.5 * xi);
+        const double cv = pi ? 0.0 : std::cos(0.5 * xi);
+        s2[k] = sv * sv;
+        c2[k] = cv * cv;
+      }
+      if (p->esz == 8) {
+        p->off_tw[q][a] = put(h.tw.data(), h.tw.size() * 8);
+        p->off_qw[q][a] = put(h.qw.data(), h.qw.size() * 8);
+        p->off_S2[q][a] = put(s2.data(), s2.size() * 8);
+        p->off_C2[q][a] = put(c2.data(), c2.size() * 8);
+      } else {
+        std::vector<float> tw(h.tw.begin(), h.tw.end()), qw(h.qw.begin(), h.qw.end());
+        std::vector<float> s2f(s2.begin(), s2.end()), c2f(c2.begin(), c2.end());
+        p->off_tw[q][a] = put(tw.data(), tw.size() * 4);
+        p->off_qw[q][a] = put(qw.data(), qw.size() * 4);
+        p->off_S2[q][a] = put(s2f.data(), s2f.size() * 4);
+        p->off_C2[q][a] = put(c2f.data(), c2f.size() * 4);
+      }
+    }
+  CU(cudaMalloc(&p->tables, tab.size()));
+  CU(cudaMemcpy(p->tables, tab.data(), tab.size(), cudaMemcpyHostToDevice));
+  // ---- law tables ----
+  std::vector<int> lid(desc->n_phases);
+  std::vector<double> lc((size_t)desc->n_phases * LAWC, 0.0);
+  for (int i = 0; i < desc->n_phases; ++i) {
+    const fftm_material& m = desc->materials[i];
+    lid[i] = m.law;
+    double* c = &lc[(size_t)i * LAWC];
+    if (m.law == FFTM_LAW_CUBIC_ELASTIC) {
+      double R[3][3], Cm[6][6];
+      quat_rot(m.quat, R);
+      cubic_mandel(m.params[0], m.params[1], m.params[2], R, Cm);
+      int k = 0;
+      for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b) c[k++] = Cm[a][b];
+    } else {
+      c[0] = m.params[0];
+      c[1] = m.params[1];
+    }
+  }
+  CU(cudaMalloc(&p->law_id, lid.size() * sizeof(int)));
+  CU(cudaMemcpy(p->law_id, lid.data(), lid.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CU(cudaMalloc(&p->law_c, lc.size() * p->esz));
+  if (p->esz == 8) {
+    CU(cudaMemcpy(p->law_c, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> lf(lc.begin(), lc.end());
+    CU(cudaMemcpy(p->law_c, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
+  }
+  CU(cudaStreamSynchronize(s));
+  *out = p.release();
+  return FFTM_OK;
+}
+
+int fftm_set_phase(fftm_problem* p, const uint16_t* phase) {
+  if (!p || !phase) return set_err(FFTM_E_INVALID, "null argument");
+  CU(cudaSetDevice(p->ctx->device));
+  CU(cudaMemcpyAsync(p->phase, phase, p->nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, p->ctx->stream));
+  CU(cudaStreamSynchronize(p->ctx->stream));
+  return FFTM_OK;
+}
+
+int fftm_set_load(fftm_problem* p, const fftm_load* load) {
+  if (!p || !load) return set_err(FFTM_E_INVALID, "null argument");
+  for (int a = 0; a < 3; ++a)
+    if (p->periodic[a])
+      for (int q = 0; q < 3; ++q)
+        if (load->A[q][a] != 0.0) return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
+  p->load = *load;
+  return FFTM_OK;
+}
+
+int fftm_solve_step(fftm_problem* p, fftm_step_report* report, double* err_history, int* accel_history,
+                    int history_len) {
+  if (!p || !report) return set_err(FFTM_E_INVALID, "null argument");
+  CU(cudaSetDevice(p->ctx->device));
+  if (p->esz == 8) return solve_step_t<double>(p, report, err_history, accel_history, history_len);
+  return solve_step_t<float>(p, report, err_history, accel_history, history_len);
+}
+
+int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes) {
+  if (!p || !bytes) return set_err(FFTM_E_INVALID, "null argument");
+  const size_t nodes = (size_t)p->N[0] * p->N[1] * p->N[2];
+  const size_t npp = p->tetra ? 2 : 1;
+  switch (field) {
+    case FFTM_FIELD_U:
+    case FFTM_FIELD_WORK:
+    case FFTM_FIELD_D: *bytes = 3 * nodes * p->esz; return FFTM_OK;
+    case FFTM_FIELD_GRAD: *bytes = 9 * npp * p->nvox * p->esz; return FFTM_OK;
+    case FFTM_FIELD_STRESS: *bytes = 6 * npp * p->nvox * p->esz; return FFTM_OK;
+    default: return set_err(FFTM_E_INVALID, "unknown field");
+  }
+}
+
+static int ensure_scratch(fftm_problem* p, size_t bytes) {
+  if (p->scratch_bytes >= bytes) return FFTM_OK;
+  cudaFree(p->scratch);
+  p->scratch = nullptr;
+  p->scratch_bytes = 0;
+  if (cudaMalloc(&p->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return set_err(FFTM_E_NOMEM, "scratch allocation failed");
+  }
+  p->scratch_bytes = bytes;
+  return FFTM_OK;
+}
+
+}  // extern "C"
+
+template <typename T>
+static int get_field_t(fftm_problem* p, int field, void* dst, int dst_is_device, size_t bytes) {
+  cudaStream_t s = p->ctx->stream;
+  void* target = dst;
+  if (!dst_is_device) {
+    int rc = ensure_scratch(p, bytes);
+    if (rc) return rc;
+    target = p->scratch;
+  }
+  if (field == FFTM_FIELD_U || field == FFTM_FIELD_WORK || field == FFTM_FIELD_D) {
+    const T* src[3];
+    for (int q = 0; q < 3; ++q) {
+      if (field == FFTM_FIELD_D) {
+        if (!p->Dbuf) return set_err(FFTM_E_INVALID, "D is written by FFTM_OP_RESIDUAL first");
+        src[q] = reinterpret_cast<const T*>(p->Dbuf) + q * p->comp_stride;
+      } else {
+        src[q] = field_ptr<T>(p, field == FFTM_FIELD_U ? SET_UH + p->cur : SET_WORK, q);
+      }
+    }
+    CU(launch_pack<T>(src, reinterpret_cast<T*>(target), p->N[0], p->N[1], p->N[2], p->sy, p->sz, 0, s));
+  } else {
+    ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
+    T* g = field == FFTM_FIELD_GRAD ? reinterpret_cast<T*>(target) : nullptr;
+    T* st = field == FFTM_FIELD_STRESS ? reinterpret_cast<T*>(target) : nullptr;
+    CU(launch_voxel_fields<T>(R, p->tetra, g, st, s));
+  }
+  p->launches++;
+  if (!dst_is_device) CU(cudaMemcpyAsync(dst, target, bytes, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  return FFTM_OK;
+}
+
+extern "C" {
+
+int fftm_get_field(fftm_problem* p, int field, void* dst, int dst_is_device, size_t bytes) {
+  if (!p || !dst) return set_err(FFTM_E_INVALID, "null argument");
+  size_t need;
+  int rc = fftm_field_bytes(p, field, &need);
+  if (rc) return rc;
+  if (bytes != need) return set_err(FFTM_E_INVALID, "byte count does not match the field");
+  CU(cudaSetDevice(p->ctx->device));
+  if (p->esz == 8) return get_field_t<double>(p, field, dst, dst_is_device, bytes);
+  return get_field_t<float>(p, field, dst, dst_is_device, bytes);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int set_field_t(fftm_problem* p, int field, const void* src, int src_is_device, size_t bytes) {
+  cudaStream_t s = p->ctx->stream;
+  const void* from = src;
+  if (!src_is_device) {
+    int rc = ensure_scratch(p, bytes);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(p->scratch, src, bytes, cudaMemcpyHostToDevice, s));
+    from = p->scratch;
+  }
+  T* dst[3];
+  for (int q = 0; q < 3; ++q) dst[q] = field_ptr<T>(p, field == FFTM_FIELD_U ? SET_UH + p->cur : SET_WORK, q);
+  if (field == FFTM_FIELD_U && p->esz == 4)
+    for (int q = 0; q < 3; ++q)
+      CU(cudaMemsetAsync(field_ptr<T>(p, SET_UL + p->cur, q), 0, p->comp_stride * sizeof(T), s));
+  CU(launch_pack<T>((const T* const*)dst, const_cast<T*>(reinterpret_cast<const T*>(from)), p->N[0], p->N[1],
+                    p->N[2], p->sy, p->sz, 1, s));
+  CU(launch_mask<T>(dst, p->lo, p->hi, p->N[0], p->N[1], p->N[2], p->sy, p->sz, s));
+  p->launches += 2;
+  CU(cudaStreamSynchronize(s));
+  return FFTM_OK;
+}
+
+extern "C" {
+
+int fftm_set_field(fftm_problem* p, int field, const void* src, int src_is_device, size_t bytes) {
+  if (!p || !src) return set_err(FFTM_E_INVALID, "null argument");
+  if (field != FFTM_FIELD_U && field != FFTM_FIELD_WORK) return set_err(FFTM_E_INVALID, "only U and WORK are settable");
+  size_t need;
+  int rc = fftm_field_bytes(p, field, &need);
+  if (rc) return rc;
+  if (bytes != need) return set_err(FFTM_E_INVALID, "byte count does not match the field");
+  CU(cudaSetDevice(p->ctx->device));
+  if (p->esz == 8) return set_field_t<double>(p, field, src, src_is_device, bytes);
+  return set_field_t<float>(p, field, src, src_is_device, bytes);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int apply_t(fftm_problem* p, int op, double* norms) {
+  cudaStream_t s = p->ctx->stream;
+  int rc = FFTM_OK;
+  switch (op) {
+    case FFTM_OP_RESIDUAL: {
+      rc = run_residual<T>(p, p->cur, true);
+      if (rc) return rc;
+      CU(cudaMemcpyAsync(p->hpin, p->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CU(cudaStreamSynchronize(s));
+      if (norms) {
+        norms[0] = p->hpin[0];
+        norms[1] = p->hpin[1];
+        norms[2] = error_of(p, p->hpin[0], p->hpin[1]);
+      }
+      return FFTM_OK;
+    }
+    case FFTM_OP_DT_FORWARD:
+      for (int a = 0; a < 3 && !rc; ++a) rc = run_pass<T>(p, a, 0, 0, SET_WORK, SET_WORK, false);
+      break;
+    case FFTM_OP_DT_INVERSE:
+      for (int a = 2; a >= 0 && !rc; --a) rc = run_pass<T>(p, a, 1, 0, SET_WORK, SET_WORK, true);
+      break;
+    case FFTM_OP_GREEN: {
+      PassParams<T> P = pass_params<T>(p, 2, 0, 0, SET_WORK, SET_WORK);
+      GreenParams<T> G;
+      std::memset(&G, 0, sizeof(G));
+      for (int q = 0; q < 3; ++q) {
+        G.f[q] = field_ptr<T>(p, SET_WORK, q);
+        G.gscale[q] = T(1);
+        for (int a = 0; a < 3; ++a) {
+          G.S2[q][a] = P.S2[q][a];
+          G.C2[q][a] = P.C2[q][a];
+          G.flo[q][a] = P.flo[q][a];
+          G.fL[q][a] = P.fL[q][a];
+        }
+      }
+      for (int a = 0; a < 3; ++a) {
+        G.N[a] = p->N[a];
+        G.hf[a] = P.hf[a];
+      }
+      G.sy = p->sy;
+      G.sz = p->sz;
+      G.two_mu0 = P.two_mu0;
+      G.lam0 = P.lam0;
+      G.tetra = p->tetra;
+      CU(launch_green<T>(G, s));
+      p->launches++;
+      break;
+    }
+    case FFTM_OP_GREEN_UPDATE:
+      // u^f = Gamma(WORK) into the current slot (low part cleared)
+      if (p->esz == 4)
+        for (int q = 0; q < 3; ++q)
+          CU(cudaMemsetAsync(field_ptr<T>(p, SET_UL + p->cur, q), 0, p->comp_stride * sizeof(T), s));
+      rc = green_apply<T>(p, SET_WORK, -1, -1, SET_UH + p->cur, -1, false);
+      break;
+    default:
+      return set_err(FFTM_E_INVALID, "unknown op");
+  }
+  if (rc) return rc;
+  CU(cudaStreamSynchronize(s));
+  return FFTM_OK;
+}
+
+extern "C" {
+
+int fftm_apply(fftm_problem* p, int op, double* norms) {
+  if (!p) return set_err(FFTM_E_INVALID, "null problem");
+  CU(cudaSetDevice(p->ctx->device));
+  if (p->esz == 8) return apply_t<double>(p, op, norms);
+  return apply_t<float>(p, op, norms);
+}
+
+int fftm_reset_state(fftm_problem* p) {
+  if (!p) return set_err(FFTM_E_INVALID, "null problem");
+  CU(cudaSetDevice(p->ctx->device));
+  Sizes sz = sizes_of(&p->desc);
+  CU(cudaMemsetAsync(p->fields, 0, sz.fields, p->ctx->stream));
+  CU(cudaStreamSynchronize(p->ctx->stream));
+  p->cur = 0;
+  return FFTM_OK;
+}
+
+int fftm_set_profiling(fftm_problem* p, int enable) {
+  if (!p) return set_err(FFTM_E_INVALID, "null problem");
+  CU(cudaSetDevice(p->ctx->device));
+  CU(cudaStreamSynchronize(p->ctx->stream));
+  prof_flush(p);
+  p->prof = enable != 0;
+  for (int c = 0; c < FFTM_KCAT_COUNT; ++c) {
+    p->prof_ms[c] = 0.0;
+    p->prof_cnt[c] = 0;
+  }
+  return FFTM_OK;
+}
+
+int fftm_kernel_times(const fftm_problem* p, double* ms, long long* launches, int n) {
+  if (!p || !ms || !launches || n < FFTM_KCAT_COUNT) return set_err(FFTM_E_INVALID, "bad arguments");
+  for (int c = 0; c < FFTM_KCAT_COUNT; ++c) {
+    ms[c] = p->prof_ms[c];
+    launches[c] = p->prof_cnt[c];
+  }
+  return FFTM_OK;
+}
+
+int fftm_kernel_launches(const fftm_problem* p, long long* count) {
+  if (!p || !count) return set_err(FFTM_E_INVALID, "null argument");
+  *count = p->launches;
+  return FFTM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+// Internal types of the fftm library: transform plans, kernel parameter
+// blocks and the launchers each .cu file provides.  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fftm {
+
+// One-dimensional transform kinds, one per pair of face symmetries of a node
+// field (Table 1): P/P -> DFT, S/S -> DCT-I, S/A -> DCT-III, A/A -> DST-I,
+// A/S -> DST-III.
+enum Kind { K_DFT = 0, K_DCT1 = 1, K_DCT3 = 2, K_DST1 = 3, K_DST3 = 4 };
+
+template <typename T> struct V2;
+template <> struct V2<float> { using t = float2; };
+template <> struct V2<double> { using t = double2; };
+
+constexpr int MAX_STAGES = 16;
+
+// Plan of the 1D transform of one displacement component along one axis.
+// Every DT is evaluated through one complex FFT of length M (M = n for the
+// DFT, 2n for the DCT/DST kinds), two real pencils packed per complex pencil.
+template <typename T>
+struct AxisPlan {
+  int kind;
+  int n;      // voxels along the axis
+  int lo, L;  // node range of the transform (positions lo .. lo + L - 1)
+  int M;      // complex FFT length
+  int nst;    // number of FFT stages
+  int radix[MAX_STAGES];
+  const int16_t* perm;               // M: input position of sequence index m
+  const typename V2<T>::t* tw;       // M: exp(-2 pi i t / M)
+  const typename V2<T>::t* qw;       // n + 1: exp(i pi j / (2 n))
+};
+
+// One axis pass over the three components of a node field.
+template <typename T>
+struct PassParams {
+  const T* in[3];
+  T* out[3];
+  // optional accumulation at store (last inverse pass of the solver update):
+  // out = base + scale * value, as an unevaluated hi + lo pair when out_lo is set
+  const T* base[3];
+  const T* base_lo[3];
+  T* out_lo[3];
+  int axis;
+  int N[3];             // node dims
+  long long stride[3];  // element strides of x, y, z
+  AxisPlan<T> plan[3];
+  int inverse;
+  T scale[3];
+  // fused forward z -> Green -> inverse z (axis 2 only)
+  int fused;
+  const T* S2[3][3];  // [q][axis] sin^2(xi/2) by frequency index
+  const T* C2[3][3];  // [q][axis] cos^2(xi/2)
+  int flo[3][3];      // [q][axis] node position of frequency index 0
+  int fL[3][3];       // [q][axis] number of frequencies
+  T hf[3];            // 4 / h_a^2
+  T two_mu0, lam0;
+  int tetra;
+  T gscale[3];        // inverse-transform normalisation folded into the Green factor
+};
+
+// Stencil + law + divergence (one fixed-point residual evaluation).
+template <typename T>
+struct ResParams {
+  const T* u[3];    // u^f (high part in FP32)
+  const T* ulo[3];  // low part of u^f (FP32 only; null otherwise)
+  T* D[3];          // D = div P at the nodes (dismissed components 0)
+  T* p[3];          // p = div(R0 : grad u^f) - D (test variant only)
+  const uint16_t* phase;
+  const int* law_id;  // per phase
+  const T* law_c;     // per phase, LAWC coefficients
+  int n[3], N[3];
+  int periodic[3];
+  long long sy, sz;  // node strides (x stride 1)
+  long long vy, vz;  // voxel strides
+  T Gs[9];           // uniform gradient of the affine u*
+  T lam0, two_mu0;
+  T wdiv[3];         // 1 / (4 h_i)
+  T wgrad[3];        // HEX1: 1 / (4 h_i); TETRA2: 1 / (2 h_i)
+  int sgn[3][3][2];  // [q][axis][face] +1 symmetric (Neumann), -1 anti-symmetric (Dirichlet)
+  int lo[3][3], hi[3][3];  // [q][axis] transformed node range
+  int zchunk;
+  double* partial;   // per block: S_D, S_P
+  double* stats;     // optional per block: sum P (9), sum G (9)
+};
+
+constexpr int LAWC = 24;
+
+// Green factor on a spectral field (standalone step).
+template <typename T>
+struct GreenParams {
+  T* f[3];
+  int N[3];
+  long long sy, sz;
+  const T* S2[3][3];
+  const T* C2[3][3];
+  int flo[3][3], fL[3][3];
+  T hf[3];
+  T two_mu0, lam0;
+  int tetra;
+  T gscale[3];
+};
+
+// ---- launchers (return cudaError_t of the launch) ----
+template <typename T>
+cudaError_t launch_pass(const PassParams<T>& P, int maxM, int maxL, int maxn, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const ResParams<T>& P, int tetra, bool with_p, cudaStream_t s, int* blocks_out);
+template <typename T>
+int residual_blocks(const ResParams<T>& P, int tetra);
+template <typename T>
+cudaError_t launch_green(const GreenParams<T>& P, cudaStream_t s);
+
+cudaError_t launch_reduce_norms(const double* partial, int nblocks, int nvals, double* out, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_axpy_fields(T* const dst[3], const T* const a[3], const T* const b[3], T alpha,
+                               long long count, cudaStream_t s);  // dst = a + alpha b
+template <typename T>
+cudaError_t launch_copy_fields(T* const dst[3], const T* const src[3], long long count, cudaStream_t s);
+// Anderson on (u^k, D^k), newest couple last: normal matrix of D_k - D_last and
+// right-hand side <D_k - D_last, D_last>, per block (9 doubles).
+template <typename T>
+cudaError_t launch_gram(const T* const D[4][3], int m, long long count, double* partial, int nblocks,
+                        cudaStream_t s);
+cudaError_t launch_anderson_solve(const double* partial, int nblocks, int m, double pivot_tol, double* coef,
+                                  int* accepted, cudaStream_t s);
+// Dbar = sum c_k D_k -> dst;  ubar = u_last + sum_k c_k (u_k - u_last) -> (bh, bl)
+template <typename T>
+cudaError_t launch_combine(T* const dst[3], T* const bh[3], T* const bl[3], const T* const D[4][3],
+                           const T* const uh[4][3], const T* const ul[4][3], int m, const double* coef,
+                           long long count, cudaStream_t s);
+template <typename T>
+cudaError_t launch_voxel_fields(const ResParams<T>& P, int tetra, T* grad_out, T* stress_out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pack(const T* const src[3], T* dst, int N1, int N2, int N3, long long sy, long long sz,
+                        int unpack, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mask(T* const f[3], const int lo[3][3], const int hi[3][3], int N1, int N2, int N3,
+                        long long sy, long long sz, cudaStream_t s);
+
+int gram_blocks(long long count);
+template <typename T>
+cudaError_t launch_stats(const ResParams<T>& P, int tetra, double* partial, int nblocks, cudaStream_t s);
+
+}  // namespace fftm

@@ -1,0 +1,295 @@
+"""Thin ctypes binding of include/fftm.h (argument marshalling only).
+
+Every function here forwards to the C function of the same name in
+libfftm.so; all arithmetic runs in the library's CUDA kernels.  Device
+memory handed to the library comes from PyTorch tensors (``data_ptr``), and
+the CUDA stream from ``torch.cuda.current_stream()``.  Importing this module
+fails loudly when the library has not been built: there is no fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfftm.so")
+
+# status codes
+FFTM_OK = 0
+FFTM_NOT_CONVERGED = 1
+FFTM_E_INVALID = -1
+FFTM_E_NOMEM = -2
+FFTM_E_CUDA = -3
+FFTM_E_DIVERGED = -4
+FFTM_E_UNSUPPORTED = -5
+# enums
+FFTM_BC_PERIODIC, FFTM_BC_DIRICHLET, FFTM_BC_NEUMANN = 0, 1, 2
+FFTM_HEX1, FFTM_TETRA2 = 0, 1
+FFTM_GREEN_B0, FFTM_GREEN_MU0 = 0, 1
+FFTM_FP64, FFTM_FP32 = 0, 1
+FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
+FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D = 0, 1, 2, 3, 4
+FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP_GREEN_UPDATE = 0, 1, 2, 3, 4
+
+# every symbol include/fftm.h declares
+EXPORTS = [
+    "fftm_last_error", "fftm_version", "fftm_ctx_create", "fftm_ctx_destroy",
+    "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
+    "fftm_set_phase", "fftm_set_load", "fftm_solve_step", "fftm_field_bytes",
+    "fftm_get_field", "fftm_set_field", "fftm_apply", "fftm_kernel_launches",
+    "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times",
+]
+FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "other"]
+
+
+class fftm_material(ctypes.Structure):
+    _fields_ = [("law", ctypes.c_int), ("params", ctypes.c_double * 8), ("quat", ctypes.c_double * 4)]
+
+
+class fftm_problem_desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3), ("h", ctypes.c_double * 3),
+        ("phase", ctypes.POINTER(ctypes.c_uint16)), ("n_phases", ctypes.c_int),
+        ("materials", ctypes.POINTER(fftm_material)),
+        ("bc", ((ctypes.c_int * 3) * 2) * 3),
+        ("scheme", ctypes.c_int), ("green", ctypes.c_int),
+        ("lambda0", ctypes.c_double), ("mu0", ctypes.c_double),
+        ("precision", ctypes.c_int), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+        ("anderson_depth", ctypes.c_int), ("anderson_period", ctypes.c_int),
+    ]
+
+
+class fftm_load(ctypes.Structure):
+    _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3)]
+
+
+class fftm_step_report(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("err", ctypes.c_double),
+        ("n_accelerated", ctypes.c_int), ("mean_P", ctypes.c_double * 6), ("mean_G", ctypes.c_double * 9),
+    ]
+
+
+class FFTMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"fftm status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libfftm.so (raises if it is missing: build it with paper_2607_05929_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} not found: the CUDA library must be built (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "fftm_last_error": ([], ctypes.c_char_p),
+        "fftm_version": ([], ctypes.c_int),
+        "fftm_ctx_create": ([P(vp), ctypes.c_int, vp], ctypes.c_int),
+        "fftm_ctx_destroy": ([vp], ctypes.c_int),
+        "fftm_problem_workspace_bytes": ([P(fftm_problem_desc), P(ctypes.c_size_t)], ctypes.c_int),
+        "fftm_problem_create": ([vp, P(fftm_problem_desc), P(vp)], ctypes.c_int),
+        "fftm_problem_destroy": ([vp], ctypes.c_int),
+        "fftm_set_phase": ([vp, P(ctypes.c_uint16)], ctypes.c_int),
+        "fftm_set_load": ([vp, P(fftm_load)], ctypes.c_int),
+        "fftm_solve_step": ([vp, P(fftm_step_report), P(ctypes.c_double), P(ctypes.c_int), ctypes.c_int],
+                            ctypes.c_int),
+        "fftm_field_bytes": ([vp, ctypes.c_int, P(ctypes.c_size_t)], ctypes.c_int),
+        "fftm_get_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+        "fftm_set_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+        "fftm_apply": ([vp, ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
+        "fftm_kernel_launches": ([vp, P(ctypes.c_longlong)], ctypes.c_int),
+        "fftm_reset_state": ([vp], ctypes.c_int),
+        "fftm_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
+        "fftm_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_longlong), ctypes.c_int], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status < 0:
+        raise FFTMError(status, load_library().fftm_last_error().decode())
+    return status
+
+
+# ---------------------------------------------------------------------------------------
+def fftm_last_error():
+    return load_library().fftm_last_error().decode()
+
+
+def fftm_version():
+    return load_library().fftm_version()
+
+
+def fftm_ctx_create(device=0, stream=None):
+    """stream: a cudaStream_t as int, a torch.cuda.Stream, or None (legacy default stream)."""
+    if stream is not None and not isinstance(stream, int):
+        stream = stream.cuda_stream
+    ctx = ctypes.c_void_p()
+    _check(load_library().fftm_ctx_create(ctypes.byref(ctx), int(device), ctypes.c_void_p(stream or 0)))
+    return ctx
+
+
+def fftm_ctx_destroy(ctx):
+    return _check(load_library().fftm_ctx_destroy(ctx))
+
+
+def make_desc(n, phase, materials, bc, scheme="HEX1", green="B0", lambda0=0.0, mu0=1.0, precision="fp64",
+              tol=1e-6, max_iter=1000, h=(1.0, 1.0, 1.0), anderson_depth=4, anderson_period=3):
+    """Marshal a problem description.
+
+    phase: integer array indexed [x, y, z]; materials: list of (law, params, quat);
+    bc[a][f][q] in {'P','D','N'}.  Returns (desc, keepalive) -- keep `keepalive`
+    alive until fftm_problem_create returns.
+    """
+    ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint16).transpose(2, 1, 0))  # x fastest
+    mats = (fftm_material * len(materials))()
+    for i, (law, params, quat) in enumerate(materials):
+        mats[i].law = int(law)
+        for k, v in enumerate(params):
+            mats[i].params[k] = float(v)
+        for k, v in enumerate(quat):
+            mats[i].quat[k] = float(v)
+    d = fftm_problem_desc()
+    for a in range(3):
+        d.n[a] = int(n[a])
+        d.h[a] = float(h[a])
+    d.phase = ph.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))
+    d.n_phases = len(materials)
+    d.materials = ctypes.cast(mats, ctypes.POINTER(fftm_material))
+    code = {"P": FFTM_BC_PERIODIC, "D": FFTM_BC_DIRICHLET, "N": FFTM_BC_NEUMANN}
+    for a in range(3):
+        for f in range(2):
+            for q in range(3):
+                d.bc[a][f][q] = code[bc[a][f][q]]
+    d.scheme = FFTM_TETRA2 if scheme == "TETRA2" else FFTM_HEX1
+    d.green = FFTM_GREEN_MU0 if green == "MU0" else FFTM_GREEN_B0
+    d.lambda0 = float(lambda0)
+    d.mu0 = float(mu0)
+    d.precision = FFTM_FP32 if precision in ("fp32", "float32") else FFTM_FP64
+    d.tol = float(tol)
+    d.max_iter = int(max_iter)
+    d.anderson_depth = int(anderson_depth)
+    d.anderson_period = int(anderson_period)
+    return d, (ph, mats)
+
+
+def fftm_problem_workspace_bytes(desc):
+    b = ctypes.c_size_t()
+    _check(load_library().fftm_problem_workspace_bytes(ctypes.byref(desc), ctypes.byref(b)))
+    return b.value
+
+
+def fftm_problem_create(ctx, desc):
+    p = ctypes.c_void_p()
+    _check(load_library().fftm_problem_create(ctx, ctypes.byref(desc), ctypes.byref(p)))
+    return p
+
+
+def fftm_problem_destroy(p):
+    return _check(load_library().fftm_problem_destroy(p))
+
+
+def fftm_set_phase(p, phase):
+    ph = np.ascontiguousarray(np.asarray(phase, dtype=np.uint16).transpose(2, 1, 0))
+    return _check(load_library().fftm_set_phase(p, ph.ctypes.data_as(ctypes.POINTER(ctypes.c_uint16))))
+
+
+def fftm_set_phase_raw(p, host_ptr):
+    """fftm_set_phase with a host pointer to an x-fastest uint16 map (e.g. pinned memory)."""
+    return _check(load_library().fftm_set_phase(p, ctypes.cast(ctypes.c_void_p(int(host_ptr)),
+                                                                ctypes.POINTER(ctypes.c_uint16))))
+
+
+def fftm_set_load(p, A, b=(0.0, 0.0, 0.0)):
+    ld = fftm_load()
+    for q in range(3):
+        for a in range(3):
+            ld.A[q][a] = float(A[q][a])
+        ld.b[q] = float(b[q])
+    return _check(load_library().fftm_set_load(p, ctypes.byref(ld)))
+
+
+def fftm_solve_step(p, history_len=0):
+    """Returns (status, report dict, err history array, accel history array)."""
+    rep = fftm_step_report()
+    eh = np.zeros(max(history_len, 1), dtype=np.float64)
+    ah = np.zeros(max(history_len, 1), dtype=np.int32)
+    st = _check(load_library().fftm_solve_step(
+        p, ctypes.byref(rep), eh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+        ah.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), int(history_len)))
+    r = {"iterations": rep.iterations, "converged": bool(rep.converged), "err": rep.err,
+         "n_accelerated": rep.n_accelerated, "mean_P": np.array(rep.mean_P[:]),
+         "mean_G": np.array(rep.mean_G[:])}
+    n = min(history_len, rep.iterations + 1)
+    return st, r, eh[:n], ah[:n]
+
+
+def fftm_field_bytes(p, field):
+    b = ctypes.c_size_t()
+    _check(load_library().fftm_field_bytes(p, int(field), ctypes.byref(b)))
+    return b.value
+
+
+def _ptr_of(buf):
+    """(pointer, is_device, nbytes) of a torch tensor or a numpy array."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffer must be C-contiguous")
+        return buf.ctypes.data, 0, buf.nbytes
+    if not buf.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return buf.data_ptr(), int(buf.is_cuda), buf.numel() * buf.element_size()
+
+
+def fftm_get_field(p, field, out):
+    ptr, dev, nb = _ptr_of(out)
+    return _check(load_library().fftm_get_field(p, int(field), ctypes.c_void_p(ptr), dev, nb))
+
+
+def fftm_set_field(p, field, src):
+    ptr, dev, nb = _ptr_of(src)
+    return _check(load_library().fftm_set_field(p, int(field), ctypes.c_void_p(ptr), dev, nb))
+
+
+def fftm_apply(p, op):
+    """Returns (status, norms[3])."""
+    norms = (ctypes.c_double * 3)()
+    st = _check(load_library().fftm_apply(p, int(op), norms))
+    return st, np.array(norms[:])
+
+
+def fftm_kernel_launches(p):
+    c = ctypes.c_longlong()
+    _check(load_library().fftm_kernel_launches(p, ctypes.byref(c)))
+    return c.value
+
+
+def fftm_reset_state(p):
+    return _check(load_library().fftm_reset_state(p))
+
+
+def fftm_set_profiling(p, enable=True):
+    return _check(load_library().fftm_set_profiling(p, int(bool(enable))))
+
+
+def fftm_kernel_times(p):
+    """dict category -> (total ms, launches)."""
+    n = len(FFTM_KCAT_NAMES)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    _check(load_library().fftm_kernel_times(p, ms, cnt, n))
+    return {FFTM_KCAT_NAMES[i]: (ms[i], cnt[i]) for i in range(n)}
