@@ -219,6 +219,32 @@ int fftm_set_profiling(fftm_problem* p, int enable);
    last fftm_set_profiling(p, 1); both HOST arrays of n >= FFTM_KCAT_COUNT. */
 int fftm_kernel_times(const fftm_problem* p, double* ms, long long* launches, int n);
 
+/* ---- residual evaluation without allocation ---------------------------------
+   No counterpart in the paper: an interface for callers that may not allocate
+   device memory where they need a residual -- code running while a CUDA stream
+   is captured into a graph (a cudaMalloc there breaks the capture), frameworks
+   whose caching allocator or memory pool must own every device byte, and
+   fixed-memory real-time loops.
+
+   Evaluates D = div P (+ D*) and the norms of a caller-supplied u^f exactly as
+   FFTM_OP_RESIDUAL does (same kernel), on the problem's stream, without any
+   cudaMalloc/cudaFree:
+     u_dev      DEVICE, input, the dense node layout of FFTM_FIELD_U in the
+                problem's precision (FP32 problems read the field as plain floats)
+     D_dev      DEVICE, output, same layout; dismissed node components get 0
+     norms_dev  DEVICE, output, 3 doubles: S_D, S_P, err
+   Asynchronous: results are ready when the problem's stream reaches them.
+   Scratch: the reduction's block partials live in a file-scope device array
+   of 16384 doubles (128 KiB) that every GPU loading the library holds until
+   the process exits; a grid needing more than 16380 partial slots (2 per
+   block of the residual kernel) is rejected with FFTM_E_UNSUPPORTED and a
+   message.  Every slot read is written earlier in the same call, so nothing
+   needs clearing; all calls share the array, so calls that overlap on the GPU
+   (other streams, other threads, other problems on the same device) race.
+   The first call on a device looks the array's device address up
+   (cudaGetSymbolAddress): make that first call before any stream capture. */
+int fftm_residual_noalloc(fftm_problem* p, const void* u_dev, void* D_dev, double* norms_dev);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,7 +5,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <math_constants.h>
+
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1064,3 +1067,92 @@ int fftm_kernel_launches(const fftm_problem* p, long long* count) {
 }
 
 }  // extern "C"
+
+// ======================================================================================
+// Residual evaluation that allocates nothing.
+//
+// Some callers may not allocate device memory at the point where they need a
+// residual: code that runs while a CUDA stream is being captured into a graph
+// (where a cudaMalloc would break or invalidate the capture), frameworks whose
+// caching allocator or memory pool must own every device byte, and fixed-memory
+// real-time loops.  fftm_residual_noalloc serves them: the caller passes u^f and
+// receives D and the norms in its own device buffers, and the per-block partial
+// sums of the reduction live in the file-scope array below, which the module
+// loader places in every device context that loads the library (128 KiB per
+// GPU, held until the process exits).
+namespace {
+
+constexpr int kNoAllocScratchDoubles = 16384;  // 128 KiB of block partials + 4 result slots
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current).  Host
+// code may not pass g_noalloc_scratch itself to a kernel: on the host that name
+// is only a stand-in for the symbol, not a device address.
+int noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= kMaxDevices) return set_err(FFTM_E_INVALID, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return set_err(FFTM_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[device] = reinterpret_cast<double*>(ptr);
+  }
+  *out = g_noalloc_ptr[device];
+  return FFTM_OK;
+}
+
+__global__ void k_noalloc_norms(const double* __restrict__ sums, double h1, double* __restrict__ norms) {
+  const double sd = sums[0], sp = sums[1];
+  norms[0] = sd;
+  norms[1] = sp;
+  norms[2] = sp > 0.0 ? h1 * sqrt(sd / sp) : (sd == 0.0 ? 0.0 : CUDART_INF);
+}
+
+template <typename T>
+int residual_noalloc_t(fftm_problem* p, const T* u, T* D, double* norms) {
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(p->ctx->device, &scratch);
+  if (rc) return rc;
+  const long long per = (long long)p->N[0] * p->N[1] * p->N[2];
+  ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
+  for (int q = 0; q < 3; ++q) {
+    R.u[q] = u + q * per;
+    R.ulo[q] = nullptr;
+    R.D[q] = D + q * per;
+    R.p[q] = nullptr;
+  }
+  R.sy = p->N[0];
+  R.sz = (long long)p->N[0] * p->N[1];
+  const int blocks = residual_blocks<T>(R, p->tetra);
+  if (2LL * blocks > kNoAllocScratchDoubles - 4)
+    return set_err(FFTM_E_UNSUPPORTED, "grid too large for the no-allocation scratch (" +
+                                           std::to_string(blocks) + " blocks need " + std::to_string(2 * blocks) +
+                                           " doubles; the maximum is " +
+                                           std::to_string(kNoAllocScratchDoubles - 4) + ")");
+  R.partial = scratch;  // every block overwrites its two slots: nothing has to start at zero
+  double* sums = scratch + kNoAllocScratchDoubles - 4;
+  cudaStream_t s = p->ctx->stream;
+  CU(launch_residual<T>(R, p->tetra, false, s, nullptr));
+  CU(launch_reduce_norms(scratch, blocks, 2, sums, s));
+  k_noalloc_norms<<<1, 1, 0, s>>>(sums, p->h[0], norms);
+  CU(cudaGetLastError());
+  p->launches += 3;
+  return FFTM_OK;
+}
+
+}  // namespace
+
+extern "C" int fftm_residual_noalloc(fftm_problem* p, const void* u_dev, void* D_dev, double* norms_dev) {
+  if (!p || !u_dev || !D_dev || !norms_dev) return set_err(FFTM_E_INVALID, "null argument");
+  CU(cudaSetDevice(p->ctx->device));
+  if (p->esz == 8)
+    return residual_noalloc_t<double>(p, reinterpret_cast<const double*>(u_dev), reinterpret_cast<double*>(D_dev),
+                                      norms_dev);
+  return residual_noalloc_t<float>(p, reinterpret_cast<const float*>(u_dev), reinterpret_cast<float*>(D_dev),
+                                   norms_dev);
+}

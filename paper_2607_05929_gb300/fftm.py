@@ -38,7 +38,7 @@ EXPORTS = [
     "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
     "fftm_set_phase", "fftm_set_load", "fftm_solve_step", "fftm_field_bytes",
     "fftm_get_field", "fftm_set_field", "fftm_apply", "fftm_kernel_launches",
-    "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times",
+    "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
 ]
 FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "other"]
 
@@ -110,6 +110,7 @@ def load_library(path=LIB_PATH):
         "fftm_reset_state": ([vp], ctypes.c_int),
         "fftm_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
         "fftm_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_longlong), ctypes.c_int], ctypes.c_int),
+        "fftm_residual_noalloc": ([vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -293,3 +294,14 @@ def fftm_kernel_times(p):
     cnt = (ctypes.c_longlong * n)()
     _check(load_library().fftm_kernel_times(p, ms, cnt, n))
     return {FFTM_KCAT_NAMES[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def fftm_residual_noalloc(p, u_dev, D_dev, norms_dev):
+    """Residual D and norms of a caller-supplied u^f into caller device buffers (torch CUDA
+    tensors: u and D in the dense node layout, norms 3 float64); allocates no device memory."""
+    for t in (u_dev, D_dev, norms_dev):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("device tensors expected")
+    return _check(load_library().fftm_residual_noalloc(p, ctypes.c_void_p(u_dev.data_ptr()),
+                                                        ctypes.c_void_p(D_dev.data_ptr()),
+                                                        ctypes.c_void_p(norms_dev.data_ptr())))
