@@ -42,9 +42,10 @@ if ROOT not in sys.path:
 
 METRIC = "voxel-iterations/s"
 UNIT = "voxel-it/s"
-WORKLOAD_NAME = ("voronoi_polycrystal_256: 256^3 voxels, 500-grain Voronoi, cubic elastic C11/C12/C44="
-                 "168/121/75 GPa, random orientations, TETRA2, B0, x Dirichlet / y Neumann / z periodic, "
-                 "eps_xx=1e-3, tol=1e-6, Anderson 4/3")
+def workload_name(n, grains):
+    return (f"voronoi_polycrystal_{n}: {n}^3 voxels, {grains}-grain Voronoi, cubic elastic C11/C12/C44="
+            "168/121/75 GPa, random orientations, TETRA2, B0, x Dirichlet / y Neumann / z periodic, "
+            "eps_xx=1e-3, tol=1e-6, Anderson 4/3")
 REF_SLAB = 32  # z-planes of the oracle's bounded sample
 
 
@@ -284,7 +285,7 @@ def reference_arm(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "sample": sample},
+            "config": {"workload": workload_name(args.n, args.grains), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                              "threads_note": "scipy.fft with workers=-1; NumPy elementwise on one thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -391,7 +392,7 @@ def gpu_arm(args):
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_NAME, "precision": args.precision,
+            "config": {"workload": workload_name(args.n, args.grains), "precision": args.precision,
                        "iterations_per_step": iters, "anderson_steps_per_step": last["n_accelerated"],
                        "l2": "inputs larger than L2 (working set several GB; no flush needed)",
                        "parallelism": f"replicas x{dist.world}"},

@@ -236,9 +236,10 @@ int fftm_kernel_times(const fftm_problem* p, double* ms, long long* launches, in
    Asynchronous: results are ready when the problem's stream reaches them.
    Scratch: the reduction's block partials live in a file-scope device array
    of 16384 doubles (128 KiB) that every GPU loading the library holds until
-   the process exits; a grid needing more than 16380 partial slots (2 per
-   block of the residual kernel) is rejected with FFTM_E_UNSUPPORTED and a
-   message.  Every slot read is written earlier in the same call, so nothing
+   the process exits (the residual kernels use at most 2432 blocks, 2 slots
+   each; a launch needing more than 16380 slots would be rejected with
+   FFTM_E_UNSUPPORTED and a message); the voxel-point stresses go to a buffer
+   the problem allocated when it was created.  Every slot read is written earlier in the same call, so nothing
    needs clearing; all calls share the array, so calls that overlap on the GPU
    (other streams, other threads, other problems on the same device) race.
    The first call on a device looks the array's device address up

@@ -198,6 +198,9 @@ struct fftm_problem {
   double* hpin = nullptr;   // pinned host scalars
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  void* vs = nullptr;       // voxel-point stresses of the solver (NPP x NC x nvox)
+  void* vs_test = nullptr;  // with tau, for FFTM_OP_RESIDUAL (allocated on first use)
+  int sym = 1;              // every law gives a symmetric P
   // device table offsets (bytes) inside `tables`
   size_t off_perm[3][3], off_tw[3][3], off_qw[3][3], off_S2[3][3], off_C2[3][3];
   int maxM[3], maxL[3];
@@ -392,6 +395,8 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
       R.hi[q][a] = p->hi[q][a];
     }
   R.partial = p->partial;
+  R.vs = reinterpret_cast<T*>(p->vs);
+  R.sym = p->sym;
   return R;
 }
 
@@ -407,8 +412,13 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
     }
     D = reinterpret_cast<T*>(p->Dbuf);
     pp = field_ptr<T>(p, SET_WORK, 0);
+    if (!p->vs_test) {
+      const size_t b = (size_t)(p->tetra ? 2 : 1) * ((p->sym ? 6 : 9) + 9) * p->nvox * sizeof(T);
+      CU(cudaMalloc(&p->vs_test, b));
+    }
   }
   ResParams<T> R = res_params<T>(p, slot, D, pp);
+  if (test_outputs) R.vs = reinterpret_cast<T*>(p->vs_test);
   int blocks = 0;
   ProfScope ps(p, test_outputs ? FFTM_KCAT_OTHER : FFTM_KCAT_RESIDUAL);
   CU(launch_residual<T>(R, p->tetra, test_outputs, p->ctx->stream, &blocks));
@@ -658,7 +668,9 @@ int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
   if (!bytes) return set_err(FFTM_E_INVALID, "null bytes");
   Sizes s = sizes_of(desc);
   const long long nvox = (long long)desc->n[0] * desc->n[1] * desc->n[2];
-  *bytes = s.fields + s.tables + s.lawc + s.partial + nvox * sizeof(uint16_t) + desc->n_phases * sizeof(int);
+  const size_t esz = desc->precision == FFTM_FP64 ? 8 : 4;
+  const size_t vsb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 9 * nvox * esz;
+  *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + nvox * sizeof(uint16_t) + desc->n_phases * sizeof(int);
   return FFTM_OK;
 }
 
@@ -675,6 +687,8 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->dscal);
   cudaFree(p->dint);
   cudaFree(p->scratch);
+  cudaFree(p->vs);
+  cudaFree(p->vs_test);
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -736,6 +750,9 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
     return set_err(FFTM_E_NOMEM, "device allocation of the fields failed");
   }
   CU(cudaMemsetAsync(p->fields, 0, sz.fields, s));
+  for (int i = 0; i < desc->n_phases; ++i)
+    if (desc->materials[i].law == FFTM_LAW_B0_LINEAR) p->sym = 0;
+  CU(cudaMalloc(&p->vs, (size_t)(p->tetra ? 2 : 1) * (p->sym ? 6 : 9) * p->nvox * p->esz));
   CU(cudaMalloc(&p->phase, p->nvox * sizeof(uint16_t)));
   CU(cudaMemcpyAsync(p->phase, desc->phase, p->nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
   CU(cudaMalloc(&p->partial, sz.partial));

@@ -332,8 +332,10 @@ struct TileCfg {
   static constexpr int SP = TP + 1;
 };
 
+constexpr int PASS_THREADS = 512;
+
 template <typename T, int AXIS, int FUSED>
-__global__ void __launch_bounds__(256) k_pass(PassParams<T> P) {
+__global__ void __launch_bounds__(PASS_THREADS) k_pass(PassParams<T> P) {
   constexpr int TP = TileCfg<T>::TP;
   constexpr int PC = TileCfg<T>::PC;
   constexpr int SP = TileCfg<T>::SP;
@@ -390,37 +392,42 @@ __global__ void __launch_bounds__(256) k_pass(PassParams<T> P) {
 
   // ---- tables ----
   for (int i = threadIdx.x; i < M; i += blockDim.x) {
-    tw[i] = pl.tw[i];
+    cp_async_elem<T>(&tw[i].x, &pl.tw[i].x);
+    cp_async_elem<T>(&tw[i].y, &pl.tw[i].y);
     perm[i] = pl.perm[i];
   }
-  for (int i = threadIdx.x; i <= pl.n; i += blockDim.x) qw[i] = pl.qw[i];
+  for (int i = threadIdx.x; i <= pl.n; i += blockDim.x) {
+    cp_async_elem<T>(&qw[i].x, &pl.qw[i].x);
+    cp_async_elem<T>(&qw[i].y, &pl.qw[i].y);
+  }
 
   const T* __restrict__ in = P.in[q];
   T* __restrict__ out = P.out[q];
   const int L = pl.L, lo = pl.lo;
 
-  // ---- load: global -> staging ----
+  // ---- load: global -> staging (asynchronous copies, all in flight at once) ----
   if (AXIS == 0) {
     for (int idx = threadIdx.x; idx < L * TP; idx += blockDim.x) {
       const int j = idx % L;
       const int p = idx / L;
-      T v = T(0);
       if (p < npen) {
         const int r = row0 + p;
         const int y = r % N2, z = r / N2;
-        v = in[(long long)y * sy + (long long)z * sz + (long long)(lo + j) * estride];
+        cp_async_elem<T>(&st.at(j, p), in + (long long)y * sy + (long long)z * sz + (long long)(lo + j) * estride);
+      } else {
+        st.at(j, p) = T(0);
       }
-      st.at(j, p) = v;
     }
   } else {
     for (int idx = threadIdx.x; idx < L * TP; idx += blockDim.x) {
       const int p = idx % TP;
       const int j = idx / TP;
-      T v = T(0);
-      if (p < npen) v = in[base0 + p * pstride + (long long)(lo + j) * estride];
-      st.at(j, p) = v;
+      if (p < npen) cp_async_elem<T>(&st.at(j, p), in + base0 + p * pstride + (long long)(lo + j) * estride);
+      else st.at(j, p) = T(0);
     }
   }
+  cp_async_commit();
+  cp_async_wait_all();
   __syncthreads();
 
   const bool inv_first = (P.inverse != 0) && !FUSED;
@@ -536,7 +543,7 @@ static cudaError_t launch_one(const PassParams<T>& P, size_t smem, cudaStream_t 
   if (AXIS == 0) grid.x = (unsigned)((P.N[1] * P.N[2] + TP - 1) / TP);
   else grid.x = (unsigned)(((P.N[0] + TP - 1) / TP) * (AXIS == 1 ? P.N[2] : P.N[1]));
   grid.y = 3;
-  kern<<<grid, 256, smem, s>>>(P);
+  kern<<<grid, PASS_THREADS, smem, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -82,9 +82,9 @@ struct ResParams {
   T wgrad[3];        // HEX1: 1 / (4 h_i); TETRA2: 1 / (2 h_i)
   int sgn[3][3][2];  // [q][axis][face] +1 symmetric (Neumann), -1 anti-symmetric (Dirichlet)
   int lo[3][3], hi[3][3];  // [q][axis] transformed node range
-  int zchunk;
+  T* vs;             // voxel-point stress buffer [r][c][voxel] (c < NC, see fftm_stencil.cu)
+  int sym;           // 1: every law gives a symmetric P (6 stored components)
   double* partial;   // per block: S_D, S_P
-  double* stats;     // optional per block: sum P (9), sum G (9)
 };
 
 constexpr int LAWC = 24;
@@ -143,6 +143,27 @@ cudaError_t launch_mask(T* const f[3], const int lo[3][3], const int hi[3][3], i
                         long long sy, long long sz, cudaStream_t s);
 
 int gram_blocks(long long count);
+
+// Asynchronous global -> shared copies (cp.async, Ampere and later): the copy
+// is issued without a register round trip, so a thread can keep many loads in
+// flight; cp_async_wait_all() + __syncthreads() make them visible.
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  if (sizeof(T) == 8) cp_async_8(smem, gmem);
+  else cp_async_4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// wait until at most one committed group is still in flight
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 template <typename T>
 cudaError_t launch_stats(const ResParams<T>& P, int tetra, double* partial, int nblocks, cudaStream_t s);
 

@@ -78,48 +78,71 @@ int gram_blocks(long long count) {
 }
 
 // Normal matrix of the residual differences d_k = D_k - D_last (k < last) and
-// the right-hand side <d_k, D_last>, accumulated in FP64 from explicit
-// differences (no Gram-entry cancellation).
+// the right-hand side <d_k, D_last>, formed from explicit differences (no
+// Gram-entry cancellation) and reduced in FP64 across threads and blocks.
 template <typename T>
 struct GramArgs {
   const T* D[4][3];
 };
 
+// Accumulator of a sum of products: FP64 for double data; for float data an
+// unevaluated pair (hi, lo) of floats updated with error-free transformations
+// (TwoProduct through fma, TwoSum), which keeps about twice FP32's precision
+// without the FP64 pipe (whose rate is a small fraction of FP32's on this GPU).
+template <typename T>
+struct DotAcc {
+  double s = 0.0;
+  __device__ __forceinline__ void add(T a, T b) { s += (double)a * (double)b; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct DotAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);  // exact error of the product
+    const float s = hi + p;
+    const float bb = s - hi;
+    const float se = (hi - (s - bb)) + (p - bb);  // exact error of the sum
+    hi = s;
+    lo += se + pe;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gram(GramArgs<T> A, int m, long long count, double* __restrict__ partial) {
   __shared__ double red[8][9];
-  double acc[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) acc[i] = 0.0;
+  DotAcc<T> acc[9];
   const int L = m - 1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      double v[4], d[3];
+      T v[4], d[3];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = (j < m) ? (double)A.D[j][c][i] : 0.0;
-      double last = v[0];
+      for (int j = 0; j < 4; ++j) v[j] = (j < m) ? A.D[j][c][i] : T(0);
+      T last = v[0];
 #pragma unroll
       for (int j = 0; j < 4; ++j)
         if (j == L) last = v[j];
 #pragma unroll
-      for (int j = 0; j < 3; ++j) d[j] = (j < L) ? v[j] - last : 0.0;
-      acc[0] += d[0] * d[0];
-      acc[1] += d[0] * d[1];
-      acc[2] += d[0] * d[2];
-      acc[3] += d[1] * d[1];
-      acc[4] += d[1] * d[2];
-      acc[5] += d[2] * d[2];
-      acc[6] += d[0] * last;
-      acc[7] += d[1] * last;
-      acc[8] += d[2] * last;
+      for (int j = 0; j < 3; ++j) d[j] = (j < L) ? v[j] - last : T(0);
+      acc[0].add(d[0], d[0]);
+      acc[1].add(d[0], d[1]);
+      acc[2].add(d[0], d[2]);
+      acc[3].add(d[1], d[1]);
+      acc[4].add(d[1], d[2]);
+      acc[5].add(d[2], d[2]);
+      acc[6].add(d[0], last);
+      acc[7].add(d[1], last);
+      acc[8].add(d[2], last);
     }
   }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    double v = acc[k];
+    double v = acc[k].value();
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     if (l == 0) red[w][k] = v;
   }

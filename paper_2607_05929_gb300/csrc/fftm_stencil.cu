@@ -1,22 +1,23 @@
-// Fixed-point residual: gradient -> constitutive law -> divergence, fused
+// Fixed-point residual: gradient -> constitutive law -> divergence
 // (Algorithm 1: grad u, P, D = div P + D*, the error; Eq. div_pol for p).
 //
-// A CTA owns a TX x TY tile of nodes in (x, y) and marches along z.  For each
-// voxel plane it stages two node planes of u^f in shared memory, evaluates the
-// gradient at the voxel points (HEX1: Eqs. D1HG-D3HG; TETRA2: Eqs.
-// D1T1T2G-D3T1T2G) and the law, and keeps two voxel planes of P (and, for the
-// test variant, tau = R0 : grad u^f - P with B0 = 2 mu0 G + lambda0 G (.) I,
-// Sec. 2.6.3) in shared memory.  The divergence at a node plane (Remark 1:
-// node m reads the voxels m + o - 1 with the same signs) yields D = div P, and
-// the FP64 block partials of S_D = sum D^2 (transformed node components) and
-// S_P = sum ||P||^2 / n_ppv.  The test variant also writes p = div tau.
+// Two passes over the grid.  k_stress (one thread per voxel) evaluates the
+// gradient at the voxel point(s) (HEX1: Eqs. D1HG-D3HG; TETRA2: Eqs.
+// D1T1T2G-D3T1T2G) and the law, and stores P (for the test variant also
+// tau = R0 : grad u^f - P with B0 = 2 mu0 G + lambda0 G (.) I, Sec. 2.6.3).
+// k_div (one thread per node) applies Remark 1 -- node m reads the voxels
+// m + o - 1 with the same signs -- to get D = div P (and p = div tau), written
+// for the transformed node components (dismissed ones get 0).  FP64 block
+// partials of S_D = sum D^2 and S_P = sum ||P||^2 / n_ppv go to `partial`.
 //
 // Stencil sums are formed as sums of differences of neighbouring values
 // (u(o + e_i) - u(o) for HEX1; the paper's pairs for TETRA2), which are exact
 // or nearly so in floating point for smooth fields, so the gradient carries
 // the relative precision of the arithmetic instead of that of |u|.  In FP32
 // the displacement is held as an unevaluated sum hi + lo of two floats (its
-// low part carries what FP32 drops); both parts are differenced.
+// low part carries what FP32 drops); both parts are differenced.  The norm
+// partials are summed in the field precision over short runs and in FP64
+// across runs (FP64 throughput is a small fraction of FP32 on this GPU).
 //
 // TETRA2: tetrahedron T1 uses the four even-parity corners of the voxel, T2 the
 // four odd-parity ones; along axis i the paper's two differences pair each
@@ -25,10 +26,12 @@
 // reads from the voxel at node offset o the T1 point for odd-parity o and the
 // T2 point for even o, with weight sign / (4 h_i) -- the HEX1 weights.
 //
-// Ghost voxels (outside non-periodic faces) are never computed: a read is
+// Ghost voxels (outside non-periodic faces) are never stored: a read is
 // redirected to the mirror voxel inside, with the sign sigma(u_q, face) *
 // (-1 if i is the face normal) on component (i, q), and with T1 <-> T2
 // swapped once per face crossed (Sec. 2.2, Sec. 2.5.2).  Periodic axes wrap.
+#include <algorithm>
+
 #include "fftm_internal.cuh"
 
 namespace fftm {
@@ -118,67 +121,109 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-template <typename T, int TETRA, int TX, int TY, bool WITH_P, bool LO>
-__global__ void __launch_bounds__(TX * TY) k_residual(ResParams<T> P) {
-  constexpr int NPP = TETRA ? 2 : 1;
-  constexpr int NE = WITH_P ? 18 : 9;  // P (9) [+ tau (9)] per voxel point
-  constexpr int VX = TX + 1, VY = TY + 1, VPL = VX * VY;
-  constexpr int NX = TX + 2, NY = TY + 2, NPL = NX * NY;
-  constexpr int NLO = LO ? 2 : 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* nodes = reinterpret_cast<T*>(smem_raw);  // [NLO][2][3][NPL]
-  T* vox = nodes + NLO * 2 * 3 * NPL;         // [2][NPP*NE][VPL]
-  __shared__ double red[32];
+// ---- the residual as two passes over the grid ----------------------------------
+// k_stress: one thread per voxel evaluates the gradient and the law at its
+// point(s) and stores P (and tau for the test variant) in the voxel-point
+// buffer vs[(r * NC + c) * nvox + voxel]: NC = 6 (11, 22, 33, 23, 13, 12) when
+// every law gives a symmetric P, else 9 (c = 3 i + q); tau follows at c + NC.
+// k_div: one thread per node gathers D = div P (and p = div tau) from the 8
+// voxels around it.  Both run over 32 x 8 (x, y) tiles of one z plane with a
+// fixed number of blocks, so the per-block FP64 partials (S_D from k_div, S_P
+// from k_stress, same block index) have a bounded count.
+constexpr int RTX = 32, RTY = 8, RBLOCKS = 2432;
 
-  const int tid = threadIdx.x;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
-  const int N1 = P.N[0], N2 = P.N[1], N3 = P.N[2];
-  const int px = P.periodic[0], py = P.periodic[1], pz = P.periodic[2];
-  const int zc0 = blockIdx.z * P.zchunk;
-  const int zc1 = min(zc0 + P.zchunk, N3);
-  double SD = 0.0, SP = 0.0;
+// Tiles of RTX x RTY (x, y) positions of one z plane over the box [o, o + e).
+struct TileIdx {
+  int tx, ty, ntile;
+  int ox, oy, oz;  // origin of the box
+  int ex, ey, ez;  // extents of the box
+  __device__ __forceinline__ void at(int t, int* x0, int* y0, int* z) const {
+    *x0 = ox + (t % tx) * RTX;
+    const int r = t / tx;
+    *y0 = oy + (r % ty) * RTY;
+    *z = oz + r / ty;
+  }
+};
 
-  auto compute_plane = [&](int vz, int slot, bool owned) {
-    // node planes vz and vz + 1 (wrapped on a periodic z)
-    const int za = vz, zb = pz ? (vz + 1) % n3 : vz + 1;
-    __syncthreads();
-    for (int idx = tid; idx < NLO * 2 * 3 * NPL; idx += TX * TY) {
-      const int e = idx % NPL;
-      const int c = (idx / NPL) % 3;
-      const int pl = (idx / (3 * NPL)) % 2;
-      const int part = idx / (6 * NPL);
-      int gx = x0 - 1 + e % NX, gy = y0 - 1 + e / NX;
-      bool ok = true;
-      if (px) gx = (gx + n1) % n1; else ok = ok && gx >= 0 && gx < N1;
-      if (py) gy = (gy + n2) % n2; else ok = ok && gy >= 0 && gy < N2;
-      const int gz = pl ? zb : za;
-      const T* src = part ? P.ulo[c] : P.u[c];
-      nodes[idx] = ok ? src[gx + gy * P.sy + (long long)gz * P.sz] : T(0);
+static TileIdx make_tiles(int ox, int oy, int oz, int ex, int ey, int ez) {
+  TileIdx ti;
+  ti.ox = ox; ti.oy = oy; ti.oz = oz;
+  ti.ex = ex; ti.ey = ey; ti.ez = ez;
+  ti.tx = (ex + RTX - 1) / RTX;
+  ti.ty = (ey + RTY - 1) / RTY;
+  ti.ntile = (ex > 0 && ey > 0 && ez > 0) ? ti.tx * ti.ty * ez : 0;
+  return ti;
+}
+
+// Nodes on non-periodic faces, each once: segment a holds the nodes with
+// m_a in {0, n_a}, m_b interior for the non-periodic axes b < a.
+struct FaceIdx {
+  int count;
+  int seg[3];     // nodes in segment a (0 for a periodic axis)
+  int ext[3][3];  // extent along each axis in segment a
+  int org[3][3];  // origin along each axis in segment a
+  __device__ __forceinline__ bool at(int t, int n_face[3], int* m) const {
+    for (int a = 0; a < 3; ++a) {
+      if (t < seg[a]) {
+        const int side = t & 1;
+        int r = t >> 1;
+        for (int b = 0; b < 3; ++b) {
+          if (b == a) {
+            m[b] = side ? n_face[a] : 0;
+          } else {
+            m[b] = org[a][b] + r % ext[a][b];
+            r /= ext[a][b];
+          }
+        }
+        return true;
+      }
+      t -= seg[a];
     }
-    __syncthreads();
-    T* V = vox + slot * (NPP * NE * VPL);
-    for (int e = tid; e < VPL; e += TX * TY) {
-      const int lx = e % VX, ly = e / VX;
-      const int vx = x0 - 1 + lx, vy = y0 - 1 + ly;
-      if (vx >= n1 || vy >= n2) continue;
-      if ((vx < 0 && !px) || (vy < 0 && !py)) continue;
-      const int vxw = vx < 0 ? vx + n1 : vx, vyw = vy < 0 ? vy + n2 : vy;
+    return false;
+  }
+};
+
+__device__ __forceinline__ int sym_index(int i, int q) {
+  if (i == q) return i;
+  return 6 - i - q;  // (1,2) -> 3, (0,2) -> 4, (0,1) -> 5
+}
+
+template <typename T, int TETRA, bool WITH_P, bool LO, bool SYM>
+__global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti) {
+  constexpr int NPP = TETRA ? 2 : 1;
+  constexpr int NC = SYM ? 6 : 9;
+  constexpr int NCT = WITH_P ? NC + 9 : NC;
+  __shared__ double red[32];
+  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+  const long long nvox = (long long)n1 * n2 * n3;
+  const int sy = (int)P.sy, sz = (int)P.sz, vy = (int)P.vy, vz_ = (int)P.vz;
+  T sp = T(0);
+  double SP = 0.0;
+  int run = 0;
+  for (int t = blockIdx.x; t < ti.ntile; t += gridDim.x) {
+    int x0, y0, vz;
+    ti.at(t, &x0, &y0, &vz);
+    const int vx = x0 + (threadIdx.x % RTX), vy_ = y0 + (threadIdx.x / RTX);
+    if (vx < n1 && vy_ < n2) {
       T uh[3][8], ul[3][8];
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        int gx = vx + (o & 1), gy = vy_ + ((o >> 1) & 1), gz = vz + (o >> 2);
+        if (P.periodic[0] && gx == n1) gx = 0;
+        if (P.periodic[1] && gy == n2) gy = 0;
+        if (P.periodic[2] && gz == n3) gz = 0;
+        const int at = gx + gy * sy + gz * sz;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const int at = (oz * 3 + c) * NPL + (ly + oy) * NX + lx + ox;
-          uh[c][o] = nodes[at];
-          ul[c][o] = LO ? nodes[6 * NPL + at] : T(0);
+          uh[c][o] = __ldg(P.u[c] + at);
+          ul[c][o] = LO ? __ldg(P.ulo[c] + at) : T(0);
         }
       }
-      const int ph = P.phase[vxw + vyw * P.vy + (long long)vz * P.vz];
+      const int v = vx + vy_ * vy + vz * vz_;
+      const int ph = P.phase[v];
       const int law = __ldg(P.law_id + ph);
       const T* lc = P.law_c + (size_t)ph * LAWC;
-      const bool own = owned && lx >= 1 && ly >= 1;
+      T spv = T(0);
 #pragma unroll
       for (int r = 0; r < NPP; ++r) {
         T Gf[9], Gt[9], Pp[9];
@@ -186,171 +231,258 @@ __global__ void __launch_bounds__(TX * TY) k_residual(ResParams<T> P) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
         law_eval<T>(law, lc, Gt, Pp);
-        T* dst = V + (r * NE) * VPL + e;
-        double pn = 0.0;
+        T* base = P.vs + (size_t)(r * NCT) * nvox + v;
+        if (SYM) {
+          const T s6[6] = {Pp[0], Pp[4], Pp[8], Pp[5], Pp[2], Pp[1]};
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-          dst[i * VPL] = Pp[i];
-          pn += (double)Pp[i] * (double)Pp[i];
+          for (int c = 0; c < 6; ++c) base[(size_t)c * nvox] = s6[c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) base[(size_t)c * nvox] = Pp[c];
         }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) spv += Pp[c] * Pp[c];
         if (WITH_P) {
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-              T t = P.two_mu0 * Gf[i * 3 + q] - Pp[i * 3 + q];
-              if (i == q) t += P.lam0 * Gf[i * 3 + i];
-              dst[(9 + i * 3 + q) * VPL] = t;
+              T tq = P.two_mu0 * Gf[i * 3 + q] - Pp[i * 3 + q];
+              if (i == q) tq += P.lam0 * Gf[i * 3 + i];
+              base[(size_t)(NC + i * 3 + q) * nvox] = tq;
             }
         }
-        if (own) SP += pn / NPP;
+      }
+      sp += spv;
+    }
+    if (++run == 16) {  // fold the run into FP64
+      SP += (double)sp;
+      sp = T(0);
+      run = 0;
+    }
+  }
+  SP += (double)sp;
+  const double tot = block_sum(SP, red);
+  if (threadIdx.x == 0) P.partial[2 * blockIdx.x + 1] = tot / NPP;
+}
+
+// General divergence at node (mx, my, mz), with the ghost rules on face nodes.
+template <typename T, int TETRA, bool WITH_P, bool SYM>
+__device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, int my, int mz, T Dq[3], T pq[3]) {
+  constexpr int NC = SYM ? 6 : 9;
+  constexpr int NCT = WITH_P ? NC + 9 : NC;
+  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+  const int px = P.periodic[0], py = P.periodic[1], pz = P.periodic[2];
+  const long long nvox = (long long)n1 * n2 * n3;
+  auto corner = [&](int o, int i, int q, T* f) -> long long {
+    const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+    int vx = mx + ox - 1, vy = my + oy - 1, vz = mz + oz - 1, cross = 0, sgn = 1;
+    if (vx < 0 || vx >= n1) {
+      if (px) vx = (vx + n1) % n1;
+      else {
+        sgn *= P.sgn[q][0][vx < 0 ? 0 : 1] * (i == 0 ? -1 : 1);
+        vx = vx < 0 ? 0 : n1 - 1;
+        ++cross;
       }
     }
+    if (vy < 0 || vy >= n2) {
+      if (py) vy = (vy + n2) % n2;
+      else {
+        sgn *= P.sgn[q][1][vy < 0 ? 0 : 1] * (i == 1 ? -1 : 1);
+        vy = vy < 0 ? 0 : n2 - 1;
+        ++cross;
+      }
+    }
+    if (vz < 0 || vz >= n3) {
+      if (pz) vz = (vz + n3) % n3;
+      else {
+        sgn *= P.sgn[q][2][vz < 0 ? 0 : 1] * (i == 2 ? -1 : 1);
+        vz = vz < 0 ? 0 : n3 - 1;
+        ++cross;
+      }
+    }
+    int r = 0;
+    if (TETRA) {
+      r = ((ox + oy + oz) & 1) ? 0 : 1;  // odd corner -> T1 point (div_T2), even -> T2 (div_T1)
+      if (cross & 1) r ^= 1;
+    }
+    *f = T(sgn);
+    return (long long)(r * NCT) * nvox + vx + vy * P.vy + (long long)vz * P.vz;
   };
+  for (int i = 0; i < 3; ++i) {
+    for (int q = 0; q < 3; ++q) {
+      const int c = SYM ? sym_index(i, q) : i * 3 + q;
+      T s = T(0), st = T(0);
+      for (int o = 0; o < 8; ++o) {
+        if ((o >> i) & 1) continue;
+        const int o1 = o | (1 << i);
+        T f0, f1;
+        const long long a0 = corner(o, i, q, &f0);
+        const long long a1 = corner(o1, i, q, &f1);
+        s += f1 * P.vs[a1 + c * nvox] - f0 * P.vs[a0 + c * nvox];
+        if (WITH_P) st += f1 * P.vs[a1 + (NC + i * 3 + q) * nvox] - f0 * P.vs[a0 + (NC + i * 3 + q) * nvox];
+      }
+      Dq[q] += P.wdiv[i] * s;
+      if (WITH_P) pq[q] += P.wdiv[i] * st;
+    }
+  }
+}
 
-  int prev = 0, cur = 1;
-  if (zc0 >= 1) compute_plane(zc0 - 1, prev, false);
-  else if (pz) compute_plane(n3 - 1, prev, false);
+template <typename T, bool WITH_P>
+__device__ __forceinline__ T store_node(const ResParams<T>& P, int mx, int my, int mz, const T Dq[3], const T pq[3]) {
+  const int off = mx + my * (int)P.sy + mz * (int)P.sz;
+  T sdn = T(0);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const bool dof = mx >= P.lo[q][0] && mx < P.hi[q][0] && my >= P.lo[q][1] && my < P.hi[q][1] &&
+                     mz >= P.lo[q][2] && mz < P.hi[q][2];
+    P.D[q][off] = dof ? Dq[q] : T(0);
+    if (WITH_P) P.p[q][off] = dof ? pq[q] : T(0);
+    if (dof) sdn += Dq[q] * Dq[q];
+  }
+  return sdn;
+}
 
-  for (int mz = zc0; mz < zc1; ++mz) {
-    if (mz < n3) compute_plane(mz, cur, true);
-    __syncthreads();
-    const int lx = tid % TX, ly = tid / TX;
-    const int mx = x0 + lx, my = y0 + ly;
-    if (mx < N1 && my < N2) {
-      // voxel read for corner offset o: pointer to its point values and the
-      // ghost signs (ghost factor per (i, q) = sq[q] * (crossed axis i ? -1 : 1))
-      const T* Vp[8];
-      int crossm[8];
-      T sqv[8][3];
+// Interior nodes: all 8 neighbouring voxels exist (or wrap); plain differences.
+template <typename T, int TETRA, bool WITH_P, bool SYM>
+__global__ void __launch_bounds__(RTX * RTY) k_div(ResParams<T> P, TileIdx ti, FaceIdx fi) {
+  constexpr int NC = SYM ? 6 : 9;
+  constexpr int NCT = WITH_P ? NC + 9 : NC;
+  __shared__ double red[32];
+  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+  const long long nvox = (long long)n1 * n2 * n3;
+  const int vy = (int)P.vy, vz_ = (int)P.vz;
+  T sd = T(0);
+  double SD = 0.0;
+  int run = 0;
+  for (int t = blockIdx.x; t < ti.ntile; t += gridDim.x) {
+    int x0, y0, mz;
+    ti.at(t, &x0, &y0, &mz);
+    const int mx = x0 + (threadIdx.x % RTX), my = y0 + (threadIdx.x / RTX);
+    if (mx < ti.ox + ti.ex && my < ti.oy + ti.ey) {
+      T Dq[3] = {T(0), T(0), T(0)}, pq[3] = {T(0), T(0), T(0)};
+      int vidx[8];
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        const int vx = mx + ox - 1, vy = my + oy - 1, vz = mz + oz - 1;
-        int tlx = lx + ox, tly = ly + oy;
-        int slot = oz ? cur : prev;
-        int cross = 0, sx = 0, sy = 0, sz = 0;
-        if (!px) {
-          if (vx < 0) { tlx += 1; cross |= 1; sx = 0; }
-          else if (vx >= n1) { tlx -= 1; cross |= 1; sx = 1; }
-        }
-        if (!py) {
-          if (vy < 0) { tly += 1; cross |= 2; sy = 0; }
-          else if (vy >= n2) { tly -= 1; cross |= 2; sy = 1; }
-        }
-        if (!pz) {
-          if (vz < 0) { slot = cur; cross |= 4; sz = 0; }
-          else if (vz >= n3) { slot = prev; cross |= 4; sz = 1; }
-        }
-        int r = 0;
-        if (TETRA) {
-          r = ((ox + oy + oz) & 1) ? 0 : 1;  // odd corner -> T1 point (div_T2), even -> T2 (div_T1)
-          if (__popc(cross) & 1) r ^= 1;
-        }
-        Vp[o] = vox + slot * (NPP * NE * VPL) + (r * NE) * VPL + tly * VX + tlx;
-        crossm[o] = cross;
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          int s = 1;
-          if (cross & 1) s *= P.sgn[q][0][sx];
-          if (cross & 2) s *= P.sgn[q][1][sy];
-          if (cross & 4) s *= P.sgn[q][2][sz];
-          sqv[o][q] = T(s);
-        }
+        int vx = mx + (o & 1) - 1, vyy = my + ((o >> 1) & 1) - 1, vz = mz + (o >> 2) - 1;
+        if (vx < 0) vx += n1;
+        if (vyy < 0) vyy += n2;
+        if (vz < 0) vz += n3;
+        vidx[o] = vx + vyy * vy + vz * vz_;
       }
-      T Dq[3] = {T(0), T(0), T(0)}, pq[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
+          const int c = SYM ? sym_index(i, q) : i * 3 + q;
+          const T* b0 = P.vs + (size_t)c * nvox;                  // T1 point
+          const T* b1 = P.vs + (size_t)(NCT + c) * nvox;          // T2 point
+          const T* t0 = P.vs + (size_t)(NC + i * 3 + q) * nvox;   // tau, T1
+          const T* t1 = P.vs + (size_t)(NCT + NC + i * 3 + q) * nvox;
           T s = T(0), st = T(0);
 #pragma unroll
           for (int o = 0; o < 8; ++o) {
             if ((o >> i) & 1) continue;
             const int o1 = o | (1 << i);
-            const T f0 = ((crossm[o] >> i) & 1) ? -sqv[o][q] : sqv[o][q];
-            const T f1 = ((crossm[o1] >> i) & 1) ? -sqv[o1][q] : sqv[o1][q];
-            s += f1 * Vp[o1][(i * 3 + q) * VPL] - f0 * Vp[o][(i * 3 + q) * VPL];
-            if (WITH_P) st += f1 * Vp[o1][(9 + i * 3 + q) * VPL] - f0 * Vp[o][(9 + i * 3 + q) * VPL];
+            // odd-parity corner -> T1 point, even -> T2 point (HEX1: the single point)
+            const bool odd0 = (((o & 1) + ((o >> 1) & 1) + (o >> 2)) & 1) != 0;
+            const bool odd1 = !odd0;
+            const T* p0 = (!TETRA || odd0) ? b0 : b1;
+            const T* p1 = (!TETRA || odd1) ? b0 : b1;
+            s += __ldg(p1 + vidx[o1]) - __ldg(p0 + vidx[o]);
+            if (WITH_P) {
+              const T* q0 = (!TETRA || odd0) ? t0 : t1;
+              const T* q1 = (!TETRA || odd1) ? t0 : t1;
+              st += __ldg(q1 + vidx[o1]) - __ldg(q0 + vidx[o]);
+            }
           }
           Dq[q] += P.wdiv[i] * s;
           if (WITH_P) pq[q] += P.wdiv[i] * st;
         }
       }
-      const long long off = mx + my * P.sy + (long long)mz * P.sz;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const bool dof = mx >= P.lo[q][0] && mx < P.hi[q][0] && my >= P.lo[q][1] && my < P.hi[q][1] &&
-                         mz >= P.lo[q][2] && mz < P.hi[q][2];
-        P.D[q][off] = dof ? Dq[q] : T(0);
-        if (WITH_P) P.p[q][off] = dof ? pq[q] : T(0);
-        if (dof) SD += (double)Dq[q] * (double)Dq[q];
-      }
+      sd += store_node<T, WITH_P>(P, mx, my, mz, Dq, pq);
     }
-    __syncthreads();
-    const int t = prev;
-    prev = cur;
-    cur = t;
+    if (++run == 16) {
+      SD += (double)sd;
+      sd = T(0);
+      run = 0;
+    }
   }
-
-  const double sd = block_sum(SD, red);
-  const double sp = block_sum(SP, red);
-  if (tid == 0) {
-    const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-    P.partial[2 * b] = sd;
-    P.partial[2 * b + 1] = sp;
+  // face nodes, each once, with the ghost rules
+  int nface[3] = {n1, n2, n3};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < fi.count; t += gridDim.x * blockDim.x) {
+    int m[3];
+    if (!fi.at(t, nface, m)) continue;
+    T Dq[3] = {T(0), T(0), T(0)}, pq[3] = {T(0), T(0), T(0)};
+    node_div_general<T, TETRA, WITH_P, SYM>(P, m[0], m[1], m[2], Dq, pq);
+    SD += (double)store_node<T, WITH_P>(P, m[0], m[1], m[2], Dq, pq);
   }
+  SD += (double)sd;
+  const double tot = block_sum(SD, red);
+  if (threadIdx.x == 0) P.partial[2 * blockIdx.x] = tot;
 }
 
-template <typename T>
-struct ResTile;
-template <>
-struct ResTile<float> { static constexpr int TX = 32, TY = 8; };
-template <>
-struct ResTile<double> { static constexpr int TX = 32, TY = 4; };
+static TileIdx voxel_tiles(const int n[3]) { return make_tiles(0, 0, 0, n[0], n[1], n[2]); }
 
 template <typename T>
-static dim3 res_grid(const ResParams<T>& P, int* zchunk) {
-  constexpr int TX = ResTile<T>::TX, TY = ResTile<T>::TY;
-  const int bx = (P.N[0] + TX - 1) / TX, by = (P.N[1] + TY - 1) / TY;
-  int chunks = (4 * 152 + bx * by - 1) / (bx * by);
-  chunks = max(1, min(chunks, (P.N[2] + 7) / 8));
-  const int zc = (P.N[2] + chunks - 1) / chunks;
-  *zchunk = zc;
-  return dim3(bx, by, (P.N[2] + zc - 1) / zc);
+static void interior_and_faces(const ResParams<T>& P, TileIdx* ti, FaceIdx* fi) {
+  int o[3], e[3];
+  for (int a = 0; a < 3; ++a) {
+    o[a] = P.periodic[a] ? 0 : 1;              // interior node range [1, n) on a non-periodic axis
+    e[a] = P.periodic[a] ? P.N[a] : P.n[a] - 1;
+  }
+  *ti = make_tiles(o[0], o[1], o[2], e[0], e[1], e[2]);
+  fi->count = 0;
+  for (int a = 0; a < 3; ++a) {
+    fi->seg[a] = 0;
+    for (int b = 0; b < 3; ++b) {
+      fi->org[a][b] = 0;
+      fi->ext[a][b] = 1;
+    }
+    if (P.periodic[a]) continue;
+    int cnt = 2;
+    for (int b = 0; b < 3; ++b) {
+      if (b == a) continue;
+      if (b < a && !P.periodic[b]) {
+        fi->org[a][b] = 1;
+        fi->ext[a][b] = P.n[b] - 1;
+      } else {
+        fi->org[a][b] = 0;
+        fi->ext[a][b] = P.N[b];
+      }
+      cnt *= fi->ext[a][b];
+    }
+    fi->seg[a] = cnt;
+    fi->count += cnt;
+  }
 }
 
 template <typename T>
 int residual_blocks(const ResParams<T>& P, int tetra) {
   (void)tetra;
-  int zc;
-  dim3 g = res_grid<T>(P, &zc);
-  return (int)(g.x * g.y * g.z);
+  return RBLOCKS;
 }
 
-template <typename T, int TETRA, bool WITH_P, bool LO>
-static cudaError_t launch_res_t(ResParams<T> P, cudaStream_t s, int* blocks_out) {
-  constexpr int TX = ResTile<T>::TX, TY = ResTile<T>::TY;
-  constexpr int NPP = TETRA ? 2 : 1;
-  constexpr int NE = WITH_P ? 18 : 9;
-  int zc;
-  dim3 grid = res_grid<T>(P, &zc);
-  P.zchunk = zc;
-  const size_t smem =
-      sizeof(T) * ((LO ? 2 : 1) * 2 * 3 * (TX + 2) * (TY + 2) + 2 * NPP * NE * (TX + 1) * (TY + 1));
-  auto kern = k_residual<T, TETRA, TX, TY, WITH_P, LO>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <typename T, int TETRA, bool WITH_P, bool SYM>
+static cudaError_t launch_res_t(const ResParams<T>& P, bool lo, cudaStream_t s, int* blocks_out) {
+  const TileIdx tv = voxel_tiles(P.n);
+  TileIdx tn;
+  FaceIdx fi;
+  interior_and_faces<T>(P, &tn, &fi);
+  if (lo) k_stress<T, TETRA, WITH_P, true, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+  else k_stress<T, TETRA, WITH_P, false, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  kern<<<grid, TX * TY, smem, s>>>(P);
-  if (blocks_out) *blocks_out = (int)(grid.x * grid.y * grid.z);
+  k_div<T, TETRA, WITH_P, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tn, fi);
+  if (blocks_out) *blocks_out = RBLOCKS;
   return cudaGetLastError();
 }
 
 template <typename T, int TETRA>
 static cudaError_t launch_res_s(const ResParams<T>& P, bool with_p, cudaStream_t s, int* b) {
   const bool lo = P.ulo[0] != nullptr;
-  if (with_p) return lo ? launch_res_t<T, TETRA, true, true>(P, s, b) : launch_res_t<T, TETRA, true, false>(P, s, b);
-  return lo ? launch_res_t<T, TETRA, false, true>(P, s, b) : launch_res_t<T, TETRA, false, false>(P, s, b);
+  if (with_p) return P.sym ? launch_res_t<T, TETRA, true, true>(P, lo, s, b) : launch_res_t<T, TETRA, true, false>(P, lo, s, b);
+  return P.sym ? launch_res_t<T, TETRA, false, true>(P, lo, s, b) : launch_res_t<T, TETRA, false, false>(P, lo, s, b);
 }
 
 template <typename T>
