@@ -58,7 +58,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--grains", type=int, default=500)
-    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp32_tc", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed beside (0 = skip)")
@@ -360,8 +360,8 @@ def gpu_arm(args):
     iters = last["iterations"]
 
     # ---- roofline of the dominant kernel (algorithmic bytes / CUDA-event time) ----
-    esz = 4 if args.precision == "fp32" else 8
-    lo = 2 if args.precision == "fp32" else 1  # u^f carried as hi + lo in FP32
+    esz = 8 if args.precision == "fp64" else 4
+    lo = 1 if args.precision == "fp64" else 2  # u^f carried as hi + lo in FP32
     nodes, per_axis = element_counts(wl)
     it_total = iters * args.steps
     acc_total = last["n_accelerated"] * args.steps
@@ -390,7 +390,7 @@ def gpu_arm(args):
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * sec_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(args.n, args.grains), "precision": args.precision,
                        "iterations_per_step": iters, "anderson_steps_per_step": last["n_accelerated"],
@@ -399,7 +399,7 @@ def gpu_arm(args):
             "roofline": roofline, "gpu_launches": launches, "clocks": clk}
 
     # ---- FP64 path beside it (same workload, device-resident) ----
-    if args.fp64_steps > 0 and args.precision == "fp32":
+    if args.fp64_steps > 0 and args.precision != "fp64":
         F.fftm_problem_destroy(prob)
         prob = make("fp64")
         step()  # warm-up

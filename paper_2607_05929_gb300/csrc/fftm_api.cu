@@ -166,6 +166,65 @@ void cubic_mandel(double C11, double C12, double C44, const double R[3][3], doub
     }
 }
 
+// Dense forward matrix of a Table 1 transform over its node range (rows k,
+// columns j - lo): periodic axes in halfcomplex order (real part of frequency k
+// in row k, imaginary part in row n - k).
+void dense_forward(int kind, int n, std::vector<double>* M, int* Lout) {
+  int lo, L;
+  kind_range(kind, n, &lo, &L);
+  *Lout = L;
+  M->assign((size_t)L * L, 0.0);
+  for (int k = 0; k < L; ++k)
+    for (int c = 0; c < L; ++c) {
+      const int j = lo + c;
+      double v = 0.0;
+      switch (kind) {
+        case K_DFT:
+          if (2 * k <= n) v = std::cos(2.0 * kPi * j * k / n);
+          else v = -std::sin(2.0 * kPi * j * (n - k) / n);
+          break;
+        case K_DCT1: v = (2.0 - (j == 0) - (j == n)) * std::cos(kPi * j * k / n); break;
+        case K_DCT3: v = (2.0 - (j == 0)) * std::cos(kPi * j * (k + 0.5) / n); break;
+        case K_DST1: v = 2.0 * std::sin(kPi * j * (k + 1.0) / n); break;
+        default: v = (2.0 - (j == n)) * std::sin(kPi * j * (k + 0.5) / n); break;
+      }
+      (*M)[(size_t)k * L + c] = v;
+    }
+}
+
+// Its exact inverse (rows j - lo, columns k): DCT-I/(2n), DCT-II/(2n),
+// DST-I/(2n), DST-II/(2n), and the halfcomplex-to-real DFT divided by n.
+void dense_inverse(int kind, int n, std::vector<double>* M) {
+  int lo, L;
+  kind_range(kind, n, &lo, &L);
+  M->assign((size_t)L * L, 0.0);
+  for (int r = 0; r < L; ++r)
+    for (int k = 0; k < L; ++k) {
+      const int j = lo + r;
+      double v = 0.0;
+      switch (kind) {
+        case K_DFT:
+          if (2 * k <= n) v = ((k == 0 || 2 * k == n) ? 1.0 : 2.0) * std::cos(2.0 * kPi * j * k / n) / n;
+          else v = -2.0 * std::sin(2.0 * kPi * j * (n - k) / n) / n;
+          break;
+        case K_DCT1: v = (2.0 - (k == 0) - (k == n)) * std::cos(kPi * j * k / n) / (2.0 * n); break;
+        case K_DCT3: v = std::cos(kPi * j * (k + 0.5) / n) / n; break;
+        case K_DST1: v = std::sin(kPi * j * (k + 1.0) / n) / n; break;
+        default: v = std::sin(kPi * j * (k + 0.5) / n) / n; break;
+      }
+      (*M)[(size_t)r * L + k] = v;
+    }
+}
+
+// Round to BF16 (nearest, ties to even) from FP64 through FP32.
+uint16_t to_bf16(double d) {
+  const float f = (float)d;
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
+}
+
 }  // namespace
 
 struct fftm_problem {
@@ -201,6 +260,11 @@ struct fftm_problem {
   void* vs = nullptr;       // voxel-point stresses of the solver (NPP x NC x nvox)
   void* vs_test = nullptr;  // with tau, for FFTM_OP_RESIDUAL (allocated on first use)
   int sym = 1;              // every law gives a symmetric P
+  // tensor-core transforms (FFTM_FP32_TC): BF16 matrices, Kp x Kp per component and axis
+  int tc = 0;
+  void* tcmat = nullptr;
+  size_t off_tcf[3][3], off_tci[3][3];
+  int tcKp[3][3];
   // device table offsets (bytes) inside `tables`
   size_t off_perm[3][3], off_tw[3][3], off_qw[3][3], off_S2[3][3], off_C2[3][3];
   int maxM[3], maxL[3];
@@ -357,6 +421,50 @@ int run_pass(fftm_problem* p, int axis, int inverse, int fused, int in_set, int 
   return launch_pp<T>(p, P, axis);
 }
 
+TcPassParams tc_params(fftm_problem* p, int axis, int inverse, int fused, int in_set, int out_set) {
+  TcPassParams P;
+  std::memset(&P, 0, sizeof(P));
+  const char* base = reinterpret_cast<const char*>(p->tcmat);
+  for (int q = 0; q < 3; ++q) {
+    P.in[q] = field_ptr<float>(p, in_set, q);
+    P.out[q] = field_ptr<float>(p, out_set, q);
+    P.lo[q] = p->plans[q][axis].lo;
+    P.L[q] = p->plans[q][axis].L;
+    P.Kp[q] = p->tcKp[q][axis];
+    P.A[q] = reinterpret_cast<const uint16_t*>(base + (inverse ? p->off_tci[q][axis] : p->off_tcf[q][axis]));
+    P.A2[q] = reinterpret_cast<const uint16_t*>(base + p->off_tci[q][axis]);
+    P.scale[q] = 1.f;
+    for (int a = 0; a < 3; ++a) {
+      P.S2[q][a] = tptr<float>(p, p->off_S2[q][a]);
+      P.C2[q][a] = tptr<float>(p, p->off_C2[q][a]);
+      P.flo[q][a] = p->plans[q][a].lo;
+      P.fL[q][a] = p->plans[q][a].L;
+    }
+    P.gscale[q] = 1.f;  // the inverse matrices carry the normalisation
+  }
+  P.axis = axis;
+  for (int a = 0; a < 3; ++a) {
+    P.N[a] = p->N[a];
+    P.hf[a] = (float)(4.0 / (p->h[a] * p->h[a]));
+  }
+  P.stride[0] = 1;
+  P.stride[1] = p->sy;
+  P.stride[2] = p->sz;
+  P.fused = fused;
+  const double lam0 = p->desc.green == FFTM_GREEN_MU0 ? 0.0 : p->desc.lambda0;
+  P.two_mu0 = (float)(2.0 * p->desc.mu0);
+  P.lam0 = (float)lam0;
+  P.tetra = p->tetra;
+  return P;
+}
+
+int launch_tc(fftm_problem* p, const TcPassParams& P) {
+  ProfScope ps(p, P.axis == 0 ? FFTM_KCAT_PASS_X : (P.axis == 1 ? FFTM_KCAT_PASS_Y : FFTM_KCAT_PASS_Z));
+  CU(launch_pass_tc(P, p->ctx->stream));
+  p->launches++;
+  return FFTM_OK;
+}
+
 template <typename T>
 ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   ResParams<T> R;
@@ -434,6 +542,25 @@ template <typename T>
 int green_apply(fftm_problem* p, int in_set, int base_set, int base_lo_set, int out_set, int out_lo_set,
                 bool negate) {
   int rc;
+  if (p->tc) {
+    if ((rc = launch_tc(p, tc_params(p, 0, 0, 0, in_set, SET_WORK)))) return rc;
+    if ((rc = launch_tc(p, tc_params(p, 1, 0, 0, SET_WORK, SET_WORK)))) return rc;
+    {
+      TcPassParams P = tc_params(p, 2, 0, 1, SET_WORK, SET_WORK);
+      if (negate)
+        for (int q = 0; q < 3; ++q) P.gscale[q] = -1.f;
+      if ((rc = launch_tc(p, P))) return rc;
+    }
+    if ((rc = launch_tc(p, tc_params(p, 1, 1, 0, SET_WORK, SET_WORK)))) return rc;
+    TcPassParams P = tc_params(p, 0, 1, 0, SET_WORK, out_set);
+    if (base_set >= 0)
+      for (int q = 0; q < 3; ++q) {
+        P.base[q] = field_ptr<float>(p, base_set, q);
+        P.base_lo[q] = base_lo_set >= 0 ? field_ptr<float>(p, base_lo_set, q) : nullptr;
+        P.out_lo[q] = out_lo_set >= 0 ? field_ptr<float>(p, out_lo_set, q) : nullptr;
+      }
+    return launch_tc(p, P);
+  }
   if ((rc = run_pass<T>(p, 0, 0, 0, in_set, SET_WORK, false))) return rc;
   if ((rc = run_pass<T>(p, 1, 0, 0, SET_WORK, SET_WORK, false))) return rc;
   {
@@ -595,7 +722,11 @@ int validate(const fftm_problem_desc* d) {
   if (d->scheme != FFTM_HEX1 && d->scheme != FFTM_TETRA2) return set_err(FFTM_E_INVALID, "bad scheme");
   if (d->green != FFTM_GREEN_B0 && d->green != FFTM_GREEN_MU0) return set_err(FFTM_E_INVALID, "bad green");
   if (!(d->mu0 > 0.0) || !(d->lambda0 >= 0.0)) return set_err(FFTM_E_INVALID, "need mu0 > 0, lambda0 >= 0");
-  if (d->precision != FFTM_FP64 && d->precision != FFTM_FP32) return set_err(FFTM_E_INVALID, "bad precision");
+  if (d->precision != FFTM_FP64 && d->precision != FFTM_FP32 && d->precision != FFTM_FP32_TC)
+    return set_err(FFTM_E_INVALID, "bad precision");
+  if (d->precision == FFTM_FP32_TC)
+    for (int a = 0; a < 3; ++a)
+      if (d->n[a] + 1 > 384) return set_err(FFTM_E_UNSUPPORTED, "tensor-core transforms need n <= 383 per axis");
   if (!(d->tol > 0.0) || d->max_iter < 1) return set_err(FFTM_E_INVALID, "need tol > 0 and max_iter >= 1");
   if (d->anderson_depth != 0 && (d->anderson_depth < 2 || d->anderson_depth > 4))
     return set_err(FFTM_E_INVALID, "anderson_depth must be 0 or 2..4");
@@ -689,6 +820,7 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->scratch);
   cudaFree(p->vs);
   cudaFree(p->vs_test);
+  cudaFree(p->tcmat);
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -797,6 +929,30 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
     }
   CU(cudaMalloc(&p->tables, tab.size()));
   CU(cudaMemcpy(p->tables, tab.data(), tab.size(), cudaMemcpyHostToDevice));
+  if (desc->precision == FFTM_FP32_TC) {
+    p->tc = 1;
+    std::vector<uint16_t> mats;
+    auto put_mat = [&](const std::vector<double>& M, int L, int Kp) {
+      size_t off = (mats.size() + 63) & ~(size_t)63;  // 128-byte aligned
+      mats.resize(off + (size_t)Kp * Kp, 0);
+      for (int r = 0; r < L; ++r)
+        for (int c = 0; c < L; ++c) mats[off + (size_t)r * Kp + c] = to_bf16(M[(size_t)r * L + c]);
+      return off * sizeof(uint16_t);
+    };
+    for (int q = 0; q < 3; ++q)
+      for (int a = 0; a < 3; ++a) {
+        std::vector<double> F, I;
+        int L;
+        dense_forward(p->kind[q][a], p->n[a], &F, &L);
+        dense_inverse(p->kind[q][a], p->n[a], &I);
+        const int Kp = (L + 15) / 16 * 16;
+        p->tcKp[q][a] = Kp;
+        p->off_tcf[q][a] = put_mat(F, L, Kp);
+        p->off_tci[q][a] = put_mat(I, L, Kp);
+      }
+    CU(cudaMalloc(&p->tcmat, mats.size() * sizeof(uint16_t)));
+    CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+  }
   // ---- law tables ----
   std::vector<int> lid(desc->n_phases);
   std::vector<double> lc((size_t)desc->n_phases * LAWC, 0.0);
@@ -989,10 +1145,14 @@ static int apply_t(fftm_problem* p, int op, double* norms) {
       return FFTM_OK;
     }
     case FFTM_OP_DT_FORWARD:
-      for (int a = 0; a < 3 && !rc; ++a) rc = run_pass<T>(p, a, 0, 0, SET_WORK, SET_WORK, false);
+      for (int a = 0; a < 3 && !rc; ++a)
+        rc = p->tc ? launch_tc(p, tc_params(p, a, 0, 0, SET_WORK, SET_WORK))
+                   : run_pass<T>(p, a, 0, 0, SET_WORK, SET_WORK, false);
       break;
     case FFTM_OP_DT_INVERSE:
-      for (int a = 2; a >= 0 && !rc; --a) rc = run_pass<T>(p, a, 1, 0, SET_WORK, SET_WORK, true);
+      for (int a = 2; a >= 0 && !rc; --a)
+        rc = p->tc ? launch_tc(p, tc_params(p, a, 1, 0, SET_WORK, SET_WORK))
+                   : run_pass<T>(p, a, 1, 0, SET_WORK, SET_WORK, true);
       break;
     case FFTM_OP_GREEN: {
       PassParams<T> P = pass_params<T>(p, 2, 0, 0, SET_WORK, SET_WORK);

@@ -89,6 +89,33 @@ struct ResParams {
 
 constexpr int LAWC = 24;
 
+// One axis pass as a dense contraction on the tensor cores (FP32 data, BF16
+// matrices).  A: the Kp x Kp (zero-padded) transform matrix, row-major BF16
+// bits; A2: the inverse z matrix of the fused z pass.
+struct TcPassParams {
+  const float* in[3];
+  float* out[3];
+  const float* base[3];
+  const float* base_lo[3];
+  float* out_lo[3];
+  int axis;
+  int N[3];
+  long long stride[3];
+  int lo[3], L[3], Kp[3];
+  const uint16_t* A[3];
+  const uint16_t* A2[3];
+  float scale[3];
+  int fused;
+  const float* S2[3][3];
+  const float* C2[3][3];
+  int flo[3][3], fL[3][3];
+  float hf[3];
+  float two_mu0, lam0;
+  int tetra;
+  float gscale[3];
+};
+cudaError_t launch_pass_tc(const TcPassParams& P, cudaStream_t s);
+
 // Green factor on a spectral field (standalone step).
 template <typename T>
 struct GreenParams {

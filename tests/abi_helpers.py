@@ -31,7 +31,7 @@ class GpuProblem:
 
     def __init__(self, wl, precision="fp64", ctx=None, tol=None, max_iter=None):
         self.wl = wl
-        self.dtype = np.float64 if precision == "fp64" else np.float32
+        self.dtype = np.float64 if precision == "fp64" else np.float32  # fp32 and fp32_tc
         self.ctx = ctx if ctx is not None else F.fftm_ctx_create(0, None)
         mats = [(m.law, m.params, m.quat) for m in wl.materials]
         desc, self._keep = F.make_desc(

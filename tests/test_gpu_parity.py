@@ -325,3 +325,74 @@ def test_invalid_descriptors_are_rejected():
     with pytest.raises(F.FFTMError):
         F.fftm_set_load(p.p, [[0, 0, 1e-3], [0, 0, 0], [0, 0, 0]])  # depends on the periodic z
     p.close()
+
+
+# ---- tensor-core transforms (FFTM_FP32_TC: BF16 operands, FP32 accumulation) ----
+TC_TOL = 1e-2  # BF16 operands: 8-bit significands
+
+
+@pytest.mark.parametrize("case", range(len(DT_CASES)))
+def test_tc_dt_forward_and_round_trip(case):
+    n, kinds = DT_CASES[case]
+    wl = _wl(n, _bc_for(*kinds, mix=True))
+    g = Grid(wl.n, wl.bc)
+    gp = GpuProblem(wl, "fp32_tc")
+    try:
+        rng = np.random.default_rng(case)
+        x = rng.standard_normal(g.node_shape)
+        for q in range(3):
+            x[q][~g.dof_mask(q)] = 0.0
+        gp.set_node(F.FFTM_FIELD_WORK, x)
+        F.fftm_apply(gp.p, F.FFTM_OP_DT_FORWARD)
+        got = gp.get_node(F.FFTM_FIELD_WORK)
+        for q in range(3):
+            ref = oracle_r2r_forward(x[q], g.kind[q], g.n, g.N)
+            assert rel_l2(got[q], ref) < TC_TOL, (q, g.kind[q])
+        F.fftm_apply(gp.p, F.FFTM_OP_DT_INVERSE)
+        back = gp.get_node(F.FFTM_FIELD_WORK)
+        assert rel_l2(back, x) < TC_TOL
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("case", [0, 1, 2, 4])
+def test_tc_green_update_fused(case):
+    n, bc, scheme = RES_CASES[case]
+    wl = _cubic_wl(n, bc, scheme)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, "fp32_tc")
+    try:
+        rng = np.random.default_rng(case + 20)
+        # a smooth field (what the solver transforms), not white noise
+        u = np.zeros(pr.grid.node_shape)
+        for q in range(3):
+            u[q] = rng.standard_normal() * np.sin(np.linspace(0, np.pi, pr.grid.N[0]))[:, None, None]
+            u[q][~pr.grid.dof_mask(q)] = 0.0
+        p = pr.residual(u, 0 * pr.grad_ustar())[0]  # div(B0 : grad u) - D(u): a realistic p
+        gp.set_node(F.FFTM_FIELD_WORK, p)
+        F.fftm_apply(gp.p, F.FFTM_OP_GREEN_UPDATE)
+        got = gp.get_node(F.FFTM_FIELD_U)
+        assert rel_l2(got, pr.green_update(p)) < 3 * TC_TOL
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("name", ["sphere32_hex", "voronoi_tet", "voronoi_hex_mu0"])
+def test_tc_solve_matches_fp64_oracle(name):
+    """The converged fields depend on the FP32 residual only: BF16 transforms may change the
+    iteration count, not the answer (1e-5 relative L2 at tolerance 1e-6)."""
+    wl = SOLVE_CASES[name]()
+    wl.tol = 1e-6
+    pr = Problem(wl)
+    uf, rep = pr.solve_step()
+    gp = GpuProblem(wl, "fp32_tc")
+    try:
+        st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+        assert r["converged"], r
+        assert r["iterations"] <= 2 * rep.iterations + 5, (r["iterations"], rep.iterations)
+        Pg = gp.get_voxel(F.FFTM_FIELD_STRESS)
+        Gg = gp.get_voxel(F.FFTM_FIELD_GRAD)
+        assert rel_l2(Pg, sym6(pr.last["P"])) < 1e-5
+        assert rel_l2(sym6(_strain(Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:]))), sym6(_strain(pr.last["G"]))) < 1e-5
+    finally:
+        gp.close()
