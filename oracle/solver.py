@@ -61,17 +61,21 @@ class Problem:
         self.uf = np.zeros(self.grid.node_shape)
 
     # --- a0: prescribed displacement and its discrete gradient ------------------------
-    def ustar_full(self, A=None, b=None):
-        """u* on the full (n+1)^3 node grid (affine: u*_q = A[q] . x + b[q])."""
+    def ustar_full(self, A=None, b=None, B=None):
+        """u* on the full (n+1)^3 node grid: u*_q = A[q] . x + b[q] + B[q] x_1 x_2
+        (affine, plus the bilinear term of a bending load)."""
         A = self.wl.A if A is None else A
         b = self.wl.b if b is None else b
+        B = getattr(self.wl, "B", np.zeros(3)) if B is None else B
         n, h = self.grid.n, self.grid.h
         x = [np.arange(n[a] + 1) * h[a] for a in range(3)]
         X = np.meshgrid(*x, indexing="ij")
-        return np.stack([A[q, 0] * X[0] + A[q, 1] * X[1] + A[q, 2] * X[2] + b[q] for q in range(3)])
+        return np.stack([A[q, 0] * X[0] + A[q, 1] * X[1] + A[q, 2] * X[2] + b[q] + B[q] * X[0] * X[1]
+                         for q in range(3)])
 
-    def grad_ustar(self, A=None, b=None):
-        return grad_full(self.ustar_full(A, b), self.grid, self.scheme)
+    def grad_ustar(self, A=None, b=None, B=None):
+        """Discrete gradient of u* at the voxel points (the scheme's stencil on the node values)."""
+        return grad_full(self.ustar_full(A, b, B), self.grid, self.scheme)
 
     # --- pieces of one iteration ------------------------------------------------------
     def residual(self, uf, Gs):
@@ -105,11 +109,11 @@ class Problem:
         return out
 
     # --- Algorithm 1, one load step -----------------------------------------------------
-    def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True):
+    def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True, B=None):
         wl = self.wl
         tol = wl.tol if tol is None else tol
         max_iter = wl.max_iter if max_iter is None else max_iter
-        Gs = self.grad_ustar(A, b)
+        Gs = self.grad_ustar(A, b, B)
         uf = self.uf.copy() if uf0 is None else np.array(uf0, dtype=np.float64)
         hist = []  # (q_j, g_j) couples
         q_prev = None

@@ -34,4 +34,6 @@ from .workloads import (  # noqa: F401
     x_laminate,
     y_laminate,
     iso_lame,
+    bending_load,
+    sphere_composite_bending,
 )

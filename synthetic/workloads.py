@@ -3,8 +3,9 @@
 A workload is plain data.  Boundary conditions are given per axis, face and
 displacement component as 'P' (periodic), 'D' (Dirichlet) or 'N' (Neumann);
 `bc[a][f][q]`, a = axis, f = 0 (face containing the origin) or 1, q = component.
-The prescribed displacement u* is affine, u*_q(x) = sum_a A[q][a] x_a + b[q],
-with x the physical coordinates of the nodes (node j on axis a at j*h_a).
+The prescribed displacement is u*_q(x) = sum_a A[q][a] x_a + b[q] + B[q] x_1 x_2,
+with x the physical coordinates of the nodes (node j on axis a at j*h_a); the
+bilinear term carries the bending loads.
 """
 
 from dataclasses import dataclass, field
@@ -13,7 +14,7 @@ from typing import List, Optional
 import numpy as np
 
 from .draws import shoemake_quaternions
-from .microstructure import centred_sphere, voronoi, laminate
+from .microstructure import centred_sphere, voronoi, laminate, random_spheres
 
 # law identifiers (same integers as the C ABI)
 ISO_ELASTIC = 0
@@ -45,6 +46,7 @@ class Workload:
     h: tuple = (1.0, 1.0, 1.0)
     A: np.ndarray = field(default_factory=lambda: np.zeros((3, 3)))
     b: np.ndarray = field(default_factory=lambda: np.zeros(3))
+    B: np.ndarray = field(default_factory=lambda: np.zeros(3))  # coefficient of x_1 x_2 in u*_q
     anderson_depth: int = 4
     anderson_period: int = 3
     note: Optional[str] = None
@@ -130,3 +132,32 @@ def y_laminate(n=(6, 9, 4), period=3, E=(1.0, 5.0), nu=0.25, scheme="HEX1", eps=
     return Workload(
         name="y_laminate", n=tuple(n), phase=phase, materials=mats, bc=bc,
         scheme=scheme, green="B0", lambda0=max(lam), mu0=max(mu), tol=1e-11, A=A)
+
+
+def bending_load(n, h, theta):
+    """Rotation theta of the x = L_1 face about the mid-line x_2 = L_2 / 2 (x = 0 at rest):
+    u*_1 = (x_1 / L_1) theta (x_2 - L_2 / 2), u*_2 = u*_3 = 0.  Returns (A, b, B)."""
+    L1, L2 = n[0] * h[0], n[1] * h[1]
+    A = np.zeros((3, 3))
+    A[0, 0] = -theta * L2 / (2.0 * L1)
+    B = np.zeros(3)
+    B[0] = theta / L1
+    return A, np.zeros(3), B
+
+
+def sphere_composite_bending(n=128, fraction=0.30, r_min=4.0, r_max=10.0, seed=4, scheme="HEX1",
+                             E=200.0, nu=0.3, sigma_y=0.3, H=2.0, steps=20, theta_max=0.012, tol=1e-6):
+    """Elasto-plastic matrix (J2, linear isotropic hardening; GPa) with elastic spherical
+    particles of the same elastic moduli (overlapping random spheres, 30 % by volume, radii
+    uniform in [4, 10] voxels, seed 4).  x faces Dirichlet (every component), y and z
+    traction-free; bending by `bending_load` with theta_k = k theta_max / steps, k = 1..steps.
+    B0 with the elastic moduli as the reference material.  Returns (workload, loads)."""
+    nn = (n, n, n) if np.isscalar(n) else tuple(n)
+    phase = random_spheres(nn, fraction, r_min, r_max, seed)
+    lam, mu = iso_lame(E, nu)
+    mats = [Material(J2_LINHARD, (lam, mu, sigma_y, H)), Material(ISO_ELASTIC, (lam, mu))]
+    wl = Workload(name=f"sphere_composite_bending_{nn[0]}", n=nn, phase=phase, materials=mats,
+                  bc=axis_bc("D", "N", "N"), scheme=scheme, green="B0", lambda0=lam, mu0=mu, tol=tol)
+    loads = [bending_load(nn, wl.h, k * theta_max / steps) for k in range(1, steps + 1)]
+    wl.A, wl.b, wl.B = loads[0]
+    return wl, loads

@@ -146,3 +146,26 @@ def test_green_null_pattern():
             else:
                 null = all(zero) or all(pi)
             assert (f[k] == 0.0) == null, (scheme, k)
+
+
+def test_gradient_of_the_bilinear_bending_field_closed_form():
+    """u = x_1 x_2 on the node grid.  HEX1 (Eqs. D1HG-D3HG) averages over the voxel's
+    edges: D_1 u = x_2 and D_2 u = x_1 at the centre, D_3 u = 0.  TETRA2 (Eqs.
+    D1T1T2G-D3T1T2G) gives the same D_1 and D_2 and D_3 u = -+ h_1 h_2 / (2 h_3) on T1 / T2
+    (worked out by hand from the four corners of each tetrahedron)."""
+    h = (0.7, 1.3, 0.9)
+    n = (5, 4, 3)
+    g = Grid(n, [[["P"] * 3] * 2] * 3, h)
+    X = np.meshgrid(*[np.arange(n[a] + 1) * h[a] for a in range(3)], indexing="ij")
+    u = np.zeros((3,) + tuple(v + 1 for v in n))
+    u[1] = X[0] * X[1]  # component q = 1 only
+    xc = [(np.arange(n[a]) + 0.5) * h[a] for a in range(3)]
+    Xc = np.meshgrid(*xc, indexing="ij")
+    for scheme in ("HEX1", "TETRA2"):
+        G = grad_full(u, g, scheme)
+        assert np.abs(G[:, :, [0, 2]]).max() == 0.0
+        for r in range(G.shape[0]):
+            assert np.allclose(G[r, 0, 1], Xc[1], rtol=0, atol=1e-13)
+            assert np.allclose(G[r, 1, 1], Xc[0], rtol=0, atol=1e-13)
+            d3 = 0.0 if scheme == "HEX1" else (-1.0 if r == 0 else 1.0) * h[0] * h[1] / (2 * h[2])
+            assert np.allclose(G[r, 2, 1], d3, rtol=0, atol=1e-13)

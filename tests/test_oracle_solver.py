@@ -122,3 +122,66 @@ def test_anderson_recovers_an_exact_cancellation_and_skips_degenerate_history():
     assert anderson.coefficients(same) is None
     assert anderson.accelerate_now(5, 3, 4, 4) and not anderson.accelerate_now(4, 3, 4, 4)
     assert not anderson.accelerate_now(2, 3, 2, 4)
+
+
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_bending_load_matches_direct_sparse_solve(scheme):
+    """T7 with the bilinear u* of a bending load (x faces clamped, y and z traction-free)."""
+    n = (8, 6, 5)
+    ph = syn.random_spheres(n, 0.3, 1.0, 2.0, 11)
+    mats = [Material(0, syn.iso_lame(1.0, 0.3)), Material(0, syn.iso_lame(4.0, 0.25))]
+    A, b, B = syn.bending_load(n, (1.0, 1.0, 1.0), 0.01)
+    wl = Workload("t7b", n, ph, mats, axis_bc("D", "N", "N"), scheme=scheme, lambda0=1.6, mu0=1.0,
+                  tol=1e-12, A=A, b=b, B=B, max_iter=3000)
+    pr = Problem(wl)
+    uf, rep = pr.solve_step()
+    assert rep.converged
+    ud = direct.solve(wl, pr.grad_ustar())
+    e1 = _strain(grad(uf, pr.grid, scheme))
+    e2 = _strain(grad(ud, pr.grid, scheme))
+    assert np.abs(e1 - e2).max() < 1e-9 * np.abs(e2).max()
+    # a bending moment, not a net force: the mean axial stress is far below its extreme values
+    P = pr.last["P"]
+    assert abs(P[:, 0, 0].mean()) < 0.2 * np.abs(P[:, 0, 0]).max()
+
+
+def _uniaxial_j2_history(strains, E, sy, H):
+    """1D plasticity with linear isotropic hardening (the uniaxial-stress form of J2):
+    sigma = E (eps - eps_p), |sigma| <= sy + H p, backward-Euler return at each step."""
+    ep, p, out = 0.0, 0.0, []
+    for eps in strains:
+        trial = E * (eps - ep)
+        f = abs(trial) - (sy + H * p)
+        if f > 0.0:
+            dp = f / (E + H)
+            ep += dp * np.sign(trial)
+            p += dp
+        out.append((E * (eps - ep), p))
+    return out
+
+
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_j2_bar_loading_and_unloading_follow_the_uniaxial_closed_form(scheme):
+    """A homogeneous J2 bar, normal-only Dirichlet on x and traction-free elsewhere, is in
+    uniaxial stress at every step; loading past yield and unloading checks the committed
+    state (eps^p, p) carried from step to step (Algorithm 1, step commit)."""
+    E, nu, sy, H = 200.0, 0.3, 0.3, 2.0
+    lam, mu = syn.iso_lame(E, nu)
+    n = (5, 4, 3)
+    bc = axis_bc("D", "N", "N")
+    bc[0] = [["D", "N", "N"], ["D", "N", "N"]]
+    wl = Workload("j2bar", n, np.zeros(n, np.uint16), [Material(2, (lam, mu, sy, H))], bc,
+                  scheme=scheme, lambda0=lam, mu0=mu, tol=1e-11, max_iter=3000)
+    pr = Problem(wl)
+    strains = [1e-3, 2e-3, 3e-3, 2.5e-3, 1e-3, 3.5e-3]
+    expect = _uniaxial_j2_history(strains, E, sy, H)
+    for eps, (s11, p) in zip(strains, expect):
+        A = np.zeros((3, 3))
+        A[0, 0] = eps
+        _, rep = pr.solve_step(A=A)
+        assert rep.converged, rep.err[-3:]
+        P = pr.last["P"]
+        assert np.abs(P[:, 0, 0] - s11).max() < 1e-8 * abs(s11), (eps, P[:, 0, 0].mean(), s11)
+        assert np.abs(P[:, 1, 1]).max() < 1e-8 * abs(s11)
+        assert np.abs(pr.state["p"] - p).max() < 1e-8 * max(p, 1e-3)
+    assert expect[2][1] > 0 and expect[3][1] == expect[2][1]  # yielded, then unloaded elastically
