@@ -64,7 +64,11 @@ enum fftm_precision { FFTM_FP64 = 0, FFTM_FP32 = 1, FFTM_FP32_TC = 2 };
 enum fftm_law {
   FFTM_LAW_ISO_ELASTIC = 0,   /* params: lambda, mu                          */
   FFTM_LAW_CUBIC_ELASTIC = 1, /* params: C11, C12, C44; quat = orientation     */
-  FFTM_LAW_J2_LINHARD = 2,    /* params: lambda, mu, sigma_y, H  (reserved)    */
+  FFTM_LAW_J2_LINHARD = 2,    /* params: lambda, mu, sigma_y, H: small-strain
+                                 von Mises plasticity, linear isotropic hardening
+                                 (yield stress sigma_y + H p), radial return from
+                                 the committed state (Sec. 3.2); the state is
+                                 committed when a load step converges           */
   FFTM_LAW_B0_LINEAR = 3      /* params: lambda, mu: P = 2 mu G + lambda G.*I  */
 };
 
@@ -98,12 +102,15 @@ typedef struct fftm_problem_desc {
   int anderson_period;       /* accelerate when m % period == period - 1     */
 } fftm_problem_desc;
 
-/* Affine prescribed displacement u*_q(x) = sum_a A[q][a] x_a + b[q],
+/* Prescribed displacement u*_q(x) = sum_a A[q][a] x_a + b[q] + B[q] x_1 x_2,
    x = physical node coordinates (node j of axis a at j*h_a).  u* supplies the
-   Dirichlet values (Sec. 2.2); it must not depend on a periodic coordinate. */
+   Dirichlet values (Sec. 2.2); it must not depend on a periodic coordinate
+   (FFTM_E_INVALID).  The bilinear term carries bending loads (a face rotation
+   that grows along x_1); its discrete gradient is exact at the voxel points. */
 typedef struct fftm_load {
   double A[3][3];
   double b[3];
+  double B[3];
 } fftm_load;
 
 typedef struct fftm_step_report {
@@ -147,7 +154,9 @@ int fftm_set_phase(fftm_problem* p, const uint16_t* phase);
 int fftm_set_load(fftm_problem* p, const fftm_load* load);
 
 /* Run Algorithm 1 for one load step from the current u^f (the previous
-   step's converged field, zero initially).  Blocks until the report is
+   step's converged field, zero initially).  When the step converges, the
+   internal variables of J2 phases are committed from the converged field (a
+   step that does not converge commits nothing).  Blocks until the report is
    written.  Returns FFTM_OK, FFTM_NOT_CONVERGED, or an error.  `err_history`
    (HOST, may be NULL) receives up to `history_len` per-iteration errors;
    `accel_history` (HOST, may be NULL) receives 1/0 per iteration for an
@@ -161,8 +170,12 @@ enum fftm_field {
   FFTM_FIELD_WORK = 1,   /* the p / spectral work field, node layout (3 comps)   */
   FFTM_FIELD_GRAD = 2,   /* total gradient G at voxel points (9 comps)           */
   FFTM_FIELD_STRESS = 3, /* stress P at voxel points (6 comps)                   */
-  FFTM_FIELD_D = 4       /* residual D = div P at the nodes (3 comps), dismissed
+  FFTM_FIELD_D = 4,      /* residual D = div P at the nodes (3 comps), dismissed
                             node components 0; written by FFTM_OP_RESIDUAL       */
+  FFTM_FIELD_STATE = 5   /* committed J2 state at voxel points (7 comps: eps^p
+                            11, 22, 33, 23, 13, 12 and the cumulated plastic
+                            strain p; zero in non-J2 voxels); only for problems
+                            with a J2 phase, else FFTM_E_INVALID                */
 };
 
 /* Bytes of a field (dense layout above, problem precision). */
@@ -173,8 +186,9 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
    the current u^f on demand. */
 int fftm_get_field(fftm_problem* p, int field, void* dst, int dst_is_device, size_t bytes);
 
-/* Copy a field in (FFTM_FIELD_U or FFTM_FIELD_WORK only).  Values at
-   dismissed node components are ignored and stored as zero. */
+/* Copy a field in (FFTM_FIELD_U, FFTM_FIELD_WORK or FFTM_FIELD_STATE).
+   Values at dismissed node components are ignored and stored as zero; STATE
+   is stored as given (a restart from a saved state). */
 int fftm_set_field(fftm_problem* p, int field, const void* src, int src_is_device, size_t bytes);
 
 /* ---- single steps of one iteration (each a row of the hot path) -------- */
@@ -201,7 +215,7 @@ int fftm_apply(fftm_problem* p, int op, double* norms);
 /* Number of kernels the library launched on this problem since creation. */
 int fftm_kernel_launches(const fftm_problem* p, long long* count);
 
-/* Zero u^f and the acceleration history (a fresh load sequence). */
+/* Zero u^f, the acceleration history and the J2 state (a fresh load sequence). */
 int fftm_reset_state(fftm_problem* p);
 
 /* Per-kernel timing with CUDA events on the problem's stream (off by default).

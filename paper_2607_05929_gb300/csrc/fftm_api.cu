@@ -260,6 +260,11 @@ struct fftm_problem {
   void* vs = nullptr;       // voxel-point stresses of the solver (NPP x NC x nvox)
   void* vs_test = nullptr;  // with tau, for FFTM_OP_RESIDUAL (allocated on first use)
   int sym = 1;              // every law gives a symmetric P
+  void* state = nullptr;    // committed J2 state [r][7][voxel]: elastic strain e_n, p_n (only if a phase is J2)
+  void* un = nullptr;       // u^f at the last commit: 3 comps (FP64) or 3 high + 3 low (FP32)
+  fftm_load load_n;         // the load at the last commit
+  void* Dn = nullptr;       // residual D at the last commit (3 comps)
+  int committed = 0;        // a load step has been committed since creation or reset
   // tensor-core transforms (FFTM_FP32_TC): BF16 matrices, Kp x Kp per component and axis
   int tc = 0;
   void* tcmat = nullptr;
@@ -505,6 +510,36 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   R.partial = p->partial;
   R.vs = reinterpret_cast<T*>(p->vs);
   R.sym = p->sym;
+  R.state = reinterpret_cast<T*>(p->state);
+  R.bend = 0;
+  R.dbend = 0;
+  for (int q = 0; q < 3; ++q) {
+    R.Bq[q] = T(p->load.B[q]);
+    R.bend |= p->load.B[q] != 0.0;
+    const double dB = p->load.B[q] - p->load_n.B[q];
+    R.dBq[q] = T(dB);
+    R.dbend |= dB != 0.0;
+    R.un[q] = p->un ? reinterpret_cast<const T*>(p->un) + q * p->comp_stride : nullptr;
+    R.unlo[q] = (p->un && lo) ? reinterpret_cast<const T*>(p->un) + (3 + q) * p->comp_stride : nullptr;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int q = 0; q < 3; ++q) R.dGs[i * 3 + q] = T(p->load.A[q][i] - p->load_n.A[q][i]);
+  for (int a = 0; a < 3; ++a) R.hh[a] = T(p->h[a]);
+  return R;
+}
+
+// Parameters whose u^f and u* are those of the last commit (state conversion).
+template <typename T>
+ResParams<T> commit_params(fftm_problem* p) {
+  ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
+  for (int q = 0; q < 3; ++q) {
+    R.u[q] = R.un[q];
+    R.ulo[q] = R.unlo[q];
+    R.Bq[q] = T(p->load_n.B[q]);
+  }
+  R.bend = p->load_n.B[0] != 0.0 || p->load_n.B[1] != 0.0 || p->load_n.B[2] != 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int q = 0; q < 3; ++q) R.Gs[i * 3 + q] = T(p->load_n.A[q][i]);
   return R;
 }
 
@@ -527,6 +562,10 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
   }
   ResParams<T> R = res_params<T>(p, slot, D, pp);
   if (test_outputs) R.vs = reinterpret_cast<T*>(p->vs_test);
+  if (!test_outputs && p->committed) {  // incremental form from the last commit
+    R.inc = 1;
+    for (int q = 0; q < 3; ++q) R.Dn[q] = reinterpret_cast<const T*>(p->Dn) + q * p->comp_stride;
+  }
   int blocks = 0;
   ProfScope ps(p, test_outputs ? FFTM_KCAT_OTHER : FFTM_KCAT_RESIDUAL);
   CU(launch_residual<T>(R, p->tetra, test_outputs, p->ctx->stream, &blocks));
@@ -673,6 +712,27 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     p->launches += 2;
   }
   CU(cudaMemcpyAsync(p->hpin + 16, p->dscal + 16, 18 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (converged && p->state) {  // a9: commit the internal variables of the converged step
+    ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
+    ProfScope ps(p, FFTM_KCAT_OTHER);
+    CU(launch_commit<T>(R, p->tetra, s));
+    p->launches += 1;
+    for (int q = 0; q < 3; ++q) {
+      T* un = reinterpret_cast<T*>(p->un);
+      CU(cudaMemcpyAsync(un + q * cnt, field_ptr<T>(p, SET_UH + p->cur, q), cnt * sizeof(T),
+                         cudaMemcpyDeviceToDevice, s));
+      if (lo)
+        CU(cudaMemcpyAsync(un + (3 + q) * cnt, field_ptr<T>(p, SET_UL + p->cur, q), cnt * sizeof(T),
+                           cudaMemcpyDeviceToDevice, s));
+    }
+    p->load_n = p->load;
+    p->committed = 1;
+    // D_n = div P_n evaluated afresh (plain form) so that rounding does not accumulate
+    // from step to step through the incremental form
+    ResParams<T> Rn = res_params<T>(p, p->cur, reinterpret_cast<T*>(p->Dn), nullptr);
+    CU(launch_residual<T>(Rn, p->tetra, false, s, nullptr));
+    p->launches += 2;
+  }
   CU(cudaStreamSynchronize(s));
   prof_flush(p);
   std::memset(rep, 0, sizeof(*rep));
@@ -703,9 +763,14 @@ int validate(const fftm_problem_desc* d) {
     return set_err(FFTM_E_INVALID, "n_phases must be in [1, 65535] with a materials array");
   for (int i = 0; i < d->n_phases; ++i) {
     const int law = d->materials[i].law;
-    if (law == FFTM_LAW_J2_LINHARD) return set_err(FFTM_E_UNSUPPORTED, "J2 law not available in this build");
-    if (law != FFTM_LAW_ISO_ELASTIC && law != FFTM_LAW_CUBIC_ELASTIC && law != FFTM_LAW_B0_LINEAR)
+    if (law != FFTM_LAW_ISO_ELASTIC && law != FFTM_LAW_CUBIC_ELASTIC && law != FFTM_LAW_B0_LINEAR &&
+        law != FFTM_LAW_J2_LINHARD)
       return set_err(FFTM_E_INVALID, "unknown law");
+    if (law == FFTM_LAW_J2_LINHARD) {
+      const double* c = d->materials[i].params;
+      if (!(c[1] > 0.0) || !(3.0 * c[0] + 2.0 * c[1] > 0.0) || !(c[2] > 0.0) || !(c[3] >= 0.0))
+        return set_err(FFTM_E_INVALID, "J2 needs mu > 0, 3 lambda + 2 mu > 0, sigma_y > 0, H >= 0");
+    }
   }
   for (int a = 0; a < 3; ++a) {
     int np = 0;
@@ -801,7 +866,12 @@ int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
   const long long nvox = (long long)desc->n[0] * desc->n[1] * desc->n[2];
   const size_t esz = desc->precision == FFTM_FP64 ? 8 : 4;
   const size_t vsb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 9 * nvox * esz;
-  *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + nvox * sizeof(uint16_t) + desc->n_phases * sizeof(int);
+  size_t stb = 0;
+  for (int i = 0; i < desc->n_phases; ++i)
+    if (desc->materials[i].law == FFTM_LAW_J2_LINHARD)
+      stb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 7 * nvox * esz + (esz == 4 ? 9 : 6) * s.comp_stride * esz;
+  *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + stb + nvox * sizeof(uint16_t) +
+           desc->n_phases * sizeof(int);
   return FFTM_OK;
 }
 
@@ -820,6 +890,9 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->scratch);
   cudaFree(p->vs);
   cudaFree(p->vs_test);
+  cudaFree(p->state);
+  cudaFree(p->un);
+  cudaFree(p->Dn);
   cudaFree(p->tcmat);
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
@@ -843,6 +916,8 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
   p->esz = desc->precision == FFTM_FP64 ? 8 : 4;
   p->tetra = desc->scheme == FFTM_TETRA2;
   std::memset(&p->load, 0, sizeof(p->load));
+  std::memset(&p->load_n, 0, sizeof(p->load_n));
+  p->committed = 0;
   for (int a = 0; a < 3; ++a) {
     p->n[a] = desc->n[a];
     p->h[a] = desc->h[a];
@@ -885,6 +960,17 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
   for (int i = 0; i < desc->n_phases; ++i)
     if (desc->materials[i].law == FFTM_LAW_B0_LINEAR) p->sym = 0;
   CU(cudaMalloc(&p->vs, (size_t)(p->tetra ? 2 : 1) * (p->sym ? 6 : 9) * p->nvox * p->esz));
+  for (int i = 0; i < desc->n_phases; ++i)
+    if (desc->materials[i].law == FFTM_LAW_J2_LINHARD && !p->state) {
+      const size_t sb = (size_t)(p->tetra ? 2 : 1) * 7 * p->nvox * p->esz;
+      CU(cudaMalloc(&p->state, sb));
+      CU(cudaMemsetAsync(p->state, 0, sb, s));
+      const size_t ub = (size_t)(p->esz == 4 ? 6 : 3) * p->comp_stride * p->esz;
+      CU(cudaMalloc(&p->un, ub));
+      CU(cudaMemsetAsync(p->un, 0, ub, s));
+      CU(cudaMalloc(&p->Dn, 3 * p->comp_stride * p->esz));
+      CU(cudaMemsetAsync(p->Dn, 0, 3 * p->comp_stride * p->esz, s));
+    }
   CU(cudaMalloc(&p->phase, p->nvox * sizeof(uint16_t)));
   CU(cudaMemcpyAsync(p->phase, desc->phase, p->nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
   CU(cudaMalloc(&p->partial, sz.partial));
@@ -967,6 +1053,8 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
       int k = 0;
       for (int a = 0; a < 6; ++a)
         for (int b = a; b < 6; ++b) c[k++] = Cm[a][b];
+    } else if (m.law == FFTM_LAW_J2_LINHARD) {
+      for (int k = 0; k < 4; ++k) c[k] = m.params[k];
     } else {
       c[0] = m.params[0];
       c[1] = m.params[1];
@@ -999,7 +1087,8 @@ int fftm_set_load(fftm_problem* p, const fftm_load* load) {
   for (int a = 0; a < 3; ++a)
     if (p->periodic[a])
       for (int q = 0; q < 3; ++q)
-        if (load->A[q][a] != 0.0) return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
+        if (load->A[q][a] != 0.0 || (a < 2 && load->B[q] != 0.0))
+          return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
   p->load = *load;
   return FFTM_OK;
 }
@@ -1022,6 +1111,10 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes) {
     case FFTM_FIELD_D: *bytes = 3 * nodes * p->esz; return FFTM_OK;
     case FFTM_FIELD_GRAD: *bytes = 9 * npp * p->nvox * p->esz; return FFTM_OK;
     case FFTM_FIELD_STRESS: *bytes = 6 * npp * p->nvox * p->esz; return FFTM_OK;
+    case FFTM_FIELD_STATE:
+      if (!p->state) return set_err(FFTM_E_INVALID, "the problem has no J2 phase (no state)");
+      *bytes = 7 * npp * p->nvox * p->esz;
+      return FFTM_OK;
     default: return set_err(FFTM_E_INVALID, "unknown field");
   }
 }
@@ -1049,6 +1142,13 @@ static int get_field_t(fftm_problem* p, int field, void* dst, int dst_is_device,
     int rc = ensure_scratch(p, bytes);
     if (rc) return rc;
     target = p->scratch;
+  }
+  if (field == FFTM_FIELD_STATE) {
+    CU(launch_state_io<T>(commit_params<T>(p), p->tetra, reinterpret_cast<T*>(target), nullptr, s));
+    p->launches++;
+    if (!dst_is_device) CU(cudaMemcpyAsync(dst, target, bytes, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    return FFTM_OK;
   }
   if (field == FFTM_FIELD_U || field == FFTM_FIELD_WORK || field == FFTM_FIELD_D) {
     const T* src[3];
@@ -1115,12 +1215,31 @@ extern "C" {
 
 int fftm_set_field(fftm_problem* p, int field, const void* src, int src_is_device, size_t bytes) {
   if (!p || !src) return set_err(FFTM_E_INVALID, "null argument");
-  if (field != FFTM_FIELD_U && field != FFTM_FIELD_WORK) return set_err(FFTM_E_INVALID, "only U and WORK are settable");
+  if (field != FFTM_FIELD_U && field != FFTM_FIELD_WORK && field != FFTM_FIELD_STATE)
+    return set_err(FFTM_E_INVALID, "only U, WORK and STATE are settable");
   size_t need;
   int rc = fftm_field_bytes(p, field, &need);
   if (rc) return rc;
   if (bytes != need) return set_err(FFTM_E_INVALID, "byte count does not match the field");
   CU(cudaSetDevice(p->ctx->device));
+  if (field == FFTM_FIELD_STATE) {
+    const void* from = src;
+    if (!src_is_device) {
+      rc = ensure_scratch(p, bytes);
+      if (rc) return rc;
+      CU(cudaMemcpyAsync(p->scratch, src, bytes, cudaMemcpyHostToDevice, p->ctx->stream));
+      from = p->scratch;
+    }
+    if (p->esz == 8)
+      CU(launch_state_io<double>(commit_params<double>(p), p->tetra, nullptr, reinterpret_cast<const double*>(from),
+                                 p->ctx->stream));
+    else
+      CU(launch_state_io<float>(commit_params<float>(p), p->tetra, nullptr, reinterpret_cast<const float*>(from),
+                                p->ctx->stream));
+    p->launches++;
+    CU(cudaStreamSynchronize(p->ctx->stream));
+    return FFTM_OK;
+  }
   if (p->esz == 8) return set_field_t<double>(p, field, src, src_is_device, bytes);
   return set_field_t<float>(p, field, src, src_is_device, bytes);
 }
@@ -1210,6 +1329,12 @@ int fftm_reset_state(fftm_problem* p) {
   CU(cudaSetDevice(p->ctx->device));
   Sizes sz = sizes_of(&p->desc);
   CU(cudaMemsetAsync(p->fields, 0, sz.fields, p->ctx->stream));
+  if (p->state) {
+    CU(cudaMemsetAsync(p->state, 0, (size_t)(p->tetra ? 2 : 1) * 7 * p->nvox * p->esz, p->ctx->stream));
+    CU(cudaMemsetAsync(p->un, 0, (size_t)(p->esz == 4 ? 6 : 3) * p->comp_stride * p->esz, p->ctx->stream));
+  }
+  std::memset(&p->load_n, 0, sizeof(p->load_n));
+  p->committed = 0;
   CU(cudaStreamSynchronize(p->ctx->stream));
   p->cur = 0;
   return FFTM_OK;

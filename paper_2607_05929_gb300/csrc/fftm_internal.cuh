@@ -76,7 +76,24 @@ struct ResParams {
   int periodic[3];
   long long sy, sz;  // node strides (x stride 1)
   long long vy, vz;  // voxel strides
-  T Gs[9];           // uniform gradient of the affine u*
+  T Gs[9];           // uniform gradient of the affine part of u*
+  int bend;          // 1 if u* has the bilinear term B_q x_1 x_2
+  T Bq[3];           // its coefficients
+  T hh[3];           // voxel sizes
+  // J2 phases are evaluated incrementally from the last commit: the state holds the
+  // elastic strain e_n (11,22,33,23,13,12) and p_n per voxel point [r][7][voxel], and
+  // the trial strain is e_n + sym(grad(u^f - u^f_n) + grad(u* - u*_n)).
+  T* state;          // null: no J2 phase
+  const T* un[3];    // u^f at the last commit (high part in FP32)
+  const T* unlo[3];  // its low part (FP32 only)
+  T dGs[9];          // gradient of the affine part of u* - u*_n
+  int dbend;         // 1 if the bilinear part of u* - u*_n is non-zero
+  T dBq[3];          // its coefficients
+  // Incremental residual (J2 problems after their first commit): k_stress stores the
+  // stress increment P - P_n and k_div adds D_n = div P_n, the residual at the commit,
+  // so that FP32 rounding scales with the increment instead of the stress.
+  int inc;
+  const T* Dn[3];
   T lam0, two_mu0;
   T wdiv[3];         // 1 / (4 h_i)
   T wgrad[3];        // HEX1: 1 / (4 h_i); TETRA2: 1 / (2 h_i)
@@ -140,6 +157,16 @@ template <typename T>
 int residual_blocks(const ResParams<T>& P, int tetra);
 template <typename T>
 cudaError_t launch_green(const GreenParams<T>& P, cudaStream_t s);
+// a9: recompute the J2 return at every voxel point from the current u^f and the
+// committed state, and store the returned state (the step's commit).
+template <typename T>
+cudaError_t launch_commit(const ResParams<T>& P, int tetra, cudaStream_t s);
+// The committed state as (eps^p, p) = (sym G_n - e_n, p_n) (out != null), or the
+// elastic strain e_n = sym G_n - eps^p from a given (eps^p, p) (in != null); G_n is
+// the total gradient at the commit, from P.u = u^f_n and P.Gs, P.Bq = the load at
+// the commit.  Dense layout [r][7][voxel]; zero outside J2 voxels.
+template <typename T>
+cudaError_t launch_state_io(const ResParams<T>& P, int tetra, T* out, const T* in, cudaStream_t s);
 
 cudaError_t launch_reduce_norms(const double* partial, int nblocks, int nvals, double* out, cudaStream_t s);
 

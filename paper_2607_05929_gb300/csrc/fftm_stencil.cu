@@ -85,6 +85,97 @@ __device__ __forceinline__ void law_eval(int law, const T* __restrict__ c, const
   }
 }
 
+// J2 plasticity with linear isotropic hardening (Sec. 3.2, small strain), radial
+// return written as an increment from the committed state st = (e_n as 11, 22, 33,
+// 23, 13, 12; p_n), e_n the elastic strain at the commit, for the gradient
+// increment dG since the commit.  With K = lambda + 2 mu / 3, d the deviator of e_n
+// and dd that of sym(dG):
+//   trial von Mises stress q = 2 mu sqrt(3/2 (d + dd):(d + dd)), written as
+//   q_n + dq with dq = (q^2 - q_n^2) / (q + q_n) (a small quantity);
+//   yield function f = (q_n - sigma_y - H p_n) + dq; on yield dp = f / (3 mu + H)
+//   and the deviator is scaled by k = 1 + km1, km1 = -3 mu dp / q;
+//   P - P_n = K tr(dG) I + 2 mu (k dd + km1 d),  P_n = K tr(e_n) I + 2 mu d.
+// In exact arithmetic this is the classical return on e = e_n + sym(dG); written
+// this way every rounding is relative to the increment, not to the stress.
+// c = (lambda, mu, sigma_y, H).  dP (may be null): P - P_n; Pf: P; stn (may be
+// null): the returned state (e_{n+1} = volumetric part + k times the deviator).
+template <typename T>
+__device__ __forceinline__ void j2_inc(const T* __restrict__ c, const T dG[9], const T st[7], T* dP, T Pf[9],
+                                       T* stn) {
+  const T lam = __ldg(c), mu = __ldg(c + 1), sy = __ldg(c + 2), H = __ldg(c + 3);
+  const T de[6] = {dG[0], dG[4], dG[8], T(0.5) * (dG[5] + dG[7]), T(0.5) * (dG[2] + dG[6]),
+                   T(0.5) * (dG[1] + dG[3])};
+  const T dtr = de[0] + de[1] + de[2], dm = dtr * T(1.0 / 3.0);
+  const T trn = st[0] + st[1] + st[2], mn = trn * T(1.0 / 3.0);
+  const T dd[6] = {de[0] - dm, de[1] - dm, de[2] - dm, de[3], de[4], de[5]};
+  const T dn[6] = {st[0] - mn, st[1] - mn, st[2] - mn, st[3], st[4], st[5]};
+  auto dot = [](const T* a, const T* b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2] + T(2) * (a[3] * b[3] + a[4] * b[4] + a[5] * b[5]);
+  };
+  const T c2 = T(6) * mu * mu;  // 3/2 (2 mu)^2
+  const T qn = sqrt(c2 * dot(dn, dn));
+  const T dq2 = c2 * (T(2) * dot(dn, dd) + dot(dd, dd));
+  const T q2 = qn * qn + dq2;
+  const T q = q2 > T(0) ? sqrt(q2) : T(0);
+  const T dq = (q + qn) > T(0) ? dq2 / (q + qn) : T(0);
+  const T f = (qn - (sy + H * st[6])) + dq;
+  T dp = T(0), km1 = T(0);
+  if (f > T(0)) {
+    dp = f / (T(3) * mu + H);
+    km1 = -T(3) * mu * dp / q;
+  }
+  const T K = lam + T(2.0 / 3.0) * mu, m2 = T(2) * mu;
+  T d6[6], p6[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    d6[i] = m2 * ((T(1) + km1) * dd[i] + km1 * dn[i]) + (i < 3 ? K * dtr : T(0));
+    p6[i] = (m2 * dn[i] + (i < 3 ? K * trn : T(0))) + d6[i];
+  }
+  constexpr int map9[9] = {0, 5, 4, 5, 1, 3, 4, 3, 2};  // G[i*3+q] -> symmetric slot
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    Pf[i] = p6[map9[i]];
+    if (dP) dP[i] = d6[map9[i]];
+  }
+  if (stn) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) stn[i] = (i < 3 ? mn + dm : T(0)) + (T(1) + km1) * (dn[i] + dd[i]);
+    stn[6] = st[6] + dp;
+  }
+}
+
+// Law at voxel point r of voxel v from the gradient G (elastic laws: the total
+// gradient; J2: the increment since the commit).
+template <typename T>
+__device__ __forceinline__ void point_law(const ResParams<T>& P, int law, const T* lc, const T G[9], int r,
+                                          long long v, long long nvox, T Pout[9], T* stn) {
+  if (law == LAW_J2) {
+    const T* sp = P.state + (long long)(r * 7) * nvox + v;
+    T st[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) st[c] = sp[c * nvox];
+    j2_inc<T>(lc, G, st, nullptr, Pout, stn);
+  } else {
+    law_eval<T>(law, lc, G, Pout);
+  }
+}
+
+// Bilinear part B_q x_1 x_2 of u*: its discrete gradient at voxel (vx, vy, .), point r,
+// is x_2 (D_1) and x_1 (D_2) at the voxel centre for both schemes; D_3 is 0 for HEX1
+// and -h_1 h_2 / (2 h_3) on T1, +h_1 h_2 / (2 h_3) on T2 (the four corners of each
+// tetrahedron in Eqs. D1T1T2G-D3T1T2G applied to x_1 x_2).
+template <typename T, int TETRA>
+__device__ __forceinline__ void add_bend(const T hh[3], const T Bq[3], int r, int vx, int vy, T G[9]) {
+  const T x1 = (T(vx) + T(0.5)) * hh[0], x2 = (T(vy) + T(0.5)) * hh[1];
+  const T d3 = TETRA ? (r == 0 ? T(-0.5) : T(0.5)) * hh[0] * hh[1] / hh[2] : T(0);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    G[q] += Bq[q] * x2;
+    G[3 + q] += Bq[q] * x1;
+    G[6 + q] += Bq[q] * d3;
+  }
+}
+
 // Gradient at point r from the 8 corner values (corner o = ox + 2 oy + 4 oz),
 // as a sum of differences; ul (low parts) may be null.
 template <typename T, int TETRA, bool LO>
@@ -105,6 +196,23 @@ __device__ __forceinline__ void point_grad(const T uh[3][8], const T ul[3][8], i
       }
       G[i * 3 + q] = wg[i] * (LO ? s + sl : s);
     }
+  }
+}
+
+// Gradient that the law of voxel (vx, vy) takes at point r, from the corner values
+// (for J2 voxels the caller has already subtracted u^f_n from them).
+template <typename T, int TETRA, bool LO>
+__device__ __forceinline__ void law_grad(const ResParams<T>& P, bool j2, const T uh[3][8], const T ul[3][8], int r,
+                                         int vx, int vy, T Gf[9], T Gt[9]) {
+  point_grad<T, TETRA, LO>(uh, ul, r, P.wgrad, Gf);
+  if (j2) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.dGs[i];
+    if (P.dbend) add_bend<T, TETRA>(P.hh, P.dBq, r, vx, vy, Gt);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
+    if (P.bend) add_bend<T, TETRA>(P.hh, P.Bq, r, vx, vy, Gt);
   }
 }
 
@@ -188,7 +296,7 @@ __device__ __forceinline__ int sym_index(int i, int q) {
   return 6 - i - q;  // (1,2) -> 3, (0,2) -> 4, (0,1) -> 5
 }
 
-template <typename T, int TETRA, bool WITH_P, bool LO, bool SYM>
+template <typename T, int TETRA, bool WITH_P, bool LO, bool SYM, bool J2>
 __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti) {
   constexpr int NPP = TETRA ? 2 : 1;
   constexpr int NC = SYM ? 6 : 9;
@@ -206,31 +314,41 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
     const int vx = x0 + (threadIdx.x % RTX), vy_ = y0 + (threadIdx.x / RTX);
     if (vx < n1 && vy_ < n2) {
       T uh[3][8], ul[3][8];
+      int at[8];
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         int gx = vx + (o & 1), gy = vy_ + ((o >> 1) & 1), gz = vz + (o >> 2);
         if (P.periodic[0] && gx == n1) gx = 0;
         if (P.periodic[1] && gy == n2) gy = 0;
         if (P.periodic[2] && gz == n3) gz = 0;
-        const int at = gx + gy * sy + gz * sz;
+        at[o] = gx + gy * sy + gz * sz;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          uh[c][o] = __ldg(P.u[c] + at);
-          ul[c][o] = LO ? __ldg(P.ulo[c] + at) : T(0);
+          uh[c][o] = __ldg(P.u[c] + at[o]);
+          ul[c][o] = LO ? __ldg(P.ulo[c] + at[o]) : T(0);
         }
       }
       const int v = vx + vy_ * vy + vz * vz_;
       const int ph = P.phase[v];
       const int law = __ldg(P.law_id + ph);
+      const bool j2 = J2 && law == LAW_J2;
       const T* lc = P.law_c + (size_t)ph * LAWC;
+      if (j2) {  // J2 takes the increment since the commit
+#pragma unroll
+        for (int o = 0; o < 8; ++o)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            uh[c][o] -= __ldg(P.un[c] + at[o]);
+            if (LO) ul[c][o] -= __ldg(P.unlo[c] + at[o]);
+          }
+      }
       T spv = T(0);
 #pragma unroll
       for (int r = 0; r < NPP; ++r) {
         T Gf[9], Gt[9], Pp[9];
-        point_grad<T, TETRA, LO>(uh, ul, r, P.wgrad, Gf);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
-        law_eval<T>(law, lc, Gt, Pp);
+        law_grad<T, TETRA, LO>(P, j2, uh, ul, r, vx, vy_, Gf, Gt);
+        if (J2) point_law<T>(P, law, lc, Gt, r, v, nvox, Pp, nullptr);
+        else law_eval<T>(law, lc, Gt, Pp);
         T* base = P.vs + (size_t)(r * NCT) * nvox + v;
         if (SYM) {
           const T s6[6] = {Pp[0], Pp[4], Pp[8], Pp[5], Pp[2], Pp[1]};
@@ -243,6 +361,22 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
 #pragma unroll
         for (int c = 0; c < 9; ++c) spv += Pp[c] * Pp[c];
         if (WITH_P) {
+          if (j2) {  // tau takes grad u^f: add grad u^f_n back to the increment's gradient
+            T nh[3][8], nl[3][8], Gn[9];
+            for (int o = 0; o < 8; ++o) {
+              int gx = vx + (o & 1), gy = vy_ + ((o >> 1) & 1), gz = vz + (o >> 2);
+              if (P.periodic[0] && gx == n1) gx = 0;
+              if (P.periodic[1] && gy == n2) gy = 0;
+              if (P.periodic[2] && gz == n3) gz = 0;
+              const int at = gx + gy * sy + gz * sz;
+              for (int c = 0; c < 3; ++c) {
+                nh[c][o] = P.un[c][at];
+                nl[c][o] = LO ? P.unlo[c][at] : T(0);
+              }
+            }
+            point_grad<T, TETRA, LO>(nh, nl, r, P.wgrad, Gn);
+            for (int i = 0; i < 9; ++i) Gf[i] += Gn[i];
+          }
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -256,6 +390,101 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
       sp += spv;
     }
     if (++run == 16) {  // fold the run into FP64
+      SP += (double)sp;
+      sp = T(0);
+      run = 0;
+    }
+  }
+  SP += (double)sp;
+  const double tot = block_sum(SP, red);
+  if (threadIdx.x == 0) P.partial[2 * blockIdx.x + 1] = tot / NPP;
+}
+
+// Incremental variant of k_stress (J2 problems after their first commit): stores
+// P - P_n, with P_n the stress at the commit (elastic laws: the law applied to the
+// gradient increment; J2: j2_inc).  S_P still takes the full P.
+template <typename T, int TETRA, bool LO, bool SYM>
+__global__ void __launch_bounds__(RTX * RTY) k_stress_inc(ResParams<T> P, TileIdx ti) {
+  constexpr int NPP = TETRA ? 2 : 1;
+  constexpr int NC = SYM ? 6 : 9;
+  __shared__ double red[32];
+  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+  const long long nvox = (long long)n1 * n2 * n3;
+  const int sy = (int)P.sy, sz = (int)P.sz, vy = (int)P.vy, vz_ = (int)P.vz;
+  T sp = T(0);
+  double SP = 0.0;
+  int run = 0;
+  for (int t = blockIdx.x; t < ti.ntile; t += gridDim.x) {
+    int x0, y0, vz;
+    ti.at(t, &x0, &y0, &vz);
+    const int vx = x0 + (threadIdx.x % RTX), vy_ = y0 + (threadIdx.x / RTX);
+    if (vx < n1 && vy_ < n2) {
+      const int v = vx + vy_ * vy + vz * vz_;
+      const int ph = P.phase[v];
+      const int law = __ldg(P.law_id + ph);
+      const bool j2 = law == LAW_J2;
+      const T* lc = P.law_c + (size_t)ph * LAWC;
+      T uh[3][8], ul[3][8];
+      int at[8];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        int gx = vx + (o & 1), gy = vy_ + ((o >> 1) & 1), gz = vz + (o >> 2);
+        if (P.periodic[0] && gx == n1) gx = 0;
+        if (P.periodic[1] && gy == n2) gy = 0;
+        if (P.periodic[2] && gz == n3) gz = 0;
+        at[o] = gx + gy * sy + gz * sz;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          uh[c][o] = __ldg(P.u[c] + at[o]);
+          ul[c][o] = LO ? __ldg(P.ulo[c] + at[o]) : T(0);
+        }
+      }
+      T spv = T(0);
+      if (!j2) {  // |P|^2 of the elastic law on the total gradient
+#pragma unroll
+        for (int r = 0; r < NPP; ++r) {
+          T Gf[9], Gt[9], Pp[9];
+          law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy_, Gf, Gt);
+          law_eval<T>(law, lc, Gt, Pp);
+#pragma unroll
+          for (int c = 0; c < 9; ++c) spv += Pp[c] * Pp[c];
+        }
+      }
+#pragma unroll
+      for (int o = 0; o < 8; ++o)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          uh[c][o] -= __ldg(P.un[c] + at[o]);
+          if (LO) ul[c][o] -= __ldg(P.unlo[c] + at[o]);
+        }
+#pragma unroll
+      for (int r = 0; r < NPP; ++r) {
+        T Gd[9], dG[9], dP[9];
+        law_grad<T, TETRA, LO>(P, true, uh, ul, r, vx, vy_, Gd, dG);
+        if (j2) {
+          const T* stp = P.state + (long long)(r * 7) * nvox + v;
+          T st[7], Pf[9];
+#pragma unroll
+          for (int c = 0; c < 7; ++c) st[c] = stp[c * nvox];
+          j2_inc<T>(lc, dG, st, dP, Pf, nullptr);
+#pragma unroll
+          for (int c = 0; c < 9; ++c) spv += Pf[c] * Pf[c];
+        } else {
+          law_eval<T>(law, lc, dG, dP);
+        }
+        T* base = P.vs + (size_t)(r * NC) * nvox + v;
+        if (SYM) {
+          const T s6[6] = {dP[0], dP[4], dP[8], dP[5], dP[2], dP[1]};
+#pragma unroll
+          for (int c = 0; c < 6; ++c) base[(size_t)c * nvox] = s6[c];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) base[(size_t)c * nvox] = dP[c];
+        }
+      }
+      sp += spv;
+    }
+    if (++run == 16) {
       SP += (double)sp;
       sp = T(0);
       run = 0;
@@ -328,7 +557,7 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
   }
 }
 
-template <typename T, bool WITH_P>
+template <typename T, bool WITH_P, bool INC>
 __device__ __forceinline__ T store_node(const ResParams<T>& P, int mx, int my, int mz, const T Dq[3], const T pq[3]) {
   const int off = mx + my * (int)P.sy + mz * (int)P.sz;
   T sdn = T(0);
@@ -336,15 +565,16 @@ __device__ __forceinline__ T store_node(const ResParams<T>& P, int mx, int my, i
   for (int q = 0; q < 3; ++q) {
     const bool dof = mx >= P.lo[q][0] && mx < P.hi[q][0] && my >= P.lo[q][1] && my < P.hi[q][1] &&
                      mz >= P.lo[q][2] && mz < P.hi[q][2];
-    P.D[q][off] = dof ? Dq[q] : T(0);
+    const T d = INC ? Dq[q] + __ldg(P.Dn[q] + off) : Dq[q];
+    P.D[q][off] = dof ? d : T(0);
     if (WITH_P) P.p[q][off] = dof ? pq[q] : T(0);
-    if (dof) sdn += Dq[q] * Dq[q];
+    if (dof) sdn += d * d;
   }
   return sdn;
 }
 
 // Interior nodes: all 8 neighbouring voxels exist (or wrap); plain differences.
-template <typename T, int TETRA, bool WITH_P, bool SYM>
+template <typename T, int TETRA, bool WITH_P, bool SYM, bool INC>
 __global__ void __launch_bounds__(RTX * RTY) k_div(ResParams<T> P, TileIdx ti, FaceIdx fi) {
   constexpr int NC = SYM ? 6 : 9;
   constexpr int NCT = WITH_P ? NC + 9 : NC;
@@ -400,7 +630,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_div(ResParams<T> P, TileIdx ti, F
           if (WITH_P) pq[q] += P.wdiv[i] * st;
         }
       }
-      sd += store_node<T, WITH_P>(P, mx, my, mz, Dq, pq);
+      sd += store_node<T, WITH_P, INC>(P, mx, my, mz, Dq, pq);
     }
     if (++run == 16) {
       SD += (double)sd;
@@ -415,7 +645,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_div(ResParams<T> P, TileIdx ti, F
     if (!fi.at(t, nface, m)) continue;
     T Dq[3] = {T(0), T(0), T(0)}, pq[3] = {T(0), T(0), T(0)};
     node_div_general<T, TETRA, WITH_P, SYM>(P, m[0], m[1], m[2], Dq, pq);
-    SD += (double)store_node<T, WITH_P>(P, m[0], m[1], m[2], Dq, pq);
+    SD += (double)store_node<T, WITH_P, INC>(P, m[0], m[1], m[2], Dq, pq);
   }
   SD += (double)sd;
   const double tot = block_sum(SD, red);
@@ -469,11 +699,23 @@ static cudaError_t launch_res_t(const ResParams<T>& P, bool lo, cudaStream_t s, 
   TileIdx tn;
   FaceIdx fi;
   interior_and_faces<T>(P, &tn, &fi);
-  if (lo) k_stress<T, TETRA, WITH_P, true, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
-  else k_stress<T, TETRA, WITH_P, false, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+  const bool inc = !WITH_P && P.inc;
+  if (inc) {
+    if (lo) k_stress_inc<T, TETRA, true, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+    else k_stress_inc<T, TETRA, false, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+  } else {
+    if (P.state) {
+      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, true><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+      else k_stress<T, TETRA, WITH_P, false, SYM, true><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+    } else {
+      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, false><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+      else k_stress<T, TETRA, WITH_P, false, SYM, false><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+    }
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_div<T, TETRA, WITH_P, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tn, fi);
+  if (inc) k_div<T, TETRA, false, SYM, true><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tn, fi);
+  else k_div<T, TETRA, WITH_P, SYM, false><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tn, fi);
   if (blocks_out) *blocks_out = RBLOCKS;
   return cudaGetLastError();
 }
@@ -497,13 +739,18 @@ template int residual_blocks<double>(const ResParams<double>&, int);
 
 // ---- per-voxel evaluation shared by the output and statistics kernels ----
 template <typename T, int TETRA, bool LO>
-__device__ __forceinline__ void voxel_eval(const ResParams<T>& P, long long v, T Gt_out[2][9], T P_out[2][9]) {
+__device__ __forceinline__ int voxel_eval(const ResParams<T>& P, long long v, T Gt_out[2][9], T P_out[2][9],
+                                          T (*stn)[7] = nullptr) {
   const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
   const int vx = (int)(v % n1);
   const long long r1 = v / n1;
   const int vy = (int)(r1 % n2);
   const int vz = (int)(r1 / n2);
-  T uh[3][8], ul[3][8];
+  const int ph = P.phase[vx + vy * P.vy + (long long)vz * P.vz];
+  const int law = __ldg(P.law_id + ph);
+  const bool j2 = law == LAW_J2;
+  const T* lc = P.law_c + (size_t)ph * LAWC;
+  T uh[3][8], ul[3][8], nh[3][8], nl[3][8];
 #pragma unroll
   for (int o = 0; o < 8; ++o) {
     int gx = vx + (o & 1), gy = vy + ((o >> 1) & 1), gz = vz + (o >> 2);
@@ -515,20 +762,125 @@ __device__ __forceinline__ void voxel_eval(const ResParams<T>& P, long long v, T
     for (int c = 0; c < 3; ++c) {
       uh[c][o] = P.u[c][at];
       ul[c][o] = LO ? P.ulo[c][at] : T(0);
+      nh[c][o] = j2 ? P.un[c][at] : T(0);
+      nl[c][o] = (j2 && LO) ? P.unlo[c][at] : T(0);
     }
   }
-  const int ph = P.phase[vx + vy * P.vy + (long long)vz * P.vz];
-  const int law = __ldg(P.law_id + ph);
-  const T* lc = P.law_c + (size_t)ph * LAWC;
 #pragma unroll
   for (int r = 0; r < (TETRA ? 2 : 1); ++r) {
     T Gf[9];
-    point_grad<T, TETRA, LO>(uh, ul, r, P.wgrad, Gf);
+    law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy, Gf, Gt_out[r]);  // total gradient (reported)
+    if (j2) {
+      T du[3][8], dl[3][8], Gd[9], Ginc[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Gt_out[r][i] = Gf[i] + P.Gs[i];
-    law_eval<T>(law, lc, Gt_out[r], P_out[r]);
+      for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          du[c][o] = uh[c][o] - nh[c][o];
+          dl[c][o] = ul[c][o] - nl[c][o];
+        }
+      law_grad<T, TETRA, LO>(P, true, du, dl, r, vx, vy, Gd, Ginc);
+      point_law<T>(P, law, lc, Ginc, r, v, (long long)n1 * n2 * n3, P_out[r], stn ? stn[r] : nullptr);
+    } else {
+      point_law<T>(P, law, lc, Gt_out[r], r, v, (long long)n1 * n2 * n3, P_out[r], nullptr);
+    }
+  }
+  return law;
+}
+
+template <typename T, int TETRA, bool LO>
+__global__ void k_commit(ResParams<T> P) {
+  const long long nv = (long long)P.n[0] * P.n[1] * P.n[2];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+       v += (long long)gridDim.x * blockDim.x) {
+    if (__ldg(P.law_id + P.phase[v]) != LAW_J2) continue;  // voxel index == phase index (dense)
+    T Gt[2][9], Pp[2][9], stn[2][7];
+    voxel_eval<T, TETRA, LO>(P, v, Gt, Pp, stn);
+#pragma unroll
+    for (int r = 0; r < (TETRA ? 2 : 1); ++r)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) P.state[v + nv * (c + 7 * r)] = stn[r][c];
   }
 }
+
+template <typename T>
+cudaError_t launch_commit(const ResParams<T>& P, int tetra, cudaStream_t s) {
+  if (!P.state) return cudaSuccess;
+  const bool lo = P.ulo[0] != nullptr;
+  if (tetra) {
+    if (lo) k_commit<T, 1, true><<<1216, 256, 0, s>>>(P);
+    else k_commit<T, 1, false><<<1216, 256, 0, s>>>(P);
+  } else {
+    if (lo) k_commit<T, 0, true><<<1216, 256, 0, s>>>(P);
+    else k_commit<T, 0, false><<<1216, 256, 0, s>>>(P);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_commit<float>(const ResParams<float>&, int, cudaStream_t);
+template cudaError_t launch_commit<double>(const ResParams<double>&, int, cudaStream_t);
+
+template <typename T, int TETRA, bool LO>
+__global__ void k_state_io(ResParams<T> P, T* __restrict__ out, const T* __restrict__ in) {
+  const long long nv = (long long)P.n[0] * P.n[1] * P.n[2];
+  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
+       v += (long long)gridDim.x * blockDim.x) {
+    const bool j2 = __ldg(P.law_id + P.phase[v]) == LAW_J2;
+    if (!j2) {
+      if (out)
+        for (int c = 0; c < 7 * (TETRA ? 2 : 1); ++c) out[v + nv * c] = T(0);
+      continue;
+    }
+    const int vx = (int)(v % n1);
+    const long long r1 = v / n1;
+    const int vy = (int)(r1 % n2), vz = (int)(r1 / n2);
+    T uh[3][8], ul[3][8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      int gx = vx + (o & 1), gy = vy + ((o >> 1) & 1), gz = vz + (o >> 2);
+      if (P.periodic[0] && gx == n1) gx = 0;
+      if (P.periodic[1] && gy == n2) gy = 0;
+      if (P.periodic[2] && gz == n3) gz = 0;
+      const long long at = gx + gy * P.sy + (long long)gz * P.sz;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        uh[c][o] = P.u[c][at];
+        ul[c][o] = LO ? P.ulo[c][at] : T(0);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < (TETRA ? 2 : 1); ++r) {
+      T Gf[9], G[9];
+      law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy, Gf, G);
+      const T es[6] = {G[0], G[4], G[8], T(0.5) * (G[5] + G[7]), T(0.5) * (G[2] + G[6]), T(0.5) * (G[1] + G[3])};
+      T* st = P.state + v + nv * (7 * r);
+      if (out) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) out[v + nv * (c + 7 * r)] = es[c] - st[nv * c];
+        out[v + nv * (6 + 7 * r)] = st[nv * 6];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) st[nv * c] = es[c] - in[v + nv * (c + 7 * r)];
+        st[nv * 6] = in[v + nv * (6 + 7 * r)];
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_state_io(const ResParams<T>& P, int tetra, T* out, const T* in, cudaStream_t s) {
+  const bool lo = P.ulo[0] != nullptr;
+  if (tetra) {
+    if (lo) k_state_io<T, 1, true><<<1216, 256, 0, s>>>(P, out, in);
+    else k_state_io<T, 1, false><<<1216, 256, 0, s>>>(P, out, in);
+  } else {
+    if (lo) k_state_io<T, 0, true><<<1216, 256, 0, s>>>(P, out, in);
+    else k_state_io<T, 0, false><<<1216, 256, 0, s>>>(P, out, in);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t launch_state_io<float>(const ResParams<float>&, int, float*, const float*, cudaStream_t);
+template cudaError_t launch_state_io<double>(const ResParams<double>&, int, double*, const double*, cudaStream_t);
 
 template <typename T, int TETRA, bool LO>
 __global__ void k_voxel_fields(ResParams<T> P, T* __restrict__ gout, T* __restrict__ sout) {

@@ -29,7 +29,7 @@ FFTM_HEX1, FFTM_TETRA2 = 0, 1
 FFTM_GREEN_B0, FFTM_GREEN_MU0 = 0, 1
 FFTM_FP64, FFTM_FP32, FFTM_FP32_TC = 0, 1, 2
 FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
-FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D = 0, 1, 2, 3, 4
+FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D, FFTM_FIELD_STATE = 0, 1, 2, 3, 4, 5
 FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP_GREEN_UPDATE = 0, 1, 2, 3, 4
 
 # every symbol include/fftm.h declares
@@ -61,7 +61,7 @@ class fftm_problem_desc(ctypes.Structure):
 
 
 class fftm_load(ctypes.Structure):
-    _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3)]
+    _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3), ("B", ctypes.c_double * 3)]
 
 
 class fftm_step_report(ctypes.Structure):
@@ -216,12 +216,13 @@ def fftm_set_phase_raw(p, host_ptr):
                                                                 ctypes.POINTER(ctypes.c_uint16))))
 
 
-def fftm_set_load(p, A, b=(0.0, 0.0, 0.0)):
+def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), B=(0.0, 0.0, 0.0)):
     ld = fftm_load()
     for q in range(3):
         for a in range(3):
             ld.A[q][a] = float(A[q][a])
         ld.b[q] = float(b[q])
+        ld.B[q] = float(B[q])
     return _check(load_library().fftm_set_load(p, ctypes.byref(ld)))
 
 

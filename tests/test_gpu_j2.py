@@ -1,0 +1,170 @@
+"""J2 elasto-plasticity and the bending load on the GPU against the oracle, over load steps.
+
+The sphere-composite bending workload (J2 matrix with linear hardening, elastic
+spheres, x faces clamped and rotated, y and z traction-free) at a size the oracle
+runs in seconds, over load steps that take the matrix past yield: every step must
+reproduce the oracle's iteration count, stresses, strains and committed plastic
+state (FP64), or stay within the fp32 bar (iterations +-2, fields 1e-5 relative L2).
+"""
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from abi_helpers import GpuProblem, rel_l2, sym6
+from oracle.solver import Problem
+from paper_2607_05929_gb300 import build
+from paper_2607_05929_gb300 import fftm as F
+from synthetic.workloads import Material, Workload, axis_bc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    F.load_library()
+
+
+def _strain(G):
+    return 0.5 * (G + np.swapaxes(G, 1, 2))
+
+
+def _bending(scheme, n=(16, 12, 8), steps=20, tol=1e-8):
+    """The load schedule of the 128^3 bending workload (20 equal rotation increments up to
+    a surface strain of about four times the yield strain) on a grid the oracle runs in
+    seconds."""
+    wl, loads = syn.sphere_composite_bending(n, r_min=2.0, r_max=3.5, seed=4, scheme=scheme, steps=steps,
+                                             theta_max=0.012 * n[0] / n[1], tol=tol)
+    return wl, loads
+
+
+def _state6(st):
+    """oracle state -> (npp, 7, n1, n2, n3) in the ABI order (eps^p 11, 22, 33, 23, 13, 12; p)."""
+    ep = st["ep"]
+    return np.concatenate([sym6(ep), st["p"][:, None]], axis=1)
+
+
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_j2_bending_steps_fp64_match_the_oracle(scheme):
+    wl, loads = _bending(scheme)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, "fp64")
+    try:
+        yielded = False
+        for k, (A, b, B) in enumerate(loads):
+            _, rep = pr.solve_step(A=A, b=b, B=B)
+            assert rep.converged
+            gp.set_load(A, b, B)
+            st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+            assert st == F.FFTM_OK and r["converged"]
+            assert r["iterations"] == rep.iterations, (k, r["iterations"], rep.iterations)
+            assert [i for i, a in enumerate(ah) if a] == rep.accelerated
+            Pg = gp.get_voxel(F.FFTM_FIELD_STRESS)
+            Gg = gp.get_voxel(F.FFTM_FIELD_GRAD)
+            assert rel_l2(Pg, sym6(pr.last["P"])) < 1e-9, k
+            Gg = Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:])
+            assert rel_l2(Gg, pr.last["G"]) < 1e-9, k
+            Sg = gp.get_voxel(F.FFTM_FIELD_STATE)
+            So = _state6(pr.state)
+            if np.abs(So).max() > 0:
+                yielded = True
+                assert rel_l2(Sg, So) < 1e-8, k
+            else:  # read back as sym(G_n) - e_n: zero up to rounding of the strain
+                assert np.abs(Sg).max() < 1e-12 * np.abs(pr.last["G"]).max(), k
+        assert yielded, "the load path must take the matrix past yield"
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_j2_bending_steps_fp32_vs_fp64_oracle(scheme):
+    wl, loads = _bending(scheme, tol=1e-6)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, "fp32")
+    try:
+        for k, (A, b, B) in enumerate(loads):
+            _, rep = pr.solve_step(A=A, b=b, B=B)
+            assert rep.converged
+            gp.set_load(A, b, B)
+            st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+            assert r["converged"], (k, r)
+            assert abs(r["iterations"] - rep.iterations) <= 2, (k, r["iterations"], rep.iterations)
+            Pg = gp.get_voxel(F.FFTM_FIELD_STRESS)
+            Gg = gp.get_voxel(F.FFTM_FIELD_GRAD)
+            assert rel_l2(Pg, sym6(pr.last["P"])) < 1e-5, k
+            Gg = Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:])
+            assert rel_l2(sym6(_strain(Gg)), sym6(_strain(pr.last["G"]))) < 1e-5, k
+    finally:
+        gp.close()
+
+
+def test_j2_bar_uniaxial_load_unload_on_the_gpu():
+    """The homogeneous J2 bar of the oracle pins, run through the library in FP64: every
+    step's mean axial stress follows the uniaxial closed form."""
+    E, nu, sy, H = 200.0, 0.3, 0.3, 2.0
+    lam, mu = syn.iso_lame(E, nu)
+    n = (8, 6, 4)
+    bc = axis_bc("D", "N", "N")
+    bc[0] = [["D", "N", "N"], ["D", "N", "N"]]
+    wl = Workload("j2bar", n, np.zeros(n, np.uint16), [Material(2, (lam, mu, sy, H))], bc,
+                  scheme="HEX1", lambda0=lam, mu0=mu, tol=1e-11, max_iter=3000)
+    gp = GpuProblem(wl, "fp64")
+    try:
+        ep = p = 0.0
+        for eps in [1e-3, 2e-3, 3e-3, 2.5e-3, 1e-3, 3.5e-3]:
+            trial = E * (eps - ep)
+            f = abs(trial) - (sy + H * p)
+            if f > 0:
+                ep += f / (E + H) * np.sign(trial)
+                p += f / (E + H)
+            A = np.zeros((3, 3))
+            A[0, 0] = eps
+            gp.set_load(A, np.zeros(3), np.zeros(3))
+            st, r, _, _ = F.fftm_solve_step(gp.p)
+            assert st == F.FFTM_OK
+            s11 = E * (eps - ep)
+            assert abs(r["mean_P"][0] - s11) < 1e-8 * abs(s11), (eps, r["mean_P"][0], s11)
+            S = gp.get_voxel(F.FFTM_FIELD_STATE)
+            assert np.abs(S[:, 6] - p).max() < 1e-8 * max(p, 1e-3)
+    finally:
+        gp.close()
+
+
+def test_state_field_round_trip_and_reset():
+    wl, _ = _bending("TETRA2", n=(6, 4, 4), steps=1)
+    gp = GpuProblem(wl, "fp32")
+    try:
+        nb = F.fftm_field_bytes(gp.p, F.FFTM_FIELD_STATE)
+        assert nb == 2 * 7 * 6 * 4 * 4 * 4
+        s = np.random.default_rng(3).standard_normal((2, 7, 4, 4, 6)).astype(np.float32)  # [r][c][z][y][x]
+        j2 = (wl.phase == 0).transpose(2, 1, 0)  # matrix (J2) voxels in the dense layout
+        s[:, :, ~j2] = 0.0  # the state is defined in J2 voxels only; the rest read back as zero
+        F.fftm_set_field(gp.p, F.FFTM_FIELD_STATE, s)
+        back = np.zeros_like(s)
+        F.fftm_get_field(gp.p, F.FFTM_FIELD_STATE, back)
+        # stored as the elastic strain sym(G_n) - eps^p with G_n = 0 here: exact round trip
+        assert np.array_equal(back, s)
+        F.fftm_reset_state(gp.p)
+        F.fftm_get_field(gp.p, F.FFTM_FIELD_STATE, back)
+        assert not back.any()
+    finally:
+        gp.close()
+
+
+def test_invalid_j2_and_bending_inputs_are_rejected():
+    n = (4, 4, 4)
+    mats = [(2, (1.0, 1.0, -0.1, 0.5), (1.0, 0.0, 0.0, 0.0))]
+    desc, keep = F.make_desc(n, np.zeros(n, np.uint16), mats, axis_bc("D", "N", "N"))
+    with pytest.raises(F.FFTMError):
+        F.fftm_problem_create(F.fftm_ctx_create(0, None), desc)
+    wl = Workload("bad", n, np.zeros(n, np.uint16), [Material(0, (1.0, 1.0))], axis_bc("N", "P", "N"),
+                  lambda0=1.0, mu0=1.0)
+    gp = GpuProblem(wl, "fp64")
+    try:
+        with pytest.raises(F.FFTMError):
+            gp.set_load(np.zeros((3, 3)), np.zeros(3), np.array([1e-3, 0.0, 0.0]))  # x_2 is periodic
+        with pytest.raises(F.FFTMError):
+            F.fftm_field_bytes(gp.p, F.FFTM_FIELD_STATE)  # no J2 phase
+    finally:
+        gp.close()
