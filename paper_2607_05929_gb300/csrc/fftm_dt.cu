@@ -103,10 +103,15 @@ __device__ void fft_stages(v2<T>* buf, const AxisPlan<T>& pl, const v2<T>* tw) {
     const int Ls = Lp * R;
     const int nb = M / R;
     const int tstep = M / Ls;
+    // b / Lp as a multiply-high: exact for b < 2^16 and 2 <= Lp <= 2^13 with
+    // magic = ceil(2^32 / Lp) (the rounding excess b (magic Lp - 2^32) / 2^32 < 2^-16
+    // stays below 1 / Lp); the first stage has Lp = 1
+    const unsigned magic =
+        Lp > 1 ? (unsigned)((0x100000000ull + (unsigned long long)Lp - 1) / (unsigned long long)Lp) : 0u;
     for (int idx = threadIdx.x; idx < nb * PC; idx += blockDim.x) {
       const int pc = idx % PC;
       const int b = idx / PC;
-      const int g = b / Lp;
+      const int g = Lp > 1 ? (int)__umulhi((unsigned)b, magic) : b;
       const int k = b - g * Lp;
       const int base = g * Ls + k;
       v2<T> x[8];
@@ -131,6 +136,12 @@ __device__ void fft_stages(v2<T>* buf, const AxisPlan<T>& pl, const v2<T>* tw) {
   }
 }
 
+// Complex work buffer: buf[m * PC + pc], pencils interleaved, FFT input digit-reversed.
+template <int PC>
+struct BufIx {
+  static __device__ __forceinline__ int at(int pc, int m) { return m * PC + pc; }
+};
+
 // Staging accessors: stg[row * SP + pencil], row = position - lo.
 template <typename T>
 struct Stage {
@@ -140,12 +151,12 @@ struct Stage {
 };
 
 // Forward pre-processing: sequence value at index m for complex pencil pc.
-template <typename T>
+template <typename T, int KIND>
 __device__ __forceinline__ v2<T> pre_forward(const AxisPlan<T>& pl, const Stage<T>& st, int pc, int m,
                                              const v2<T>* qw) {
   const int n = pl.n;
   const int pa = 2 * pc, pb = pa + 1;
-  switch (pl.kind) {
+  switch (KIND) {
     case K_DFT:
       return mk<T>(st.at(m, pa), st.at(m, pb));
     case K_DCT1: {
@@ -160,7 +171,7 @@ __device__ __forceinline__ v2<T> pre_forward(const AxisPlan<T>& pl, const Stage<
     }
     default: {  // DCT3 (rows j = 0..n-1) or DST3 (rows j-1 for nodes j = 1..n, read reversed)
       if (m == n) return mk<T>(T(0), T(0));
-      const bool rev = (pl.kind == K_DST3);
+      const bool rev = (KIND == K_DST3);
       const int j = (m < n) ? m : 2 * n - m;  // index into the (reversed) input sequence
       const int row = rev ? (n - j) - 1 : j;  // DST3: x'_j = g_{n-j}, stored at row (n - j) - 1
       const v2<T> z = mk<T>(st.at(row, pa), st.at(row, pb));
@@ -174,15 +185,16 @@ __device__ __forceinline__ v2<T> pre_forward(const AxisPlan<T>& pl, const Stage<
 }
 
 // Forward post-processing: writes output row(s) of complex pencil pc for item k.
-template <typename T>
+template <typename T, int KIND, int PC>
 __device__ __forceinline__ void post_forward(const AxisPlan<T>& pl, const v2<T>* buf, const Stage<T>& st,
-                                             int pc, int k, int PC) {
+                                             int pc, int k) {
+  using B = BufIx<PC>;
   const int n = pl.n;
   const int pa = 2 * pc, pb = pa + 1;
-  switch (pl.kind) {
+  switch (KIND) {
     case K_DFT: {  // k in [0, n/2]
-      const v2<T> Zk = buf[k * PC + pc];
-      const v2<T> Zn = buf[((n - k) % n) * PC + pc];
+      const v2<T> Zk = buf[B::at(pc, k)];
+      const v2<T> Zn = buf[B::at(pc, (n - k) % n)];
       const T ax = T(0.5) * (Zk.x + Zn.x), ay = T(0.5) * (Zk.y - Zn.y);
       const T dx = Zk.x - Zn.x, dy = Zk.y + Zn.y;
       const T bx = T(0.5) * dy, by = T(-0.5) * dx;
@@ -195,20 +207,20 @@ __device__ __forceinline__ void post_forward(const AxisPlan<T>& pl, const v2<T>*
       break;
     }
     case K_DCT1: {  // k in [0, n]
-      const v2<T> Y = buf[k * PC + pc];
+      const v2<T> Y = buf[B::at(pc, k)];
       st.at(k, pa) = Y.x;
       st.at(k, pb) = Y.y;
       break;
     }
     case K_DST1: {  // k in [0, n-2], DFT bin k + 1
-      const v2<T> Z = buf[(k + 1) * PC + pc];
+      const v2<T> Z = buf[B::at(pc, k + 1)];
       st.at(k, pa) = -Z.y;
       st.at(k, pb) = Z.x;
       break;
     }
     default: {  // DCT3 / DST3, k in [0, n-1]
-      const v2<T> R = buf[k * PC + pc];
-      const T sg = (pl.kind == K_DST3 && (k & 1)) ? T(-1) : T(1);
+      const v2<T> R = buf[B::at(pc, k)];
+      const T sg = (KIND == K_DST3 && (k & 1)) ? T(-1) : T(1);
       st.at(k, pa) = sg * R.x;
       st.at(k, pb) = -sg * R.y;
       break;
@@ -216,17 +228,12 @@ __device__ __forceinline__ void post_forward(const AxisPlan<T>& pl, const v2<T>*
   }
 }
 
-template <typename T>
-__device__ __forceinline__ int n_post_items(const AxisPlan<T>& pl) {
-  return pl.kind == K_DFT ? pl.n / 2 + 1 : pl.L;
-}
-
 // Inverse pre-processing: sequence value at index m for complex pencil pc.
-template <typename T>
+template <typename T, int KIND>
 __device__ __forceinline__ v2<T> pre_inverse(const AxisPlan<T>& pl, const Stage<T>& st, int pc, int m) {
   const int n = pl.n;
   const int pa = 2 * pc, pb = pa + 1;
-  switch (pl.kind) {
+  switch (KIND) {
     case K_DFT: {
       // halfcomplex rows -> spectra A (of a) and B (of b) at frequency m -> Z = A + i B
       T ax, ay, bx, by;
@@ -247,7 +254,7 @@ __device__ __forceinline__ v2<T> pre_inverse(const AxisPlan<T>& pl, const Stage<
     case K_DST1: {
       // DCT-I and DST-I are their own inverses up to 1/(2n)
       const int nn = n;
-      if (pl.kind == K_DCT1) {
+      if (KIND == K_DCT1) {
         const int j = (m <= nn) ? m : 2 * nn - m;
         return mk<T>(st.at(j, pa), st.at(j, pb));
       }
@@ -258,51 +265,113 @@ __device__ __forceinline__ v2<T> pre_inverse(const AxisPlan<T>& pl, const Stage<
     }
     default: {  // DCT-II (inverse of DCT3) / DST-II via DCT-II of (-1)^m Y_m
       if (m >= n) return mk<T>(T(0), T(0));
-      const T sg = (pl.kind == K_DST3 && (m & 1)) ? T(-1) : T(1);
+      const T sg = (KIND == K_DST3 && (m & 1)) ? T(-1) : T(1);
       return mk<T>(sg * st.at(m, pa), sg * st.at(m, pb));
     }
   }
 }
 
 // Inverse post-processing: output item j of complex pencil pc.
-template <typename T>
+template <typename T, int KIND, int PC>
 __device__ __forceinline__ void post_inverse(const AxisPlan<T>& pl, const v2<T>* buf, const Stage<T>& st,
-                                             int pc, int j, int PC, const v2<T>* qw) {
+                                             int pc, int j, const v2<T>* qw) {
+  using B = BufIx<PC>;
   const int n = pl.n;
   const int pa = 2 * pc, pb = pa + 1;
-  switch (pl.kind) {
+  switch (KIND) {
     case K_DFT: {  // j in [0, n)
-      const v2<T> R = buf[j * PC + pc];
+      const v2<T> R = buf[B::at(pc, j)];
       st.at(j, pa) = R.x;
       st.at(j, pb) = -R.y;
       break;
     }
     case K_DCT1: {  // j in [0, n]
-      const v2<T> Y = buf[j * PC + pc];
+      const v2<T> Y = buf[B::at(pc, j)];
       st.at(j, pa) = Y.x;
       st.at(j, pb) = Y.y;
       break;
     }
     case K_DST1: {  // output rows j in [0, n-2] <- bin j + 1
-      const v2<T> Z = buf[(j + 1) * PC + pc];
+      const v2<T> Z = buf[B::at(pc, j + 1)];
       st.at(j, pa) = -Z.y;
       st.at(j, pb) = Z.x;
       break;
     }
     default: {  // DCT-II item j in [0, n)
-      const v2<T> Zj = buf[j * PC + pc];
-      const v2<T> Zc = buf[((2 * n - j) % (2 * n)) * PC + pc];
+      const v2<T> Zj = buf[B::at(pc, j)];
+      const v2<T> Zc = buf[B::at(pc, (2 * n - j) % (2 * n))];
       const T ax = T(0.5) * (Zj.x + Zc.x), ay = T(0.5) * (Zj.y - Zc.y);
       const T dx = Zj.x - Zc.x, dy = Zj.y + Zc.y;
       const T bx = T(0.5) * dy, by = T(-0.5) * dx;
       const v2<T> w = qw[j];  // (cos, sin)(pi j / 2n)
       const T oa = T(2) * (ax * w.x + ay * w.y);
       const T ob = T(2) * (bx * w.x + by * w.y);
-      const int row = (pl.kind == K_DST3) ? (n - j) - 1 : j;  // DST-II: node n - j, row n - j - 1
+      const int row = (KIND == K_DST3) ? (n - j) - 1 : j;  // DST-II: node n - j, row n - j - 1
       st.at(row, pa) = oa;
       st.at(row, pb) = ob;
       break;
     }
+  }
+}
+
+// The pre- and post-processing loops of one CTA with the transform kind resolved
+// at compile time (one switch per CTA instead of one per element).
+template <typename T, int PC, int KIND>
+__device__ __forceinline__ void pre_loop(const AxisPlan<T>& pl, const Stage<T>& st, v2<T>* buf, const int16_t* perm,
+                                         const v2<T>* qw, bool inverse) {
+  using B = BufIx<PC>;
+  const int M = pl.M;
+  if (inverse) {
+    for (int idx = threadIdx.x; idx < M * PC; idx += blockDim.x) {
+      const int pc = idx % PC, m = idx / PC;
+      buf[B::at(pc, perm[m])] = pre_inverse<T, KIND>(pl, st, pc, m);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < M * PC; idx += blockDim.x) {
+      const int pc = idx % PC, m = idx / PC;
+      buf[B::at(pc, perm[m])] = pre_forward<T, KIND>(pl, st, pc, m, qw);
+    }
+  }
+}
+
+template <typename T, int PC, int KIND>
+__device__ __forceinline__ void post_loop(const AxisPlan<T>& pl, const Stage<T>& st, const v2<T>* buf,
+                                          const v2<T>* qw, bool inverse) {
+  if (inverse) {
+    for (int idx = threadIdx.x; idx < pl.L * PC; idx += blockDim.x) {
+      const int pc = idx % PC, j = idx / PC;
+      post_inverse<T, KIND, PC>(pl, buf, st, pc, j, qw);
+    }
+  } else {
+    const int nitems = KIND == K_DFT ? pl.n / 2 + 1 : pl.L;
+    for (int idx = threadIdx.x; idx < nitems * PC; idx += blockDim.x) {
+      const int pc = idx % PC, k = idx / PC;
+      post_forward<T, KIND, PC>(pl, buf, st, pc, k);
+    }
+  }
+}
+
+template <typename T, int PC>
+__device__ __forceinline__ void pre_dispatch(const AxisPlan<T>& pl, const Stage<T>& st, v2<T>* buf,
+                                             const int16_t* perm, const v2<T>* qw, bool inverse) {
+  switch (pl.kind) {
+    case K_DFT: pre_loop<T, PC, K_DFT>(pl, st, buf, perm, qw, inverse); break;
+    case K_DCT1: pre_loop<T, PC, K_DCT1>(pl, st, buf, perm, qw, inverse); break;
+    case K_DST1: pre_loop<T, PC, K_DST1>(pl, st, buf, perm, qw, inverse); break;
+    case K_DCT3: pre_loop<T, PC, K_DCT3>(pl, st, buf, perm, qw, inverse); break;
+    default: pre_loop<T, PC, K_DST3>(pl, st, buf, perm, qw, inverse); break;
+  }
+}
+
+template <typename T, int PC>
+__device__ __forceinline__ void post_dispatch(const AxisPlan<T>& pl, const Stage<T>& st, const v2<T>* buf,
+                                              const v2<T>* qw, bool inverse) {
+  switch (pl.kind) {
+    case K_DFT: post_loop<T, PC, K_DFT>(pl, st, buf, qw, inverse); break;
+    case K_DCT1: post_loop<T, PC, K_DCT1>(pl, st, buf, qw, inverse); break;
+    case K_DST1: post_loop<T, PC, K_DST1>(pl, st, buf, qw, inverse); break;
+    case K_DCT3: post_loop<T, PC, K_DCT3>(pl, st, buf, qw, inverse); break;
+    default: post_loop<T, PC, K_DST3>(pl, st, buf, qw, inverse); break;
   }
 }
 
@@ -407,15 +476,15 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(PassParams<T> P) {
 
   // ---- load: global -> staging (asynchronous copies, all in flight at once) ----
   if (AXIS == 0) {
-    for (int idx = threadIdx.x; idx < L * TP; idx += blockDim.x) {
-      const int j = idx % L;
-      const int p = idx / L;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int p = warp; p < TP; p += PASS_THREADS / 32) {
       if (p < npen) {
         const int r = row0 + p;
         const int y = r % N2, z = r / N2;
-        cp_async_elem<T>(&st.at(j, p), in + (long long)y * sy + (long long)z * sz + (long long)(lo + j) * estride);
+        const T* src = in + (long long)y * sy + (long long)z * sz + (long long)lo * estride;
+        for (int j = lane; j < L; j += 32) cp_async_elem<T>(&st.at(j, p), src + (long long)j * estride);
       } else {
-        st.at(j, p) = T(0);
+        for (int j = lane; j < L; j += 32) st.at(j, p) = T(0);
       }
     }
   } else {
@@ -432,27 +501,10 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(PassParams<T> P) {
 
   const bool inv_first = (P.inverse != 0) && !FUSED;
   // ---- forward (or the inverse when not fused) ----
-  for (int idx = threadIdx.x; idx < M * PC; idx += blockDim.x) {
-    const int pc = idx % PC;
-    const int m = idx / PC;
-    buf[perm[m] * PC + pc] = inv_first ? pre_inverse<T>(pl, st, pc, m) : pre_forward<T>(pl, st, pc, m, qw);
-  }
+  pre_dispatch<T, PC>(pl, st, buf, perm, qw, inv_first);
   __syncthreads();
   fft_stages<T, PC>(buf, pl, tw);
-  if (inv_first) {
-    for (int idx = threadIdx.x; idx < L * PC; idx += blockDim.x) {
-      const int pc = idx % PC;
-      const int j = idx / PC;
-      post_inverse<T>(pl, buf, st, pc, j, PC, qw);
-    }
-  } else {
-    const int nitems = n_post_items<T>(pl);
-    for (int idx = threadIdx.x; idx < nitems * PC; idx += blockDim.x) {
-      const int pc = idx % PC;
-      const int k = idx / PC;
-      post_forward<T>(pl, buf, st, pc, k, PC);
-    }
-  }
+  post_dispatch<T, PC>(pl, st, buf, qw, inv_first);
   __syncthreads();
 
   if (FUSED) {
@@ -467,18 +519,10 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(PassParams<T> P) {
       st.at(kz, p) *= g;
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < M * PC; idx += blockDim.x) {
-      const int pc = idx % PC;
-      const int m = idx / PC;
-      buf[perm[m] * PC + pc] = pre_inverse<T>(pl, st, pc, m);
-    }
+    pre_dispatch<T, PC>(pl, st, buf, perm, qw, true);
     __syncthreads();
     fft_stages<T, PC>(buf, pl, tw);
-    for (int idx = threadIdx.x; idx < L * PC; idx += blockDim.x) {
-      const int pc = idx % PC;
-      const int j = idx / PC;
-      post_inverse<T>(pl, buf, st, pc, j, PC, qw);
-    }
+    post_dispatch<T, PC>(pl, st, buf, qw, true);
     __syncthreads();
   }
 
@@ -488,13 +532,13 @@ __global__ void __launch_bounds__(PASS_THREADS) k_pass(PassParams<T> P) {
     const T* __restrict__ bh = P.base[q];
     const T* __restrict__ bl = P.base_lo[q];
     T* __restrict__ ol = P.out_lo[q];
-    for (int idx = threadIdx.x; idx < L * TP; idx += blockDim.x) {
-      const int j = idx % L;
-      const int p = idx / L;
-      if (p < npen) {
-        const int r = row0 + p;
-        const int y = r % N2, z = r / N2;
-        const long long at = (long long)y * sy + (long long)z * sz + (long long)(lo + j) * estride;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int p = warp; p < npen; p += PASS_THREADS / 32) {
+      const int r = row0 + p;
+      const int y = r % N2, z = r / N2;
+      const long long at0 = (long long)y * sy + (long long)z * sz + (long long)lo * estride;
+      for (int j = lane; j < L; j += 32) {
+        const long long at = at0 + (long long)j * estride;
         const T v = sc * st.at(j, p);
         if (bh == nullptr) {
           out[at] = v;
