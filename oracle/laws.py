@@ -13,6 +13,7 @@ G[r, i, q] = D_i u_q; the small strain is eps = (G + G^T)/2 and P = sigma
   of Sec. 3.2 with yield stress sigma_y + H p.
 * B0_LINEAR: P = 2 mu G + lambda G (.) I -- the B0 preconditioner itself
   (Sec. 2.6.3), a test law for which one fixed-point iteration is exact.
+* SVK_CUBIC, NEO_HOOKE, CP_FCC: finite-strain laws, in oracle/finite.py.
 """
 
 import numpy as np
@@ -21,6 +22,9 @@ ISO_ELASTIC = 0
 CUBIC_ELASTIC = 1
 J2_LINHARD = 2
 B0_LINEAR = 3
+SVK_CUBIC = 4
+NEO_HOOKE = 5
+CP_FCC = 6
 
 I3 = np.eye(3)
 
@@ -108,10 +112,16 @@ def stress(G, materials, groups, state=None):
     shp = G.shape
     Gf = G.reshape(npp, 3, 3, -1)
     P = np.zeros_like(Gf)
+    from . import finite
     new_state = None
     if state is not None:
-        new_state = {"ep": state["ep"].reshape(npp, 3, 3, -1).copy(),
-                     "p": state["p"].reshape(npp, -1).copy()}
+        new_state = {}
+        if "ep" in state:
+            new_state["ep"] = state["ep"].reshape(npp, 3, 3, -1).copy()
+            new_state["p"] = state["p"].reshape(npp, -1).copy()
+        if "Fp" in state:
+            new_state["Fp"] = state["Fp"].reshape(npp, 3, 3, -1).copy()
+            new_state["gam"] = state["gam"].reshape(npp, -1).copy()
     for ph, mat in enumerate(materials):
         idx = groups[ph]
         if idx.size == 0:
@@ -145,11 +155,34 @@ def stress(G, materials, groups, state=None):
             if new_state is not None:
                 new_state["ep"][..., idx] = ep
                 new_state["p"][..., idx] = p
+        elif mat.law == SVK_CUBIC:
+            P[..., idx] = finite.svk_cubic(Gv, mat.params, mat.quat)
+        elif mat.law == NEO_HOOKE:
+            P[..., idx] = finite.neo_hooke(Gv, mat.params)
+        elif mat.law == CP_FCC:
+            if state is None:
+                Fp_n = np.broadcast_to(I3[None, :, :, None], (npp, 3, 3, idx.size)).copy()
+                gam_n = np.zeros((npp, idx.size))
+            else:
+                Fp_n = new_state["Fp"][..., idx]
+                gam_n = new_state["gam"][..., idx]
+            S, Fp, gam = finite.cp_fcc(Gv, mat.params, mat.quat, Fp_n, gam_n)
+            P[..., idx] = S
+            if new_state is not None:
+                new_state["Fp"][..., idx] = Fp
+                new_state["gam"][..., idx] = gam
         else:
             raise ValueError(f"unknown law {mat.law}")
     P = P.reshape(shp)
     if new_state is not None:
-        new_state = {"ep": new_state["ep"].reshape(shp), "p": new_state["p"].reshape((npp,) + shp[3:])}
+        out = {}
+        if "ep" in new_state:
+            out["ep"] = new_state["ep"].reshape(shp)
+            out["p"] = new_state["p"].reshape((npp,) + shp[3:])
+        if "Fp" in new_state:
+            out["Fp"] = new_state["Fp"].reshape(shp)
+            out["gam"] = new_state["gam"].reshape((npp,) + shp[3:])
+        new_state = out
     return P, new_state
 
 

@@ -53,29 +53,35 @@ class Problem:
         self.fast = fast
         self.masks = [self.grid.dof_mask(q) for q in range(3)]
         self.factors = [green_factor(self.grid, q, wl.scheme, self.lambda0, self.mu0) for q in range(3)]
-        has_j2 = any(m.law == 2 for m in wl.materials)
         self.state = None
-        if has_j2:
-            shp = (self.npp,) + self.grid.n
+        shp = (self.npp,) + self.grid.n
+        if any(m.law == 2 for m in wl.materials):  # J2: (eps^p, p)
             self.state = {"ep": np.zeros((self.npp, 3, 3) + self.grid.n), "p": np.zeros(shp)}
+        if any(m.law == 6 for m in wl.materials):  # crystal plasticity: (F^p, Gamma)
+            self.state = self.state or {}
+            self.state["Fp"] = np.broadcast_to(np.eye(3)[None, :, :, None, None, None],
+                                               (self.npp, 3, 3) + self.grid.n).copy()
+            self.state["gam"] = np.zeros(shp)
         self.uf = np.zeros(self.grid.node_shape)
 
     # --- a0: prescribed displacement and its discrete gradient ------------------------
-    def ustar_full(self, A=None, b=None, B=None):
-        """u* on the full (n+1)^3 node grid: u*_q = A[q] . x + b[q] + B[q] x_1 x_2
-        (affine, plus the bilinear term of a bending load)."""
+    def ustar_full(self, A=None, b=None, Q=None):
+        """u* on the full (n+1)^3 node grid: u*_q = A[q] . x + b[q] + sum_k Q[q][k] m_k(x),
+        m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2) (affine plus the quadratic terms of
+        bending and torsion loads)."""
         A = self.wl.A if A is None else A
         b = self.wl.b if b is None else b
-        B = getattr(self.wl, "B", np.zeros(3)) if B is None else B
+        Q = getattr(self.wl, "Q", np.zeros((3, 6))) if Q is None else Q
         n, h = self.grid.n, self.grid.h
         x = [np.arange(n[a] + 1) * h[a] for a in range(3)]
         X = np.meshgrid(*x, indexing="ij")
-        return np.stack([A[q, 0] * X[0] + A[q, 1] * X[1] + A[q, 2] * X[2] + b[q] + B[q] * X[0] * X[1]
-                         for q in range(3)])
+        mono = [X[0] * X[0], X[1] * X[1], X[2] * X[2], X[1] * X[2], X[0] * X[2], X[0] * X[1]]
+        return np.stack([A[q, 0] * X[0] + A[q, 1] * X[1] + A[q, 2] * X[2] + b[q]
+                         + sum(Q[q][k] * mono[k] for k in range(6)) for q in range(3)])
 
-    def grad_ustar(self, A=None, b=None, B=None):
+    def grad_ustar(self, A=None, b=None, Q=None):
         """Discrete gradient of u* at the voxel points (the scheme's stencil on the node values)."""
-        return grad_full(self.ustar_full(A, b, B), self.grid, self.scheme)
+        return grad_full(self.ustar_full(A, b, Q), self.grid, self.scheme)
 
     # --- pieces of one iteration ------------------------------------------------------
     def residual(self, uf, Gs):
@@ -109,11 +115,11 @@ class Problem:
         return out
 
     # --- Algorithm 1, one load step -----------------------------------------------------
-    def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True, B=None):
+    def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True, Q=None):
         wl = self.wl
         tol = wl.tol if tol is None else tol
         max_iter = wl.max_iter if max_iter is None else max_iter
-        Gs = self.grad_ustar(A, b, B)
+        Gs = self.grad_ustar(A, b, Q)
         uf = self.uf.copy() if uf0 is None else np.array(uf0, dtype=np.float64)
         hist = []  # (q_j, g_j) couples
         q_prev = None

@@ -35,5 +35,6 @@ from .workloads import (  # noqa: F401
     y_laminate,
     iso_lame,
     bending_load,
+    torsion_bending_load,
     sphere_composite_bending,
 )

@@ -3,9 +3,10 @@
 A workload is plain data.  Boundary conditions are given per axis, face and
 displacement component as 'P' (periodic), 'D' (Dirichlet) or 'N' (Neumann);
 `bc[a][f][q]`, a = axis, f = 0 (face containing the origin) or 1, q = component.
-The prescribed displacement is u*_q(x) = sum_a A[q][a] x_a + b[q] + B[q] x_1 x_2,
-with x the physical coordinates of the nodes (node j on axis a at j*h_a); the
-bilinear term carries the bending loads.
+The prescribed displacement is u*_q(x) = sum_a A[q][a] x_a + b[q] + sum_k Q[q][k] m_k(x)
+with the quadratic monomials m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2) and x the
+physical coordinates of the nodes (node j on axis a at j*h_a); the quadratic terms
+carry bending and torsion loads.
 """
 
 from dataclasses import dataclass, field
@@ -21,12 +22,15 @@ ISO_ELASTIC = 0
 CUBIC_ELASTIC = 1
 J2_LINHARD = 2
 B0_LINEAR = 3  # P = 2 mu G + lambda G (.) I : the preconditioner itself (test law)
+SVK_CUBIC = 4  # finite strain: St-Venant-Kirchhoff, (C11, C12, C44), quat
+NEO_HOOKE = 5  # finite strain: (mu, K)
+CP_FCC = 6     # finite strain crystal plasticity: (C11, C12, C44, gdot0, n, tau0, tau_inf, h0, dt), quat
 
 
 @dataclass
 class Material:
     law: int
-    params: tuple  # ISO: (lambda, mu); CUBIC: (C11, C12, C44); J2: (lambda, mu, sigma_y, H); B0: (lambda, mu)
+    params: tuple  # ISO: (lambda, mu); CUBIC, SVK: (C11, C12, C44); J2: (lambda, mu, sigma_y, H); B0: (lambda, mu)
     quat: tuple = (1.0, 0.0, 0.0, 0.0)  # crystal -> sample rotation, (w, x, y, z)
 
 
@@ -46,7 +50,7 @@ class Workload:
     h: tuple = (1.0, 1.0, 1.0)
     A: np.ndarray = field(default_factory=lambda: np.zeros((3, 3)))
     b: np.ndarray = field(default_factory=lambda: np.zeros(3))
-    B: np.ndarray = field(default_factory=lambda: np.zeros(3))  # coefficient of x_1 x_2 in u*_q
+    Q: np.ndarray = field(default_factory=lambda: np.zeros((3, 6)))  # quadratic coefficients of u*_q
     anderson_depth: int = 4
     anderson_period: int = 3
     note: Optional[str] = None
@@ -136,13 +140,37 @@ def y_laminate(n=(6, 9, 4), period=3, E=(1.0, 5.0), nu=0.25, scheme="HEX1", eps=
 
 def bending_load(n, h, theta):
     """Rotation theta of the x = L_1 face about the mid-line x_2 = L_2 / 2 (x = 0 at rest):
-    u*_1 = (x_1 / L_1) theta (x_2 - L_2 / 2), u*_2 = u*_3 = 0.  Returns (A, b, B)."""
+    u*_1 = (x_1 / L_1) theta (x_2 - L_2 / 2), u*_2 = u*_3 = 0.  Returns (A, b, Q)."""
     L1, L2 = n[0] * h[0], n[1] * h[1]
     A = np.zeros((3, 3))
     A[0, 0] = -theta * L2 / (2.0 * L1)
-    B = np.zeros(3)
-    B[0] = theta / L1
-    return A, np.zeros(3), B
+    Q = np.zeros((3, 6))
+    Q[0, 5] = theta / L1  # x1 x2
+    return A, np.zeros(3), Q
+
+
+def rotation_e1_e3(phi, theta):
+    """R = R_3(theta) R_1(phi): rotation phi about e1 (torsion) then theta about e3 (bending)."""
+    c, s = np.cos(phi), np.sin(phi)
+    R1 = np.array([[1.0, 0.0, 0.0], [0.0, c, -s], [0.0, s, c]])
+    c, s = np.cos(theta), np.sin(theta)
+    R3 = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    return R3 @ R1
+
+
+def torsion_bending_load(n, h, phi, theta):
+    """x = 0 at rest; the x = L_1 face turned rigidly by R = R_3(theta) R_1(phi) about its centre
+    line (x2, x3) = (L2/2, L3/2), interpolated linearly in x1:
+    u*(x) = (x1 / L1) (R - 1) (0, x2 - L2/2, x3 - L3/2).  Returns (A, b, Q)."""
+    L1, L2, L3 = (n[a] * h[a] for a in range(3))
+    W = rotation_e1_e3(phi, theta) - np.eye(3)
+    A = np.zeros((3, 3))
+    Q = np.zeros((3, 6))
+    for q in range(3):
+        Q[q, 5] = W[q, 1] / L1  # x1 x2
+        Q[q, 4] = W[q, 2] / L1  # x1 x3
+        A[q, 0] = -(W[q, 1] * L2 / 2.0 + W[q, 2] * L3 / 2.0) / L1
+    return A, np.zeros(3), Q
 
 
 def sphere_composite_bending(n=128, fraction=0.30, r_min=4.0, r_max=10.0, seed=4, scheme="HEX1",
@@ -159,5 +187,5 @@ def sphere_composite_bending(n=128, fraction=0.30, r_min=4.0, r_max=10.0, seed=4
     wl = Workload(name=f"sphere_composite_bending_{nn[0]}", n=nn, phase=phase, materials=mats,
                   bc=axis_bc("D", "N", "N"), scheme=scheme, green="B0", lambda0=lam, mu0=mu, tol=tol)
     loads = [bending_load(nn, wl.h, k * theta_max / steps) for k in range(1, steps + 1)]
-    wl.A, wl.b, wl.B = loads[0]
+    wl.A, wl.b, wl.Q = loads[0]
     return wl, loads

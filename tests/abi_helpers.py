@@ -40,7 +40,7 @@ class GpuProblem:
             max_iter=wl.max_iter if max_iter is None else max_iter, h=wl.h,
             anderson_depth=wl.anderson_depth, anderson_period=wl.anderson_period)
         self.p = F.fftm_problem_create(self.ctx, desc)
-        F.fftm_set_load(self.p, wl.A, wl.b, wl.B)
+        F.fftm_set_load(self.p, wl.A, wl.b, wl.Q)
         self.N = tuple(wl.n[a] if wl.bc[a][0][0] == "P" else wl.n[a] + 1 for a in range(3))
         self.npp = 2 if wl.scheme == "TETRA2" else 1
 
@@ -55,8 +55,8 @@ class GpuProblem:
         F.fftm_get_field(self.p, field, out)
         return node_from_abi(out).astype(np.float64)
 
-    def set_load(self, A, b, B):
-        F.fftm_set_load(self.p, A, b, B)
+    def set_load(self, A, b, Q):
+        F.fftm_set_load(self.p, A, b, Q)
 
     def get_voxel(self, field):
         nc = {F.FFTM_FIELD_GRAD: 9, F.FFTM_FIELD_STATE: 7}.get(field, 6)

@@ -52,10 +52,10 @@ def test_j2_bending_steps_fp64_match_the_oracle(scheme):
     gp = GpuProblem(wl, "fp64")
     try:
         yielded = False
-        for k, (A, b, B) in enumerate(loads):
-            _, rep = pr.solve_step(A=A, b=b, B=B)
+        for k, (A, b, Q) in enumerate(loads):
+            _, rep = pr.solve_step(A=A, b=b, Q=Q)
             assert rep.converged
-            gp.set_load(A, b, B)
+            gp.set_load(A, b, Q)
             st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
             assert st == F.FFTM_OK and r["converged"]
             assert r["iterations"] == rep.iterations, (k, r["iterations"], rep.iterations)
@@ -83,10 +83,10 @@ def test_j2_bending_steps_fp32_vs_fp64_oracle(scheme):
     pr = Problem(wl)
     gp = GpuProblem(wl, "fp32")
     try:
-        for k, (A, b, B) in enumerate(loads):
-            _, rep = pr.solve_step(A=A, b=b, B=B)
+        for k, (A, b, Q) in enumerate(loads):
+            _, rep = pr.solve_step(A=A, b=b, Q=Q)
             assert rep.converged
-            gp.set_load(A, b, B)
+            gp.set_load(A, b, Q)
             st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
             assert r["converged"], (k, r)
             assert abs(r["iterations"] - rep.iterations) <= 2, (k, r["iterations"], rep.iterations)
@@ -120,7 +120,7 @@ def test_j2_bar_uniaxial_load_unload_on_the_gpu():
                 p += f / (E + H)
             A = np.zeros((3, 3))
             A[0, 0] = eps
-            gp.set_load(A, np.zeros(3), np.zeros(3))
+            gp.set_load(A, np.zeros(3), np.zeros((3, 6)))
             st, r, _, _ = F.fftm_solve_step(gp.p)
             assert st == F.FFTM_OK
             s11 = E * (eps - ep)
@@ -163,7 +163,7 @@ def test_invalid_j2_and_bending_inputs_are_rejected():
     gp = GpuProblem(wl, "fp64")
     try:
         with pytest.raises(F.FFTMError):
-            gp.set_load(np.zeros((3, 3)), np.zeros(3), np.array([1e-3, 0.0, 0.0]))  # x_2 is periodic
+            gp.set_load(np.zeros((3, 3)), np.zeros(3), np.array([[0, 0, 0, 0, 0, 1e-3], [0] * 6, [0] * 6]))  # x_2 periodic
         with pytest.raises(F.FFTMError):
             F.fftm_field_bytes(gp.p, F.FFTM_FIELD_STATE)  # no J2 phase
     finally:

@@ -148,24 +148,27 @@ def test_green_null_pattern():
             assert (f[k] == 0.0) == null, (scheme, k)
 
 
-def test_gradient_of_the_bilinear_bending_field_closed_form():
-    """u = x_1 x_2 on the node grid.  HEX1 (Eqs. D1HG-D3HG) averages over the voxel's
-    edges: D_1 u = x_2 and D_2 u = x_1 at the centre, D_3 u = 0.  TETRA2 (Eqs.
-    D1T1T2G-D3T1T2G) gives the same D_1 and D_2 and D_3 u = -+ h_1 h_2 / (2 h_3) on T1 / T2
-    (worked out by hand from the four corners of each tetrahedron)."""
+def test_gradient_of_quadratic_load_fields_closed_form():
+    """The monomials of a quadratic u* on the node grid.  Worked out by hand from the four
+    (TETRA2, Eqs. D1T1T2G-D3T1T2G) or eight (HEX1, Eqs. D1HG-D3HG) corners:
+    D_i (x_a^2) = 2 x_a delta_ia at the voxel centre for both schemes;
+    D_i (x_a x_b) = x_b delta_ia + x_a delta_ib, plus, on the third axis c, 0 for HEX1 and
+    -h_a h_b / (2 h_c) on T1, +h_a h_b / (2 h_c) on T2."""
     h = (0.7, 1.3, 0.9)
     n = (5, 4, 3)
     g = Grid(n, [[["P"] * 3] * 2] * 3, h)
     X = np.meshgrid(*[np.arange(n[a] + 1) * h[a] for a in range(3)], indexing="ij")
-    u = np.zeros((3,) + tuple(v + 1 for v in n))
-    u[1] = X[0] * X[1]  # component q = 1 only
-    xc = [(np.arange(n[a]) + 0.5) * h[a] for a in range(3)]
-    Xc = np.meshgrid(*xc, indexing="ij")
-    for scheme in ("HEX1", "TETRA2"):
-        G = grad_full(u, g, scheme)
-        assert np.abs(G[:, :, [0, 2]]).max() == 0.0
-        for r in range(G.shape[0]):
-            assert np.allclose(G[r, 0, 1], Xc[1], rtol=0, atol=1e-13)
-            assert np.allclose(G[r, 1, 1], Xc[0], rtol=0, atol=1e-13)
-            d3 = 0.0 if scheme == "HEX1" else (-1.0 if r == 0 else 1.0) * h[0] * h[1] / (2 * h[2])
-            assert np.allclose(G[r, 2, 1], d3, rtol=0, atol=1e-13)
+    Xc = np.meshgrid(*[(np.arange(n[a]) + 0.5) * h[a] for a in range(3)], indexing="ij")
+    pairs = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    for a, b in pairs:
+        u = np.zeros((3,) + tuple(v + 1 for v in n))
+        u[2] = X[a] * X[b]  # component q = 2 only
+        for scheme in ("HEX1", "TETRA2"):
+            G = grad_full(u, g, scheme)
+            assert np.abs(G[:, :, :2]).max() == 0.0
+            for r in range(G.shape[0]):
+                for i in range(3):
+                    expect = (Xc[b] if i == a else 0.0) + (Xc[a] if i == b else 0.0)
+                    if a != b and i not in (a, b) and scheme == "TETRA2":
+                        expect = expect + (-1.0 if r == 0 else 1.0) * h[a] * h[b] / (2 * h[i])
+                    assert np.allclose(G[r, i, 2], expect, rtol=0, atol=1e-12), (a, b, scheme, r, i)

@@ -130,9 +130,9 @@ def test_bending_load_matches_direct_sparse_solve(scheme):
     n = (8, 6, 5)
     ph = syn.random_spheres(n, 0.3, 1.0, 2.0, 11)
     mats = [Material(0, syn.iso_lame(1.0, 0.3)), Material(0, syn.iso_lame(4.0, 0.25))]
-    A, b, B = syn.bending_load(n, (1.0, 1.0, 1.0), 0.01)
+    A, b, Q = syn.bending_load(n, (1.0, 1.0, 1.0), 0.01)
     wl = Workload("t7b", n, ph, mats, axis_bc("D", "N", "N"), scheme=scheme, lambda0=1.6, mu0=1.0,
-                  tol=1e-12, A=A, b=b, B=B, max_iter=3000)
+                  tol=1e-12, A=A, b=b, Q=Q, max_iter=3000)
     pr = Problem(wl)
     uf, rep = pr.solve_step()
     assert rep.converged
