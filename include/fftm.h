@@ -30,7 +30,10 @@
  *   index = x + n1*(y + n2*(z + n3*(c + nc*r))), r = voxel point (HEX1: one
  *   point; TETRA2: r = 0 tetrahedron T1, r = 1 tetrahedron T2), c = tensor
  *   component.  Gradients use G[i][q] = D_i u_q (c = 3 i + q); symmetric
- *   stresses use c = 0..5 for (11, 22, 33, 23, 13, 12).
+ *   stresses use c = 0..5 for (11, 22, 33, 23, 13, 12).  A problem with a
+ *   finite-strain law or FFTM_LAW_B0_LINEAR has non-symmetric stresses, stored
+ *   with 9 components c = 3 i + q holding P_qi (P the first Piola-Kirchhoff
+ *   stress, (div P)_q = d P_qi / d x_i).
  * - Field element type = the problem's precision (double for FFTM_FP64,
  *   float for FFTM_FP32).
  */
@@ -69,7 +72,14 @@ enum fftm_law {
                                  (yield stress sigma_y + H p), radial return from
                                  the committed state (Sec. 3.2); the state is
                                  committed when a load step converges           */
-  FFTM_LAW_B0_LINEAR = 3      /* params: lambda, mu: P = 2 mu G + lambda G.*I  */
+  FFTM_LAW_B0_LINEAR = 3,     /* params: lambda, mu: P = 2 mu G + lambda G.*I  */
+  FFTM_LAW_SVK_CUBIC = 4,     /* finite strain, F = 1 + grad u: second Piola-
+                                 Kirchhoff Pi = C : E, E = (F^T F - 1)/2, C cubic
+                                 (params C11, C12, C44; quat), P = F Pi
+                                 (Sec. 3.1.2)                                   */
+  FFTM_LAW_NEO_HOOKE = 5      /* finite strain, params mu, K: psi = mu/2 (J^(-2/3)
+                                 tr(F^T F) - 3) + K/2 (J - 1)^2, P = F dpsi/dE
+                                 (Appendix B)                                   */
 };
 
 /* ---- descriptors ------------------------------------------------------ */
@@ -102,15 +112,18 @@ typedef struct fftm_problem_desc {
   int anderson_period;       /* accelerate when m % period == period - 1     */
 } fftm_problem_desc;
 
-/* Prescribed displacement u*_q(x) = sum_a A[q][a] x_a + b[q] + B[q] x_1 x_2,
+/* Prescribed displacement
+     u*_q(x) = sum_a A[q][a] x_a + b[q] + sum_k Q[q][k] m_k(x),
+     m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2),
    x = physical node coordinates (node j of axis a at j*h_a).  u* supplies the
    Dirichlet values (Sec. 2.2); it must not depend on a periodic coordinate
-   (FFTM_E_INVALID).  The bilinear term carries bending loads (a face rotation
-   that grows along x_1); its discrete gradient is exact at the voxel points. */
+   (FFTM_E_INVALID).  The quadratic terms carry bending and torsion loads (face
+   rotations that grow along an axis); their discrete gradients are applied in
+   closed form at the voxel points. */
 typedef struct fftm_load {
   double A[3][3];
   double b[3];
-  double B[3];
+  double Q[3][6];
 } fftm_load;
 
 typedef struct fftm_step_report {
@@ -169,7 +182,8 @@ enum fftm_field {
   FFTM_FIELD_U = 0,      /* u^f, node field (3 comps)                           */
   FFTM_FIELD_WORK = 1,   /* the p / spectral work field, node layout (3 comps)   */
   FFTM_FIELD_GRAD = 2,   /* total gradient G at voxel points (9 comps)           */
-  FFTM_FIELD_STRESS = 3, /* stress P at voxel points (6 comps)                   */
+  FFTM_FIELD_STRESS = 3, /* stress at voxel points (6 comps, or 9 for problems
+                            with non-symmetric stresses, see the layout above)  */
   FFTM_FIELD_D = 4,      /* residual D = div P at the nodes (3 comps), dismissed
                             node components 0; written by FFTM_OP_RESIDUAL       */
   FFTM_FIELD_STATE = 5   /* committed J2 state at voxel points (7 comps: eps^p

@@ -511,14 +511,16 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   R.vs = reinterpret_cast<T*>(p->vs);
   R.sym = p->sym;
   R.state = reinterpret_cast<T*>(p->state);
-  R.bend = 0;
-  R.dbend = 0;
+  R.quad = 0;
+  R.dquad = 0;
   for (int q = 0; q < 3; ++q) {
-    R.Bq[q] = T(p->load.B[q]);
-    R.bend |= p->load.B[q] != 0.0;
-    const double dB = p->load.B[q] - p->load_n.B[q];
-    R.dBq[q] = T(dB);
-    R.dbend |= dB != 0.0;
+    for (int k = 0; k < 6; ++k) {
+      R.Qc[q][k] = T(p->load.Q[q][k]);
+      R.quad |= p->load.Q[q][k] != 0.0;
+      const double dq = p->load.Q[q][k] - p->load_n.Q[q][k];
+      R.dQ[q][k] = T(dq);
+      R.dquad |= dq != 0.0;
+    }
     R.un[q] = p->un ? reinterpret_cast<const T*>(p->un) + q * p->comp_stride : nullptr;
     R.unlo[q] = (p->un && lo) ? reinterpret_cast<const T*>(p->un) + (3 + q) * p->comp_stride : nullptr;
   }
@@ -535,9 +537,13 @@ ResParams<T> commit_params(fftm_problem* p) {
   for (int q = 0; q < 3; ++q) {
     R.u[q] = R.un[q];
     R.ulo[q] = R.unlo[q];
-    R.Bq[q] = T(p->load_n.B[q]);
   }
-  R.bend = p->load_n.B[0] != 0.0 || p->load_n.B[1] != 0.0 || p->load_n.B[2] != 0.0;
+  R.quad = 0;
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < 6; ++k) {
+      R.Qc[q][k] = T(p->load_n.Q[q][k]);
+      R.quad |= p->load_n.Q[q][k] != 0.0;
+    }
   for (int i = 0; i < 3; ++i)
     for (int q = 0; q < 3; ++q) R.Gs[i * 3 + q] = T(p->load_n.A[q][i]);
   return R;
@@ -764,8 +770,10 @@ int validate(const fftm_problem_desc* d) {
   for (int i = 0; i < d->n_phases; ++i) {
     const int law = d->materials[i].law;
     if (law != FFTM_LAW_ISO_ELASTIC && law != FFTM_LAW_CUBIC_ELASTIC && law != FFTM_LAW_B0_LINEAR &&
-        law != FFTM_LAW_J2_LINHARD)
+        law != FFTM_LAW_J2_LINHARD && law != FFTM_LAW_SVK_CUBIC && law != FFTM_LAW_NEO_HOOKE)
       return set_err(FFTM_E_INVALID, "unknown law");
+    if (law == FFTM_LAW_NEO_HOOKE && !(d->materials[i].params[0] > 0.0 && d->materials[i].params[1] > 0.0))
+      return set_err(FFTM_E_INVALID, "Neo-Hookean needs mu > 0 and K > 0");
     if (law == FFTM_LAW_J2_LINHARD) {
       const double* c = d->materials[i].params;
       if (!(c[1] > 0.0) || !(3.0 * c[0] + 2.0 * c[1] > 0.0) || !(c[2] > 0.0) || !(c[3] >= 0.0))
@@ -957,8 +965,10 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
     return set_err(FFTM_E_NOMEM, "device allocation of the fields failed");
   }
   CU(cudaMemsetAsync(p->fields, 0, sz.fields, s));
-  for (int i = 0; i < desc->n_phases; ++i)
-    if (desc->materials[i].law == FFTM_LAW_B0_LINEAR) p->sym = 0;
+  for (int i = 0; i < desc->n_phases; ++i) {
+    const int law = desc->materials[i].law;
+    if (law == FFTM_LAW_B0_LINEAR || law == FFTM_LAW_SVK_CUBIC || law == FFTM_LAW_NEO_HOOKE) p->sym = 0;
+  }
   CU(cudaMalloc(&p->vs, (size_t)(p->tetra ? 2 : 1) * (p->sym ? 6 : 9) * p->nvox * p->esz));
   for (int i = 0; i < desc->n_phases; ++i)
     if (desc->materials[i].law == FFTM_LAW_J2_LINHARD && !p->state) {
@@ -1046,7 +1056,7 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
     const fftm_material& m = desc->materials[i];
     lid[i] = m.law;
     double* c = &lc[(size_t)i * LAWC];
-    if (m.law == FFTM_LAW_CUBIC_ELASTIC) {
+    if (m.law == FFTM_LAW_CUBIC_ELASTIC || m.law == FFTM_LAW_SVK_CUBIC) {
       double R[3][3], Cm[6][6];
       quat_rot(m.quat, R);
       cubic_mandel(m.params[0], m.params[1], m.params[2], R, Cm);
@@ -1087,8 +1097,13 @@ int fftm_set_load(fftm_problem* p, const fftm_load* load) {
   for (int a = 0; a < 3; ++a)
     if (p->periodic[a])
       for (int q = 0; q < 3; ++q)
-        if (load->A[q][a] != 0.0 || (a < 2 && load->B[q] != 0.0))
-          return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
+        if (load->A[q][a] != 0.0) return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
+  // quadratic monomials x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2 and the axes they contain
+  static const int mono_axes[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+  for (int q = 0; q < 3; ++q)
+    for (int k = 0; k < 6; ++k)
+      if (load->Q[q][k] != 0.0 && (p->periodic[mono_axes[k][0]] || p->periodic[mono_axes[k][1]]))
+        return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
   p->load = *load;
   return FFTM_OK;
 }
@@ -1110,7 +1125,7 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes) {
     case FFTM_FIELD_WORK:
     case FFTM_FIELD_D: *bytes = 3 * nodes * p->esz; return FFTM_OK;
     case FFTM_FIELD_GRAD: *bytes = 9 * npp * p->nvox * p->esz; return FFTM_OK;
-    case FFTM_FIELD_STRESS: *bytes = 6 * npp * p->nvox * p->esz; return FFTM_OK;
+    case FFTM_FIELD_STRESS: *bytes = (p->sym ? 6 : 9) * npp * p->nvox * p->esz; return FFTM_OK;
     case FFTM_FIELD_STATE:
       if (!p->state) return set_err(FFTM_E_INVALID, "the problem has no J2 phase (no state)");
       *bytes = 7 * npp * p->nvox * p->esz;

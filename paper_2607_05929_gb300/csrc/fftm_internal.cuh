@@ -77,8 +77,8 @@ struct ResParams {
   long long sy, sz;  // node strides (x stride 1)
   long long vy, vz;  // voxel strides
   T Gs[9];           // uniform gradient of the affine part of u*
-  int bend;          // 1 if u* has the bilinear term B_q x_1 x_2
-  T Bq[3];           // its coefficients
+  int quad;          // 1 if u* has quadratic terms
+  T Qc[3][6];        // their coefficients: x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2
   T hh[3];           // voxel sizes
   // J2 phases are evaluated incrementally from the last commit: the state holds the
   // elastic strain e_n (11,22,33,23,13,12) and p_n per voxel point [r][7][voxel], and
@@ -87,8 +87,8 @@ struct ResParams {
   const T* un[3];    // u^f at the last commit (high part in FP32)
   const T* unlo[3];  // its low part (FP32 only)
   T dGs[9];          // gradient of the affine part of u* - u*_n
-  int dbend;         // 1 if the bilinear part of u* - u*_n is non-zero
-  T dBq[3];          // its coefficients
+  int dquad;         // 1 if the quadratic part of u* - u*_n is non-zero
+  T dQ[3][6];        // its coefficients
   // Incremental residual (J2 problems after their first commit): k_stress stores the
   // stress increment P - P_n and k_div adds D_n = div P_n, the residual at the commit,
   // so that FP32 rounding scales with the increment instead of the stress.
@@ -104,7 +104,7 @@ struct ResParams {
   double* partial;   // per block: S_D, S_P
 };
 
-constexpr int LAWC = 24;
+constexpr int LAWC = 40;
 
 // One axis pass as a dense contraction on the tensor cores (FP32 data, BF16
 // matrices).  A: the Kp x Kp (zero-padded) transform matrix, row-major BF16
@@ -163,7 +163,7 @@ template <typename T>
 cudaError_t launch_commit(const ResParams<T>& P, int tetra, cudaStream_t s);
 // The committed state as (eps^p, p) = (sym G_n - e_n, p_n) (out != null), or the
 // elastic strain e_n = sym G_n - eps^p from a given (eps^p, p) (in != null); G_n is
-// the total gradient at the commit, from P.u = u^f_n and P.Gs, P.Bq = the load at
+// the total gradient at the commit, from P.u = u^f_n and P.Gs, P.Qc = the load at
 // the commit.  Dense layout [r][7][voxel]; zero outside J2 voxels.
 template <typename T>
 cudaError_t launch_state_io(const ResParams<T>& P, int tetra, T* out, const T* in, cudaStream_t s);

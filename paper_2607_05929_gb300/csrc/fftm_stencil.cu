@@ -36,7 +36,96 @@
 
 namespace fftm {
 
-enum { LAW_ISO = 0, LAW_CUBIC = 1, LAW_J2 = 2, LAW_B0 = 3 };
+enum { LAW_ISO = 0, LAW_CUBIC = 1, LAW_J2 = 2, LAW_B0 = 3, LAW_SVK = 4, LAW_NEOHOOKE = 5, LAW_CP = 6 };
+
+// Symmetric tensor (11, 22, 33, 23, 13, 12) -> C : E with the Mandel 6x6 stiffness stored as
+// its upper triangle row-major in c[0..20].
+template <typename T>
+__device__ __forceinline__ void mandel_apply(const T* __restrict__ c, const T e[6], T s[6]) {
+  const T r2 = T(1.41421356237309504880), ir2 = T(0.70710678118654752440);
+  const T em[6] = {e[0], e[1], e[2], r2 * e[3], r2 * e[4], r2 * e[5]};
+  T sm[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  int k = 0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int b = a; b < 6; ++b) {
+      const T v = __ldg(c + k++);
+      sm[a] += v * em[b];
+      if (b != a) sm[b] += v * em[a];
+    }
+  s[0] = sm[0];
+  s[1] = sm[1];
+  s[2] = sm[2];
+  s[3] = ir2 * sm[3];
+  s[4] = ir2 * sm[4];
+  s[5] = ir2 * sm[5];
+}
+
+// Finite strain (Sec. 3.1.2, Appendix B): F = 1 + H with H_qi = G[i*3+q]; the
+// Green-Lagrange strain E = (H + H^T + H^T H) / 2 is formed from H so that it keeps
+// its relative precision.  S[i*3+q] = P_qi with P = F Pi.
+template <typename T>
+__device__ __forceinline__ void green_lagrange(const T G[9], T H[3][3], T E[6]) {
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) H[q][i] = G[i * 3 + q];
+  auto e = [&](int i, int j) {
+    return T(0.5) * (H[i][j] + H[j][i] + H[0][i] * H[0][j] + H[1][i] * H[1][j] + H[2][i] * H[2][j]);
+  };
+  E[0] = e(0, 0);
+  E[1] = e(1, 1);
+  E[2] = e(2, 2);
+  E[3] = e(1, 2);
+  E[4] = e(0, 2);
+  E[5] = e(0, 1);
+}
+
+template <typename T>
+__device__ __forceinline__ void first_piola(const T H[3][3], const T Pi[6], T S[9]) {
+  const T M[3][3] = {{Pi[0], Pi[5], Pi[4]}, {Pi[5], Pi[1], Pi[3]}, {Pi[4], Pi[3], Pi[2]}};
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) S[i * 3 + q] = M[q][i] + H[q][0] * M[0][i] + H[q][1] * M[1][i] + H[q][2] * M[2][i];
+}
+
+// Neo-Hookean (Appendix B): Pi = mu J^(-2/3) dev(C) C^-1 + K (J - 1) J C^-1 with C = 1 + 2E,
+// J - 1 = tr H + ((tr H)^2 - tr(H^2)) / 2 + det H; c = (mu, K).
+template <typename T>
+__device__ __forceinline__ void neo_hooke(const T* __restrict__ c, const T G[9], T S[9]) {
+  const T mu = __ldg(c), K = __ldg(c + 1);
+  T H[3][3], E[6];
+  green_lagrange<T>(G, H, E);
+  const T trH = H[0][0] + H[1][1] + H[2][2];
+  T trH2 = T(0);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) trH2 += H[i][j] * H[j][i];
+  const T detH = H[0][0] * (H[1][1] * H[2][2] - H[1][2] * H[2][1]) - H[0][1] * (H[1][0] * H[2][2] - H[1][2] * H[2][0]) +
+                 H[0][2] * (H[1][0] * H[2][1] - H[1][1] * H[2][0]);
+  const T Jm1 = trH + T(0.5) * (trH * trH - trH2) + detH;
+  const T J = T(1) + Jm1;
+  // C = 1 + 2E and its inverse (adjugate / det C, det C = J^2)
+  const T C00 = T(1) + T(2) * E[0], C11 = T(1) + T(2) * E[1], C22 = T(1) + T(2) * E[2];
+  const T C12 = T(2) * E[3], C02 = T(2) * E[4], C01 = T(2) * E[5];
+  const T ij2 = T(1) / (J * J);
+  const T I00 = (C11 * C22 - C12 * C12) * ij2, I11 = (C00 * C22 - C02 * C02) * ij2, I22 = (C00 * C11 - C01 * C01) * ij2;
+  const T I12 = (C02 * C01 - C00 * C12) * ij2, I02 = (C01 * C12 - C02 * C11) * ij2, I01 = (C02 * C12 - C01 * C22) * ij2;
+  const T Ci[3][3] = {{I00, I01, I02}, {I01, I11, I12}, {I02, I12, I22}};
+  const T tE = (E[0] + E[1] + E[2]) * T(2.0 / 3.0);
+  const T Dv[3][3] = {{T(2) * E[0] - tE, T(2) * E[5], T(2) * E[4]},
+                      {T(2) * E[5], T(2) * E[1] - tE, T(2) * E[3]},
+                      {T(2) * E[4], T(2) * E[3], T(2) * E[2] - tE}};
+  const T a = mu * exp(T(-2.0 / 3.0) * log1p(Jm1)), b = K * Jm1 * J;
+  auto pi = [&](int i, int j) {
+    return a * (Dv[i][0] * Ci[0][j] + Dv[i][1] * Ci[1][j] + Dv[i][2] * Ci[2][j]) + b * Ci[i][j];
+  };
+  const T Pi[6] = {pi(0, 0), pi(1, 1), pi(2, 2), pi(1, 2), pi(0, 2), pi(0, 1)};
+  first_piola<T>(H, Pi, S);
+}
 
 // Small-strain law on the total gradient G[i*3+q]; P returned as 9 components.
 template <typename T>
@@ -66,6 +155,13 @@ __device__ __forceinline__ void law_eval(int law, const T* __restrict__ c, const
     Pout[5] = Pout[7] = ir2 * sm[3];
     Pout[2] = Pout[6] = ir2 * sm[4];
     Pout[1] = Pout[3] = ir2 * sm[5];
+  } else if (law == LAW_SVK) {  // St-Venant-Kirchhoff, Pi = C : E (Sec. 3.1.2)
+    T H[3][3], E[6], Pi[6];
+    green_lagrange<T>(G, H, E);
+    mandel_apply<T>(c, E, Pi);
+    first_piola<T>(H, Pi, Pout);
+  } else if (law == LAW_NEOHOOKE) {
+    neo_hooke<T>(c, G, Pout);
   } else if (law == LAW_B0) {
     const T lam = __ldg(c), mu2 = T(2) * __ldg(c + 1);
 #pragma unroll
@@ -160,19 +256,22 @@ __device__ __forceinline__ void point_law(const ResParams<T>& P, int law, const 
   }
 }
 
-// Bilinear part B_q x_1 x_2 of u*: its discrete gradient at voxel (vx, vy, .), point r,
-// is x_2 (D_1) and x_1 (D_2) at the voxel centre for both schemes; D_3 is 0 for HEX1
-// and -h_1 h_2 / (2 h_3) on T1, +h_1 h_2 / (2 h_3) on T2 (the four corners of each
-// tetrahedron in Eqs. D1T1T2G-D3T1T2G applied to x_1 x_2).
+// Quadratic part sum_k Q_qk m_k of u*, m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2): its
+// discrete gradient at voxel (vx, vy, vz), point r, worked out from the stencils'
+// corners: D_i (x_a^2) = 2 x_a delta_ia at the voxel centre (both schemes);
+// D_i (x_a x_b) = x_b delta_ia + x_a delta_ib, plus on the third axis c 0 for HEX1
+// and -h_a h_b / (2 h_c) on T1, +h_a h_b / (2 h_c) on T2 (Eqs. D1HG-D3HG, D1T1T2G-D3T1T2G).
 template <typename T, int TETRA>
-__device__ __forceinline__ void add_bend(const T hh[3], const T Bq[3], int r, int vx, int vy, T G[9]) {
-  const T x1 = (T(vx) + T(0.5)) * hh[0], x2 = (T(vy) + T(0.5)) * hh[1];
-  const T d3 = TETRA ? (r == 0 ? T(-0.5) : T(0.5)) * hh[0] * hh[1] / hh[2] : T(0);
+__device__ __forceinline__ void add_quad(const T hh[3], const T Q[3][6], int r, int vx, int vy, int vz, T G[9]) {
+  const T x0 = (T(vx) + T(0.5)) * hh[0], x1 = (T(vy) + T(0.5)) * hh[1], x2 = (T(vz) + T(0.5)) * hh[2];
+  const T sg = TETRA ? (r == 0 ? T(-0.5) : T(0.5)) : T(0);
+  const T k23 = sg * hh[1] * hh[2] / hh[0], k13 = sg * hh[0] * hh[2] / hh[1], k12 = sg * hh[0] * hh[1] / hh[2];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
-    G[q] += Bq[q] * x2;
-    G[3 + q] += Bq[q] * x1;
-    G[6 + q] += Bq[q] * d3;
+    const T a = Q[q][0], b = Q[q][1], c = Q[q][2], d = Q[q][3], e = Q[q][4], f = Q[q][5];
+    G[q] += T(2) * a * x0 + e * x2 + f * x1 + d * k23;
+    G[3 + q] += T(2) * b * x1 + d * x2 + f * x0 + e * k13;
+    G[6 + q] += T(2) * c * x2 + d * x1 + e * x0 + f * k12;
   }
 }
 
@@ -203,16 +302,16 @@ __device__ __forceinline__ void point_grad(const T uh[3][8], const T ul[3][8], i
 // (for J2 voxels the caller has already subtracted u^f_n from them).
 template <typename T, int TETRA, bool LO>
 __device__ __forceinline__ void law_grad(const ResParams<T>& P, bool j2, const T uh[3][8], const T ul[3][8], int r,
-                                         int vx, int vy, T Gf[9], T Gt[9]) {
+                                         int vx, int vy, int vz, T Gf[9], T Gt[9]) {
   point_grad<T, TETRA, LO>(uh, ul, r, P.wgrad, Gf);
   if (j2) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.dGs[i];
-    if (P.dbend) add_bend<T, TETRA>(P.hh, P.dBq, r, vx, vy, Gt);
+    if (P.dquad) add_quad<T, TETRA>(P.hh, P.dQ, r, vx, vy, vz, Gt);
   } else {
 #pragma unroll
     for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
-    if (P.bend) add_bend<T, TETRA>(P.hh, P.Bq, r, vx, vy, Gt);
+    if (P.quad) add_quad<T, TETRA>(P.hh, P.Qc, r, vx, vy, vz, Gt);
   }
 }
 
@@ -346,7 +445,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
 #pragma unroll
       for (int r = 0; r < NPP; ++r) {
         T Gf[9], Gt[9], Pp[9];
-        law_grad<T, TETRA, LO>(P, j2, uh, ul, r, vx, vy_, Gf, Gt);
+        law_grad<T, TETRA, LO>(P, j2, uh, ul, r, vx, vy_, vz, Gf, Gt);
         if (J2) point_law<T>(P, law, lc, Gt, r, v, nvox, Pp, nullptr);
         else law_eval<T>(law, lc, Gt, Pp);
         T* base = P.vs + (size_t)(r * NCT) * nvox + v;
@@ -444,7 +543,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress_inc(ResParams<T> P, TileId
 #pragma unroll
         for (int r = 0; r < NPP; ++r) {
           T Gf[9], Gt[9], Pp[9];
-          law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy_, Gf, Gt);
+          law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy_, vz, Gf, Gt);
           law_eval<T>(law, lc, Gt, Pp);
 #pragma unroll
           for (int c = 0; c < 9; ++c) spv += Pp[c] * Pp[c];
@@ -460,7 +559,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress_inc(ResParams<T> P, TileId
 #pragma unroll
       for (int r = 0; r < NPP; ++r) {
         T Gd[9], dG[9], dP[9];
-        law_grad<T, TETRA, LO>(P, true, uh, ul, r, vx, vy_, Gd, dG);
+        law_grad<T, TETRA, LO>(P, true, uh, ul, r, vx, vy_, vz, Gd, dG);
         if (j2) {
           const T* stp = P.state + (long long)(r * 7) * nvox + v;
           T st[7], Pf[9];
@@ -769,7 +868,7 @@ __device__ __forceinline__ int voxel_eval(const ResParams<T>& P, long long v, T 
 #pragma unroll
   for (int r = 0; r < (TETRA ? 2 : 1); ++r) {
     T Gf[9];
-    law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy, Gf, Gt_out[r]);  // total gradient (reported)
+    law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy, vz, Gf, Gt_out[r]);  // total gradient (reported)
     if (j2) {
       T du[3][8], dl[3][8], Gd[9], Ginc[9];
 #pragma unroll
@@ -779,7 +878,7 @@ __device__ __forceinline__ int voxel_eval(const ResParams<T>& P, long long v, T 
           du[c][o] = uh[c][o] - nh[c][o];
           dl[c][o] = ul[c][o] - nl[c][o];
         }
-      law_grad<T, TETRA, LO>(P, true, du, dl, r, vx, vy, Gd, Ginc);
+      law_grad<T, TETRA, LO>(P, true, du, dl, r, vx, vy, vz, Gd, Ginc);
       point_law<T>(P, law, lc, Ginc, r, v, (long long)n1 * n2 * n3, P_out[r], stn ? stn[r] : nullptr);
     } else {
       point_law<T>(P, law, lc, Gt_out[r], r, v, (long long)n1 * n2 * n3, P_out[r], nullptr);
@@ -851,7 +950,7 @@ __global__ void k_state_io(ResParams<T> P, T* __restrict__ out, const T* __restr
 #pragma unroll
     for (int r = 0; r < (TETRA ? 2 : 1); ++r) {
       T Gf[9], G[9];
-      law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy, Gf, G);
+      law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy, vz, Gf, G);
       const T es[6] = {G[0], G[4], G[8], T(0.5) * (G[5] + G[7]), T(0.5) * (G[2] + G[6]), T(0.5) * (G[1] + G[3])};
       T* st = P.state + v + nv * (7 * r);
       if (out) {
@@ -895,10 +994,13 @@ __global__ void k_voxel_fields(ResParams<T> P, T* __restrict__ gout, T* __restri
 #pragma unroll
         for (int i = 0; i < 9; ++i) gout[v + nv * (i + 9 * r)] = Gt[r][i];
       }
-      if (sout) {
+      if (sout && P.sym) {
         const int map[6] = {0, 4, 8, 5, 2, 1};  // 11, 22, 33, 23, 13, 12
 #pragma unroll
         for (int c = 0; c < 6; ++c) sout[v + nv * (c + 6 * r)] = Pp[r][map[c]];
+      } else if (sout) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) sout[v + nv * (c + 9 * r)] = Pp[r][c];
       }
     }
   }

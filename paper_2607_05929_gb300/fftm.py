@@ -61,7 +61,7 @@ class fftm_problem_desc(ctypes.Structure):
 
 
 class fftm_load(ctypes.Structure):
-    _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3), ("B", ctypes.c_double * 3)]
+    _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3), ("Q", (ctypes.c_double * 6) * 3)]
 
 
 class fftm_step_report(ctypes.Structure):
@@ -216,13 +216,15 @@ def fftm_set_phase_raw(p, host_ptr):
                                                                 ctypes.POINTER(ctypes.c_uint16))))
 
 
-def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), B=(0.0, 0.0, 0.0)):
+def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None):
+    """u*_q = A[q] . x + b[q] + sum_k Q[q][k] m_k(x), m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2)."""
     ld = fftm_load()
     for q in range(3):
         for a in range(3):
             ld.A[q][a] = float(A[q][a])
         ld.b[q] = float(b[q])
-        ld.B[q] = float(B[q])
+        for k in range(6):
+            ld.Q[q][k] = 0.0 if Q is None else float(Q[q][k])
     return _check(load_library().fftm_set_load(p, ctypes.byref(ld)))
 
 

@@ -59,8 +59,8 @@ class GpuProblem:
         F.fftm_set_load(self.p, A, b, Q)
 
     def get_voxel(self, field):
-        nc = {F.FFTM_FIELD_GRAD: 9, F.FFTM_FIELD_STATE: 7}.get(field, 6)
         n = self.wl.n
+        nc = F.fftm_field_bytes(self.p, field) // (np.dtype(self.dtype).itemsize * self.npp * n[0] * n[1] * n[2])
         out = np.zeros(self.npp * nc * n[0] * n[1] * n[2], dtype=self.dtype)
         F.fftm_get_field(self.p, field, out)
         return voxel_from_abi(out, self.npp, nc, n).astype(np.float64)
