@@ -77,15 +77,24 @@ enum fftm_law {
                                  Kirchhoff Pi = C : E, E = (F^T F - 1)/2, C cubic
                                  (params C11, C12, C44; quat), P = F Pi
                                  (Sec. 3.1.2)                                   */
-  FFTM_LAW_NEO_HOOKE = 5      /* finite strain, params mu, K: psi = mu/2 (J^(-2/3)
+  FFTM_LAW_NEO_HOOKE = 5,     /* finite strain, params mu, K: psi = mu/2 (J^(-2/3)
                                  tr(F^T F) - 3) + K/2 (J - 1)^2, P = F dpsi/dE
                                  (Appendix B)                                   */
+  FFTM_LAW_CP_FCC = 6         /* finite-strain FCC crystal plasticity (Sec. 3.4):
+                                 F = F^e F^p, Pi = C : E^e (cubic C11, C12, C44,
+                                 quat = lattice orientation), 12 {111}<110>
+                                 systems, gdot_s = gdot0 |tau_s/tau_c|^n sign,
+                                 Voce tau_c(Gamma) = tau0 + (tau_inf - tau0)
+                                 (1 - exp(-h0 Gamma / (tau_inf - tau0))), one
+                                 implicit increment of length dt per load step.
+                                 params: C11, C12, C44, gdot0, n, tau0, tau_inf,
+                                 h0, dt.  Not combinable with J2 phases.         */
 };
 
 /* ---- descriptors ------------------------------------------------------ */
 typedef struct fftm_material {
   int law;           /* enum fftm_law */
-  double params[8];  /* law parameters, see enum fftm_law */
+  double params[12]; /* law parameters, see enum fftm_law */
   double quat[4];    /* unit quaternion (w, x, y, z): crystal frame -> sample
                         frame; used by FFTM_LAW_CUBIC_ELASTIC */
 } fftm_material;
@@ -186,10 +195,12 @@ enum fftm_field {
                             with non-symmetric stresses, see the layout above)  */
   FFTM_FIELD_D = 4,      /* residual D = div P at the nodes (3 comps), dismissed
                             node components 0; written by FFTM_OP_RESIDUAL       */
-  FFTM_FIELD_STATE = 5   /* committed J2 state at voxel points (7 comps: eps^p
-                            11, 22, 33, 23, 13, 12 and the cumulated plastic
-                            strain p; zero in non-J2 voxels); only for problems
-                            with a J2 phase, else FFTM_E_INVALID                */
+  FFTM_FIELD_STATE = 5   /* committed internal variables at voxel points: J2
+                            problems 7 comps (eps^p 11, 22, 33, 23, 13, 12 and
+                            the cumulated plastic strain p), crystal plasticity
+                            10 comps (F^p row-major, cumulated slip Gamma);
+                            zero in voxels of other laws; FFTM_E_INVALID for
+                            problems without such a phase                    */
 };
 
 /* Bytes of a field (dense layout above, problem precision). */

@@ -265,6 +265,10 @@ struct fftm_problem {
   fftm_load load_n;         // the load at the last commit
   void* Dn = nullptr;       // residual D at the last commit (3 comps)
   int committed = 0;        // a load step has been committed since creation or reset
+  int nst = 0;              // state components per voxel point (7 J2, 10 crystal plasticity, 0 none)
+  void* state_next = nullptr;  // the state committed by the last converged step, swapped in when
+  int commit_pending = 0;      // the next step starts (readouts until then see the step's own state)
+  int inc_ok = 0;           // incremental residual after a commit (J2 with linear small-strain laws)
   // tensor-core transforms (FFTM_FP32_TC): BF16 matrices, Kp x Kp per component and axis
   int tc = 0;
   void* tcmat = nullptr;
@@ -511,6 +515,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   R.vs = reinterpret_cast<T*>(p->vs);
   R.sym = p->sym;
   R.state = reinterpret_cast<T*>(p->state);
+  R.nst = p->nst;
   R.quad = 0;
   R.dquad = 0;
   for (int q = 0; q < 3; ++q) {
@@ -534,6 +539,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
 template <typename T>
 ResParams<T> commit_params(fftm_problem* p) {
   ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
+  if (p->commit_pending) R.state = reinterpret_cast<T*>(p->state_next);
   for (int q = 0; q < 3; ++q) {
     R.u[q] = R.un[q];
     R.ulo[q] = R.unlo[q];
@@ -649,6 +655,10 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     p->dint_len = max_iter + 1;
   }
   CU(cudaMemsetAsync(p->dint, 0, (max_iter + 1) * sizeof(int), s));
+  if (p->commit_pending) {  // the previous step's commit becomes the state of this step
+    std::swap(p->state, p->state_next);
+    p->commit_pending = 0;
+  }
   const int cur0 = p->cur;
   int m = 0, converged = 0;
   double err = 0.0;
@@ -721,8 +731,18 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
   if (converged && p->state) {  // a9: commit the internal variables of the converged step
     ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
     ProfScope ps(p, FFTM_KCAT_OTHER);
-    CU(launch_commit<T>(R, p->tetra, s));
+    // J2 is rate-independent: its return at the converged field from the committed state
+    // gives back the converged stress, so it commits in place.  The rate-dependent crystal
+    // plasticity law would slip further; its commit waits in state_next for the next step.
+    if (p->nst == 10) {
+      CU(launch_commit<T>(R, p->tetra, reinterpret_cast<T*>(p->state_next), s));
+      p->commit_pending = 1;
+    } else {
+      CU(launch_commit<T>(R, p->tetra, reinterpret_cast<T*>(p->state), s));
+    }
     p->launches += 1;
+  }
+  if (converged && p->inc_ok) {
     for (int q = 0; q < 3; ++q) {
       T* un = reinterpret_cast<T*>(p->un);
       CU(cudaMemcpyAsync(un + q * cnt, field_ptr<T>(p, SET_UH + p->cur, q), cnt * sizeof(T),
@@ -770,8 +790,16 @@ int validate(const fftm_problem_desc* d) {
   for (int i = 0; i < d->n_phases; ++i) {
     const int law = d->materials[i].law;
     if (law != FFTM_LAW_ISO_ELASTIC && law != FFTM_LAW_CUBIC_ELASTIC && law != FFTM_LAW_B0_LINEAR &&
-        law != FFTM_LAW_J2_LINHARD && law != FFTM_LAW_SVK_CUBIC && law != FFTM_LAW_NEO_HOOKE)
+        law != FFTM_LAW_J2_LINHARD && law != FFTM_LAW_SVK_CUBIC && law != FFTM_LAW_NEO_HOOKE &&
+        law != FFTM_LAW_CP_FCC)
       return set_err(FFTM_E_INVALID, "unknown law");
+    if (law == FFTM_LAW_CP_FCC) {
+      const double* c = d->materials[i].params;
+      if (!(c[0] > 0 && c[1] > 0 && c[2] > 0 && c[3] > 0 && c[4] >= 1 && c[5] > 0 && c[6] >= c[5] && c[7] >= 0 &&
+            c[8] > 0))
+        return set_err(FFTM_E_INVALID,
+                       "crystal plasticity needs C11, C12, C44, gdot0 > 0, n >= 1, tau0 > 0, tau_inf >= tau0, h0 >= 0, dt > 0");
+    }
     if (law == FFTM_LAW_NEO_HOOKE && !(d->materials[i].params[0] > 0.0 && d->materials[i].params[1] > 0.0))
       return set_err(FFTM_E_INVALID, "Neo-Hookean needs mu > 0 and K > 0");
     if (law == FFTM_LAW_J2_LINHARD) {
@@ -779,6 +807,14 @@ int validate(const fftm_problem_desc* d) {
       if (!(c[1] > 0.0) || !(3.0 * c[0] + 2.0 * c[1] > 0.0) || !(c[2] > 0.0) || !(c[3] >= 0.0))
         return set_err(FFTM_E_INVALID, "J2 needs mu > 0, 3 lambda + 2 mu > 0, sigma_y > 0, H >= 0");
     }
+  }
+  {
+    bool j2 = false, cp = false;
+    for (int i = 0; i < d->n_phases; ++i) {
+      j2 |= d->materials[i].law == FFTM_LAW_J2_LINHARD;
+      cp |= d->materials[i].law == FFTM_LAW_CP_FCC;
+    }
+    if (j2 && cp) return set_err(FFTM_E_UNSUPPORTED, "J2 and crystal-plasticity phases in one problem");
   }
   for (int a = 0; a < 3; ++a) {
     int np = 0;
@@ -878,6 +914,8 @@ int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
   for (int i = 0; i < desc->n_phases; ++i)
     if (desc->materials[i].law == FFTM_LAW_J2_LINHARD)
       stb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 7 * nvox * esz + (esz == 4 ? 9 : 6) * s.comp_stride * esz;
+    else if (desc->materials[i].law == FFTM_LAW_CP_FCC)
+      stb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 10 * nvox * esz;
   *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + stb + nvox * sizeof(uint16_t) +
            desc->n_phases * sizeof(int);
   return FFTM_OK;
@@ -899,6 +937,7 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->vs);
   cudaFree(p->vs_test);
   cudaFree(p->state);
+  cudaFree(p->state_next);
   cudaFree(p->un);
   cudaFree(p->Dn);
   cudaFree(p->tcmat);
@@ -965,22 +1004,34 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
     return set_err(FFTM_E_NOMEM, "device allocation of the fields failed");
   }
   CU(cudaMemsetAsync(p->fields, 0, sz.fields, s));
+  bool has_j2 = false, has_cp = false, finite = false;
   for (int i = 0; i < desc->n_phases; ++i) {
     const int law = desc->materials[i].law;
-    if (law == FFTM_LAW_B0_LINEAR || law == FFTM_LAW_SVK_CUBIC || law == FFTM_LAW_NEO_HOOKE) p->sym = 0;
+    if (law == FFTM_LAW_B0_LINEAR || law == FFTM_LAW_SVK_CUBIC || law == FFTM_LAW_NEO_HOOKE || law == FFTM_LAW_CP_FCC)
+      p->sym = 0;
+    has_j2 |= law == FFTM_LAW_J2_LINHARD;
+    has_cp |= law == FFTM_LAW_CP_FCC;
+    finite |= law == FFTM_LAW_SVK_CUBIC || law == FFTM_LAW_NEO_HOOKE || law == FFTM_LAW_CP_FCC;
   }
+  p->nst = has_cp ? 10 : (has_j2 ? 7 : 0);
+  p->inc_ok = has_j2 && !finite;
   CU(cudaMalloc(&p->vs, (size_t)(p->tetra ? 2 : 1) * (p->sym ? 6 : 9) * p->nvox * p->esz));
-  for (int i = 0; i < desc->n_phases; ++i)
-    if (desc->materials[i].law == FFTM_LAW_J2_LINHARD && !p->state) {
-      const size_t sb = (size_t)(p->tetra ? 2 : 1) * 7 * p->nvox * p->esz;
-      CU(cudaMalloc(&p->state, sb));
-      CU(cudaMemsetAsync(p->state, 0, sb, s));
+  if (p->nst) {
+    const size_t sb = (size_t)(p->tetra ? 2 : 1) * p->nst * p->nvox * p->esz;
+    CU(cudaMalloc(&p->state, sb));
+    CU(cudaMemsetAsync(p->state, 0, sb, s));  // J2: e = 0, p = 0; crystal plasticity: F^p - 1 = 0, Gamma = 0
+    CU(cudaMalloc(&p->state_next, sb));
+    CU(cudaMemsetAsync(p->state_next, 0, sb, s));
+  }
+  if (p->inc_ok) {
+    {
       const size_t ub = (size_t)(p->esz == 4 ? 6 : 3) * p->comp_stride * p->esz;
       CU(cudaMalloc(&p->un, ub));
       CU(cudaMemsetAsync(p->un, 0, ub, s));
       CU(cudaMalloc(&p->Dn, 3 * p->comp_stride * p->esz));
       CU(cudaMemsetAsync(p->Dn, 0, 3 * p->comp_stride * p->esz, s));
     }
+  }
   CU(cudaMalloc(&p->phase, p->nvox * sizeof(uint16_t)));
   CU(cudaMemcpyAsync(p->phase, desc->phase, p->nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
   CU(cudaMalloc(&p->partial, sz.partial));
@@ -1065,6 +1116,16 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         for (int b = a; b < 6; ++b) c[k++] = Cm[a][b];
     } else if (m.law == FFTM_LAW_J2_LINHARD) {
       for (int k = 0; k < 4; ++k) c[k] = m.params[k];
+    } else if (m.law == FFTM_LAW_CP_FCC) {
+      double R[3][3], Cm[6][6];
+      quat_rot(m.quat, R);
+      cubic_mandel(m.params[0], m.params[1], m.params[2], R, Cm);
+      int k = 0;
+      for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b) c[k++] = Cm[a][b];
+      for (int j = 0; j < 6; ++j) c[21 + j] = m.params[3 + j];  // gdot0, n, tau0, tau_inf, h0, dt
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) c[27 + 3 * a + b] = R[a][b];
     } else {
       c[0] = m.params[0];
       c[1] = m.params[1];
@@ -1127,8 +1188,8 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes) {
     case FFTM_FIELD_GRAD: *bytes = 9 * npp * p->nvox * p->esz; return FFTM_OK;
     case FFTM_FIELD_STRESS: *bytes = (p->sym ? 6 : 9) * npp * p->nvox * p->esz; return FFTM_OK;
     case FFTM_FIELD_STATE:
-      if (!p->state) return set_err(FFTM_E_INVALID, "the problem has no J2 phase (no state)");
-      *bytes = 7 * npp * p->nvox * p->esz;
+      if (!p->state) return set_err(FFTM_E_INVALID, "the problem has no phase with internal variables");
+      *bytes = (size_t)p->nst * npp * p->nvox * p->esz;
       return FFTM_OK;
     default: return set_err(FFTM_E_INVALID, "unknown field");
   }
@@ -1345,9 +1406,12 @@ int fftm_reset_state(fftm_problem* p) {
   Sizes sz = sizes_of(&p->desc);
   CU(cudaMemsetAsync(p->fields, 0, sz.fields, p->ctx->stream));
   if (p->state) {
-    CU(cudaMemsetAsync(p->state, 0, (size_t)(p->tetra ? 2 : 1) * 7 * p->nvox * p->esz, p->ctx->stream));
-    CU(cudaMemsetAsync(p->un, 0, (size_t)(p->esz == 4 ? 6 : 3) * p->comp_stride * p->esz, p->ctx->stream));
+    CU(cudaMemsetAsync(p->state, 0, (size_t)(p->tetra ? 2 : 1) * p->nst * p->nvox * p->esz, p->ctx->stream));
+    CU(cudaMemsetAsync(p->state_next, 0, (size_t)(p->tetra ? 2 : 1) * p->nst * p->nvox * p->esz, p->ctx->stream));
   }
+  p->commit_pending = 0;
+  if (p->un)
+    CU(cudaMemsetAsync(p->un, 0, (size_t)(p->esz == 4 ? 6 : 3) * p->comp_stride * p->esz, p->ctx->stream));
   std::memset(&p->load_n, 0, sizeof(p->load_n));
   p->committed = 0;
   CU(cudaStreamSynchronize(p->ctx->stream));

@@ -83,7 +83,8 @@ struct ResParams {
   // J2 phases are evaluated incrementally from the last commit: the state holds the
   // elastic strain e_n (11,22,33,23,13,12) and p_n per voxel point [r][7][voxel], and
   // the trial strain is e_n + sym(grad(u^f - u^f_n) + grad(u* - u*_n)).
-  T* state;          // null: no J2 phase
+  T* state;          // null: no phase with internal variables
+  int nst;           // state components per voxel point: 7 (J2) or 10 (crystal plasticity)
   const T* un[3];    // u^f at the last commit (high part in FP32)
   const T* unlo[3];  // its low part (FP32 only)
   T dGs[9];          // gradient of the affine part of u* - u*_n
@@ -157,10 +158,10 @@ template <typename T>
 int residual_blocks(const ResParams<T>& P, int tetra);
 template <typename T>
 cudaError_t launch_green(const GreenParams<T>& P, cudaStream_t s);
-// a9: recompute the J2 return at every voxel point from the current u^f and the
-// committed state, and store the returned state (the step's commit).
+// a9: recompute the return (J2, crystal plasticity) at every voxel point from the
+// current u^f and the state of the step, and store the returned state in `out`.
 template <typename T>
-cudaError_t launch_commit(const ResParams<T>& P, int tetra, cudaStream_t s);
+cudaError_t launch_commit(const ResParams<T>& P, int tetra, T* out, cudaStream_t s);
 // The committed state as (eps^p, p) = (sym G_n - e_n, p_n) (out != null), or the
 // elastic strain e_n = sym G_n - eps^p from a given (eps^p, p) (in != null); G_n is
 // the total gradient at the commit, from P.u = u^f_n and P.Gs, P.Qc = the load at

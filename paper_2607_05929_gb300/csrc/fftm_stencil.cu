@@ -127,6 +127,244 @@ __device__ __forceinline__ void neo_hooke(const T* __restrict__ c, const T G[9],
   first_piola<T>(H, Pi, S);
 }
 
+
+// ---- FCC crystal plasticity, finite strain (Sec. 3.4) ----------------------------
+// The 12 {111}<110> systems in the crystal frame (unnormalised plane normal, slip
+// direction); the normalisation 1/sqrt(6) of m (x) n is applied at use.
+__constant__ signed char c_fcc_sys[12][6] = {
+    {1, 1, 1, 0, 1, -1},  {1, 1, 1, 1, 0, -1},  {1, 1, 1, 1, -1, 0},  {-1, 1, 1, 0, 1, -1},
+    {-1, 1, 1, 1, 0, 1},  {-1, 1, 1, 1, 1, 0},  {1, -1, 1, 0, 1, 1},  {1, -1, 1, 1, 0, -1},
+    {1, -1, 1, 1, 1, 0},  {1, 1, -1, 0, 1, 1},  {1, 1, -1, 1, 0, 1},  {1, 1, -1, 1, -1, 0}};
+
+// (1 + K)^-1 - 1 for a small K, without forming 1 + K: with Cayley-Hamilton,
+// adj(1 + K) = 1 + D, D = (tr K + c2) 1 - (1 + tr K) K + K^2, det(1 + K) = 1 + d,
+// d = tr K + c2 + det K, c2 = ((tr K)^2 - tr K^2) / 2; the result is (D - d 1) / (1 + d).
+template <typename T>
+__device__ __forceinline__ void inv_minus_identity(const T K[9], T Y[9]) {
+  const T tr = K[0] + K[4] + K[8];
+  T K2[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) K2[i * 3 + j] = K[i * 3] * K[j] + K[i * 3 + 1] * K[3 + j] + K[i * 3 + 2] * K[6 + j];
+  const T trK2 = K2[0] + K2[4] + K2[8];
+  const T c2 = T(0.5) * (tr * tr - trK2);
+  const T det = K[0] * (K[4] * K[8] - K[5] * K[7]) - K[1] * (K[3] * K[8] - K[5] * K[6]) + K[2] * (K[3] * K[7] - K[4] * K[6]);
+  const T d = tr + c2 + det;
+  const T inv = T(1) / (T(1) + d);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T Dm = ((i % 4 == 0) ? (tr + c2) : T(0)) - (T(1) + tr) * K[i] + K2[i];
+    Y[i] = (Dm - ((i % 4 == 0) ? d : T(0))) * inv;
+  }
+}
+
+// (1 + X)(1 + Y) - 1 = X + Y + X Y
+template <typename T>
+__device__ __forceinline__ void compose_minus_identity(const T X[9], const T Y[9], T W[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      W[i * 3 + j] = X[i * 3 + j] + Y[i * 3 + j] + X[i * 3] * Y[j] + X[i * 3 + 1] * Y[3 + j] + X[i * 3 + 2] * Y[6 + j];
+}
+
+// One implicit increment at a voxel point (Kalidindi, Bronkhorst and Anand 1992):
+// unknown second Piola-Kirchhoff Pi (6 components 11, 22, 33, 23, 13, 12),
+//   R(Pi) = Pi - Pi_tr + sum_s dgamma_s(tau_s) C : sym(A P_s),  tau_s = Pi : P_s,
+//   dgamma_s = dt gdot0 |tau_s / tau_c|^n sign(tau_s),  tau_c = Voce(Gamma_n),
+// Newton from the trial stress scaled onto the yield surface of the most stressed
+// system, with backtracking on max |R|; then F^p = (1 + sum dgamma_s P_s) F^p_n,
+// Gamma += sum |dgamma_s|, P = F^e Pi F^p^-T.  State st = (F^p - 1 row-major, Gamma).
+// c = Mandel C (21), gdot0, n, tau0, tau_inf, h0, dt, R (crystal -> sample, row-major).
+template <typename T>
+__device__ void cp_eval(const T* __restrict__ c, const T G[9], const T st[10], T S[9], T* stn) {
+  const T gdot0 = __ldg(c + 21), nexp = __ldg(c + 22), tau0 = __ldg(c + 23), tinf = __ldg(c + 24);
+  const T h0 = __ldg(c + 25), dt = __ldg(c + 26);
+  T Rm[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) Rm[i] = __ldg(c + 27 + i);
+  // Schmid tensors, symmetric parts (6 components) and full (9)
+  T sP[12][6], Pf[12][9];
+  const T inv6 = T(0.40824829046386301637);  // 1 / sqrt(6)
+#pragma unroll
+  for (int s = 0; s < 12; ++s) {
+    T nv[3], mv[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      nv[i] = Rm[i * 3] * T(c_fcc_sys[s][0]) + Rm[i * 3 + 1] * T(c_fcc_sys[s][1]) + Rm[i * 3 + 2] * T(c_fcc_sys[s][2]);
+      mv[i] = Rm[i * 3] * T(c_fcc_sys[s][3]) + Rm[i * 3 + 1] * T(c_fcc_sys[s][4]) + Rm[i * 3 + 2] * T(c_fcc_sys[s][5]);
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Pf[s][i * 3 + j] = inv6 * mv[i] * nv[j];
+    sP[s][0] = Pf[s][0];
+    sP[s][1] = Pf[s][4];
+    sP[s][2] = Pf[s][8];
+    sP[s][3] = T(0.5) * (Pf[s][5] + Pf[s][7]);
+    sP[s][4] = T(0.5) * (Pf[s][2] + Pf[s][6]);
+    sP[s][5] = T(0.5) * (Pf[s][1] + Pf[s][3]);
+  }
+  // trial elastic state: W = F F^p_n^-1 - 1, E_tr = (W + W^T + W^T W) / 2, A = 1 + 2 E_tr
+  T H[9], Y[9], W[9];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) H[q * 3 + i] = G[i * 3 + q];
+  inv_minus_identity<T>(st, Y);
+  compose_minus_identity<T>(H, Y, W);
+  auto ew = [&](int i, int j) {
+    return T(0.5) * (W[i * 3 + j] + W[j * 3 + i] + W[i] * W[j] + W[3 + i] * W[3 + j] + W[6 + i] * W[6 + j]);
+  };
+  const T Etr[6] = {ew(0, 0), ew(1, 1), ew(2, 2), ew(1, 2), ew(0, 2), ew(0, 1)};
+  T Ptr[6];
+  mandel_apply<T>(c, Etr, Ptr);
+  // C : sym(A P_s) = C : sym(P_s) + 2 C : sym(E_tr P_s)
+  T Cs[12][6];
+  {
+    const T Em[3][3] = {{Etr[0], Etr[5], Etr[4]}, {Etr[5], Etr[1], Etr[3]}, {Etr[4], Etr[3], Etr[2]}};
+#pragma unroll
+    for (int s = 0; s < 12; ++s) {
+      T B[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+          B[i][j] = Em[i][0] * Pf[s][j] + Em[i][1] * Pf[s][3 + j] + Em[i][2] * Pf[s][6 + j];
+      const T v[6] = {sP[s][0] + T(2) * B[0][0], sP[s][1] + T(2) * B[1][1], sP[s][2] + T(2) * B[2][2],
+                      sP[s][3] + (B[1][2] + B[2][1]), sP[s][4] + (B[0][2] + B[2][0]), sP[s][5] + (B[0][1] + B[1][0])};
+      mandel_apply<T>(c, v, Cs[s]);
+    }
+  }
+  const T gam_n = st[9];
+  const T tauc = tinf > tau0 ? tau0 + (tinf - tau0) * (T(1) - exp(-h0 * gam_n / (tinf - tau0))) : tau0;
+  auto tau_of = [&](const T Pi[6], int s) {
+    return Pi[0] * sP[s][0] + Pi[1] * sP[s][1] + Pi[2] * sP[s][2] +
+           T(2) * (Pi[3] * sP[s][3] + Pi[4] * sP[s][4] + Pi[5] * sP[s][5]);
+  };
+  auto slip = [&](T tau, T* ddg) {
+    const T x = tau / tauc, ax = fabs(x);
+    const T pw = ax > T(0) ? exp((nexp - T(1)) * log(ax)) : T(0);  // |x|^(n-1)
+    if (ddg) *ddg = dt * gdot0 * nexp * pw / tauc;
+    return copysign(dt * gdot0 * pw * ax, x);
+  };
+  auto resid = [&](const T Pi[6], T R[6]) {
+    T m = T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) R[k] = Pi[k] - Ptr[k];
+    for (int s = 0; s < 12; ++s) {
+      const T dg = slip(tau_of(Pi, s), nullptr);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) R[k] += dg * Cs[s][k];
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) m = fmax(m, fabs(R[k]));
+    return m;
+  };
+  T taumax = T(0), scale = tauc;
+  for (int s = 0; s < 12; ++s) taumax = fmax(taumax, fabs(tau_of(Ptr, s)));
+#pragma unroll
+  for (int k = 0; k < 6; ++k) scale = fmax(scale, fabs(Ptr[k]));
+  const T s0 = taumax > tauc ? tauc / taumax : T(1);
+  T Pi[6], R[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) Pi[k] = s0 * Ptr[k];
+  T rn = resid(Pi, R);
+  // FP32: about two units in the last place of the largest stress component, the level at
+  // which the residual itself is rounding; FP64: the oracle's tolerance
+  const T tol = (sizeof(T) == 8 ? T(1e-12) : T(1.2e-7)) * scale;
+  for (int it = 0; it < 200 && rn > tol; ++it) {
+    // Jacobian: 1 + sum_s ddgamma_s C_s (x) dtau_s/dPi
+    T J[6][7];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+#pragma unroll
+      for (int b = 0; b < 6; ++b) J[a][b] = (a == b) ? T(1) : T(0);
+      J[a][6] = -R[a];
+    }
+    for (int s = 0; s < 12; ++s) {
+      T ddg;
+      slip(tau_of(Pi, s), &ddg);
+      const T g[6] = {sP[s][0], sP[s][1], sP[s][2], T(2) * sP[s][3], T(2) * sP[s][4], T(2) * sP[s][5]};
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = 0; b < 6; ++b) J[a][b] += ddg * Cs[s][a] * g[b];
+    }
+    // Gaussian elimination with partial pivoting
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      int piv = k;
+      for (int a = k + 1; a < 6; ++a)
+        if (fabs(J[a][k]) > fabs(J[piv][k])) piv = a;
+      if (piv != k)
+        for (int b = 0; b < 7; ++b) {
+          const T t = J[k][b];
+          J[k][b] = J[piv][b];
+          J[piv][b] = t;
+        }
+      const T ip = T(1) / J[k][k];
+      for (int a = k + 1; a < 6; ++a) {
+        const T f = J[a][k] * ip;
+        for (int b = k; b < 7; ++b) J[a][b] -= f * J[k][b];
+      }
+    }
+    T d[6];
+    for (int k = 5; k >= 0; --k) {
+      T v = J[k][6];
+      for (int b = k + 1; b < 6; ++b) v -= J[k][b] * d[b];
+      d[k] = v / J[k][k];
+    }
+    // backtracking on max |R|
+    T step = T(1), Pn[6], Rn[6], rnew = rn;
+    for (int bt = 0; bt < (sizeof(T) == 8 ? 60 : 24); ++bt) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Pn[k] = Pi[k] + step * d[k];
+      rnew = resid(Pn, Rn);
+      if (rnew < rn || step <= T(1e-12)) break;
+      step *= T(0.5);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      Pi[k] = Pn[k];
+      R[k] = Rn[k];
+    }
+    if (!(rnew < rn)) break;  // no descent left at this precision
+    rn = rnew;
+  }
+  // plastic update: K' = (1 + L)(1 + K) - 1, L = sum dgamma_s P_s; Gamma += sum |dgamma_s|
+  T L[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)}, dgam = T(0);
+  for (int s = 0; s < 12; ++s) {
+    const T dg = slip(tau_of(Pi, s), nullptr);
+    dgam += fabs(dg);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) L[i] += dg * Pf[s][i];
+  }
+  T K1[9], Y1[9], W1[9];
+  compose_minus_identity<T>(L, st, K1);
+  inv_minus_identity<T>(K1, Y1);
+  compose_minus_identity<T>(H, Y1, W1);
+  // P = (1 + W1) Pi (1 + Y1)^T; S[i*3+q] = P_qi
+  const T M[3][3] = {{Pi[0], Pi[5], Pi[4]}, {Pi[5], Pi[1], Pi[3]}, {Pi[4], Pi[3], Pi[2]}};
+  T FM[3][3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      FM[q][j] = M[q][j] + W1[q * 3] * M[0][j] + W1[q * 3 + 1] * M[1][j] + W1[q * 3 + 2] * M[2][j];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+      S[i * 3 + q] = FM[q][i] + FM[q][0] * Y1[i * 3] + FM[q][1] * Y1[i * 3 + 1] + FM[q][2] * Y1[i * 3 + 2];
+  if (stn) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) stn[i] = K1[i];
+    stn[9] = gam_n + dgam;
+  }
+}
+
 // Small-strain law on the total gradient G[i*3+q]; P returned as 9 components.
 template <typename T>
 __device__ __forceinline__ void law_eval(int law, const T* __restrict__ c, const T G[9], T Pout[9]) {
@@ -242,15 +480,21 @@ __device__ __forceinline__ void j2_inc(const T* __restrict__ c, const T dG[9], c
 
 // Law at voxel point r of voxel v from the gradient G (elastic laws: the total
 // gradient; J2: the increment since the commit).
-template <typename T>
+template <typename T, int SL = 3>
 __device__ __forceinline__ void point_law(const ResParams<T>& P, int law, const T* lc, const T G[9], int r,
                                           long long v, long long nvox, T Pout[9], T* stn) {
-  if (law == LAW_J2) {
-    const T* sp = P.state + (long long)(r * 7) * nvox + v;
+  if ((SL & 1) && law == LAW_J2) {
+    const T* sp = P.state + (long long)(r * P.nst) * nvox + v;
     T st[7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) st[c] = sp[c * nvox];
     j2_inc<T>(lc, G, st, nullptr, Pout, stn);
+  } else if ((SL & 2) && law == LAW_CP) {
+    const T* sp = P.state + (long long)(r * P.nst) * nvox + v;
+    T st[10];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) st[c] = sp[c * nvox];
+    cp_eval<T>(lc, G, st, Pout, stn);
   } else {
     law_eval<T>(law, lc, G, Pout);
   }
@@ -395,8 +639,9 @@ __device__ __forceinline__ int sym_index(int i, int q) {
   return 6 - i - q;  // (1,2) -> 3, (0,2) -> 4, (0,1) -> 5
 }
 
-template <typename T, int TETRA, bool WITH_P, bool LO, bool SYM, bool J2>
+template <typename T, int TETRA, bool WITH_P, bool LO, bool SYM, int SL>
 __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti) {
+  constexpr bool J2 = (SL & 1) != 0;
   constexpr int NPP = TETRA ? 2 : 1;
   constexpr int NC = SYM ? 6 : 9;
   constexpr int NCT = WITH_P ? NC + 9 : NC;
@@ -446,7 +691,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
       for (int r = 0; r < NPP; ++r) {
         T Gf[9], Gt[9], Pp[9];
         law_grad<T, TETRA, LO>(P, j2, uh, ul, r, vx, vy_, vz, Gf, Gt);
-        if (J2) point_law<T>(P, law, lc, Gt, r, v, nvox, Pp, nullptr);
+        if (SL) point_law<T, SL>(P, law, lc, Gt, r, v, nvox, Pp, nullptr);
         else law_eval<T>(law, lc, Gt, Pp);
         T* base = P.vs + (size_t)(r * NCT) * nvox + v;
         if (SYM) {
@@ -561,7 +806,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress_inc(ResParams<T> P, TileId
         T Gd[9], dG[9], dP[9];
         law_grad<T, TETRA, LO>(P, true, uh, ul, r, vx, vy_, vz, Gd, dG);
         if (j2) {
-          const T* stp = P.state + (long long)(r * 7) * nvox + v;
+          const T* stp = P.state + (long long)(r * P.nst) * nvox + v;
           T st[7], Pf[9];
 #pragma unroll
           for (int c = 0; c < 7; ++c) st[c] = stp[c * nvox];
@@ -803,12 +1048,15 @@ static cudaError_t launch_res_t(const ResParams<T>& P, bool lo, cudaStream_t s, 
     if (lo) k_stress_inc<T, TETRA, true, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
     else k_stress_inc<T, TETRA, false, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
   } else {
-    if (P.state) {
-      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, true><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
-      else k_stress<T, TETRA, WITH_P, false, SYM, true><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+    if (P.nst == 7) {
+      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, 1><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+      else k_stress<T, TETRA, WITH_P, false, SYM, 1><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+    } else if (P.nst == 10) {
+      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, 2><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+      else k_stress<T, TETRA, WITH_P, false, SYM, 2><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
     } else {
-      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, false><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
-      else k_stress<T, TETRA, WITH_P, false, SYM, false><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, 0><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+      else k_stress<T, TETRA, WITH_P, false, SYM, 0><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
     }
   }
   cudaError_t e = cudaGetLastError();
@@ -839,7 +1087,7 @@ template int residual_blocks<double>(const ResParams<double>&, int);
 // ---- per-voxel evaluation shared by the output and statistics kernels ----
 template <typename T, int TETRA, bool LO>
 __device__ __forceinline__ int voxel_eval(const ResParams<T>& P, long long v, T Gt_out[2][9], T P_out[2][9],
-                                          T (*stn)[7] = nullptr) {
+                                          T (*stn)[10] = nullptr) {
   const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
   const int vx = (int)(v % n1);
   const long long r1 = v / n1;
@@ -881,42 +1129,42 @@ __device__ __forceinline__ int voxel_eval(const ResParams<T>& P, long long v, T 
       law_grad<T, TETRA, LO>(P, true, du, dl, r, vx, vy, vz, Gd, Ginc);
       point_law<T>(P, law, lc, Ginc, r, v, (long long)n1 * n2 * n3, P_out[r], stn ? stn[r] : nullptr);
     } else {
-      point_law<T>(P, law, lc, Gt_out[r], r, v, (long long)n1 * n2 * n3, P_out[r], nullptr);
+      point_law<T>(P, law, lc, Gt_out[r], r, v, (long long)n1 * n2 * n3, P_out[r], stn ? stn[r] : nullptr);
     }
   }
   return law;
 }
 
 template <typename T, int TETRA, bool LO>
-__global__ void k_commit(ResParams<T> P) {
+__global__ void k_commit(ResParams<T> P, T* __restrict__ out) {
   const long long nv = (long long)P.n[0] * P.n[1] * P.n[2];
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
        v += (long long)gridDim.x * blockDim.x) {
-    if (__ldg(P.law_id + P.phase[v]) != LAW_J2) continue;  // voxel index == phase index (dense)
-    T Gt[2][9], Pp[2][9], stn[2][7];
+    const int law = __ldg(P.law_id + P.phase[v]);
+    if (law != LAW_J2 && law != LAW_CP) continue;
+    T Gt[2][9], Pp[2][9], stn[2][10];
     voxel_eval<T, TETRA, LO>(P, v, Gt, Pp, stn);
-#pragma unroll
+    const int nc = law == LAW_J2 ? 7 : 10;
     for (int r = 0; r < (TETRA ? 2 : 1); ++r)
-#pragma unroll
-      for (int c = 0; c < 7; ++c) P.state[v + nv * (c + 7 * r)] = stn[r][c];
+      for (int c = 0; c < nc; ++c) out[v + nv * (c + P.nst * r)] = stn[r][c];
   }
 }
 
 template <typename T>
-cudaError_t launch_commit(const ResParams<T>& P, int tetra, cudaStream_t s) {
+cudaError_t launch_commit(const ResParams<T>& P, int tetra, T* out, cudaStream_t s) {
   if (!P.state) return cudaSuccess;
   const bool lo = P.ulo[0] != nullptr;
   if (tetra) {
-    if (lo) k_commit<T, 1, true><<<1216, 256, 0, s>>>(P);
-    else k_commit<T, 1, false><<<1216, 256, 0, s>>>(P);
+    if (lo) k_commit<T, 1, true><<<1216, 256, 0, s>>>(P, out);
+    else k_commit<T, 1, false><<<1216, 256, 0, s>>>(P, out);
   } else {
-    if (lo) k_commit<T, 0, true><<<1216, 256, 0, s>>>(P);
-    else k_commit<T, 0, false><<<1216, 256, 0, s>>>(P);
+    if (lo) k_commit<T, 0, true><<<1216, 256, 0, s>>>(P, out);
+    else k_commit<T, 0, false><<<1216, 256, 0, s>>>(P, out);
   }
   return cudaGetLastError();
 }
-template cudaError_t launch_commit<float>(const ResParams<float>&, int, cudaStream_t);
-template cudaError_t launch_commit<double>(const ResParams<double>&, int, cudaStream_t);
+template cudaError_t launch_commit<float>(const ResParams<float>&, int, float*, cudaStream_t);
+template cudaError_t launch_commit<double>(const ResParams<double>&, int, double*, cudaStream_t);
 
 template <typename T, int TETRA, bool LO>
 __global__ void k_state_io(ResParams<T> P, T* __restrict__ out, const T* __restrict__ in) {
@@ -924,10 +1172,23 @@ __global__ void k_state_io(ResParams<T> P, T* __restrict__ out, const T* __restr
   const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
        v += (long long)gridDim.x * blockDim.x) {
-    const bool j2 = __ldg(P.law_id + P.phase[v]) == LAW_J2;
-    if (!j2) {
+    const int law = __ldg(P.law_id + P.phase[v]);
+    if (law == LAW_CP) {  // stored as F^p - 1: read out F^p (row-major) and Gamma
+      for (int r = 0; r < (TETRA ? 2 : 1); ++r) {
+        T* st = P.state + v + nv * (P.nst * r);
+        for (int c = 0; c < 9; ++c) {
+          const T id = (c % 4 == 0) ? T(1) : T(0);
+          if (out) out[v + nv * (c + P.nst * r)] = st[nv * c] + id;
+          else st[nv * c] = in[v + nv * (c + P.nst * r)] - id;
+        }
+        if (out) out[v + nv * (9 + P.nst * r)] = st[nv * 9];
+        else st[nv * 9] = in[v + nv * (9 + P.nst * r)];
+      }
+      continue;
+    }
+    if (law != LAW_J2) {
       if (out)
-        for (int c = 0; c < 7 * (TETRA ? 2 : 1); ++c) out[v + nv * c] = T(0);
+        for (int c = 0; c < P.nst * (TETRA ? 2 : 1); ++c) out[v + nv * c] = T(0);
       continue;
     }
     const int vx = (int)(v % n1);
@@ -952,15 +1213,15 @@ __global__ void k_state_io(ResParams<T> P, T* __restrict__ out, const T* __restr
       T Gf[9], G[9];
       law_grad<T, TETRA, LO>(P, false, uh, ul, r, vx, vy, vz, Gf, G);
       const T es[6] = {G[0], G[4], G[8], T(0.5) * (G[5] + G[7]), T(0.5) * (G[2] + G[6]), T(0.5) * (G[1] + G[3])};
-      T* st = P.state + v + nv * (7 * r);
+      T* st = P.state + v + nv * (P.nst * r);
       if (out) {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) out[v + nv * (c + 7 * r)] = es[c] - st[nv * c];
-        out[v + nv * (6 + 7 * r)] = st[nv * 6];
+        for (int c = 0; c < 6; ++c) out[v + nv * (c + P.nst * r)] = es[c] - st[nv * c];
+        out[v + nv * (6 + P.nst * r)] = st[nv * 6];
       } else {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) st[nv * c] = es[c] - in[v + nv * (c + 7 * r)];
-        st[nv * 6] = in[v + nv * (6 + 7 * r)];
+        for (int c = 0; c < 6; ++c) st[nv * c] = es[c] - in[v + nv * (c + P.nst * r)];
+        st[nv * 6] = in[v + nv * (6 + P.nst * r)];
       }
     }
   }

@@ -44,7 +44,7 @@ FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "
 
 
 class fftm_material(ctypes.Structure):
-    _fields_ = [("law", ctypes.c_int), ("params", ctypes.c_double * 8), ("quat", ctypes.c_double * 4)]
+    _fields_ = [("law", ctypes.c_int), ("params", ctypes.c_double * 12), ("quat", ctypes.c_double * 4)]
 
 
 class fftm_problem_desc(ctypes.Structure):
