@@ -62,6 +62,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed beside (0 = skip)")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving stream (mixed sizes/BCs/laws, Poisson arrivals): solves/s and p50/p99 latency")
+    ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream (--serve)")
+    ap.add_argument("--slots", type=int, default=4, help="resident solves of the server (--serve)")
     return ap.parse_args(argv)
 
 
@@ -459,10 +463,91 @@ def it_total_plus1(steps, iters):
     return steps * (iters + 1)
 
 
+def serve_requests(count):
+    """The first `count` requests of the serving stream (generation is exact and seeded)."""
+    from synthetic.serving import request_spec, request_workload
+    out = []
+    for k in range(count):
+        spec = request_spec(k)
+        wl, loads = request_workload(spec)
+        out.append((spec, wl, loads))
+    return out
+
+
+def serve_arm(args):
+    """Continuous-batching server over one GPU: a closed-loop pass measures the capacity C,
+    then the same requests arrive as a Poisson stream at 0.8 C; latency = completion - arrival."""
+    from paper_2607_05929_gb300 import build as libbuild
+    from paper_2607_05929_gb300 import fftm as F
+
+    reqs = serve_requests(args.requests)  # before any GPU call
+    libbuild.build()
+    F.load_library()
+    descs = []
+    for spec, wl, loads in reqs:
+        mats = [(m.law, m.params, m.quat) for m in wl.materials]
+        descs.append(F.make_desc(wl.n, wl.phase, mats, wl.bc, scheme=wl.scheme, green=wl.green, lambda0=wl.lambda0,
+                                 mu0=wl.mu0, precision=args.precision, tol=wl.tol, max_iter=wl.max_iter))
+
+    def run(arrivals):
+        srv = F.fftm_server_create(0, 0, args.slots)
+        done = {}
+        t0 = time.monotonic()
+        ids = {}
+        try:
+            def submitter():
+                for i, at in arrivals:
+                    wait = t0 + at - time.monotonic()
+                    if wait > 0:
+                        time.sleep(wait)
+                    ids[F.fftm_server_submit(srv, descs[i][0], reqs[i][2])] = i
+            th = threading.Thread(target=submitter)
+            th.start()
+            while len(done) < len(arrivals):
+                for r in F.fftm_server_poll(srv, wait=True):
+                    done[r["id"]] = r
+                if th.is_alive() and not F.fftm_server_pending(srv)[0] and not F.fftm_server_pending(srv)[1]:
+                    time.sleep(0.001)  # nothing queued or running: the next arrival is still to come
+            th.join()
+        finally:
+            F.fftm_server_destroy(srv)
+        return [(ids[k], r) for k, r in done.items()]
+
+    warm = [i for i, (spec, _, _) in enumerate(reqs) if spec["n"] <= 48][:4]
+    run([(i, 0.0) for i in warm])  # warm-up: first launches, module loading
+    closed = run([(i, 0.0) for i in range(len(reqs))])
+    span = max(r["t_end"] for _, r in closed) - min(r["t_submit"] for _, r in closed)
+    capacity = len(reqs) / span
+    rate = 0.8 * capacity
+    gaps = np.random.default_rng(7).exponential(1.0 / rate, size=len(reqs))
+    arrivals = [(i, float(t)) for i, t in zip(range(len(reqs)), np.cumsum(gaps) - gaps[0])]
+    opened = run(arrivals)
+    lat = np.array([r["t_end"] - r["t_submit"] for _, r in opened])
+    t_first = min(r["t_submit"] for _, r in opened)
+    t_last = max(r["t_end"] for _, r in opened)
+    vox_it = sum(reqs[i][1].phase.size * r["iterations"] for i, r in opened)
+    bad = [r["status"] for _, r in opened if r["status"] != 0]
+    line = {"metric": "solves/s", "value": len(opened) / (t_last - t_first), "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
+            "capacity_solves_per_s": capacity, "arrival_rate_per_s": rate,
+            "voxel_iterations_per_s": vox_it / (t_last - t_first), "requests": len(reqs), "slots": args.slots,
+            "not_converged_or_failed": len(bad), "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"serving stream: {len(reqs)} requests (seeds 1000..{999 + len(reqs)}), sides "
+                                   "32/48/64/96/128, per-axis P/D/N, isotropic or J2 matrix, HEX1 or TETRA2, "
+                                   "spheres or Voronoi; Poisson arrivals at 0.8x the measured capacity",
+                       "precision": args.precision}}
+    print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.serve:
+        return serve_arm(args)
     return gpu_arm(args)
 
 

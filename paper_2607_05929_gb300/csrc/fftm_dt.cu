@@ -581,7 +581,10 @@ template <typename T, int AXIS, int FUSED>
 static cudaError_t launch_one(const PassParams<T>& P, size_t smem, cudaStream_t s) {
   constexpr int TP = TileCfg<T>::TP;
   auto kern = k_pass<T, AXIS, FUSED>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the same opt-in limit for every problem: the attribute is per function, so a
+  // per-problem value could be lowered by another thread between its set and our launch
+  (void)smem;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) return e;
   dim3 grid;
   if (AXIS == 0) grid.x = (unsigned)((P.N[1] * P.N[2] + TP - 1) / TP);

@@ -107,6 +107,11 @@ struct ResParams {
 
 constexpr int LAWC = 40;
 
+// Dynamic shared memory opt-in of the axis-pass kernels: one value for every launch
+// (227 KiB, the per-block maximum), since the attribute is per function and shared
+// by all host threads.
+constexpr int kMaxDynSmem = 227 * 1024;
+
 // One axis pass as a dense contraction on the tensor cores (FP32 data, BF16
 // matrices).  A: the Kp x Kp (zero-padded) transform matrix, row-major BF16
 // bits; A2: the inverse z matrix of the fused z pass.

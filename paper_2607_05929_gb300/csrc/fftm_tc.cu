@@ -223,7 +223,8 @@ template <int AXIS, int FUSED>
 static cudaError_t launch_tc_one(const TcPassParams& P, int maxKp, cudaStream_t s) {
   const size_t smem = (size_t)maxKp * TC_SP * sizeof(float);
   auto kern = k_pass_tc<AXIS, FUSED>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one opt-in limit for every problem (the attribute is per function and shared by threads)
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) return e;
   dim3 grid;
   if (AXIS == 0) grid.x = (unsigned)((P.N[1] * P.N[2] + TC_TP - 1) / TC_TP);

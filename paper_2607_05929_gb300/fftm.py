@@ -39,6 +39,7 @@ EXPORTS = [
     "fftm_set_phase", "fftm_set_load", "fftm_solve_step", "fftm_field_bytes",
     "fftm_get_field", "fftm_set_field", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
+    "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
 ]
 FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "other"]
 
@@ -62,6 +63,18 @@ class fftm_problem_desc(ctypes.Structure):
 
 class fftm_load(ctypes.Structure):
     _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3), ("Q", (ctypes.c_double * 6) * 3)]
+
+
+class fftm_request(ctypes.Structure):
+    _fields_ = [("desc", ctypes.c_void_p), ("loads", ctypes.c_void_p), ("n_loads", ctypes.c_int),
+                ("u_out", ctypes.c_void_p), ("u_out_bytes", ctypes.c_size_t)]
+
+
+class fftm_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_longlong), ("status", ctypes.c_int), ("steps", ctypes.c_int),
+                ("converged_steps", ctypes.c_int), ("iterations", ctypes.c_int), ("err", ctypes.c_double),
+                ("mean_P", ctypes.c_double * 6), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("message", ctypes.c_char * 160)]
 
 
 class fftm_step_report(ctypes.Structure):
@@ -111,6 +124,11 @@ def load_library(path=LIB_PATH):
         "fftm_set_profiling": ([vp, ctypes.c_int], ctypes.c_int),
         "fftm_kernel_times": ([vp, P(ctypes.c_double), P(ctypes.c_longlong), ctypes.c_int], ctypes.c_int),
         "fftm_residual_noalloc": ([vp, vp, vp, vp], ctypes.c_int),
+        "fftm_server_create": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_int, P(vp)], ctypes.c_int),
+        "fftm_server_submit": ([vp, P(fftm_request), P(ctypes.c_longlong)], ctypes.c_int),
+        "fftm_server_poll": ([vp, P(fftm_result), ctypes.c_int, ctypes.c_int, P(ctypes.c_int)], ctypes.c_int),
+        "fftm_server_pending": ([vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)], ctypes.c_int),
+        "fftm_server_destroy": ([vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -309,3 +327,66 @@ def fftm_residual_noalloc(p, u_dev, D_dev, norms_dev):
     return _check(load_library().fftm_residual_noalloc(p, ctypes.c_void_p(u_dev.data_ptr()),
                                                         ctypes.c_void_p(D_dev.data_ptr()),
                                                         ctypes.c_void_p(norms_dev.data_ptr())))
+
+
+# ---- serving runtime (include/fftm_server.h) ------------------------------------------
+def fftm_server_create(device=0, memory_budget=0, max_slots=4):
+    s = ctypes.c_void_p()
+    _check(load_library().fftm_server_create(int(device), int(memory_budget), int(max_slots), ctypes.byref(s)))
+    return s
+
+
+def make_loads(loads):
+    """[(A, b, Q), ...] -> ctypes array of fftm_load."""
+    arr = (fftm_load * len(loads))()
+    for k, (A, b, Q) in enumerate(loads):
+        for q in range(3):
+            for a in range(3):
+                arr[k].A[q][a] = float(A[q][a])
+            arr[k].b[q] = float(b[q])
+            for m in range(6):
+                arr[k].Q[q][m] = 0.0 if Q is None else float(Q[q][m])
+    return arr
+
+
+def fftm_server_submit(s, desc, loads, u_out=None):
+    """desc: a fftm_problem_desc (from make_desc; its keepalive must live until this returns);
+    loads: [(A, b, Q), ...]; u_out: optional C-contiguous numpy array for the final u^f, kept
+    alive by the caller until the result is polled.  Returns the request id."""
+    la = make_loads(loads)
+    req = fftm_request()
+    req.desc = ctypes.cast(ctypes.pointer(desc), ctypes.c_void_p)
+    req.loads = ctypes.cast(la, ctypes.c_void_p)
+    req.n_loads = len(loads)
+    if u_out is not None:
+        if not u_out.flags["C_CONTIGUOUS"]:
+            raise ValueError("u_out must be C-contiguous")
+        req.u_out = u_out.ctypes.data
+        req.u_out_bytes = u_out.nbytes
+    rid = ctypes.c_longlong()
+    _check(load_library().fftm_server_submit(s, ctypes.byref(req), ctypes.byref(rid)))
+    return rid.value
+
+
+def fftm_server_poll(s, max_results=64, wait=True):
+    """Finished results as dicts (completion order)."""
+    out = (fftm_result * max_results)()
+    n = ctypes.c_int()
+    _check(load_library().fftm_server_poll(s, out, int(max_results), int(bool(wait)), ctypes.byref(n)))
+    res = []
+    for r in out[:n.value]:
+        res.append({"id": r.id, "status": r.status, "steps": r.steps, "converged_steps": r.converged_steps,
+                    "iterations": r.iterations, "err": r.err, "mean_P": np.array(r.mean_P[:]),
+                    "t_submit": r.t_submit, "t_start": r.t_start, "t_end": r.t_end,
+                    "message": r.message.decode(errors="replace")})
+    return res
+
+
+def fftm_server_pending(s):
+    q, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+    _check(load_library().fftm_server_pending(s, ctypes.byref(q), ctypes.byref(a), ctypes.byref(b)))
+    return q.value, a.value, b.value
+
+
+def fftm_server_destroy(s):
+    return _check(load_library().fftm_server_destroy(s))

@@ -1,4 +1,4 @@
-"""The C-ABI library builds for sm_103a, loads, and exports every symbol include/fftm.h declares.
+"""The C-ABI library builds for sm_103a, loads, and exports every symbol the headers in include/ declare.
 
 No compute call is made here (no GPU needed).
 """
@@ -14,9 +14,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "fftm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(fftm_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(fftm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),

@@ -1,0 +1,112 @@
+"""Serving runtime (include/fftm_server.h): continuous batching over one GPU.
+
+* each result is the same alone and in the mix: a set of requests of different
+  sizes, boundary conditions, laws and schemes, run one at a time and then all
+  resident at once on four slots, gives bitwise-equal iteration counts, errors,
+  mean stresses and displacement fields;
+* admission respects the memory budget (never more reserved than the budget while
+  the queue drains) and a request larger than the budget is refused.
+"""
+
+import numpy as np
+import pytest
+
+from paper_2607_05929_gb300 import build
+from paper_2607_05929_gb300 import fftm as F
+from synthetic.serving import request_spec, request_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    F.load_library()
+
+
+def _requests(count, max_side=48):
+    out, k = [], 0
+    while len(out) < count:
+        spec = request_spec(k)
+        k += 1
+        if spec["n"] <= max_side:
+            out.append(request_workload(spec))
+    return out
+
+
+def _desc(wl):
+    mats = [(m.law, m.params, m.quat) for m in wl.materials]
+    return F.make_desc(wl.n, wl.phase, mats, wl.bc, scheme=wl.scheme, green=wl.green, lambda0=wl.lambda0,
+                       mu0=wl.mu0, precision="fp32", tol=wl.tol, max_iter=wl.max_iter)
+
+
+def _u_buffer(wl):
+    N = [wl.n[a] if wl.bc[a][0][0] == "P" else wl.n[a] + 1 for a in range(3)]
+    return np.zeros((3, N[2], N[1], N[0]), dtype=np.float32)
+
+
+def _run(reqs, slots, one_at_a_time):
+    srv = F.fftm_server_create(0, 0, slots)
+    results, us, keep = {}, {}, []
+    try:
+        for i, (wl, loads) in enumerate(reqs):
+            desc, kp = _desc(wl)
+            u = _u_buffer(wl)
+            keep.append((kp, u))
+            rid = F.fftm_server_submit(srv, desc, loads, u_out=u)
+            us[rid] = (i, u)
+            if one_at_a_time:
+                for r in F.fftm_server_poll(srv, wait=True):
+                    results[us[r["id"]][0]] = r
+        while len(results) < len(reqs):
+            for r in F.fftm_server_poll(srv, wait=True):
+                results[us[r["id"]][0]] = r
+    finally:
+        F.fftm_server_destroy(srv)
+    fields = {i: u for (i, u) in us.values()}
+    return results, fields
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix():
+    reqs = _requests(6)
+    alone, u_alone = _run(reqs, 1, True)
+    mixed, u_mixed = _run(reqs, 4, False)
+    for i in range(len(reqs)):
+        a, m = alone[i], mixed[i]
+        assert a["status"] == F.FFTM_OK and m["status"] == F.FFTM_OK, (a, m)
+        assert a["iterations"] == m["iterations"] and a["steps"] == m["steps"]
+        assert a["err"] == m["err"]
+        assert np.array_equal(a["mean_P"], m["mean_P"])
+        assert np.array_equal(u_alone[i], u_mixed[i])
+    # the mixed run overlapped requests in time
+    spans = sorted((r["t_start"], r["t_end"]) for r in mixed.values())
+    assert any(spans[j + 1][0] < spans[j][1] for j in range(len(spans) - 1))
+
+
+def test_admission_respects_the_memory_budget_and_refuses_oversize():
+    reqs = _requests(5)
+    need = []
+    for wl, _ in reqs:
+        desc, kp = _desc(wl)
+        need.append(F.fftm_problem_workspace_bytes(desc) + (64 << 20))
+    budget = int(1.5 * max(need))
+    srv = F.fftm_server_create(0, budget, 4)
+    keep, seen = [], set()
+    try:
+        for wl, loads in reqs:
+            desc, kp = _desc(wl)
+            keep.append(kp)
+            F.fftm_server_submit(srv, desc, loads)
+        while len(seen) < len(reqs):
+            q, a, b = F.fftm_server_pending(srv)
+            assert b <= budget
+            for r in F.fftm_server_poll(srv, wait=False):
+                assert r["status"] == F.FFTM_OK
+                seen.add(r["id"])
+        wl, loads = _requests(1, max_side=128)[0]
+        big = F.make_desc((128, 128, 128), np.zeros((128, 128, 128), np.uint16), [(0, (1.0, 1.0), (1, 0, 0, 0))],
+                          wl.bc, precision="fp64")
+        with pytest.raises(F.FFTMError):
+            F.fftm_server_submit(srv, big[0], loads)  # far more than the budget
+    finally:
+        F.fftm_server_destroy(srv)
