@@ -272,6 +272,7 @@ struct fftm_problem {
   // tensor-core transforms (FFTM_FP32_TC): BF16 matrices, Kp x Kp per component and axis
   int tc = 0;
   void* tcmat = nullptr;
+  int* tc_err = nullptr;  // timeout flag of the tensor-core passes
   size_t off_tcf[3][3], off_tci[3][3];
   int tcKp[3][3];
   // device table offsets (bytes) inside `tables`
@@ -464,6 +465,7 @@ TcPassParams tc_params(fftm_problem* p, int axis, int inverse, int fused, int in
   P.two_mu0 = (float)(2.0 * p->desc.mu0);
   P.lam0 = (float)lam0;
   P.tetra = p->tetra;
+  P.err = p->tc_err;
   return P;
 }
 
@@ -771,6 +773,14 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     nacc += acc[i];
   }
   rep->n_accelerated = nacc;
+  if (p->tc) {  // a tensor-core pass that gave up on a barrier leaves its result undefined
+    int e = 0;
+    CU(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      CU(cudaMemset(p->tc_err, 0, sizeof(int)));
+      return set_err(FFTM_E_CUDA, "a tensor-core transform pass timed out waiting for its MMAs");
+    }
+  }
   const double npts = (double)p->nvox * (p->tetra ? 2 : 1);
   static const int map6[6] = {0, 4, 8, 5, 2, 1};
   for (int c = 0; c < 6; ++c) rep->mean_P[c] = p->hpin[16 + map6[c]] / npts;
@@ -941,6 +951,7 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->un);
   cudaFree(p->Dn);
   cudaFree(p->tcmat);
+  cudaFree(p->tc_err);
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -1079,11 +1090,18 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
   if (desc->precision == FFTM_FP32_TC) {
     p->tc = 1;
     std::vector<uint16_t> mats;
+    // Kp x Kp zero-padded, in 32-column chunks laid out as the shared-memory core
+    // matrices the tensor cores read: element (k, jj) of chunk c at
+    // c Kp 32 + (k>>3) 256 + (jj>>3) 64 + (k&7) 8 + (jj&7) (BF16 elements)
     auto put_mat = [&](const std::vector<double>& M, int L, int Kp) {
       size_t off = (mats.size() + 63) & ~(size_t)63;  // 128-byte aligned
       mats.resize(off + (size_t)Kp * Kp, 0);
       for (int r = 0; r < L; ++r)
-        for (int c = 0; c < L; ++c) mats[off + (size_t)r * Kp + c] = to_bf16(M[(size_t)r * L + c]);
+        for (int c = 0; c < L; ++c) {
+          const int ch = c / 32, jj = c % 32;
+          const size_t at = (size_t)ch * Kp * 32 + (size_t)(r >> 3) * 256 + (jj >> 3) * 64 + (r & 7) * 8 + (jj & 7);
+          mats[off + at] = to_bf16(M[(size_t)r * L + c]);
+        }
       return off * sizeof(uint16_t);
     };
     for (int q = 0; q < 3; ++q)
@@ -1092,13 +1110,17 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         int L;
         dense_forward(p->kind[q][a], p->n[a], &F, &L);
         dense_inverse(p->kind[q][a], p->n[a], &I);
-        const int Kp = (L + 15) / 16 * 16;
+        const int Kp = (L + 31) / 32 * 32;
+        // shared memory of one CTA: about 480 Kp bytes on the x axis, within 227 KiB up to Kp = 480
+        if (Kp > 480) return set_err(FFTM_E_UNSUPPORTED, "tensor-core transforms need lengths up to 480");
         p->tcKp[q][a] = Kp;
         p->off_tcf[q][a] = put_mat(F, L, Kp);
         p->off_tci[q][a] = put_mat(I, L, Kp);
       }
     CU(cudaMalloc(&p->tcmat, mats.size() * sizeof(uint16_t)));
     CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    CU(cudaMalloc(&p->tc_err, sizeof(int)));
+    CU(cudaMemset(p->tc_err, 0, sizeof(int)));
   }
   // ---- law tables ----
   std::vector<int> lid(desc->n_phases);
@@ -1388,6 +1410,14 @@ static int apply_t(fftm_problem* p, int op, double* norms) {
   }
   if (rc) return rc;
   CU(cudaStreamSynchronize(s));
+  if (p->tc) {
+    int e = 0;
+    CU(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      CU(cudaMemset(p->tc_err, 0, sizeof(int)));
+      return set_err(FFTM_E_CUDA, "a tensor-core transform pass timed out waiting for its MMAs");
+    }
+  }
   return FFTM_OK;
 }
 

@@ -113,8 +113,10 @@ constexpr int LAWC = 40;
 constexpr int kMaxDynSmem = 227 * 1024;
 
 // One axis pass as a dense contraction on the tensor cores (FP32 data, BF16
-// matrices).  A: the Kp x Kp (zero-padded) transform matrix, row-major BF16
-// bits; A2: the inverse z matrix of the fused z pass.
+// operands, tcgen05).  A: the Kp x Kp (zero-padded, Kp = L rounded up to 32) transform
+// matrix in 32-column chunks, each in the shared-memory core-matrix order (element
+// (k, jj) of chunk c at c Kp 32 + (k>>3) 256 + (jj>>3) 64 + (k&7) 8 + (jj&7), in BF16
+// elements); A2: the inverse z matrix of the fused z pass, same layout.
 struct TcPassParams {
   const float* in[3];
   float* out[3];
@@ -136,6 +138,7 @@ struct TcPassParams {
   float two_mu0, lam0;
   int tetra;
   float gscale[3];
+  int* err;  // set to 1 by a CTA whose wait on the tensor cores timed out
 };
 cudaError_t launch_pass_tc(const TcPassParams& P, cudaStream_t s);
 
