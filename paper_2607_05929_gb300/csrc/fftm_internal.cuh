@@ -141,6 +141,8 @@ struct TcPassParams {
   int* err;  // set to 1 by a CTA whose wait on the tensor cores timed out
 };
 cudaError_t launch_pass_tc(const TcPassParams& P, cudaStream_t s);
+// Whether a transform of padded length Kp along `axis` fits one tensor-core CTA.
+bool pass_tc_fits(int Kp, int axis);
 
 // Green factor on a spectral field (standalone step).
 template <typename T>
