@@ -62,8 +62,9 @@ enum fftm_scheme { FFTM_HEX1 = 0, FFTM_TETRA2 = 1 };
 enum fftm_green { FFTM_GREEN_B0 = 0, FFTM_GREEN_MU0 = 1 };
 /* FFTM_FP32_TC: FP32 fields and residual (as FFTM_FP32), per-axis transforms
    as dense matrix contractions on the tensor cores (tcgen05) with BF16 operands
-   and FP32 accumulation (transform lengths up to 288 node positions along x and
-   320 along y and z; FFTM_E_UNSUPPORTED beyond). */
+   and FP32 accumulation (transform lengths up to 288 node positions along x, the
+   range's first node mod 4 included, and 352 along y and z; FFTM_E_UNSUPPORTED
+   beyond). */
 enum fftm_precision { FFTM_FP64 = 0, FFTM_FP32 = 1, FFTM_FP32_TC = 2 };
 enum fftm_law {
   FFTM_LAW_ISO_ELASTIC = 0,   /* params: lambda, mu                          */

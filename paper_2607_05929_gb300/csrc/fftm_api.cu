@@ -1090,20 +1090,21 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
   if (desc->precision == FFTM_FP32_TC) {
     p->tc = 1;
     std::vector<uint16_t> mats;
-    // Kp x Kp zero-padded, in 32-column chunks laid out as the shared-memory core
-    // matrices the tensor cores read: element (k, jj) of chunk c at
-    // c Kp 32 + (k>>3) 256 + (jj>>3) 64 + (k&7) 8 + (jj&7) (BF16 elements)
-    // On the x axis the tensor-core pass indexes its input by x - xb, xb = lo rounded down to
-    // a multiple of 4 (aligned row copies), so there the input columns are shifted by lo - xb.
-    auto put_mat = [&](const std::vector<double>& M, int L, int Kp, int col0) {
+    // R x Kp zero-padded (R = Kp, on the x axis Kp rounded up to 128), in 32-column chunks
+    // laid out as the shared-memory core matrices the tensor cores read: element (m, jj) of
+    // chunk c at c R 32 + (m>>3) 256 + (jj>>3) 64 + (m&7) 8 + (jj&7) (BF16 elements).
+    // On the x axis the tensor-core pass indexes its input and output by x - xb, xb = lo
+    // rounded down to a multiple of 4 (aligned row copies), so there the rows and columns
+    // are shifted by lo - xb.
+    auto put_mat = [&](const std::vector<double>& M, int L, int Kp, int R, int sh) {
       size_t off = (mats.size() + 63) & ~(size_t)63;  // 128-byte aligned
-      mats.resize(off + (size_t)Kp * Kp, 0);
-      for (int r = 0; r < L; ++r)
+      mats.resize(off + (size_t)R * Kp, 0);
+      for (int r0 = 0; r0 < L; ++r0)
         for (int c0 = 0; c0 < L; ++c0) {
-          const int c = c0 + col0;
+          const int m = r0 + sh, c = c0 + sh;
           const int ch = c / 32, jj = c % 32;
-          const size_t at = (size_t)ch * Kp * 32 + (size_t)(r >> 3) * 256 + (jj >> 3) * 64 + (r & 7) * 8 + (jj & 7);
-          mats[off + at] = to_bf16(M[(size_t)r * L + c0]);
+          const size_t at = (size_t)ch * R * 32 + (size_t)(m >> 3) * 256 + (jj >> 3) * 64 + (m & 7) * 8 + (jj & 7);
+          mats[off + at] = to_bf16(M[(size_t)r0 * L + c0]);
         }
       return off * sizeof(uint16_t);
     };
@@ -1115,13 +1116,14 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         dense_inverse(p->kind[q][a], p->n[a], &I);
         const int col0 = a == 0 ? (p->plans[q][a].lo & 3) : 0;
         const int Kp = (L + col0 + 31) / 32 * 32;
-        // shared memory of one CTA (two pencil tiles, three matrix chunks): Kp up to 288 on
-        // the x axis, 320 on y and z
+        // shared memory of one CTA (two pencil tiles, at least two matrix chunks) and TMEM:
+        // Kp up to 288 on the x axis, 352 on y and z
         if (!pass_tc_fits(Kp, a))
-          return set_err(FFTM_E_UNSUPPORTED, "tensor-core transforms need lengths up to 288 (x) and 320 (y, z)");
+          return set_err(FFTM_E_UNSUPPORTED, "tensor-core transforms need lengths up to 288 (x) and 352 (y, z)");
         p->tcKp[q][a] = Kp;
-        p->off_tcf[q][a] = put_mat(F, L, Kp, col0);
-        p->off_tci[q][a] = put_mat(I, L, Kp, col0);
+        const int R = pass_tc_rows(Kp, a);
+        p->off_tcf[q][a] = put_mat(F, L, Kp, R, col0);
+        p->off_tci[q][a] = put_mat(I, L, Kp, R, col0);
       }
     CU(cudaMalloc(&p->tcmat, mats.size() * sizeof(uint16_t)));
     CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));

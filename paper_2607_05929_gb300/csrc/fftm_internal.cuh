@@ -143,6 +143,8 @@ struct TcPassParams {
 cudaError_t launch_pass_tc(const TcPassParams& P, cudaStream_t s);
 // Whether a transform of padded length Kp along `axis` fits one tensor-core CTA.
 bool pass_tc_fits(int Kp, int axis);
+// Rows of one matrix in the tensor-core chunk layout (x: Kp padded to a multiple of 128).
+int pass_tc_rows(int Kp, int axis);
 
 // Green factor on a spectral field (standalone step).
 template <typename T>

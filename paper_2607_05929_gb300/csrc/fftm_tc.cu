@@ -30,15 +30,16 @@
 
 namespace fftm {
 
-constexpr int UM_P = 128;        // pencils per CTA (MMA M)
+constexpr int UM_P = 128;        // pencils per tile (MMA M on y and z, N on x)
 constexpr int UM_KC = 32;        // K columns per matrix chunk (2 MMA k-steps)
-// warp roles: 0-3 epilogue (TMEM lanes 32 w .. 32 w + 31), 4-11 stage pencil tiles,
-// 12 streams the matrix chunks and issues the MMAs (lane 0)
-constexpr int UM_THREADS = 416;
-constexpr int UM_PROD = 256;  // producer threads
-constexpr int UM_NBUF = 3;       // matrix chunk buffers (two chunks in flight ahead of the MMAs)
+// warp roles: 0-7 epilogue (warp w reads TMEM lanes 32 (w % 4) .. + 31), 8-14 stage pencil
+// tiles, 15 streams the matrix chunks and issues the MMAs (lane 0)
+constexpr int UM_EPI = 256;      // epilogue threads
+constexpr int UM_PROD = 224;     // producer threads
+constexpr int UM_THREADS = UM_EPI + UM_PROD + 32;
+constexpr int UM_MAXBUF = 8;     // matrix chunk buffers at most
 constexpr int UM_TMEM_COLS = 512;
-constexpr long long UM_SPIN = 1ll << 24;  // mbarrier polls before giving up (~1 s with the back-off)
+constexpr long long UM_SPIN = 1ll << 24;  // polls without progress before giving up (~1 s with the back-off)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -146,13 +147,20 @@ __device__ __forceinline__ GreenLine tc_green_line(const TcPassParams& P, int q,
   return G;
 }
 
-// Shared-memory geometry of one CTA (bytes).  Kp = padded transform length (input and
-// output), a multiple of 32.
+// Shared-memory geometry of one CTA (bytes) for a padded transform length Kp (a multiple
+// of 32).  x axis: the matrix is the A operand (M = outputs, padded to Mp = a multiple of
+// 128) and the pencil tile the B operand (N = 128 pencils, K-major); y and z axes: the
+// pencil tile is the A operand (M = 128 pencils, MN-major) and the matrix the B operand
+// (N = outputs).  Matrices are streamed in chunks of 32 K columns through a ring of nbuf
+// buffers.
 struct UmGeom {
-  uint32_t a_lbo, a_sbo, a_bytes;  // pencil tile (A operand)
-  uint32_t b_bytes;                // one matrix chunk (Kp x 32)
+  uint32_t a_lbo, a_sbo, a_bytes;  // pencil tile
+  uint32_t chunk_bytes;            // one matrix chunk (Mp x 32 BF16)
+  int mp, nbuf;
+  int acc_cols;                    // TMEM columns of one accumulator
   __host__ __device__ static UmGeom make(int Kp, int axis) {
     UmGeom g;
+    g.mp = axis == 0 ? (Kp + 127) / 128 * 128 : Kp;
     if (axis == 0) {  // K-major: element (p, j) at (p>>3) SBO + (j>>3) LBO + (p&7) 16 + (j&7) 2
       g.a_lbo = 144;  // 128 + 16: consecutive core matrices along K fall on different banks
       g.a_sbo = (uint32_t)(Kp / 8) * 144;
@@ -164,16 +172,20 @@ struct UmGeom {
     // the fused pass writes its second A operand K-major with LBO 128, SBO (Kp/8) 128
     const uint32_t fused_bytes = (uint32_t)(UM_P / 8) * (uint32_t)(Kp / 8) * 128;
     if (fused_bytes > g.a_bytes) g.a_bytes = fused_bytes;
-    // the x-axis epilogue stages 32 outputs of the 128 pencils here (pitch 33 floats)
-    if ((uint32_t)(UM_P * 33 * 4) > g.a_bytes) g.a_bytes = UM_P * 33 * 4;
     g.a_bytes = (g.a_bytes + 1023) & ~1023u;
-    g.b_bytes = (uint32_t)Kp * UM_KC * 2;
+    g.chunk_bytes = (uint32_t)g.mp * UM_KC * 2;
+    g.acc_cols = axis == 0 ? g.mp : Kp;  // x: Mp / 128 blocks of 128 pencils; y, z: Kp outputs
+    const long long room = (long long)kMaxDynSmem - (long long)fixed_bytes(g.a_bytes);
+    g.nbuf = room > 0 ? (int)(room / g.chunk_bytes) : 0;
+    if (g.nbuf > UM_MAXBUF) g.nbuf = UM_MAXBUF;
     return g;
   }
-  // two pencil-tile buffers (one staged while the other is contracted), UM_NBUF chunk buffers,
-  // barriers and flags
-  __host__ __device__ size_t smem() const { return 2 * (size_t)a_bytes + UM_NBUF * (size_t)b_bytes + 256; }
+  // two pencil-tile buffers, four tables of pencil row offsets (x pass), barriers and flags
+  __host__ __device__ static size_t fixed_bytes(uint32_t a_bytes) { return 2 * (size_t)a_bytes + 4 * UM_P * 8 + 512; }
+  __host__ __device__ size_t smem() const { return fixed_bytes(a_bytes) + (size_t)nbuf * chunk_bytes; }
 };
+
+__host__ __device__ inline UmGeom um_geom(int Kp, int axis) { return UmGeom::make(Kp, axis); }
 
 // ---- tiles ------------------------------------------------------------------------------
 // A pass enumerates, over the three components, the tiles of 128 pencils it transforms:
@@ -242,23 +254,28 @@ __device__ __forceinline__ int total_tiles(const TcPassParams& P) {
   return n;
 }
 
-// ---- the three roles ---------------------------------------------------------------------
-// Stage one tile as the BF16 A operand (UM_PROD producer threads, ptid 0 .. UM_PROD - 1),
-// eight 16-byte loads in flight per thread.  x axis: the K index is j = x - xb with xb the
-// range offset rounded down to a multiple of 4 (the host shifted the matrix columns by
-// lo - xb), so each row is read with aligned 16-byte loads and the nodes outside the range
-// are zeroed; y and z: MN-major rows of 8 pencils.
+// ---- producers --------------------------------------------------------------------------
+// Stage one tile as BF16 (UM_PROD producer threads, ptid 0 .. UM_PROD - 1), eight 16-byte
+// loads in flight per thread.  x axis: the K index is j = x - xb with xb the range offset
+// rounded down to a multiple of 4 (the host shifted the matrix columns by lo - xb), so each
+// row is read with aligned 16-byte loads and the nodes outside the range are zeroed; the
+// element offsets of the 128 pencil rows go to `offs` for the epilogue.  y and z: MN-major
+// rows of 8 pencils.
 template <int AXIS>
 __device__ __forceinline__ void stage_tile(const TcPassParams& P, const Tile& T, const UmGeom& g, unsigned char* sA,
-                                           int ptid) {
+                                           long long* offs, int ptid) {
   const float* __restrict__ in = P.in[T.q];
   const int L = T.L, Kp = T.Kp, npen = T.npen;
   if (AXIS == 0) {
-    // K-major: item (p, j4) covers the 4 nodes x = xb + j4 .. xb + j4 + 3 of pencil p; x is a
+    // item (p, j4) covers the 4 nodes x = xb + j4 .. xb + j4 + 3 of pencil p; x is a
     // multiple of 4 below N1 and the row pitch a multiple of 8 >= N1, so the load stays in
     // the row.  Element (p, j) at (p>>3) SBO + (j>>3) LBO + (p&7) 16 + (j&7) 2.
     const long long sy = P.stride[1], sz = P.stride[2];
     const int N1 = P.N[0], N2 = P.N[1], lo = T.lo, xb = T.lo & ~3;
+    if (ptid < UM_P) {
+      const int r = T.row0 + ptid;
+      offs[ptid] = ptid < npen ? (long long)(r % N2) * sy + (long long)(r / N2) * sz : 0;
+    }
     const int nx4 = Kp / 4, total = UM_P * nx4;
     for (int i0 = ptid; i0 < total; i0 += 8 * UM_PROD) {
       float4 v[8];
@@ -289,8 +306,8 @@ __device__ __forceinline__ void stage_tile(const TcPassParams& P, const Tile& T,
       }
     }
   } else {
-    // MN-major; item (pg, j) converts the 8 pencils 8 pg .. 8 pg + 7 of row j (32 aligned
-    // bytes: the tile starts at a multiple of 8 and the row pitch is a multiple of 8)
+    // item (pg, j) converts the 8 pencils 8 pg .. 8 pg + 7 of row j (32 aligned bytes: the
+    // tile starts at a multiple of 8 and the row pitch is a multiple of 8)
     const int total = (UM_P / 8) * Kp;
     for (int i0 = ptid; i0 < total; i0 += 4 * UM_PROD) {
       float4 v[4][2];
@@ -329,135 +346,255 @@ __device__ __forceinline__ void stage_tile(const TcPassParams& P, const Tile& T,
   }
 }
 
-// One contraction over Kp by the MMA warp: A operand at sA, B chunks streamed from `mat`
-// through the UM_NBUF buffers at sB (loaded UM_NBUF - 1 chunks ahead by the 32 lanes;
-// chunk c is committed to bbar[c % UM_NBUF], counted in buses[]).  Lane 0 issues the MMAs.
-__device__ __forceinline__ bool mma_contract(const uint16_t* __restrict__ mat, int Kp, unsigned char* sA,
-                                             uint32_t a_lbo, uint32_t a_sbo, bool a_mn, unsigned char* sB,
-                                             uint32_t b_stride, uint64_t* bbar, uint32_t buses[UM_NBUF],
-                                             uint32_t tmem, volatile int* abort, int lane) {
-  const int nch = Kp / UM_KC;
-  const uint32_t chunk_bytes = (uint32_t)Kp * UM_KC * 2;
-  // copies of a chunk into buffer b may start once the MMAs that last read b completed
-  auto load_chunk = [&](int c) -> bool {
-    const int b = c % UM_NBUF;
-    bool ok = true;
-    if (buses[b] & 0x80000000u) {  // an un-waited commit on b
-      ok = bar_wait(&bbar[b], buses[b] & 1, abort);
-      buses[b] = (buses[b] + 1) & 0x7FFFFFFFu;
+// ---- the MMA thread ---------------------------------------------------------------------
+// The contractions of a CTA, in issue order: C1(i) = forward matrix on tile i, C2(i) =
+// inverse matrix on the Green-scaled tile i (fused pass).  With two accumulators the
+// forward contraction of tile i + 1 is issued before C2(i), so that it runs while the
+// epilogue applies the Green factor to tile i.
+struct ContrSeq {
+  int c1 = 0, c2 = 0;
+  __device__ __forceinline__ void next(int fused, int nacc, int ntiles, int* tile, int* kind) {
+    if (!fused) {
+      *tile = c1++;
+      *kind = 0;
+    } else if (c1 < ntiles && c1 <= c2 + nacc - 1) {
+      *tile = c1++;
+      *kind = 0;
+    } else {
+      *tile = c2++;
+      *kind = 1;
     }
-    const char* src = reinterpret_cast<const char*>(mat) + (size_t)c * chunk_bytes;
-    unsigned char* dst = sB + (size_t)b * b_stride;
-    if (ok)
-      for (uint32_t off = lane * 16; off < chunk_bytes; off += 32 * 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst + off)), "l"(src + off)
-                     : "memory");
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    return ok;
-  };
-  bool ok = true;
-  for (int c = 0; c < UM_NBUF - 1; ++c) {
-    if (c < nch) ok = load_chunk(c) && ok;
-    else asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
-  for (int c = 0; c < nch && ok; ++c) {
-    const int cn = c + UM_NBUF - 1;
-    if (cn < nch) ok = load_chunk(cn) && ok;
-    else asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(UM_NBUF - 1) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncwarp();
-    if (!ok) break;
-    if (lane == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t sb = smem_u32(sB + (size_t)(c % UM_NBUF) * b_stride);
-#pragma unroll
-      for (int s = 0; s < UM_KC / 16; ++s) {
-        const int kk = c * UM_KC + s * 16;
-        const uint64_t da = smem_desc(smem_u32(sA) + (uint32_t)(kk / 8) * a_lbo, a_lbo, a_sbo);
-        for (int n0 = 0; n0 < Kp; n0 += 256) {
-          const int nn = Kp - n0 < 256 ? Kp - n0 : 256;
-          const uint64_t db = smem_desc(sb + (uint32_t)(n0 / 8) * 512 + s * 256, 128, 512);
-          mma_issue(tmem + n0, da, db, instr_desc(nn, a_mn), (c > 0 || s > 0) ? 1u : 0u);
-        }
-      }
-      mma_commit(&bbar[c % UM_NBUF]);
-    }
-    __syncwarp();
-    buses[c % UM_NBUF] |= 0x80000000u;  // its commit is now pending
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  return ok;
+};
+
+__device__ __forceinline__ bool bar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
 }
 
-// The epilogue (128 threads, warps 0-3; thread = TMEM lane = pencil p of the tile).
+__device__ __forceinline__ void bulk_load(unsigned char* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared state of the CTA's barriers.
+struct UmBars {
+  uint64_t* a_full;     // [2]  UM_PROD arrivals: tile staged
+  uint64_t* a_empty;    // [2]  1 (MMA commit): the tile's last contraction has read it
+  uint64_t* acc_full;   // [2]  1 (MMA commit): a contraction into the accumulator is done
+  uint64_t* acc_empty;  // [2]  UM_EPI arrivals: the epilogue has drained the accumulator
+  uint64_t* a2_ready;   // 1    UM_EPI arrivals: Green-scaled tile written (fused)
+  uint64_t* b_full;     // [UM_MAXBUF] transaction bytes: chunk landed
+  uint64_t* b_empty;    // [UM_MAXBUF] 1 (MMA commit): chunk consumed
+  uint64_t* done;       // 1    (MMA commit): every MMA of the CTA has completed
+};
+
+template <int AXIS, int FUSED>
+__device__ void mma_thread(const TcPassParams& P, const UmGeom& g, unsigned char* const sA[2], unsigned char* sB,
+                           const UmBars& B, uint32_t tmem, int nacc, int my_tiles, volatile int* abort) {
+  const int ncontr = my_tiles * (FUSED ? 2 : 1);
+  ContrSeq lseq, cseq;
+  // loader position: contraction lt (tile lti, kind lk), chunk lc of lnch
+  int lt = 0, lti = 0, lk = 0, lc = 0, lnch = 0;
+  const unsigned char* lmat = nullptr;
+  uint32_t lbytes = 0;
+  // consumer position
+  int ct = 0, cti = 0, ck = 0, cc = 0, cnch = 0, cstarted = 0;
+  Tile CT;
+  UmGeom cg = g;
+  long long ni = 0, nc = 0;  // chunks issued, consumed
+  long long idle = 0;
+  auto load_contr = [&]() {
+    lseq.next(FUSED, nacc, my_tiles, &lti, &lk);
+    const Tile T = tile_of<AXIS, FUSED>(P, blockIdx.x + lti * gridDim.x);
+    const UmGeom tg = um_geom(T.Kp, AXIS);
+    lmat = reinterpret_cast<const unsigned char*>(lk ? P.A2[T.q] : P.A[T.q]);
+    lbytes = tg.chunk_bytes;
+    lnch = T.Kp / UM_KC;
+    lc = 0;
+  };
+  auto cons_contr = [&]() {
+    cseq.next(FUSED, nacc, my_tiles, &cti, &ck);
+    CT = tile_of<AXIS, FUSED>(P, blockIdx.x + cti * gridDim.x);
+    cg = um_geom(CT.Kp, AXIS);
+    cnch = CT.Kp / UM_KC;
+    cc = 0;
+    cstarted = 0;
+  };
+  if (ncontr > 0) {
+    load_contr();
+    cons_contr();
+  }
+  while (ct < ncontr) {
+    bool progress = false;
+    // -- loader: the next chunk, once its ring buffer's previous chunk has been consumed
+    if (lt < ncontr && ni < nc + g.nbuf) {
+      const int b = (int)(ni % g.nbuf);
+      const long long u = ni / g.nbuf;
+      if (u == 0 || bar_test(&B.b_empty[b], (uint32_t)((u - 1) & 1))) {
+        bulk_load(sB + (size_t)b * g.chunk_bytes, lmat + (size_t)lc * lbytes, lbytes, &B.b_full[b]);
+        ++ni;
+        progress = true;
+        if (++lc == lnch && ++lt < ncontr) load_contr();
+      }
+    }
+    // -- consumer: start the contraction once its operands and accumulator are free
+    if (!cstarted) {
+      const int s = cti & 1, a = cti % nacc;
+      bool ready;
+      if (ck == 0)
+        ready = bar_test(&B.a_full[s], (uint32_t)((cti >> 1) & 1)) &&
+                (cti < nacc || bar_test(&B.acc_empty[a], (uint32_t)(((cti / nacc) - 1) & 1)));
+      else
+        ready = bar_test(B.a2_ready, (uint32_t)(cti & 1));
+      if (ready) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        cstarted = 1;
+        progress = true;
+      }
+    }
+    if (cstarted && nc < ni) {
+      const int b = (int)(nc % g.nbuf);
+      if (bar_test(&B.b_full[b], (uint32_t)((nc / g.nbuf) & 1))) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const int s = cti & 1, a = cti % nacc;
+        const uint32_t acc = tmem + (uint32_t)(a * 256);
+        const uint32_t sb = smem_u32(sB + (size_t)b * g.chunk_bytes);
+        const uint32_t sa = smem_u32(sA[s]);
+#pragma unroll
+        for (int st = 0; st < UM_KC / 16; ++st) {
+          const int kk = cc * UM_KC + st * 16;
+          const uint32_t accum = (cc > 0 || st > 0) ? 1u : 0u;
+          if (AXIS == 0) {
+            // D[m][p] += T[m][k] S[p][k]: A = matrix chunk (K-major, M blocks of 128 rows),
+            // B = pencil tile (K-major, N = 128)
+            const uint64_t db = smem_desc(sa + (uint32_t)(kk / 8) * cg.a_lbo, cg.a_lbo, cg.a_sbo);
+            for (int mb = 0; mb < cg.mp / 128; ++mb) {
+              const uint64_t da = smem_desc(sb + (uint32_t)mb * 16 * 512 + st * 256, 128, 512);
+              mma_issue(acc + mb * 128, da, db, instr_desc(UM_P, false), accum);
+            }
+          } else {
+            // D[p][k] += S[p][j] T[k][j]: A = pencil tile (MN-major; K-major for the Green-scaled
+            // tile of C2), B = matrix chunk (K-major, N = outputs in blocks of up to 256)
+            const bool mn = ck == 0;
+            const uint32_t albo = mn ? cg.a_lbo : 128u, asbo = mn ? cg.a_sbo : (uint32_t)(CT.Kp / 8) * 128;
+            const uint64_t da = smem_desc(sa + (uint32_t)(kk / 8) * albo, albo, asbo);
+            for (int n0 = 0; n0 < CT.Kp; n0 += 256) {
+              const int nn = CT.Kp - n0 < 256 ? CT.Kp - n0 : 256;
+              const uint64_t db = smem_desc(sb + (uint32_t)(n0 / 8) * 512 + st * 256, 128, 512);
+              mma_issue(acc + n0, da, db, instr_desc(nn, mn), accum);
+            }
+          }
+        }
+        mma_commit(&B.b_empty[b]);
+        ++nc;
+        progress = true;
+        if (++cc == cnch) {
+          mma_commit(&B.acc_full[a]);
+          if (!FUSED || ck == 1) mma_commit(&B.a_empty[s]);
+          if (++ct < ncontr) cons_contr();
+        }
+      }
+    }
+    if (progress) {
+      idle = 0;
+    } else if (++idle > 64) {
+      __nanosleep(64);
+      if (idle > UM_SPIN || ((idle & 255) == 0 && *abort)) {
+        *abort = 1;
+        break;
+      }
+    }
+  }
+  // copies still in flight (only after an abort) land, and every MMA completes, before the
+  // CTA frees its TMEM and exits
+  for (long long k = nc; k < ni; ++k) {
+    const int b = (int)(k % g.nbuf);
+    for (long long it = 0; it < UM_SPIN && !bar_test(&B.b_full[b], (uint32_t)((k / g.nbuf) & 1)); ++it)
+      __nanosleep(64);
+  }
+  if (nc > 0) {
+    mma_commit(B.done);
+    for (long long it = 0; it < UM_SPIN && !bar_test(B.done, 0u); ++it) __nanosleep(64);
+  }
+}
+
+// ---- the epilogue -----------------------------------------------------------------------
+// UM_EPI threads, warps 0-7: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31 and takes
+// half h = w / 4 of the accumulator's columns (x: of its M blocks).
 template <int AXIS>
-__device__ __forceinline__ void store_tile(const TcPassParams& P, const Tile& T, uint32_t tmem, float* slab,
+__device__ __forceinline__ void store_tile(const TcPassParams& P, const Tile& T, uint32_t acc, const long long* offs,
                                            int warp, int lane) {
   const int q = T.q, L = T.L, Kp = T.Kp, npen = T.npen;
   float* __restrict__ out = P.out[q];
-  const float* __restrict__ bh = P.base[q];
-  const float* __restrict__ bl = P.base_lo[q];
-  float* __restrict__ ol = P.out_lo[q];
   const float sc = P.scale[q];
-  const int p = warp * 32 + lane;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const int gq = warp & 3, h = warp >> 2;
+  const uint32_t lane_base = (uint32_t)(gq * 32) << 16;
   if (AXIS == 0) {
-    // pencils are rows of memory: stage 32 outputs of the 128 pencils (pitch 33 floats) and
-    // write each pencil's 32 outputs with one coalesced warp access, 8 rows in flight
-    const long long sy = P.stride[1], sz = P.stride[2];
-    const int N2 = P.N[1];
-    for (int s0 = 0; s0 < Kp; s0 += 32) {
-      float v[16];
-      tmem_ld16(tmem + lane_base + s0, v);
+    // lanes are outputs: M index m <-> node x = xb + m; a warp writes 32 consecutive nodes of
+    // one pencil row per store
+    const float* __restrict__ bh = P.base[q];
+    const float* __restrict__ bl = P.base_lo[q];
+    float* __restrict__ ol = P.out_lo[q];
+    const int mp = (Kp + 127) / 128 * 128, xb = T.lo & ~3;
+    for (int mb = h; mb < mp / 128; mb += 2) {
+      const int x = xb + mb * 128 + gq * 32 + lane;
+      const bool ok = x >= T.lo && x < T.lo + L;
+      for (int p0 = 0; p0 < npen; p0 += 16) {
+        float v[16];
+        tmem_ld16(acc + lane_base + (uint32_t)(mb * 128 + p0), v);
+        if (bh == nullptr) {
 #pragma unroll
-      for (int i = 0; i < 16; ++i) slab[p * 33 + i] = sc * v[i];
-      tmem_ld16(tmem + lane_base + s0 + 16, v);
+          for (int u = 0; u < 16; ++u)
+            if (ok && p0 + u < npen) out[offs[p0 + u] + x] = sc * v[u];
+        } else {
+          float a[16], b[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) slab[p * 33 + 16 + i] = sc * v[i];
-      role_sync(1);
-      const int k = s0 + lane;
-      if (k < L) {
-        for (int pp0 = warp; pp0 < npen; pp0 += 4 * 8) {
-          long long at[8];
-          float a[8], b[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int pp = pp0 + 4 * u;
-            const int r = T.row0 + (pp < npen ? pp : 0);
-            at[u] = (long long)(r % N2) * sy + (long long)(r / N2) * sz + T.lo + k;
-            a[u] = (bh && pp < npen) ? bh[at[u]] : 0.f;
-            b[u] = (ol && pp < npen) ? bl[at[u]] : 0.f;
+          for (int u = 0; u < 16; ++u) {
+            const bool live = ok && p0 + u < npen;
+            const long long at = offs[p0 + u] + x;
+            a[u] = live ? bh[at] : 0.f;
+            b[u] = (live && ol) ? bl[at] : 0.f;
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int pp = pp0 + 4 * u;
-            if (pp >= npen) break;
-            const float val = slab[pp * 33 + lane];
-            if (bh == nullptr) {
-              out[at[u]] = val;
-            } else if (ol == nullptr) {
-              out[at[u]] = a[u] + val;
+          for (int u = 0; u < 16; ++u) {
+            if (!(ok && p0 + u < npen)) continue;
+            const long long at = offs[p0 + u] + x;
+            const float val = sc * v[u];
+            if (ol == nullptr) {
+              out[at] = a[u] + val;
             } else {  // (hi, lo) = (bh, bl) + val with an error-free sum of the high parts
               const float s1 = a[u] + val;
               const float bb = s1 - a[u];
               const float er = (a[u] - (s1 - bb)) + (val - bb);
               const float tt = b[u] + er;
               const float hsum = s1 + tt;
-              out[at[u]] = hsum;
-              ol[at[u]] = tt - (hsum - s1);
+              out[at] = hsum;
+              ol[at] = tt - (hsum - s1);
             }
           }
         }
       }
-      role_sync(1);
     }
   } else {
+    // lanes are pencils (consecutive in memory): one coalesced store per output
+    const int p = gq * 32 + lane;
     const bool live = p < npen;
     const long long rowbase = T.base0 + p + (long long)T.lo * T.estride;
-    for (int c0 = 0; c0 < Kp; c0 += 16) {
+    const int half = Kp / 2;
+    for (int c0 = h * half; c0 < (h + 1) * half; c0 += 16) {
       float v[16];
-      tmem_ld16(tmem + lane_base + c0, v);  // warp-collective: every lane takes part
+      tmem_ld16(acc + lane_base + (uint32_t)c0, v);  // warp-collective: every lane takes part
       if (!live) continue;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
@@ -468,24 +605,66 @@ __device__ __forceinline__ void store_tile(const TcPassParams& P, const Tile& T,
   }
 }
 
+// Fused z pass: Green factor on (kx, ky, kz) of the forward result, written back K-major as
+// the A operand of the inverse contraction.
+__device__ __forceinline__ void green_tile(const TcPassParams& P, const Tile& T, uint32_t acc, unsigned char* sA,
+                                           int warp, int lane) {
+  const int gq = warp & 3, h = warp >> 2;
+  const uint32_t lane_base = (uint32_t)(gq * 32) << 16;
+  const int p = gq * 32 + lane;
+  const int ky = T.yfix - P.flo[T.q][1];
+  const int kx = T.x0 + p - P.flo[T.q][0];
+  const bool live = p < T.npen && kx >= 0 && kx < P.fL[T.q][0];
+  const uint32_t sbo2 = (uint32_t)(T.Kp / 8) * 128;
+  const GreenLine G = tc_green_line(P, T.q, live ? kx : 0, ky);
+  const float* __restrict__ Sz = P.S2[T.q][2];
+  const float* __restrict__ Cz = P.C2[T.q][2];
+  const int half = T.Kp / 2;
+  for (int c0 = h * half; c0 < (h + 1) * half; c0 += 16) {
+    float v[16];
+    tmem_ld16(acc + lane_base + (uint32_t)c0, v);
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = c0 + u;
+      v[u] = (live && k < T.L) ? v[u] * G.at(Sz[k], Cz[k]) : 0.f;
+    }
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh) {
+      uint4 w;
+      w.x = pack_bf16x2(v[8 * hh + 0], v[8 * hh + 1]);
+      w.y = pack_bf16x2(v[8 * hh + 2], v[8 * hh + 3]);
+      w.z = pack_bf16x2(v[8 * hh + 4], v[8 * hh + 5]);
+      w.w = pack_bf16x2(v[8 * hh + 6], v[8 * hh + 7]);
+      *reinterpret_cast<uint4*>(sA + (uint32_t)(p >> 3) * sbo2 + (uint32_t)((c0 >> 3) + hh) * 128 + (p & 7) * 16) = w;
+    }
+  }
+}
+
 template <int AXIS, int FUSED>
 __global__ void __launch_bounds__(UM_THREADS, 1) k_pass_umma(TcPassParams P, int maxKp) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const UmGeom g = UmGeom::make(maxKp, AXIS);
-  unsigned char* sA[2] = {smem, smem + g.a_bytes};
-  unsigned char* sB = smem + 2 * (size_t)g.a_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + (size_t)UM_NBUF * g.b_bytes);
-  uint64_t* a_full = bars;          // [2], UM_PROD arrivals (producers)
-  uint64_t* a_empty = bars + 2;     // [2], 128 arrivals (epilogue)
-  uint64_t* acc_full = bars + 4;    // 1 arrival (MMA commit)
-  uint64_t* acc_empty = bars + 5;   // 128 arrivals (epilogue)
-  uint64_t* a2_ready = bars + 6;    // 128 arrivals (epilogue, fused pass)
-  uint64_t* b_empty = bars + 7;     // [UM_NBUF], MMA commits
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 7 + UM_NBUF);
+  const UmGeom g = um_geom(maxKp, AXIS);
+  unsigned char* const sA[2] = {smem, smem + g.a_bytes};
+  // pencil row offsets of tile i (x pass) in table i % 4: the producers of tile i + 4 start
+  // only after the epilogue of tile i has finished with it (through the accumulator hand-over)
+  long long* offs_all = reinterpret_cast<long long*>(smem + 2 * (size_t)g.a_bytes);  // [4][UM_P]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(offs_all + 4 * UM_P);
+  UmBars B;
+  B.a_full = bars;
+  B.a_empty = bars + 2;
+  B.acc_full = bars + 4;
+  B.acc_empty = bars + 6;
+  B.a2_ready = bars + 8;
+  B.b_full = bars + 9;
+  B.b_empty = bars + 9 + UM_MAXBUF;
+  B.done = bars + 9 + 2 * UM_MAXBUF;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10 + 2 * UM_MAXBUF);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  unsigned char* sB = smem + UmGeom::fixed_bytes(g.a_bytes);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ntiles = total_tiles<AXIS, FUSED>(P);
   const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int nacc = 2 * g.acc_cols <= UM_TMEM_COLS ? 2 : 1;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
@@ -493,111 +672,64 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_pass_umma(TcPassParams P, int
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
   if (tid == 0) {
-    bar_init(&a_full[0], UM_PROD);
-    bar_init(&a_full[1], UM_PROD);
-    bar_init(&a_empty[0], 128);
-    bar_init(&a_empty[1], 128);
-    bar_init(acc_full, 1);
-    bar_init(acc_empty, 128);
-    bar_init(a2_ready, 128);
-    for (int b = 0; b < UM_NBUF; ++b) bar_init(&b_empty[b], 1);
+    for (int i = 0; i < 2; ++i) {
+      bar_init(&B.a_full[i], UM_PROD);
+      bar_init(&B.a_empty[i], 1);
+      bar_init(&B.acc_full[i], 1);
+      bar_init(&B.acc_empty[i], UM_EPI);
+    }
+    bar_init(B.a2_ready, UM_EPI);
+    bar_init(B.done, 1);
+    for (int b = 0; b < UM_MAXBUF; ++b) {
+      bar_init(&B.b_full[b], 1);
+      bar_init(&B.b_empty[b], 1);
+    }
     *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp >= 4 && warp < 4 + UM_PROD / 32) {
-    // ---- producers: stage tile i into buffer i % 2 once the epilogue of tile i - 2 freed it ----
-    const int ptid = tid - 128;
+  if (warp >= UM_EPI / 32 && warp < (UM_EPI + UM_PROD) / 32) {
+    // ---- producers: stage tile i into buffer i % 2 once the last contraction of tile i - 2
+    // has read it ----
+    const int ptid = tid - UM_EPI;
     for (int i = 0; i < my_tiles; ++i) {
       const int s = i & 1;
-      if (i >= 2 && !bar_wait(&a_empty[s], ((i >> 1) - 1) & 1, abort)) break;
+      if (i >= 2 && !bar_wait(&B.a_empty[s], ((i >> 1) - 1) & 1, abort)) break;
       const Tile T = tile_of<AXIS, FUSED>(P, blockIdx.x + i * gridDim.x);
-      stage_tile<AXIS>(P, T, UmGeom::make(T.Kp, AXIS), sA[s], ptid);
+      stage_tile<AXIS>(P, T, um_geom(T.Kp, AXIS), sA[s], offs_all + (i & 3) * UM_P, ptid);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      bar_arrive(&a_full[s]);
+      bar_arrive(&B.a_full[s]);
     }
-  } else if (warp == 4 + UM_PROD / 32) {
-    // ---- MMA warp ----
-    uint32_t buses[UM_NBUF];
-    for (int b = 0; b < UM_NBUF; ++b) buses[b] = 0u;
-    for (int i = 0; i < my_tiles; ++i) {
-      const int s = i & 1;
-      if (!bar_wait(&a_full[s], (i >> 1) & 1, abort)) break;
-      if (i >= 1 && !bar_wait(acc_empty, (i - 1) & 1, abort)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const Tile T = tile_of<AXIS, FUSED>(P, blockIdx.x + i * gridDim.x);
-      const UmGeom gt = UmGeom::make(T.Kp, AXIS);
-      if (!mma_contract(P.A[T.q], T.Kp, sA[s], gt.a_lbo, gt.a_sbo, AXIS != 0, sB, g.b_bytes, b_empty, buses, tmem,
-                        abort, lane))
-        break;
-      if (lane == 0) mma_commit(acc_full);
-      __syncwarp();
-      if (FUSED) {
-        if (!bar_wait(a2_ready, i & 1, abort)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (!mma_contract(P.A2[T.q], T.Kp, sA[s], 128, (uint32_t)(T.Kp / 8) * 128, false, sB, g.b_bytes, b_empty,
-                          buses, tmem, abort, lane))
-          break;
-        if (lane == 0) mma_commit(acc_full);
-        __syncwarp();
-      }
-    }
-    // commits still pending on the chunk buffers (they complete with the last acc_full)
-    for (int b = 0; b < UM_NBUF; ++b)
-      if (buses[b] & 0x80000000u) bar_wait(&b_empty[b], buses[b] & 1, abort);
+  } else if (warp == (UM_EPI + UM_PROD) / 32) {
+    // ---- MMA warp: lane 0 streams the matrix chunks and issues the MMAs ----
+    if (lane == 0) mma_thread<AXIS, FUSED>(P, g, sA, sB, B, tmem, nacc, my_tiles, abort);
+    __syncwarp();
   } else {
-    // ---- epilogue warps 0-3 ----
-    uint32_t acc_uses = 0;
+    // ---- epilogue warps 0-7 ----
+    uint32_t acc_uses[2] = {0u, 0u};
     for (int i = 0; i < my_tiles; ++i) {
-      const int s = i & 1;
+      const int s = i & 1, a = i % nacc;
+      const uint32_t acc = tmem + (uint32_t)(a * 256);
       const Tile T = tile_of<AXIS, FUSED>(P, blockIdx.x + i * gridDim.x);
-      if (!bar_wait(acc_full, acc_uses & 1, abort)) break;
-      ++acc_uses;
+      if (!bar_wait(&B.acc_full[a], acc_uses[a] & 1, abort)) break;
+      ++acc_uses[a];
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-      const int p = warp * 32 + lane;
       if (FUSED) {
-        // Green factor on (kx, ky, kz), written back K-major as the A operand of the inverse
-        const int ky = T.yfix - P.flo[T.q][1];
-        const int kx = T.x0 + p - P.flo[T.q][0];
-        const bool live = p < T.npen && kx >= 0 && kx < P.fL[T.q][0];
-        const uint32_t sbo2 = (uint32_t)(T.Kp / 8) * 128;
-        const GreenLine G = tc_green_line(P, T.q, live ? kx : 0, ky);
-        const float* __restrict__ Sz = P.S2[T.q][2];
-        const float* __restrict__ Cz = P.C2[T.q][2];
-        for (int c0 = 0; c0 < T.Kp; c0 += 16) {
-          float v[16];
-          tmem_ld16(tmem + lane_base + c0, v);
-#pragma unroll
-          for (int u = 0; u < 16; ++u) {
-            const int k = c0 + u;
-            v[u] = (live && k < T.L) ? v[u] * G.at(Sz[k], Cz[k]) : 0.f;
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            uint4 w;
-            w.x = pack_bf16x2(v[8 * h + 0], v[8 * h + 1]);
-            w.y = pack_bf16x2(v[8 * h + 2], v[8 * h + 3]);
-            w.z = pack_bf16x2(v[8 * h + 4], v[8 * h + 5]);
-            w.w = pack_bf16x2(v[8 * h + 6], v[8 * h + 7]);
-            *reinterpret_cast<uint4*>(sA[s] + (uint32_t)(p >> 3) * sbo2 + (uint32_t)((c0 >> 3) + h) * 128 +
-                                      (p & 7) * 16) = w;
-          }
-        }
+        green_tile(P, T, acc, sA[s], warp, lane);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        bar_arrive(a2_ready);
-        if (!bar_wait(acc_full, acc_uses & 1, abort)) break;
-        ++acc_uses;
+        bar_arrive(B.a2_ready);
+        if (!bar_wait(&B.acc_full[a], acc_uses[a] & 1, abort)) break;
+        ++acc_uses[a];
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
       }
-      store_tile<AXIS>(P, T, tmem, reinterpret_cast<float*>(sA[s]), warp, lane);
+      store_tile<AXIS>(P, T, acc, offs_all + (i & 3) * UM_P, warp, lane);
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      bar_arrive(acc_empty);
-      bar_arrive(&a_empty[s]);
+      bar_arrive(&B.acc_empty[a]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -608,7 +740,7 @@ __global__ void __launch_bounds__(UM_THREADS, 1) k_pass_umma(TcPassParams P, int
 
 template <int AXIS, int FUSED>
 static cudaError_t launch_tc_one(const TcPassParams& P, int maxKp, cudaStream_t s) {
-  const size_t smem = UmGeom::make(maxKp, AXIS).smem();
+  const size_t smem = um_geom(maxKp, AXIS).smem();
   auto kern = k_pass_umma<AXIS, FUSED>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) return e;
@@ -623,10 +755,9 @@ static cudaError_t launch_tc_one(const TcPassParams& P, int maxKp, cudaStream_t 
 cudaError_t launch_pass_tc(const TcPassParams& P, cudaStream_t s) {
   int maxKp = 0;
   for (int q = 0; q < 3; ++q) {
-    if (P.Kp[q] % UM_KC != 0 || P.Kp[q] > 512) return cudaErrorInvalidValue;
+    if (!pass_tc_fits(P.Kp[q], P.axis)) return cudaErrorInvalidValue;
     maxKp = maxKp > P.Kp[q] ? maxKp : P.Kp[q];
   }
-  if (UmGeom::make(maxKp, P.axis).smem() > (size_t)kMaxDynSmem) return cudaErrorInvalidValue;
   if (P.fused) {
     if (P.axis != 2) return cudaErrorInvalidValue;
     return launch_tc_one<2, 1>(P, maxKp, s);
@@ -637,7 +768,14 @@ cudaError_t launch_pass_tc(const TcPassParams& P, cudaStream_t s) {
 }
 
 bool pass_tc_fits(int Kp, int axis) {
-  return Kp % UM_KC == 0 && Kp <= 512 && UmGeom::make(Kp, axis).smem() <= (size_t)kMaxDynSmem;
+  if (Kp < UM_KC || Kp % UM_KC != 0) return false;
+  const UmGeom g = um_geom(Kp, axis);
+  // the accumulator (x: Mp / 128 blocks of 128 columns; y, z: Kp columns) fits TMEM, and at
+  // least two matrix chunks fit beside the two pencil tiles
+  return g.acc_cols <= UM_TMEM_COLS && g.nbuf >= 2 && g.smem() <= (size_t)kMaxDynSmem;
 }
+
+// Rows of the x-axis matrices (M padded to a multiple of 128); the y and z matrices have Kp.
+int pass_tc_rows(int Kp, int axis) { return um_geom(Kp, axis).mp; }
 
 }  // namespace fftm

@@ -331,9 +331,20 @@ def test_invalid_descriptors_are_rejected():
 TC_TOL = 1e-2  # BF16 operands: 8-bit significands
 
 
-@pytest.mark.parametrize("case", range(len(DT_CASES)))
+# lengths that take the tensor-core pass through its other shapes: two and three M blocks
+# of 128 outputs on x (one accumulator at 288), outputs past 256 on y (two N blocks, one
+# accumulator), a 288-long z
+TC_DT_CASES = DT_CASES + [
+    ((192, 8, 6), ("DST1", "DCT3", "P")),
+    ((256, 6, 4), ("DCT1", "P", "DST1")),
+    ((6, 324, 4), ("P", "DST1", "DCT1")),
+    ((4, 6, 288), ("DST3", "P", "DCT3")),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TC_DT_CASES)))
 def test_tc_dt_forward_and_round_trip(case):
-    n, kinds = DT_CASES[case]
+    n, kinds = TC_DT_CASES[case]
     wl = _wl(n, _bc_for(*kinds, mix=True))
     g = Grid(wl.n, wl.bc)
     gp = GpuProblem(wl, "fp32_tc")
