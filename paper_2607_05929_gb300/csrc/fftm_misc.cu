@@ -240,7 +240,9 @@ struct CombArgs {
 
 // Dbar = sum_k c_k D_k; ubar = u_last + sum_{k<last} c_k (u_k - u_last) (the
 // differences of nearby iterates are formed first, then added to u_last with
-// an error-free sum when the low parts are present).
+// an error-free sum when the low parts are present).  Every operand of an element is
+// loaded before the first store, so that the loads of all three components are in
+// flight together (the output arrays may alias nothing the compiler can see).
 template <typename T, bool LO>
 __global__ void k_combine(CombArgs<T> A, int m, const double* __restrict__ coef, long long count) {
   T c[4];
@@ -249,31 +251,37 @@ __global__ void k_combine(CombArgs<T> A, int m, const double* __restrict__ coef,
   const int L = m - 1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
+    T Dv[3][4], Uh[3][4], Ul[3][4];
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        Dv[q][j] = (j < m) ? __ldg(A.D[j][q] + i) : T(0);
+        Uh[q][j] = (j < m) ? __ldg(A.uh[j][q] + i) : T(0);
+        Ul[q][j] = (LO && j < m) ? __ldg(A.ul[j][q] + i) : T(0);
+      }
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       T s = T(0);
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j < m) s += c[j] * A.D[j][q][i];
-      A.dst[q][i] = s;
-      T uL = A.uh[0][q][i], lL = T(0);
+      for (int j = 0; j < 4; ++j) s += c[j] * Dv[q][j];
+      T uL = Uh[q][0], lL = Ul[q][0];
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j == L) uL = A.uh[j][q][i];
-      if (LO) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (j == L) lL = A.ul[j][q][i];
-      }
+      for (int j = 1; j < 4; ++j)
+        if (j == L) {
+          uL = Uh[q][j];
+          lL = Ul[q][j];
+        }
       T corr = T(0);
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         if (j < L) {
-          T dj = A.uh[j][q][i] - uL;
-          if (LO) dj += A.ul[j][q][i] - lL;
+          T dj = Uh[q][j] - uL;
+          if (LO) dj += Ul[q][j] - lL;
           corr += c[j] * dj;
         }
       }
+      A.dst[q][i] = s;
       if (LO) {
         const T s1 = uL + corr;
         const T bb = s1 - uL;
