@@ -112,6 +112,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive columns of the warp's 32 lanes, one wait
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
   return *reinterpret_cast<uint32_t*>(&v);
@@ -255,8 +271,8 @@ __device__ __forceinline__ int total_tiles(const TcPassParams& P) {
 }
 
 // ---- producers --------------------------------------------------------------------------
-// Stage one tile as BF16 (UM_PROD producer threads, ptid 0 .. UM_PROD - 1), eight 16-byte
-// loads in flight per thread.  x axis: the K index is j = x - xb with xb the range offset
+// Stage one tile as BF16 (UM_PROD producer threads, ptid 0 .. UM_PROD - 1), sixteen (x) or
+// eight (y, z) 16-byte loads in flight per thread.  x axis: the K index is j = x - xb with xb the range offset
 // rounded down to a multiple of 4 (the host shifted the matrix columns by lo - xb), so each
 // row is read with aligned 16-byte loads and the nodes outside the range are zeroed; the
 // element offsets of the 128 pencil rows go to `offs` for the epilogue.  y and z: MN-major
@@ -277,10 +293,10 @@ __device__ __forceinline__ void stage_tile(const TcPassParams& P, const Tile& T,
       offs[ptid] = ptid < npen ? (long long)(r % N2) * sy + (long long)(r / N2) * sz : 0;
     }
     const int nx4 = Kp / 4, total = UM_P * nx4;
-    for (int i0 = ptid; i0 < total; i0 += 8 * UM_PROD) {
-      float4 v[8];
+    for (int i0 = ptid; i0 < total; i0 += 16 * UM_PROD) {
+      float4 v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int idx = i0 + u * UM_PROD;
         const int p = idx / nx4, x = xb + (idx % nx4) * 4;
         v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -290,7 +306,7 @@ __device__ __forceinline__ void stage_tile(const TcPassParams& P, const Tile& T,
         }
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int idx = i0 + u * UM_PROD;
         if (idx >= total) break;
         const int p = idx / nx4, j = (idx % nx4) * 4, x = xb + j;
@@ -550,39 +566,54 @@ __device__ __forceinline__ void store_tile(const TcPassParams& P, const Tile& T,
     for (int mb = h; mb < mp / 128; mb += 2) {
       const int x = xb + mb * 128 + gq * 32 + lane;
       const bool ok = x >= T.lo && x < T.lo + L;
-      for (int p0 = 0; p0 < npen; p0 += 16) {
-        float v[16];
-        tmem_ld16(acc + lane_base + (uint32_t)(mb * 128 + p0), v);
-        if (bh == nullptr) {
+      if (bh == nullptr) {
+        for (int p0 = 0; p0 < npen; p0 += 32) {
+          float v[32];
+          tmem_ld32(acc + lane_base + (uint32_t)(mb * 128 + p0), v);
 #pragma unroll
-          for (int u = 0; u < 16; ++u)
+          for (int u = 0; u < 32; ++u)
             if (ok && p0 + u < npen) out[offs[p0 + u] + x] = sc * v[u];
-        } else {
-          float a[16], b[16];
+        }
+      } else {
+        // the base values of the next 16 pencils are loaded while this chunk is summed
+        float a0[16], b0[16], a1[16], b1[16];
+        auto load_base = [&](int p0, float (&aa)[16], float (&bb)[16]) {
 #pragma unroll
           for (int u = 0; u < 16; ++u) {
             const bool live = ok && p0 + u < npen;
-            const long long at = offs[p0 + u] + x;
-            a[u] = live ? bh[at] : 0.f;
-            b[u] = (live && ol) ? bl[at] : 0.f;
+            const long long at = offs[(p0 + u) & (UM_P - 1)] + x;
+            aa[u] = live ? bh[at] : 0.f;
+            bb[u] = (live && ol) ? bl[at] : 0.f;
           }
+        };
+        auto sum_store = [&](int p0, const float (&aa)[16], const float (&bb)[16]) {
+          float v[16];
+          tmem_ld16(acc + lane_base + (uint32_t)(mb * 128 + p0), v);
 #pragma unroll
           for (int u = 0; u < 16; ++u) {
             if (!(ok && p0 + u < npen)) continue;
             const long long at = offs[p0 + u] + x;
             const float val = sc * v[u];
             if (ol == nullptr) {
-              out[at] = a[u] + val;
+              out[at] = aa[u] + val;
             } else {  // (hi, lo) = (bh, bl) + val with an error-free sum of the high parts
-              const float s1 = a[u] + val;
-              const float bb = s1 - a[u];
-              const float er = (a[u] - (s1 - bb)) + (val - bb);
-              const float tt = b[u] + er;
+              const float s1 = aa[u] + val;
+              const float bs = s1 - aa[u];
+              const float er = (aa[u] - (s1 - bs)) + (val - bs);
+              const float tt = bb[u] + er;
               const float hsum = s1 + tt;
               out[at] = hsum;
               ol[at] = tt - (hsum - s1);
             }
           }
+        };
+        load_base(0, a0, b0);
+        for (int p0 = 0; p0 < npen; p0 += 32) {
+          if (p0 + 16 < npen) load_base(p0 + 16, a1, b1);
+          sum_store(p0, a0, b0);
+          if (p0 + 16 >= npen) break;
+          if (p0 + 32 < npen) load_base(p0 + 32, a0, b0);
+          sum_store(p0 + 16, a1, b1);
         }
       }
     }
@@ -591,15 +622,27 @@ __device__ __forceinline__ void store_tile(const TcPassParams& P, const Tile& T,
     const int p = gq * 32 + lane;
     const bool live = p < npen;
     const long long rowbase = T.base0 + p + (long long)T.lo * T.estride;
-    const int half = Kp / 2;
-    for (int c0 = h * half; c0 < (h + 1) * half; c0 += 16) {
-      float v[16];
-      tmem_ld16(acc + lane_base + (uint32_t)c0, v);  // warp-collective: every lane takes part
+    const int half = Kp / 2;  // a multiple of 16
+    int c0 = h * half;
+    for (; c0 + 32 <= (h + 1) * half; c0 += 32) {
+      float v[32];
+      tmem_ld32(acc + lane_base + (uint32_t)c0, v);  // warp-collective: every lane takes part
       if (!live) continue;
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
+      for (int i = 0; i < 32; ++i) {
         const int k = c0 + i;
         if (k < L) out[rowbase + (long long)k * T.estride] = sc * v[i];
+      }
+    }
+    if (c0 < (h + 1) * half) {
+      float v[16];
+      tmem_ld16(acc + lane_base + (uint32_t)c0, v);
+      if (live) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int k = c0 + i;
+          if (k < L) out[rowbase + (long long)k * T.estride] = sc * v[i];
+        }
       }
     }
   }
@@ -621,12 +664,21 @@ __device__ __forceinline__ void green_tile(const TcPassParams& P, const Tile& T,
   const float* __restrict__ Cz = P.C2[T.q][2];
   const int half = T.Kp / 2;
   for (int c0 = h * half; c0 < (h + 1) * half; c0 += 16) {
+    // the z factors of these 16 outputs (the same for every lane) are loaded first, so that
+    // their latency overlaps the TMEM load
+    float sz[16], cz[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int k = min(c0 + u, T.L - 1);
+      sz[u] = __ldg(Sz + k);
+      cz[u] = __ldg(Cz + k);
+    }
     float v[16];
     tmem_ld16(acc + lane_base + (uint32_t)c0, v);
 #pragma unroll
     for (int u = 0; u < 16; ++u) {
       const int k = c0 + u;
-      v[u] = (live && k < T.L) ? v[u] * G.at(Sz[k], Cz[k]) : 0.f;
+      v[u] = (live && k < T.L) ? v[u] * G.at(sz[u], cz[u]) : 0.f;
     }
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
