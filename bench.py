@@ -62,6 +62,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed beside (0 = skip)")
+    ap.add_argument("--tc-steps", type=int, default=3,
+                    help="tensor-core (FP32_TC) path steps timed beside the FP32 path (0 = skip)")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream (mixed sizes/BCs/laws, Poisson arrivals): solves/s and p50/p99 latency")
     ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream (--serve)")
@@ -416,6 +418,24 @@ def gpu_arm(args):
         s64 = e0.elapsed_time(e1) / 1000.0
         line["fp64_path"] = {"value": u64 / s64, "unit": UNIT, "iterations_per_step": last["iterations"],
                              "steps": args.fp64_steps}
+        F.fftm_problem_destroy(prob)
+        prob = make(args.precision)
+
+    # ---- tensor-core transforms beside it (the precision form, same workload) ----
+    if args.tc_steps > 0 and args.precision == "fp32":
+        F.fftm_problem_destroy(prob)
+        prob = make("fp32_tc")
+        step()  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        utc = sum(step() for _ in range(args.tc_steps))
+        e1.record(stream)
+        e1.synchronize()
+        stc = e0.elapsed_time(e1) / 1000.0
+        line["fp32_tc_path"] = {"value": utc / stc, "unit": UNIT, "iterations_per_step": last["iterations"],
+                                "steps": args.tc_steps, "ms_per_step": 1000.0 * stc / args.tc_steps,
+                                "note": "per-axis transforms as tcgen05 BF16 contractions, FP32 fields and residual"}
         F.fftm_problem_destroy(prob)
         prob = make(args.precision)
 
