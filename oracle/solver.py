@@ -22,6 +22,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 from . import anderson as anderson_mod
+from . import mixed as mixed_mod
 from .bc import Grid
 from .green import green_factor
 from .laws import b0_apply, phase_groups, stress
@@ -37,6 +38,8 @@ class Report:
     accelerated: list = field(default_factory=list)
     mean_P: np.ndarray = None
     mean_G: np.ndarray = None
+    mixed_err: list = field(default_factory=list)
+    A: np.ndarray = None
 
 
 class Problem:
@@ -63,6 +66,7 @@ class Problem:
                                                (self.npp, 3, 3) + self.grid.n).copy()
             self.state["gam"] = np.zeros(shp)
         self.uf = np.zeros(self.grid.node_shape)
+        self.mixed_A = None  # the affine part of u* a mixed load step converged to
 
     # --- a0: prescribed displacement and its discrete gradient ------------------------
     def ustar_full(self, A=None, b=None, Q=None):
@@ -115,10 +119,19 @@ class Problem:
         return out
 
     # --- Algorithm 1, one load step -----------------------------------------------------
-    def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True, Q=None):
+    def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True, Q=None, mixed=0):
+        """One load step.  mixed: bit mask of the symmetric strain components (Voigt order
+        11, 22, 33, 23, 13, 12) of u* that are adjusted so that the mean stress vanishes in
+        them (normal-mixed loading, mixed.py); the other components of A are imposed."""
         wl = self.wl
         tol = wl.tol if tol is None else tol
         max_iter = wl.max_iter if max_iter is None else max_iter
+        A = np.array(wl.A if A is None else A, dtype=np.float64)
+        if mixed and self.mixed_A is not None:  # free components start where they converged
+            for k in mixed_mod.free_components(mixed):
+                i, j = mixed_mod.VOIGT[k]
+                A[i, j] = self.mixed_A[i, j]
+                A[j, i] = self.mixed_A[j, i]
         Gs = self.grad_ustar(A, b, Q)
         uf = self.uf.copy() if uf0 is None else np.array(uf0, dtype=np.float64)
         hist = []  # (q_j, g_j) couples
@@ -129,7 +142,12 @@ class Problem:
             err = self.error(S_D, S_P)
             rep.err.append(err)
             rep.iterations = m
-            if err < tol:
+            mean_sig = None
+            if mixed:
+                Pm = P.mean(axis=(0, 3, 4, 5))
+                mean_sig = 0.5 * (Pm + Pm.T)
+                rep.mixed_err.append(mixed_mod.mixed_error(mean_sig, mixed))
+            if err < tol and (not mixed or rep.mixed_err[-1] < tol):
                 rep.converged = True
                 break
             if m == max_iter:
@@ -148,7 +166,13 @@ class Problem:
                     rep.accelerated.append(m)
             q_prev = q
             uf = self.green_update(q)
+            if mixed:  # the free strain components of u* for the next iteration
+                A = A + mixed_mod.mixed_increment(mean_sig, mixed, float(wl.lambda0), float(wl.mu0))
+                Gs = self.grad_ustar(A, b, Q)
         self.uf = uf
+        if mixed:
+            self.mixed_A = A.copy()
+            rep.A = A.copy()
         rep.mean_P = P.mean(axis=(0, 3, 4, 5))
         rep.mean_G = G.mean(axis=(0, 3, 4, 5))
         if self.state is not None and rep.converged:

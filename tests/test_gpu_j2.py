@@ -99,6 +99,33 @@ def test_j2_bending_steps_fp32_vs_fp64_oracle(scheme):
         gp.close()
 
 
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_j2_bending_steps_fp32_tc_vs_fp64_oracle(scheme):
+    """The precision form on its own workload: the bending schedule with the per-axis
+    transforms as tcgen05 BF16 contractions.  The transforms only precondition, so every
+    step must still reach the FP64 oracle's fields to 1e-5 at tol 1e-6; BF16 rounding may
+    slow the fixed point, bounded here by twice the oracle's iterations plus one Anderson
+    period."""
+    wl, loads = _bending(scheme, tol=1e-6)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, "fp32_tc")
+    try:
+        for k, (A, b, Q) in enumerate(loads):
+            _, rep = pr.solve_step(A=A, b=b, Q=Q)
+            assert rep.converged
+            gp.set_load(A, b, Q)
+            st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+            assert r["converged"], (k, r)
+            assert r["iterations"] <= 2 * rep.iterations + 3, (k, r["iterations"], rep.iterations)
+            Pg = gp.get_voxel(F.FFTM_FIELD_STRESS)
+            Gg = gp.get_voxel(F.FFTM_FIELD_GRAD)
+            assert rel_l2(Pg, sym6(pr.last["P"])) < 1e-5, k
+            Gg = Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:])
+            assert rel_l2(sym6(_strain(Gg)), sym6(_strain(pr.last["G"]))) < 1e-5, k
+    finally:
+        gp.close()
+
+
 def test_j2_bar_uniaxial_load_unload_on_the_gpu():
     """The homogeneous J2 bar of the oracle pins, run through the library in FP64: every
     step's mean axial stress follows the uniaxial closed form."""
