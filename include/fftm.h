@@ -130,11 +130,27 @@ typedef struct fftm_problem_desc {
    Dirichlet values (Sec. 2.2); it must not depend on a periodic coordinate
    (FFTM_E_INVALID).  The quadratic terms carry bending and torsion loads (face
    rotations that grow along an axis); their discrete gradients are applied in
-   closed form at the voxel points. */
+   closed form at the voxel points.
+
+   Normal-mixed loading (Sec. 3.2, Eq. NMBC1: one component of <grad u*> imposed,
+   the others adjusted at each iteration so that the mean stress vanishes in
+   them): `mixed` is a bit mask over the symmetric strain components of u*
+   (Voigt order 11, 22, 33, 23, 13, 12, bit k for the k-th).  After every
+   residual the free components take the increment -(C0_FF)^-1 <sigma>_F, C0 the
+   isotropic reference stiffness (lambda0, mu0), <sigma> the mean stress over the
+   voxel points; the increment is added symmetrically to A, whose skew part and
+   imposed components stay as given.  A's free entries are the first step's
+   starting guess; a later step whose load has the same mask starts them from
+   the values the previous step converged to.  The step converges when err < tol
+   and ||<sigma>_F|| / ||<sigma>|| < tol (tensor norms).  Requires small-strain
+   laws (symmetric P) and non-periodic axes i and j for every free component ij
+   (FFTM_E_INVALID otherwise).  0: A is imposed as given.  fftm_get_load returns
+   the load with the adjusted A. */
 typedef struct fftm_load {
   double A[3][3];
   double b[3];
   double Q[3][6];
+  int mixed;  /* normal-mixed mask, 0 = none */
 } fftm_load;
 
 typedef struct fftm_step_report {
@@ -176,6 +192,9 @@ int fftm_set_phase(fftm_problem* p, const uint16_t* phase);
 /* Set the prescribed displacement of the next load steps (Algorithm 1,
    "update the desired loading"). */
 int fftm_set_load(fftm_problem* p, const fftm_load* load);
+/* The current load (HOST out): as set, with the free components of a mixed load
+   at their latest adjusted values. */
+int fftm_get_load(const fftm_problem* p, fftm_load* out);
 
 /* Run Algorithm 1 for one load step from the current u^f (the previous
    step's converged field, zero initially).  When the step converges, the

@@ -17,8 +17,8 @@ C0 the isotropic reference stiffness (lambda0, mu0): sigma_ii = lambda0 tr eps +
 eps_ii, sigma_ij = 2 mu0 eps_ij.  The increment is added symmetrically to A (u*_q =
 A_qi x_i, so eps* = sym A) and leaves its skew part alone.  A step has converged when the
 equilibrium error is below tol and the mixed error ||<sigma>_F|| / ||<sigma>|| (tensor
-Frobenius norms, both off-diagonal entries counted) is below tol too.  At the next load
-step the free components start from the values they converged to.
+Frobenius norms, both off-diagonal entries counted) is below tol too.  A later load step
+with the same mask starts its free components from the values the previous one ended with.
 """
 
 import numpy as np

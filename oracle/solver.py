@@ -66,7 +66,8 @@ class Problem:
                                                (self.npp, 3, 3) + self.grid.n).copy()
             self.state["gam"] = np.zeros(shp)
         self.uf = np.zeros(self.grid.node_shape)
-        self.mixed_A = None  # the affine part of u* a mixed load step converged to
+        self.mixed_A = None  # the affine part of u* the last mixed load step ended with
+        self.mixed_mask = 0  # that step's mask
 
     # --- a0: prescribed displacement and its discrete gradient ------------------------
     def ustar_full(self, A=None, b=None, Q=None):
@@ -127,7 +128,7 @@ class Problem:
         tol = wl.tol if tol is None else tol
         max_iter = wl.max_iter if max_iter is None else max_iter
         A = np.array(wl.A if A is None else A, dtype=np.float64)
-        if mixed and self.mixed_A is not None:  # free components start where they converged
+        if mixed and mixed == self.mixed_mask:  # free components start where the last mixed step ended
             for k in mixed_mod.free_components(mixed):
                 i, j = mixed_mod.VOIGT[k]
                 A[i, j] = self.mixed_A[i, j]
@@ -172,6 +173,7 @@ class Problem:
         self.uf = uf
         if mixed:
             self.mixed_A = A.copy()
+            self.mixed_mask = mixed
             rep.A = A.copy()
         rep.mean_P = P.mean(axis=(0, 3, 4, 5))
         rep.mean_G = G.mean(axis=(0, 3, 4, 5))

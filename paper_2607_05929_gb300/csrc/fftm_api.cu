@@ -263,6 +263,8 @@ struct fftm_problem {
   void* state = nullptr;    // committed J2 state [r][7][voxel]: elastic strain e_n, p_n (only if a phase is J2)
   void* un = nullptr;       // u^f at the last commit: 3 comps (FP64) or 3 high + 3 low (FP32)
   fftm_load load_n;         // the load at the last commit
+  double mixed_A[3][3];     // A at the end of the last normal-mixed step
+  int mixed_prev = 0;       // that step's mask (0: none since creation or reset)
   void* Dn = nullptr;       // residual D at the last commit (3 comps)
   int committed = 0;        // a load step has been committed since creation or reset
   int nst = 0;              // state components per voxel point (7 J2, 10 crystal plasticity, 0 none)
@@ -638,6 +640,54 @@ double error_of(fftm_problem* p, double SD, double SP) {
   return SD == 0.0 ? 0.0 : INFINITY;
 }
 
+// Normal-mixed loading (Sec. 3.2, Eq. NMBC1): strain components of u* (Voigt order 11,
+// 22, 33, 23, 13, 12, bit k of the mask) adjusted after every residual so that the mean
+// stress vanishes in them.  The paper gives no update rule; this one takes the
+// increment -(C0_FF)^-1 <sigma>_F of the isotropic reference stiffness restricted to the
+// free components (the normal ones couple through lambda0, the shear ones decouple).
+constexpr int kVoigt[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+constexpr int kStatsBlocks = 152 * 2;  // blocks of the mean stress / strain reduction
+
+void mixed_increment(const double sig[3][3], int mask, double lam0, double mu0, double d[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) d[i][j] = 0.0;
+  int nn = 0, idx[3];
+  double M[3][4];
+  for (int k = 0; k < 3; ++k)
+    if ((mask >> k) & 1) idx[nn++] = k;
+  for (int r = 0; r < nn; ++r) {
+    for (int c = 0; c < nn; ++c) M[r][c] = lam0 + (r == c ? 2.0 * mu0 : 0.0);
+    M[r][nn] = -sig[idx[r]][idx[r]];
+  }
+  for (int c = 0; c < nn; ++c) {  // Gauss-Jordan; the matrix is symmetric positive definite
+    for (int r = 0; r < nn; ++r) {
+      if (r == c) continue;
+      const double f = M[r][c] / M[c][c];
+      for (int k = c; k <= nn; ++k) M[r][k] -= f * M[c][k];
+    }
+  }
+  for (int r = 0; r < nn; ++r) d[idx[r]][idx[r]] = M[r][nn] / M[r][r];
+  for (int k = 3; k < 6; ++k)
+    if ((mask >> k) & 1) {
+      const int i = kVoigt[k][0], j = kVoigt[k][1];
+      d[i][j] = d[j][i] = -sig[i][j] / (2.0 * mu0);
+    }
+}
+
+// ||<sigma>_F|| / ||<sigma>|| (tensor norms: both off-diagonal entries counted).
+double mixed_error(const double sig[3][3], int mask) {
+  double tot = 0.0, f = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) tot += sig[i][j] * sig[i][j];
+  if (tot == 0.0) return 0.0;
+  for (int k = 0; k < 6; ++k)
+    if ((mask >> k) & 1) {
+      const int i = kVoigt[k][0], j = kVoigt[k][1];
+      f += sig[i][j] * sig[i][j] * (i == j ? 1.0 : 2.0);
+    }
+  return std::sqrt(f / tot);
+}
+
 // Algorithm 1 for one load step.  The update of iteration m is
 //   u^{m+1} = u^m - Gamma(D^m)                                 (plain step)
 //   u^{m+1} = sum_k c_k u^k - Gamma(sum_k c_k D^k)             (Anderson step)
@@ -668,16 +718,40 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     const int sm = (cur0 + m) % NSLOT;
     int rc = run_residual<T>(p, sm, false);
     if (rc) return rc;
-    CU(cudaMemcpyAsync(p->hpin, p->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    const int mixed = p->load.mixed;
+    if (mixed) {  // the mean stress of this iterate (voxel points)
+      ResParams<T> R = res_params<T>(p, sm, nullptr, nullptr);
+      ProfScope ps(p, FFTM_KCAT_OTHER);
+      CU(launch_stats<T>(R, p->tetra, p->partial, kStatsBlocks, s));
+      CU(launch_reduce_norms(p->partial, kStatsBlocks, 18, p->dscal + 16, s));
+      p->launches += 2;
+    }
+    CU(cudaMemcpyAsync(p->hpin, p->dscal, (mixed ? 25 : 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     prof_flush(p);
     err = error_of(p, p->hpin[0], p->hpin[1]);
     if (err_hist && m < hist_len) err_hist[m] = err;
     p->cur = sm;
     if (!std::isfinite(err)) return set_err(FFTM_E_DIVERGED, "non-finite equilibrium norm");
-    if (err < p->desc.tol) {
+    double sig[3][3];
+    double mix_err = 0.0;
+    if (mixed) {
+      const double npts = (double)p->nvox * (p->tetra ? 2 : 1);
+      for (int i = 0; i < 3; ++i)
+        for (int q = 0; q < 3; ++q)
+          sig[i][q] = 0.5 * (p->hpin[16 + i * 3 + q] + p->hpin[16 + q * 3 + i]) / npts;
+      mix_err = mixed_error(sig, mixed);
+      if (!std::isfinite(mix_err)) return set_err(FFTM_E_DIVERGED, "non-finite mean stress");
+    }
+    if (err < p->desc.tol && mix_err < p->desc.tol) {
       converged = 1;
       break;
+    }
+    if (mixed && m < max_iter) {  // the free strain components of u* for the next residual
+      double d[3][3];
+      mixed_increment(sig, mixed, p->desc.lambda0, p->desc.mu0, d);
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) p->load.A[i][j] += d[i][j];
     }
     if (m >= max_iter) break;
     const int sn = (cur0 + m + 1) % NSLOT;
@@ -721,7 +795,11 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
   // report
   std::vector<int> acc(m + 1, 0);
   CU(cudaMemcpyAsync(acc.data(), p->dint, (m + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
-  const int sb = 152 * 2;
+  if (p->load.mixed) {
+    std::memcpy(p->mixed_A, p->load.A, sizeof(p->mixed_A));
+    p->mixed_prev = p->load.mixed;
+  }
+  const int sb = kStatsBlocks;
   {
     ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
     ProfScope ps(p, FFTM_KCAT_OTHER);
@@ -1195,7 +1273,28 @@ int fftm_set_load(fftm_problem* p, const fftm_load* load) {
     for (int k = 0; k < 6; ++k)
       if (load->Q[q][k] != 0.0 && (p->periodic[mono_axes[k][0]] || p->periodic[mono_axes[k][1]]))
         return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
-  p->load = *load;
+  fftm_load ld = *load;
+  if (ld.mixed) {
+    if (ld.mixed & ~0x3F) return set_err(FFTM_E_INVALID, "mixed mask has bits beyond the six strain components");
+    if (!p->sym) return set_err(FFTM_E_INVALID, "normal-mixed loading needs small-strain laws (symmetric stress)");
+    for (int k = 0; k < 6; ++k)
+      if (((ld.mixed >> k) & 1) && (p->periodic[kVoigt[k][0]] || p->periodic[kVoigt[k][1]]))
+        return set_err(FFTM_E_INVALID, "a free strain component of a mixed load lies along a periodic axis");
+    if (ld.mixed == p->mixed_prev)  // free components start where the previous mixed step ended
+      for (int k = 0; k < 6; ++k)
+        if ((ld.mixed >> k) & 1) {
+          const int i = kVoigt[k][0], j = kVoigt[k][1];
+          ld.A[i][j] = p->mixed_A[i][j];
+          ld.A[j][i] = p->mixed_A[j][i];
+        }
+  }
+  p->load = ld;
+  return FFTM_OK;
+}
+
+int fftm_get_load(const fftm_problem* p, fftm_load* out) {
+  if (!p || !out) return set_err(FFTM_E_INVALID, "null argument");
+  *out = p->load;
   return FFTM_OK;
 }
 
@@ -1452,6 +1551,7 @@ int fftm_reset_state(fftm_problem* p) {
     CU(cudaMemsetAsync(p->un, 0, (size_t)(p->esz == 4 ? 6 : 3) * p->comp_stride * p->esz, p->ctx->stream));
   std::memset(&p->load_n, 0, sizeof(p->load_n));
   p->committed = 0;
+  p->mixed_prev = 0;
   CU(cudaStreamSynchronize(p->ctx->stream));
   p->cur = 0;
   return FFTM_OK;

@@ -36,7 +36,7 @@ FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP
 EXPORTS = [
     "fftm_last_error", "fftm_version", "fftm_ctx_create", "fftm_ctx_destroy",
     "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
-    "fftm_set_phase", "fftm_set_load", "fftm_solve_step", "fftm_field_bytes",
+    "fftm_set_phase", "fftm_set_load", "fftm_get_load", "fftm_solve_step", "fftm_field_bytes",
     "fftm_get_field", "fftm_set_field", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
@@ -62,7 +62,8 @@ class fftm_problem_desc(ctypes.Structure):
 
 
 class fftm_load(ctypes.Structure):
-    _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3), ("Q", (ctypes.c_double * 6) * 3)]
+    _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3), ("Q", (ctypes.c_double * 6) * 3),
+                ("mixed", ctypes.c_int)]
 
 
 class fftm_request(ctypes.Structure):
@@ -113,6 +114,7 @@ def load_library(path=LIB_PATH):
         "fftm_problem_destroy": ([vp], ctypes.c_int),
         "fftm_set_phase": ([vp, P(ctypes.c_uint16)], ctypes.c_int),
         "fftm_set_load": ([vp, P(fftm_load)], ctypes.c_int),
+        "fftm_get_load": ([vp, P(fftm_load)], ctypes.c_int),
         "fftm_solve_step": ([vp, P(fftm_step_report), P(ctypes.c_double), P(ctypes.c_int), ctypes.c_int],
                             ctypes.c_int),
         "fftm_field_bytes": ([vp, ctypes.c_int, P(ctypes.c_size_t)], ctypes.c_int),
@@ -234,8 +236,10 @@ def fftm_set_phase_raw(p, host_ptr):
                                                                 ctypes.POINTER(ctypes.c_uint16))))
 
 
-def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None):
-    """u*_q = A[q] . x + b[q] + sum_k Q[q][k] m_k(x), m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2)."""
+def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None, mixed=0):
+    """u*_q = A[q] . x + b[q] + sum_k Q[q][k] m_k(x), m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2);
+    mixed: normal-mixed mask (Voigt order 11, 22, 33, 23, 13, 12) of the strain components
+    adjusted so that the mean stress vanishes in them."""
     ld = fftm_load()
     for q in range(3):
         for a in range(3):
@@ -243,7 +247,16 @@ def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None):
         ld.b[q] = float(b[q])
         for k in range(6):
             ld.Q[q][k] = 0.0 if Q is None else float(Q[q][k])
+    ld.mixed = int(mixed)
     return _check(load_library().fftm_set_load(p, ctypes.byref(ld)))
+
+
+def fftm_get_load(p):
+    """The current load as (A 3x3, b, Q, mixed), A with the adjusted free components."""
+    ld = fftm_load()
+    _check(load_library().fftm_get_load(p, ctypes.byref(ld)))
+    A = np.array([[ld.A[q][a] for a in range(3)] for q in range(3)])
+    return A, np.array(list(ld.b)), np.array([[ld.Q[q][k] for k in range(6)] for q in range(3)]), ld.mixed
 
 
 def fftm_solve_step(p, history_len=0):
