@@ -150,6 +150,12 @@ typedef struct fftm_load {
   double A[3][3];
   double b[3];
   double Q[3][6];
+  double T[3][2][3]; /* uniform Neumann tractions T[axis][face][component] (face 0 at
+                        x_axis = 0, 1 at x_axis = L; outward normal convention,
+                        traction_q = P_iq n_i; Sec. 2.2): the stress of the faces where
+                        that component is Neumann, imposed through P* = 2 t at the
+                        mirror voxel centres; non-zero only on such faces, else
+                        FFTM_E_INVALID.  All zero: traction-free faces. */
   int mixed;  /* normal-mixed mask, 0 = none */
 } fftm_load;
 

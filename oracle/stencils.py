@@ -142,12 +142,40 @@ def _div_one(Ei, tab, grid, scale):
     return out
 
 
-def div(S, grid, scheme):
-    """Divergence at the nodes of a voxel tensor S (npp, 3, 3, n1, n2, n3).
+def add_traction_ghosts(E, grid, T):
+    """The imposed stress of non-zero Neumann tractions (Sec. 2.2, the construction of the
+    Neumann-BC figure): P = P^f + P*, with P* zero inside the cell and P*_aq = 2 t_q at the
+    mirror voxel centres across a face normal to axis a whose u_q is Neumann, t_q =
+    (-1)^(alpha+1) T[a][alpha][q] the face value of P_aq for the traction T (outward normal
+    convention, traction_q = P_iq n_i), so that P* interpolated at the face is t.  Reading:
+    P* covers the whole ghost layer of the face, its edges and corners included, and is
+    added after the symmetry reflections (uniform T only)."""
+    n = grid.n
+    for a in range(3):
+        if grid.periodic[a]:
+            continue
+        for side in range(2):
+            for q in range(3):
+                t = T[a][side][q]
+                if t == 0.0 or grid.sym[q][a][side] != "S":
+                    continue
+                idx = [slice(None)] * 6
+                idx[1] = a
+                idx[2] = q
+                idx[3 + a] = 0 if side == 0 else n[a] + 1
+                E[tuple(idx)] += 2.0 * (1.0 if side == 1 else -1.0) * t
+    return E
+
+
+def div(S, grid, scheme, T=None):
+    """Divergence at the nodes of a voxel tensor S (npp, 3, 3, n1, n2, n3); T: uniform
+    Neumann tractions T[axis][face][component] (add_traction_ghosts) or None.
 
     HEX1: D_q = sum_i D_i^H S_iq.  TETRA2: 1/2 (div_{T2} S^{(T1)} + div_{T1} S^{(T2)}).
     """
     E = ghost_extend(S, grid, scheme)
+    if T is not None:
+        E = add_traction_ghosts(E, grid, T)
     if scheme == "HEX1":
         return _div_one(E[0], HEX1, grid, HEX1_SCALE)
     return 0.5 * (_div_one(E[0], T2, grid, T_SCALE) + _div_one(E[1], T1, grid, T_SCALE))

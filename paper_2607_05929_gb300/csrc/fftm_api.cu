@@ -536,6 +536,13 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   for (int i = 0; i < 3; ++i)
     for (int q = 0; q < 3; ++q) R.dGs[i * 3 + q] = T(p->load.A[q][i] - p->load_n.A[q][i]);
   for (int a = 0; a < 3; ++a) R.hh[a] = T(p->h[a]);
+  R.traction = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int f = 0; f < 2; ++f)
+      for (int q = 0; q < 3; ++q) {
+        R.tr[a][f][q] = T(p->load.T[a][f][q]);
+        R.traction |= p->load.T[a][f][q] != 0.0;
+      }
   return R;
 }
 
@@ -581,6 +588,14 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
   if (!test_outputs && p->committed) {  // incremental form from the last commit
     R.inc = 1;
     for (int q = 0; q < 3; ++q) R.Dn[q] = reinterpret_cast<const T*>(p->Dn) + q * p->comp_stride;
+    R.traction = 0;  // D_n holds the committed tractions' share: only their change enters
+    for (int a = 0; a < 3; ++a)
+      for (int f = 0; f < 2; ++f)
+        for (int q = 0; q < 3; ++q) {
+          const double dt = p->load.T[a][f][q] - p->load_n.T[a][f][q];
+          R.tr[a][f][q] = T(dt);
+          R.traction |= dt != 0.0;
+        }
   }
   int blocks = 0;
   ProfScope ps(p, test_outputs ? FFTM_KCAT_OTHER : FFTM_KCAT_RESIDUAL);
@@ -732,7 +747,10 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     err = error_of(p, p->hpin[0], p->hpin[1]);
     if (err_hist && m < hist_len) err_hist[m] = err;
     p->cur = sm;
-    if (!std::isfinite(err)) return set_err(FFTM_E_DIVERGED, "non-finite equilibrium norm");
+    // err is +inf while the stress is still zero under a non-zero residual (a load carried
+    // only by tractions, first iteration): not converged; NaN or an infinite norm diverged
+    if (std::isnan(err) || !std::isfinite(p->hpin[0]) || !std::isfinite(p->hpin[1]))
+      return set_err(FFTM_E_DIVERGED, "non-finite equilibrium norm");
     double sig[3][3];
     double mix_err = 0.0;
     if (mixed) {
@@ -1273,6 +1291,11 @@ int fftm_set_load(fftm_problem* p, const fftm_load* load) {
     for (int k = 0; k < 6; ++k)
       if (load->Q[q][k] != 0.0 && (p->periodic[mono_axes[k][0]] || p->periodic[mono_axes[k][1]]))
         return set_err(FFTM_E_INVALID, "u* depends on a periodic coordinate");
+  for (int a = 0; a < 3; ++a)
+    for (int f = 0; f < 2; ++f)
+      for (int q = 0; q < 3; ++q)
+        if (load->T[a][f][q] != 0.0 && p->desc.bc[a][f][q] != FFTM_BC_NEUMANN)
+          return set_err(FFTM_E_INVALID, "a traction on a face where that component is not Neumann");
   fftm_load ld = *load;
   if (ld.mixed) {
     if (ld.mixed & ~0x3F) return set_err(FFTM_E_INVALID, "mixed mask has bits beyond the six strain components");

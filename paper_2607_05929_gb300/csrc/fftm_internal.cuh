@@ -100,6 +100,11 @@ struct ResParams {
   T wgrad[3];        // HEX1: 1 / (4 h_i); TETRA2: 1 / (2 h_i)
   int sgn[3][3][2];  // [q][axis][face] +1 symmetric (Neumann), -1 anti-symmetric (Dirichlet)
   int lo[3][3], hi[3][3];  // [q][axis] transformed node range
+  // Uniform Neumann tractions tr[axis][face][q] (outward normal convention); at the nodes of
+  // a loaded face the divergence reads the imposed stress P*_aq = 2 (-1)^(face+1) tr at the
+  // ghost voxels across it (incremental form: the traction change since the commit)
+  int traction;
+  T tr[3][2][3];
   T* vs;             // voxel-point stress buffer [r][c][voxel] (c < NC, see fftm_stencil.cu)
   int sym;           // 1: every law gives a symmetric P (6 stored components)
   double* partial;   // per block: S_D, S_P

@@ -882,17 +882,25 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
     *f = T(sgn);
     return (long long)(r * NCT) * nvox + vx + vy * P.vy + (long long)vz * P.vz;
   };
+  const int mi[3] = {mx, my, mz};
   for (int i = 0; i < 3; ++i) {
     for (int q = 0; q < 3; ++q) {
       const int c = SYM ? sym_index(i, q) : i * 3 + q;
       T s = T(0), st = T(0);
+      // imposed stress of a traction on the face normal to i that this node lies on: every
+      // pair along i has its ghost corner there (Sec. 2.2, P* = 2 t at the mirror centres)
+      T ps = T(0);
+      if (P.traction && !P.periodic[i]) {
+        if (mi[i] == 0 && P.sgn[q][i][0] > 0) ps += T(2) * P.tr[i][0][q];         // - (2 (-1) t) at corner o
+        if (mi[i] == P.n[i] && P.sgn[q][i][1] > 0) ps += T(2) * P.tr[i][1][q];  // + (2 t) at corner o1
+      }
       for (int o = 0; o < 8; ++o) {
         if ((o >> i) & 1) continue;
         const int o1 = o | (1 << i);
         T f0, f1;
         const long long a0 = corner(o, i, q, &f0);
         const long long a1 = corner(o1, i, q, &f1);
-        s += f1 * P.vs[a1 + c * nvox] - f0 * P.vs[a0 + c * nvox];
+        s += f1 * P.vs[a1 + c * nvox] - f0 * P.vs[a0 + c * nvox] + ps;
         if (WITH_P) st += f1 * P.vs[a1 + (NC + i * 3 + q) * nvox] - f0 * P.vs[a0 + (NC + i * 3 + q) * nvox];
       }
       Dq[q] += P.wdiv[i] * s;

@@ -63,7 +63,7 @@ class fftm_problem_desc(ctypes.Structure):
 
 class fftm_load(ctypes.Structure):
     _fields_ = [("A", (ctypes.c_double * 3) * 3), ("b", ctypes.c_double * 3), ("Q", (ctypes.c_double * 6) * 3),
-                ("mixed", ctypes.c_int)]
+                ("T", ((ctypes.c_double * 3) * 2) * 3), ("mixed", ctypes.c_int)]
 
 
 class fftm_request(ctypes.Structure):
@@ -236,10 +236,11 @@ def fftm_set_phase_raw(p, host_ptr):
                                                                 ctypes.POINTER(ctypes.c_uint16))))
 
 
-def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None, mixed=0):
+def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None, mixed=0, T=None):
     """u*_q = A[q] . x + b[q] + sum_k Q[q][k] m_k(x), m = (x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2);
     mixed: normal-mixed mask (Voigt order 11, 22, 33, 23, 13, 12) of the strain components
-    adjusted so that the mean stress vanishes in them."""
+    adjusted so that the mean stress vanishes in them; T[axis][face][component]: uniform
+    tractions on Neumann faces."""
     ld = fftm_load()
     for q in range(3):
         for a in range(3):
@@ -247,6 +248,11 @@ def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None, mixed=0):
         ld.b[q] = float(b[q])
         for k in range(6):
             ld.Q[q][k] = 0.0 if Q is None else float(Q[q][k])
+    if T is not None:
+        for a in range(3):
+            for f in range(2):
+                for q in range(3):
+                    ld.T[a][f][q] = float(T[a][f][q])
     ld.mixed = int(mixed)
     return _check(load_library().fftm_set_load(p, ctypes.byref(ld)))
 

@@ -55,8 +55,8 @@ class GpuProblem:
         F.fftm_get_field(self.p, field, out)
         return node_from_abi(out).astype(np.float64)
 
-    def set_load(self, A, b, Q, mixed=0):
-        F.fftm_set_load(self.p, A, b, Q, mixed=mixed)
+    def set_load(self, A, b, Q, mixed=0, T=None):
+        F.fftm_set_load(self.p, A, b, Q, mixed=mixed, T=T)
 
     def get_voxel(self, field):
         n = self.wl.n
