@@ -882,7 +882,6 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
     *f = T(sgn);
     return (long long)(r * NCT) * nvox + vx + vy * P.vy + (long long)vz * P.vz;
   };
-  const int mi[3] = {mx, my, mz};
   for (int i = 0; i < 3; ++i) {
     for (int q = 0; q < 3; ++q) {
       const int c = SYM ? sym_index(i, q) : i * 3 + q;
@@ -891,8 +890,9 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
       // pair along i has its ghost corner there (Sec. 2.2, P* = 2 t at the mirror centres)
       T ps = T(0);
       if (P.traction && !P.periodic[i]) {
-        if (mi[i] == 0 && P.sgn[q][i][0] > 0) ps += T(2) * P.tr[i][0][q];         // - (2 (-1) t) at corner o
-        if (mi[i] == P.n[i] && P.sgn[q][i][1] > 0) ps += T(2) * P.tr[i][1][q];  // + (2 t) at corner o1
+        const int m_i = i == 0 ? mx : (i == 1 ? my : mz);
+        if (m_i == 0 && P.sgn[q][i][0] > 0) ps += T(2) * P.tr[i][0][q];         // - (2 (-1) t) at corner o
+        if (m_i == P.n[i] && P.sgn[q][i][1] > 0) ps += T(2) * P.tr[i][1][q];  // + (2 t) at corner o1
       }
       for (int o = 0; o < 8; ++o) {
         if ((o >> i) & 1) continue;
