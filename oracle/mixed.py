@@ -6,7 +6,7 @@ package.  Plain, slow FP64 NumPy.
 The paper imposes the volume average of grad u* with one component controlled and
 adjusts the other components at each iteration so that the volume-averaged stress
 vanishes in them (<P_rs> = 0); it does not say how.  Reading (small strain, symmetric
-stress; listed with the others in the design doc): the free components form a subset F of the
+stress): the free components form a subset F of the
 six symmetric strain components (Voigt order 11, 22, 33, 23, 13, 12, bit k of `mask`);
 after the residual of iteration m, with <sigma> the mean stress over the voxel points,
 the strain of u* takes the increment
