@@ -118,10 +118,12 @@ constexpr int LAWC = 40;
 constexpr int kMaxDynSmem = 227 * 1024;
 
 // One axis pass as a dense contraction on the tensor cores (FP32 data, BF16
-// operands, tcgen05).  A: the Kp x Kp (zero-padded, Kp = L rounded up to 32) transform
-// matrix in 32-column chunks, each in the shared-memory core-matrix order (element
-// (k, jj) of chunk c at c Kp 32 + (k>>3) 256 + (jj>>3) 64 + (k&7) 8 + (jj&7), in BF16
-// elements); A2: the inverse z matrix of the fused z pass, same layout.
+// operands, tcgen05).  A: the R x Kp transform matrix (zero-padded; Kp = L rounded up to
+// 32, on x after the shift below; R = Kp, on x Kp rounded up to 128) in 32-column
+// chunks, each in the shared-memory core-matrix order (element (m, jj) of chunk c at
+// c R 32 + (m>>3) 256 + (jj>>3) 64 + (m&7) 8 + (jj&7), in BF16 elements); on the x axis
+// rows and columns are shifted by lo mod 4 (the pass indexes nodes from lo rounded down
+// to a multiple of 4).  A2: the inverse z matrix of the fused z pass, same layout.
 struct TcPassParams {
   const float* in[3];
   float* out[3];

@@ -2,28 +2,34 @@
 // cores (the "precision form": FP32 fields, BF16 operands, FP32 accumulation in TMEM).
 //
 // Every 1D transform of Table 1 and its inverse is a real L x L matrix T over the
-// transform's node range (periodic axes in halfcomplex order).  One CTA transforms a
-// tile of 128 pencils of one component:
+// transform's node range (periodic axes in halfcomplex order).  A tile is 128 pencils of
+// one component, staged once in shared memory as BF16.  y and z axes (pencils are the
+// contiguous direction):
 //     D[p][k] = sum_j S[p][j] T[k][j]
-// with tcgen05.mma kind::f16 (M = 128 pencils, N = the padded output length, up to 256
-// per instruction, K = 16): the pencil tile S is the A operand, staged once in shared
-// memory as BF16 (K-major for the x axis, whose pencils are contiguous in memory;
-// MN-major for the y and z axes, whose pencils are the contiguous direction), and T is
-// the B operand, streamed through three shared-memory buffers in 32-column chunks that
-// the host laid out in the exact core-matrix order (one linear asynchronous copy per
-// chunk).  Each CTA is persistent (one per SM) and warp-specialised: four warps stage the
-// next tile into a second operand buffer while the MMA warp contracts the current one
-// and four epilogue warps drain the previous accumulator, handing over through mbarriers.  The accumulator D lives in TMEM (lanes = pencils, columns = outputs) and is
-// read back with tcgen05.ld for the epilogue.  The fused z pass multiplies D by the
-// Green factor, writes it back to shared memory as the A operand of a second
-// contraction with the inverse matrix, and stores only the result.
+// with the tile S as the A operand (M = 128 pencils, MN-major) and T as the B operand
+// (N = the padded output length, up to 256 per instruction), so TMEM lanes are pencils
+// and a store writes 32 consecutive pencils.  x axis (pencils are rows of memory):
+//     D[k][p] = sum_j T[k][j] S[p][j]
+// with T as the A operand (M = outputs in blocks of 128) and S as the B operand (N = 128
+// pencils, K-major), so TMEM lanes are outputs and a warp stores 32 consecutive nodes of
+// one pencil row.  T arrives in 32-column chunks, laid out by the host in the exact
+// core-matrix order, through a ring of shared-memory buffers filled by cp.async.bulk.
+//
+// Each CTA is persistent (one per SM) and warp-specialised: seven producer warps stage
+// tiles into two operand buffers, one thread keeps the matrix ring filled ahead (across
+// tile boundaries) and issues tcgen05.mma, and eight epilogue warps drain TMEM with
+// tcgen05.ld; the roles hand over through mbarriers.  With Kp <= 256 a CTA keeps two
+// accumulators, so the MMAs of one tile run while the previous one is drained.  The fused
+// z pass multiplies the forward result by the Green factor, writes it back to shared
+// memory as the A operand of a second contraction with the inverse matrix, and stores
+// only the result.
 //
 // The transforms only precondition; convergence is decided on the FP32 residual of the
 // stencil kernels, so BF16 rounding here changes the rate of the fixed point, not the
 // field it converges to.
 //
 // Every wait (an mbarrier phase) is bounded: past the limit the CTA records an error in
-// P.err, waits for its own copies, frees its TMEM and returns.
+// P.err, waits for its own copies and MMAs, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "fftm_internal.cuh"
@@ -97,8 +103,6 @@ __device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// named barrier among the 128 threads of one role (ids 1, 2; 0 is __syncthreads)
-__device__ __forceinline__ void role_sync(int id) { asm volatile("bar.sync %0, 128;\n" ::"r"(id) : "memory"); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   uint32_t r[16];
