@@ -315,6 +315,27 @@ int fftm_kernel_times(const fftm_problem* p, double* ms, long long* launches, in
    (cudaGetSymbolAddress): make that first call before any stream capture. */
 int fftm_residual_noalloc(fftm_problem* p, const void* u_dev, void* D_dev, double* norms_dev);
 
+/* ---- host-only utilities (no device work; callable without a GPU) -------- */
+
+/* 1D transform kinds of Table 1 (the kind a component takes along an axis from its
+   pair of face conditions: periodic -> DFT, N/N -> DCT-I, N/D -> DCT-III, D/D ->
+   DST-I, D/N -> DST-III). */
+enum fftm_dt_kind { FFTM_DT_DFT = 0, FFTM_DT_DCT1 = 1, FFTM_DT_DCT3 = 2, FFTM_DT_DST1 = 3, FFTM_DT_DST3 = 4 };
+
+/* The dense matrix of a 1D transform (Table 1) or of its inverse, as the tensor-core
+   path applies it: L x L over the kind's node range (L = n + 1, n, n - 1 for DCT-I,
+   DFT/DCT-III/DST-III, DST-I), row-major, out[k L + c] = weight of node lo + c in
+   output k; the DFT in halfcomplex order (row k <= n/2: the cosine sum, row n - k:
+   minus the sine sum).  n voxels, 2 <= n <= 4096; inverse 0 or 1.  out (HOST, L*L
+   doubles) may be NULL to query L; *L_out receives L.  FFTM_E_INVALID on a bad
+   argument. */
+int fftm_host_dense_transform(int kind, int n, int inverse, double* out, int* L_out);
+
+/* The normal-mixed strain increment (see fftm_load.mixed): d = -(C0_FF)^-1 <sigma>_F on
+   the free components of `mask`, zero elsewhere, C0 the isotropic reference stiffness
+   (lambda0, mu0 > 0).  sig and d_out: HOST 3x3 row-major. */
+int fftm_host_mixed_increment(const double* sig, int mask, double lambda0, double mu0, double* d_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1315,6 +1315,38 @@ int fftm_set_load(fftm_problem* p, const fftm_load* load) {
   return FFTM_OK;
 }
 
+int fftm_host_dense_transform(int kind, int n, int inverse, double* out, int* L_out) {
+  if (kind < K_DFT || kind > K_DST3 || n < 2 || n > 4096 || (inverse != 0 && inverse != 1) || !L_out)
+    return set_err(FFTM_E_INVALID, "bad transform kind, length or output");
+  std::vector<double> M;
+  int L = 0;
+  if (inverse) {
+    int lo;
+    kind_range(kind, n, &lo, &L);
+    if (out) dense_inverse(kind, n, &M);
+  } else if (out) {
+    dense_forward(kind, n, &M, &L);
+  } else {
+    int lo;
+    kind_range(kind, n, &lo, &L);
+  }
+  *L_out = L;
+  if (out) std::memcpy(out, M.data(), M.size() * sizeof(double));
+  return FFTM_OK;
+}
+
+int fftm_host_mixed_increment(const double* sig, int mask, double lambda0, double mu0, double* d_out) {
+  if (!sig || !d_out || (mask & ~0x3F) || !(mu0 > 0.0) || !(lambda0 >= 0.0))
+    return set_err(FFTM_E_INVALID, "bad mixed increment arguments");
+  double s3[3][3], d[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) s3[i][j] = sig[i * 3 + j];
+  mixed_increment(s3, mask, lambda0, mu0, d);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) d_out[i * 3 + j] = d[i][j];
+  return FFTM_OK;
+}
+
 int fftm_get_load(const fftm_problem* p, fftm_load* out) {
   if (!p || !out) return set_err(FFTM_E_INVALID, "null argument");
   *out = p->load;

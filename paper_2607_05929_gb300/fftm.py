@@ -40,7 +40,9 @@ EXPORTS = [
     "fftm_get_field", "fftm_set_field", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
+    "fftm_host_dense_transform", "fftm_host_mixed_increment",
 ]
+FFTM_DT_KINDS = {"DFT": 0, "DCT1": 1, "DCT3": 2, "DST1": 3, "DST3": 4}
 FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "other"]
 
 
@@ -115,6 +117,10 @@ def load_library(path=LIB_PATH):
         "fftm_set_phase": ([vp, P(ctypes.c_uint16)], ctypes.c_int),
         "fftm_set_load": ([vp, P(fftm_load)], ctypes.c_int),
         "fftm_get_load": ([vp, P(fftm_load)], ctypes.c_int),
+        "fftm_host_dense_transform": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
+                                       P(ctypes.c_int)], ctypes.c_int),
+        "fftm_host_mixed_increment": ([P(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       P(ctypes.c_double)], ctypes.c_int),
         "fftm_solve_step": ([vp, P(fftm_step_report), P(ctypes.c_double), P(ctypes.c_int), ctypes.c_int],
                             ctypes.c_int),
         "fftm_field_bytes": ([vp, ctypes.c_int, P(ctypes.c_size_t)], ctypes.c_int),
@@ -255,6 +261,28 @@ def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None, mixed=0, T=None):
                     ld.T[a][f][q] = float(T[a][f][q])
     ld.mixed = int(mixed)
     return _check(load_library().fftm_set_load(p, ctypes.byref(ld)))
+
+
+def fftm_host_dense_transform(kind, n, inverse=False):
+    """The L x L matrix the tensor-core path uses for a 1D transform of Table 1 (host only)."""
+    k = FFTM_DT_KINDS[kind] if isinstance(kind, str) else int(kind)
+    L = ctypes.c_int(0)
+    _check(load_library().fftm_host_dense_transform(k, int(n), int(bool(inverse)), None, ctypes.byref(L)))
+    out = np.zeros(L.value * L.value)
+    _check(load_library().fftm_host_dense_transform(k, int(n), int(bool(inverse)),
+                                                    out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                    ctypes.byref(L)))
+    return out.reshape(L.value, L.value)
+
+
+def fftm_host_mixed_increment(sig, mask, lambda0, mu0):
+    """The normal-mixed strain increment for a mean stress (host only)."""
+    s = np.ascontiguousarray(np.asarray(sig, dtype=np.float64).reshape(9))
+    d = np.zeros(9)
+    _check(load_library().fftm_host_mixed_increment(s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(mask),
+                                                    float(lambda0), float(mu0),
+                                                    d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return d.reshape(3, 3)
 
 
 def fftm_get_load(p):
