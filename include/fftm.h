@@ -141,7 +141,7 @@ typedef struct fftm_problem_desc {
    voxel points; the increment is added symmetrically to A, whose skew part and
    imposed components stay as given.  A's free entries are the first step's
    starting guess; a later step whose load has the same mask starts them from
-   the values the previous step converged to.  The step converges when err < tol
+   the values the previous mixed step ended with.  The step converges when err < tol
    and ||<sigma>_F|| / ||<sigma>|| < tol (tensor norms).  Requires small-strain
    laws (symmetric P) and non-periodic axes i and j for every free component ij
    (FFTM_E_INVALID otherwise).  0: A is imposed as given.  fftm_get_load returns
@@ -161,7 +161,7 @@ typedef struct fftm_load {
 
 typedef struct fftm_step_report {
   int iterations;       /* Green applications performed (0 = initial guess converged) */
-  int converged;        /* 1 if err < tol                                     */
+  int converged;        /* 1 if err < tol (a mixed load: and its mixed error)  */
   double err;           /* final equilibrium error (Eq. equilibrium_condition) */
   int n_accelerated;    /* Anderson steps taken                               */
   double mean_P[6];     /* volume mean of P over voxel points, (11,22,33,23,13,12) */
