@@ -20,6 +20,16 @@ stress (div P)_q = d P_qi / d x_i.
   Pi = C : (A - 1)/2 - sum_s dgamma_s C : sym(A P_s), A = F^p_n^{-T} F^T F F^p_n^{-1},
   tau_s = Pi : P_s (the Mandel stress with C^e ~ 1 in the resolved shear), tau_c at the
   committed Gamma_n.  params = (C11, C12, C44, gdot0, n, tau0, tau_inf, h0, dt).
+* LOG_J2: perfect von Mises plasticity in the logarithmic framework the paper uses for the
+  porous medium (Sec. 3.2, after Miehe, Apel and Lambrecht): Hencky strain H = log(F^T F)/2
+  split additively, H = H^e + H^p; the stress conjugate to H is T = 2 mu dev H^e + K tr H^e 1
+  (K = lambda + 2 mu / 3); f = sqrt(3/2 dev T : dev T) - sigma0 <= 0 with normality in H^p.
+  Reading (the paper calls T the Cauchy stress and gives no integration): backward-Euler
+  radial return from the committed (H^p_n, p_n) on the trial H^e = H - H^p_n; the second
+  Piola-Kirchhoff stress is T : dH/dE = T : d log C / d C (E = (C - 1)/2), evaluated in the
+  eigenbasis of C = sum_a lam_a N_a (x) N_a with the divided differences of the logarithm
+  (theta_aa = 1 / lam_a, theta_ab = (log lam_a - log lam_b) / (lam_a - lam_b)); P = F S.
+  params = (lambda, mu, sigma0).
 """
 
 import numpy as np
@@ -165,3 +175,46 @@ def cp_fcc(G, params, quat, Fp_n, gam_n):
     P, Fp, gam, _ = cp_update(F, Fpn, gam_n.reshape(npp * m), C, Ps, gdot0, nexp, tau0, tau_inf, h0, dt)
     S = to_S(P.reshape(npp, m, 3, 3))
     return S, np.moveaxis(Fp.reshape(npp, m, 3, 3), 1, 3), gam.reshape(npp, m)
+
+
+def _log_divided_differences(w):
+    """theta[..., a, b] = (log w_a - log w_b) / (w_a - w_b), 1 / w_a on the diagonal and in
+    the limit of equal eigenvalues (log1p keeps nearby pairs accurate)."""
+    wa = w[..., :, None]
+    wb = w[..., None, :]
+    r = (wa - wb) / wb
+    with np.errstate(divide="ignore", invalid="ignore"):
+        th = np.log1p(r) / (wb * r)
+    near = np.abs(r) < 1e-10
+    return np.where(near, 1.0 / (0.5 * (wa + wb)), th)
+
+
+def log_j2(G, params, Hp_n, p_n):
+    """G (npp, 3, 3, m); Hp_n (npp, 3, 3, m) committed plastic Hencky strain, p_n (npp, m)
+    cumulated plastic strain.  Returns (S[i, q] = P[q, i], Hp, p)."""
+    lam, mu, sigma0 = params[:3]
+    K = lam + 2.0 * mu / 3.0
+    F = deformation_gradient(G)  # (npp, m, 3, 3)
+    C = np.einsum("rmki,rmkj->rmij", F, F)
+    w, V = np.linalg.eigh(C)  # C = V diag(w) V^T
+    H = np.einsum("rmia,rma,rmja->rmij", V, 0.5 * np.log(w), V)
+    Hp = np.moveaxis(Hp_n, 3, 1)  # (npp, m, 3, 3)
+    He = H - Hp
+    tr = np.trace(He, axis1=2, axis2=3)
+    dev = He - (tr / 3.0)[..., None, None] * I3
+    s_tr = 2.0 * mu * dev
+    seq = np.sqrt(1.5 * np.einsum("rmij,rmij->rm", s_tr, s_tr))
+    f = seq - sigma0
+    yld = f > 0.0
+    dp = np.where(yld, f / (3.0 * mu), 0.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        scale = np.where(yld, sigma0 / seq, 1.0)
+        nflow = np.where(yld[..., None, None], 1.5 * s_tr / seq[..., None, None], 0.0)
+    s = scale[..., None, None] * s_tr
+    T = s + (K * tr)[..., None, None] * I3
+    Hp_new = Hp + dp[..., None, None] * nflow
+    # S = T : d log C / d C in the eigenbasis of C
+    Tt = np.einsum("rmia,rmij,rmjb->rmab", V, T, V)
+    St = _log_divided_differences(w) * Tt
+    S = np.einsum("rmia,rmab,rmjb->rmij", V, St, V)
+    return to_S(F @ S), np.moveaxis(Hp_new, 1, 3), p_n + dp

@@ -25,6 +25,7 @@ B0_LINEAR = 3
 SVK_CUBIC = 4
 NEO_HOOKE = 5
 CP_FCC = 6
+LOG_J2 = 7  # finite strain (finite.log_j2)
 
 I3 = np.eye(3)
 
@@ -122,6 +123,9 @@ def stress(G, materials, groups, state=None):
         if "Fp" in state:
             new_state["Fp"] = state["Fp"].reshape(npp, 3, 3, -1).copy()
             new_state["gam"] = state["gam"].reshape(npp, -1).copy()
+        if "Hp" in state:
+            new_state["Hp"] = state["Hp"].reshape(npp, 3, 3, -1).copy()
+            new_state["pl"] = state["pl"].reshape(npp, -1).copy()
     for ph, mat in enumerate(materials):
         idx = groups[ph]
         if idx.size == 0:
@@ -171,6 +175,18 @@ def stress(G, materials, groups, state=None):
             if new_state is not None:
                 new_state["Fp"][..., idx] = Fp
                 new_state["gam"][..., idx] = gam
+        elif mat.law == LOG_J2:
+            if state is None:
+                Hp_n = np.zeros((npp, 3, 3, idx.size))
+                pl_n = np.zeros((npp, idx.size))
+            else:
+                Hp_n = new_state["Hp"][..., idx]
+                pl_n = new_state["pl"][..., idx]
+            S, Hp, pl = finite.log_j2(Gv, mat.params, Hp_n, pl_n)
+            P[..., idx] = S
+            if new_state is not None:
+                new_state["Hp"][..., idx] = Hp
+                new_state["pl"][..., idx] = pl
         else:
             raise ValueError(f"unknown law {mat.law}")
     P = P.reshape(shp)
@@ -182,6 +198,9 @@ def stress(G, materials, groups, state=None):
         if "Fp" in new_state:
             out["Fp"] = new_state["Fp"].reshape(shp)
             out["gam"] = new_state["gam"].reshape((npp,) + shp[3:])
+        if "Hp" in new_state:
+            out["Hp"] = new_state["Hp"].reshape(shp)
+            out["pl"] = new_state["pl"].reshape((npp,) + shp[3:])
         new_state = out
     return P, new_state
 

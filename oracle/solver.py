@@ -60,6 +60,10 @@ class Problem:
         shp = (self.npp,) + self.grid.n
         if any(m.law == 2 for m in wl.materials):  # J2: (eps^p, p)
             self.state = {"ep": np.zeros((self.npp, 3, 3) + self.grid.n), "p": np.zeros(shp)}
+        if any(m.law == 7 for m in wl.materials):  # logarithmic J2: (H^p, p)
+            self.state = self.state or {}
+            self.state["Hp"] = np.zeros((self.npp, 3, 3) + self.grid.n)
+            self.state["pl"] = np.zeros(shp)
         if any(m.law == 6 for m in wl.materials):  # crystal plasticity: (F^p, Gamma)
             self.state = self.state or {}
             self.state["Fp"] = np.broadcast_to(np.eye(3)[None, :, :, None, None, None],

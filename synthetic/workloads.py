@@ -25,6 +25,7 @@ B0_LINEAR = 3  # P = 2 mu G + lambda G (.) I : the preconditioner itself (test l
 SVK_CUBIC = 4  # finite strain: St-Venant-Kirchhoff, (C11, C12, C44), quat
 NEO_HOOKE = 5  # finite strain: (mu, K)
 CP_FCC = 6     # finite strain crystal plasticity: (C11, C12, C44, gdot0, n, tau0, tau_inf, h0, dt), quat
+LOG_J2 = 7     # finite strain perfect J2 in the logarithmic framework: (lambda, mu, sigma0)
 
 
 @dataclass
