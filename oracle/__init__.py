@@ -13,14 +13,19 @@ Modules and what they restate:
 * ``transforms``  the five forward DTs of Table 1 and their inverses (Sec. 2.4, Sec. 2.7.2)
 * ``stencils``    HEX1 / TETRA2 gradient and divergence with ghost voxels (Sec. 2.5, Remark 1)
 * ``green``       B0 and 2mu0 discrete Green operators (Sec. 2.6.2-2.6.3, Eqs. NSGO1_*, NSGO2_*)
-* ``laws``        small-strain constitutive laws (Sec. 3.1; cubic elasticity as in Sec. 3.3)
+* ``laws``        small-strain constitutive laws (Sec. 3.1; cubic elasticity as in Sec. 3.3; J2, Sec. 3.2)
+* ``finite``      finite-strain laws: St-Venant-Kirchhoff, Neo-Hookean (Appendix B), FCC crystal
+                  plasticity (Sec. 3.4), logarithmic J2 (Sec. 3.2)
+* ``mixed``       normal-mixed loading (Eq. NMBC1)
 * ``anderson``    Anderson acceleration on p (Sec. 2.3, Algorithm 1)
-* ``solver``      Algorithm 1, one load step
+* ``solver``      Algorithm 1, one load step (with Neumann tractions through ``stencils``)
 * ``direct``      the same discrete problem assembled as a sparse matrix and solved directly
 
 Parity status of each part is stated in the module headers; Anderson's
 acceleration step has no closed form to pin it against beyond its own
 definition (parity unpinned beyond self-consistency: its decisions are fixed
 by the stated rule and the fixed point it reaches is pinned by the direct
-solve and the laminate closed forms).
+solve and the laminate closed forms).  The crystal-plasticity law is pinned by its
+single-slip recursion; its full-field polycrystal response is parity unpinned beyond
+the oracle itself (no closed form).
 """
