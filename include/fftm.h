@@ -55,6 +55,10 @@ extern "C" {
 #define FFTM_E_CUDA (-3)      /* a CUDA runtime call failed */
 #define FFTM_E_DIVERGED (-4)  /* NaN / Inf in the equilibrium norms */
 #define FFTM_E_UNSUPPORTED (-5)
+#define FFTM_E_TIMEOUT (-6)   /* a bounded device-side wait gave up (a tensor-core pass
+                                 whose MMA hand-over did not complete within about a
+                                 second); the result of that call is undefined, the
+                                 CUDA context stays usable */
 
 /* ---- enumerations ----------------------------------------------------- */
 enum fftm_bc { FFTM_BC_PERIODIC = 0, FFTM_BC_DIRICHLET = 1, FFTM_BC_NEUMANN = 2 };
@@ -232,6 +236,12 @@ enum fftm_field {
 
 /* Bytes of a field (dense layout above, problem precision). */
 int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
+
+/* Node dimensions N[3] of the problem's node fields (N_a = n_a + 1 on a non-periodic
+   axis, n_a on a periodic one; Sec. 2.1), its precision (enum fftm_precision) and its
+   CUDA device, so a caller can size, type and place the device buffers it passes to the
+   library.  HOST outputs; each may be NULL. */
+int fftm_problem_layout(const fftm_problem* p, int N[3], int* precision, int* device);
 
 /* Copy a field out.  dst is a device pointer if dst_is_device, else host.
    bytes must equal fftm_field_bytes().  GRAD and STRESS are evaluated from

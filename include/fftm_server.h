@@ -55,7 +55,11 @@ typedef struct fftm_result {
 } fftm_result;
 
 /* Start a server on `device` with `max_slots` (1..64) resident solves and a device
-   memory budget in bytes (0: nine tenths of the memory free at creation). */
+   memory budget in bytes (0: nine tenths of the memory free at creation).  Returns
+   after every worker has started or failed to start (its CUDA stream or library
+   context could not be created); FFTM_E_CUDA, with no server, if none started.  A
+   server whose workers have all stopped fails its queued requests with FFTM_E_CUDA
+   and refuses new ones. */
 int fftm_server_create(int device, size_t memory_budget, int max_slots, fftm_server** out);
 
 /* Queue a request; *id (may be NULL) receives its id.  FFTM_E_NOMEM if the request
@@ -72,6 +76,11 @@ int fftm_server_pending(fftm_server* s, int* queued, int* active, size_t* bytes_
 
 /* Finish every queued request, join the threads, free the server. */
 int fftm_server_destroy(fftm_server* s);
+
+/* Test hook (host only, no device work): the next `count` workers started by
+   fftm_server_create fail at start-up as if their stream or context could not be
+   created.  With count >= max_slots the create call needs no device at all. */
+int fftm_server_inject_start_failures(int count);
 
 #ifdef __cplusplus
 }

@@ -143,8 +143,7 @@ class Problem:
                 A[j, i] = self.mixed_A[j, i]
         Gs = self.grad_ustar(A, b, Q)
         uf = self.uf.copy() if uf0 is None else np.array(uf0, dtype=np.float64)
-        hist = []  # (q_j, g_j) couples
-        q_prev = None
+        mixer = anderson_mod.Mixer(wl.anderson_depth, wl.anderson_period, enabled=anderson)
         rep = Report(iterations=0, converged=False)
         for m in range(max_iter + 1):
             p, D, P, G, S_D, S_P = self.residual(uf, Gs, T)
@@ -163,17 +162,9 @@ class Problem:
                 break
             if np.isnan(err) or not (np.isfinite(S_D) and np.isfinite(S_P)):
                 break  # diverged (err is +inf, and the iteration goes on, while P is still zero)
-            if q_prev is not None:
-                hist.append((q_prev, p))
-                if len(hist) > wl.anderson_depth:
-                    hist.pop(0)
-            q = p
-            if anderson and anderson_mod.accelerate_now(m, wl.anderson_period, len(hist), wl.anderson_depth):
-                c = anderson_mod.coefficients([g_ - q_ for q_, g_ in hist])
-                if c is not None:
-                    q = sum(cj * g_ for cj, (_, g_) in zip(c, hist))
-                    rep.accelerated.append(m)
-            q_prev = q
+            q, mixed_step = mixer.propose(m, p)
+            if mixed_step:
+                rep.accelerated.append(m)
             uf = self.green_update(q)
             if mixed:  # the free strain components of u* for the next iteration
                 A = A + mixed_mod.mixed_increment(mean_sig, mixed, float(wl.lambda0), float(wl.mu0))

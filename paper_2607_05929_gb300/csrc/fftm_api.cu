@@ -874,7 +874,7 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     CU(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
       CU(cudaMemset(p->tc_err, 0, sizeof(int)));
-      return set_err(FFTM_E_CUDA, "a tensor-core transform pass timed out waiting for its MMAs");
+      return set_err(FFTM_E_TIMEOUT, "a tensor-core transform pass timed out waiting for its MMAs");
     }
   }
   const double npts = (double)p->nvox * (p->tetra ? 2 : 1);
@@ -1379,6 +1379,15 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes) {
   }
 }
 
+int fftm_problem_layout(const fftm_problem* p, int N[3], int* precision, int* device) {
+  if (!p) return set_err(FFTM_E_INVALID, "null problem");
+  if (N)
+    for (int a = 0; a < 3; ++a) N[a] = p->N[a];
+  if (precision) *precision = p->desc.precision;
+  if (device) *device = p->ctx->device;
+  return FFTM_OK;
+}
+
 static int ensure_scratch(fftm_problem* p, size_t bytes) {
   if (p->scratch_bytes >= bytes) return FFTM_OK;
   cudaFree(p->scratch);
@@ -1577,7 +1586,7 @@ static int apply_t(fftm_problem* p, int op, double* norms) {
     CU(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
       CU(cudaMemset(p->tc_err, 0, sizeof(int)));
-      return set_err(FFTM_E_CUDA, "a tensor-core transform pass timed out waiting for its MMAs");
+      return set_err(FFTM_E_TIMEOUT, "a tensor-core transform pass timed out waiting for its MMAs");
     }
   }
   return FFTM_OK;

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -59,11 +60,18 @@ struct fftm_server {
   std::deque<std::unique_ptr<Request>> queue;
   std::deque<fftm_result> done;
   int active = 0;
+  int live = 0;      // workers that created their stream and context and are serving
+  int started = 0;   // workers that finished starting up (successfully or not)
+  std::condition_variable cv_start;
   std::vector<std::thread> workers;
   std::string error;
 };
 
 namespace {
+
+// Host-side fault injection for the tests: the next g_fail_starts workers fail to start as if
+// their stream or context could not be created.
+std::atomic<int> g_fail_starts{0};
 
 int fail(fftm_server* s, const std::string& msg, int code) {
   std::lock_guard<std::mutex> lk(s->mu);
@@ -102,14 +110,41 @@ void run_request(fftm_ctx* ctx, Request& q, fftm_result& r) {
   r.t_end = now_s();
 }
 
+// Fail every queued request (no worker is left to run them).
+void fail_queue_locked(fftm_server* s) {
+  while (!s->queue.empty()) {
+    fftm_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.id = s->queue.front()->id;
+    r.t_submit = s->queue.front()->t_submit;
+    r.t_start = r.t_end = now_s();
+    r.status = FFTM_E_CUDA;
+    std::strncpy(r.message, "no server worker is running", sizeof(r.message) - 1);
+    s->queue.pop_front();
+    s->done.push_back(r);
+  }
+}
+
 void worker_main(fftm_server* s) {
-  cudaSetDevice(s->device);
   cudaStream_t stream = nullptr;
   fftm_ctx* ctx = nullptr;
-  if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
-      fftm_ctx_create(&ctx, s->device, stream) != FFTM_OK) {
+  bool ok = false;
+  int expected = g_fail_starts.load();
+  while (expected > 0 && !g_fail_starts.compare_exchange_weak(expected, expected - 1)) {
+  }
+  if (expected <= 0)
+    ok = cudaSetDevice(s->device) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) == cudaSuccess &&
+         fftm_ctx_create(&ctx, s->device, stream) == FFTM_OK;
+  {
     std::lock_guard<std::mutex> lk(s->mu);
-    s->error = "worker could not create its stream or context";
+    s->started += 1;
+    if (ok) s->live += 1;
+    else s->error = "worker could not create its stream or context";
+  }
+  s->cv_start.notify_all();
+  if (!ok) {
+    if (stream) cudaStreamDestroy(stream);
     return;
   }
   for (;;) {
@@ -146,6 +181,12 @@ void worker_main(fftm_server* s) {
   }
   fftm_ctx_destroy(ctx);
   cudaStreamDestroy(stream);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->live -= 1;
+    if (s->live == 0) fail_queue_locked(s);
+  }
+  s->cv_done.notify_all();
 }
 
 }  // namespace
@@ -154,13 +195,17 @@ extern "C" {
 
 int fftm_server_create(int device, size_t memory_budget, int max_slots, fftm_server** out) {
   if (!out || max_slots < 1 || max_slots > 64) return FFTM_E_INVALID;
-  int count = 0;
-  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return FFTM_E_INVALID;
-  if (memory_budget == 0) {
-    size_t free_b = 0, total_b = 0;
-    cudaSetDevice(device);
-    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return FFTM_E_CUDA;
-    memory_budget = free_b / 10 * 9;  // leave a tenth for the runtime and other users
+  // every worker set to fail at start needs no device (host-side tests of that path)
+  const bool all_fail = g_fail_starts.load() >= max_slots;
+  if (!all_fail) {
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) return FFTM_E_INVALID;
+    if (memory_budget == 0) {
+      size_t free_b = 0, total_b = 0;
+      cudaSetDevice(device);
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return FFTM_E_CUDA;
+      memory_budget = free_b / 10 * 9;  // leave a tenth for the runtime and other users
+    }
   }
   fftm_server* s = new (std::nothrow) fftm_server;
   if (!s) return FFTM_E_NOMEM;
@@ -168,6 +213,22 @@ int fftm_server_create(int device, size_t memory_budget, int max_slots, fftm_ser
   s->budget = memory_budget;
   s->max_slots = max_slots;
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker_main, s);
+  int live = 0;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_start.wait(lk, [&] { return s->started == max_slots; });
+    live = s->live;
+  }
+  if (live == 0) {  // nothing could start: report it instead of queueing requests nobody runs
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      s->stopping = true;
+    }
+    s->cv_work.notify_all();
+    for (auto& t : s->workers) t.join();
+    delete s;
+    return FFTM_E_CUDA;
+  }
   *out = s;
   return FFTM_OK;
 }
@@ -193,6 +254,7 @@ int fftm_server_submit(fftm_server* s, const fftm_request* req, long long* id) {
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return FFTM_E_INVALID;
+    if (s->live == 0) return FFTM_E_CUDA;
     q->id = s->next_id++;
     if (id) *id = q->id;
     s->queue.push_back(std::move(q));
@@ -205,7 +267,7 @@ int fftm_server_poll(fftm_server* s, fftm_result* out, int max_results, int wait
   if (!s || !n_out || (max_results > 0 && !out)) return FFTM_E_INVALID;
   std::unique_lock<std::mutex> lk(s->mu);
   if (wait_for_one)
-    s->cv_done.wait(lk, [&] { return !s->done.empty() || (s->queue.empty() && s->active == 0); });
+    s->cv_done.wait(lk, [&] { return !s->done.empty() || (s->queue.empty() && s->active == 0) || s->live == 0; });
   int n = 0;
   while (n < max_results && !s->done.empty()) {
     out[n++] = s->done.front();
@@ -233,6 +295,12 @@ int fftm_server_destroy(fftm_server* s) {
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
   delete s;
+  return FFTM_OK;
+}
+
+int fftm_server_inject_start_failures(int count) {
+  if (count < 0) return FFTM_E_INVALID;
+  g_fail_starts.store(count);
   return FFTM_OK;
 }
 

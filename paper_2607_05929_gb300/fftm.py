@@ -23,6 +23,7 @@ FFTM_E_NOMEM = -2
 FFTM_E_CUDA = -3
 FFTM_E_DIVERGED = -4
 FFTM_E_UNSUPPORTED = -5
+FFTM_E_TIMEOUT = -6
 # enums
 FFTM_BC_PERIODIC, FFTM_BC_DIRICHLET, FFTM_BC_NEUMANN = 0, 1, 2
 FFTM_HEX1, FFTM_TETRA2 = 0, 1
@@ -37,9 +38,10 @@ EXPORTS = [
     "fftm_last_error", "fftm_version", "fftm_ctx_create", "fftm_ctx_destroy",
     "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
     "fftm_set_phase", "fftm_set_load", "fftm_get_load", "fftm_solve_step", "fftm_field_bytes",
-    "fftm_get_field", "fftm_set_field", "fftm_apply", "fftm_kernel_launches",
+    "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
+    "fftm_server_inject_start_failures",
     "fftm_host_dense_transform", "fftm_host_mixed_increment",
 ]
 FFTM_DT_KINDS = {"DFT": 0, "DCT1": 1, "DCT3": 2, "DST1": 3, "DST3": 4}
@@ -124,6 +126,7 @@ def load_library(path=LIB_PATH):
         "fftm_solve_step": ([vp, P(fftm_step_report), P(ctypes.c_double), P(ctypes.c_int), ctypes.c_int],
                             ctypes.c_int),
         "fftm_field_bytes": ([vp, ctypes.c_int, P(ctypes.c_size_t)], ctypes.c_int),
+        "fftm_problem_layout": ([vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)], ctypes.c_int),
         "fftm_get_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "fftm_set_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "fftm_apply": ([vp, ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
@@ -137,6 +140,7 @@ def load_library(path=LIB_PATH):
         "fftm_server_poll": ([vp, P(fftm_result), ctypes.c_int, ctypes.c_int, P(ctypes.c_int)], ctypes.c_int),
         "fftm_server_pending": ([vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)], ctypes.c_int),
         "fftm_server_destroy": ([vp], ctypes.c_int),
+        "fftm_server_inject_start_failures": ([ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -314,6 +318,14 @@ def fftm_field_bytes(p, field):
     return b.value
 
 
+def fftm_problem_layout(p):
+    """(N (3 node dims), precision enum, CUDA device) of a problem."""
+    N = (ctypes.c_int * 3)()
+    prec, dev = ctypes.c_int(), ctypes.c_int()
+    _check(load_library().fftm_problem_layout(p, N, ctypes.byref(prec), ctypes.byref(dev)))
+    return tuple(N[:]), prec.value, dev.value
+
+
 def _ptr_of(buf):
     """(pointer, is_device, nbytes) of a torch tensor or a numpy array."""
     if isinstance(buf, np.ndarray):
@@ -365,12 +377,34 @@ def fftm_kernel_times(p):
     return {FFTM_KCAT_NAMES[i]: (ms[i], cnt[i]) for i in range(n)}
 
 
+def check_noalloc_args(layout, u_dev, D_dev, norms_dev):
+    """Refuse buffers the residual kernels would read or write out of bounds: u and D must be
+    contiguous CUDA tensors on the problem's device, of the problem's precision (float64 for
+    FFTM_FP64, float32 otherwise), with exactly 3 N1 N2 N3 elements; norms a contiguous
+    float64 CUDA tensor of at least 3 elements on the same device.  Raises ValueError."""
+    N, prec, dev = layout
+    want_size = 8 if prec == FFTM_FP64 else 4
+    need = 3 * N[0] * N[1] * N[2]
+    for name, t in (("u_dev", u_dev), ("D_dev", D_dev), ("norms_dev", norms_dev)):
+        if not getattr(t, "is_cuda", False) or not t.is_contiguous():
+            raise ValueError(f"{name}: a contiguous CUDA tensor is expected")
+        if t.device.index != dev:
+            raise ValueError(f"{name}: on cuda:{t.device.index}, the problem is on cuda:{dev}")
+    for name, t in (("u_dev", u_dev), ("D_dev", D_dev)):
+        if not t.is_floating_point() or t.element_size() != want_size:
+            raise ValueError(f"{name}: dtype {t.dtype} does not match the problem precision "
+                             f"({'float64' if want_size == 8 else 'float32'})")
+        if t.numel() != need:
+            raise ValueError(f"{name}: {t.numel()} elements, the node field has 3 x {N} = {need}")
+    if not norms_dev.is_floating_point() or norms_dev.element_size() != 8 or norms_dev.numel() < 3:
+        raise ValueError("norms_dev: a float64 tensor of at least 3 elements is expected")
+
+
 def fftm_residual_noalloc(p, u_dev, D_dev, norms_dev):
     """Residual D and norms of a caller-supplied u^f into caller device buffers (torch CUDA
-    tensors: u and D in the dense node layout, norms 3 float64); allocates no device memory."""
-    for t in (u_dev, D_dev, norms_dev):
-        if not (t.is_cuda and t.is_contiguous()):
-            raise ValueError("device tensors expected")
+    tensors: u and D in the dense node layout, norms 3 float64); allocates no device memory.
+    The buffers are checked against the problem's layout first (check_noalloc_args)."""
+    check_noalloc_args(fftm_problem_layout(p), u_dev, D_dev, norms_dev)
     return _check(load_library().fftm_residual_noalloc(p, ctypes.c_void_p(u_dev.data_ptr()),
                                                         ctypes.c_void_p(D_dev.data_ptr()),
                                                         ctypes.c_void_p(norms_dev.data_ptr())))
@@ -437,3 +471,7 @@ def fftm_server_pending(s):
 
 def fftm_server_destroy(s):
     return _check(load_library().fftm_server_destroy(s))
+
+
+def fftm_server_inject_start_failures(count):
+    return _check(load_library().fftm_server_inject_start_failures(int(count)))

@@ -81,11 +81,27 @@ DT_CASES = [
 ]
 
 
+# an axis of 256 voxels, the benchmark's length, for every kind (255, 256 or 257 transformed
+# node positions: complex FFTs of 512 or 256 points, more than 48 KB of shared memory per CTA)
+DT_CASES_256 = [
+    ((256, 6, 4), ("DST1", "DCT3", "P")),
+    ((256, 4, 6), ("DCT1", "P", "DST3")),
+    ((256, 6, 4), ("DST3", "DST1", "P")),
+    ((256, 4, 6), ("P", "DCT1", "DCT3")),
+    ((8, 256, 4), ("DCT3", "DST3", "P")),
+    ((6, 256, 8), ("P", "DCT3", "DCT1")),
+    ((8, 6, 256), ("DST1", "DCT1", "P")),
+    ((6, 8, 256), ("DCT3", "DST3", "DCT1")),
+    ((6, 8, 256), ("P", "DCT1", "DST1")),
+]
+ALL_DT_CASES = DT_CASES + DT_CASES_256
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("case", range(len(DT_CASES)))
+@pytest.mark.parametrize("case", range(len(ALL_DT_CASES)))
 @pytest.mark.parametrize("mix", [False, True])
 def test_dt_forward_and_round_trip(precision, case, mix):
-    n, kinds = DT_CASES[case]
+    n, kinds = ALL_DT_CASES[case]
     wl = _wl(n, _bc_for(*kinds, mix=mix))
     g = Grid(wl.n, wl.bc)
     gp = GpuProblem(wl, precision)
@@ -294,6 +310,26 @@ def test_solve_step_fp32_vs_fp64_oracle(name):
         G = pr.last["G"]
         assert rel_l2(Pg, sym6(P)) < 1e-5
         assert rel_l2(sym6(_strain(Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:]))), sym6(_strain(G))) < 1e-5
+    finally:
+        gp.close()
+
+
+def test_anderson_step_lands_on_the_solution_with_three_free_dofs():
+    """The oracle's pin of how the Anderson mix feeds the loop, on the GPU (FP64): with one
+    interior node (3 free components) the map of one iteration is affine in dimension 3, so
+    the first accepted mix of 4 couples lands on the solution to rounding."""
+    from test_oracle_anderson import _three_dof_problem
+
+    wl = _three_dof_problem()
+    pr = Problem(wl)
+    _, rep = pr.solve_step()
+    gp = GpuProblem(wl, "fp64")
+    try:
+        st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+        assert st == F.FFTM_NOT_CONVERGED and r["iterations"] == wl.max_iter
+        assert [i for i, a in enumerate(ah) if a] == rep.accelerated == [5]
+        assert np.allclose(eh[:6], rep.err[:6], rtol=1e-9, atol=0.0)
+        assert eh[5] > 1e-4 * eh[0] and eh[6] < 1e-12 * eh[0], list(eh)
     finally:
         gp.close()
 

@@ -67,3 +67,60 @@ def test_noalloc_residual_matches_the_regular_entry_point_on_two_calls(precision
             assert np.allclose(norms, norms_ref, rtol=TOL[precision], atol=0.0), (call, norms, norms_ref)
     finally:
         gp.close()
+
+
+def _j2_bending():
+    wl, loads = syn.sphere_composite_bending((12, 10, 8), r_min=2.0, r_max=3.0, seed=4, scheme="HEX1", steps=20,
+                                             theta_max=0.012 * 12 / 10, tol=1e-8)
+    return wl, loads[:8]  # the last steps take the matrix past yield: a committed plastic state
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["cubic", "j2_after_commits"])
+def test_noalloc_residual_matches_the_oracle(precision, case):
+    """D and the norms of fftm_residual_noalloc against the FP64 oracle's residual (a1-a4), on
+    a cubic polycrystal and on a J2 composite after eight committed bending steps (past yield):
+    the entry point evaluates the residual in the plain form from the committed state, the
+    solver after a commit in the incremental one; both must equal the oracle's D."""
+    from oracle.solver import Problem
+
+    build.build()
+    F.load_library()
+    if case == "cubic":
+        wl, loads = _workload(), []
+    else:
+        wl, loads = _j2_bending()
+    pr = Problem(wl)
+    gp = GpuProblem(wl, precision)
+    try:
+        for A, b, Q in loads:
+            _, rep = pr.solve_step(A=A, b=b, Q=Q)
+            assert rep.converged
+            gp.set_load(A, b, Q)
+            st, r, _, _ = F.fftm_solve_step(gp.p)
+            assert r["converged"]
+        if loads:
+            assert float(np.abs(pr.state["p"]).max()) > 0.0, "the schedule should reach yield"
+            Gs = pr.grad_ustar(*loads[-1])
+        else:
+            Gs = pr.grad_ustar()
+        rng = np.random.default_rng(23)
+        u = pr.uf + 1e-4 * np.abs(pr.uf).max() * rng.standard_normal(pr.grid.node_shape) if loads else \
+            1e-3 * rng.standard_normal(pr.grid.node_shape)
+        for q in range(3):
+            u[q][~pr.grid.dof_mask(q)] = 0.0
+        _, D_ref, _, _, SD, SP = pr.residual(u, Gs)
+        tdt = torch.float64 if precision == "fp64" else torch.float32
+        u_dev = torch.from_numpy(node_to_abi(u).astype(gp.dtype)).cuda()
+        D_dev = torch.full(u_dev.shape, float("nan"), dtype=tdt, device="cuda")
+        norms_dev = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+        F.fftm_residual_noalloc(gp.p, u_dev, D_dev, norms_dev)
+        torch.cuda.synchronize()
+        D = node_from_abi(D_dev.cpu().numpy()).astype(np.float64)
+        norms = norms_dev.cpu().numpy()
+        # FP64: the committed states of the two sides agree to about 1e-9 (the J2 parity bar)
+        tol = {"fp64": 1e-11 if not loads else 1e-7, "fp32": 2e-5 if not loads else 1e-4}[precision]
+        assert rel_l2(D, D_ref) < tol
+        assert abs(norms[0] - SD) < 10 * tol * SD and abs(norms[1] - SP) < tol * SP
+    finally:
+        gp.close()
