@@ -501,6 +501,8 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   }
   R.sy = p->sy;
   R.sz = p->sz;
+  R.nsy = p->sy;
+  R.nsz = p->sz;
   R.vy = p->n[0];
   R.vz = (long long)p->n[0] * p->n[1];
   for (int i = 0; i < 3; ++i)

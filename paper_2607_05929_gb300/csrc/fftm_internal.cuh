@@ -86,6 +86,7 @@ struct ResParams {
   T* state;          // null: no phase with internal variables
   int nst;           // state components per voxel point: 7 (J2) or 10 (crystal plasticity)
   const T* un[3];    // u^f at the last commit (high part in FP32)
+  long long nsy, nsz;  // node strides of un (the problem's layout; sy, sz may describe a caller's)
   const T* unlo[3];  // its low part (FP32 only)
   T dGs[9];          // gradient of the affine part of u* - u*_n
   int dquad;         // 1 if the quadratic part of u* - u*_n is non-zero

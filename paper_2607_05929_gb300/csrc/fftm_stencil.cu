@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
     const int vx = x0 + (threadIdx.x % RTX), vy_ = y0 + (threadIdx.x / RTX);
     if (vx < n1 && vy_ < n2) {
       T uh[3][8], ul[3][8];
-      int at[8];
+      int at[8], atn[8];
 #pragma unroll
       for (int o = 0; o < 8; ++o) {
         int gx = vx + (o & 1), gy = vy_ + ((o >> 1) & 1), gz = vz + (o >> 2);
@@ -666,6 +666,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
         if (P.periodic[1] && gy == n2) gy = 0;
         if (P.periodic[2] && gz == n3) gz = 0;
         at[o] = gx + gy * sy + gz * sz;
+        atn[o] = gx + gy * (int)P.nsy + gz * (int)P.nsz;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           uh[c][o] = __ldg(P.u[c] + at[o]);
@@ -677,14 +678,17 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
       const int law = __ldg(P.law_id + ph);
       const bool j2 = J2 && law == LAW_J2;
       const T* lc = P.law_c + (size_t)ph * LAWC;
-      if (j2) {  // J2 takes the increment since the commit
+      if (j2) {  // J2 takes the increment since the commit (u^f_n in the problem's own layout)
 #pragma unroll
-        for (int o = 0; o < 8; ++o)
+        for (int o = 0; o < 8; ++o) {
+          const int an = atn[o];
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
-            uh[c][o] -= __ldg(P.un[c] + at[o]);
-            if (LO) ul[c][o] -= __ldg(P.unlo[c] + at[o]);
+            uh[c][o] -= __ldg(P.un[c] + an);
+            if (LO) ul[c][o] -= __ldg(P.unlo[c] + an);
+            else if (P.unlo[c]) uh[c][o] -= __ldg(P.unlo[c] + an);  // a caller field without low part
           }
+        }
       }
       T spv = T(0);
 #pragma unroll
@@ -1039,10 +1043,436 @@ static void interior_and_faces(const ResParams<T>& P, TileIdx* ti, FaceIdx* fi) 
   }
 }
 
+// ---- the residual as one pass (small-strain elastic laws) -----------------------
+// k_residual_fused: a block marches a tile of FX x FY voxels (x, y) through a chunk of z
+// planes.  Per z step it (1) stores the next node plane of u^f (FX+1 x FY+1 nodes, hi and
+// lo parts) in shared memory, (2) evaluates the gradient and the law of its voxel layer
+// from the two node planes around it (the lower plane's corners stay in registers from the
+// previous step) and keeps the voxel-point stresses in shared memory, and (3) forms D at
+// the node plane between this voxel layer and the previous one, from the 8 voxels around
+// each node, as the same sums of neighbour differences as k_div (Remark 1).  The block's
+// voxel tile overlaps its neighbours' by one voxel in x and y so that the (FX-1) x (FY-1)
+// nodes it owns see all their voxels; the stresses never leave the SM.  Nodes on
+// non-periodic faces take the ghost rules in k_face_div, which reads the stresses of the
+// boundary voxel layers that this kernel stores to the voxel-point buffer.
+constexpr int FX = 32, FY = 8, FNX = FX + 1, FNY = FY + 1, FTHREADS = FX * FY;
+
+// u^f at a node in shared memory: (hi, lo) in FP32, the value in FP64
+template <typename T, bool LO> struct NodeV { using t = T; };
+template <> struct NodeV<float, true> { using t = float2; };
+__device__ __forceinline__ float nv_hi(float2 v) { return v.x; }
+__device__ __forceinline__ float nv_lo(float2 v) { return v.y; }
+__device__ __forceinline__ float nv_hi(float v) { return v; }
+__device__ __forceinline__ float nv_lo(float) { return 0.f; }
+__device__ __forceinline__ double nv_hi(double v) { return v; }
+__device__ __forceinline__ double nv_lo(double) { return 0.0; }
+
+// Work decomposition of the fused residual: per axis, the interior node range [a0, a1)
+// (every node on a periodic axis, [1, n) on a non-periodic one), tiles of FX-1 (x) and
+// FY-1 (y) nodes, chunks of zc node planes in z.
+struct FusedGeom {
+  int a0[3], a1[3];
+  int ntx, nty, nzc, zc;
+  int items;
+  int faces;  // 1 if some axis is non-periodic: boundary voxel layers go to the stress buffer
+};
+
+template <typename T>
+static FusedGeom fused_geom(const ResParams<T>& P) {
+  FusedGeom g;
+  for (int a = 0; a < 3; ++a) {
+    g.a0[a] = P.periodic[a] ? 0 : 1;
+    g.a1[a] = P.n[a];
+  }
+  g.ntx = (g.a1[0] - g.a0[0] + FX - 2) / (FX - 1);
+  g.nty = (g.a1[1] - g.a0[1] + FY - 2) / (FY - 1);
+  const int nz = g.a1[2] - g.a0[2];
+  const long long cols = (long long)g.ntx * g.nty;
+  // chunks of at least 16 planes, few enough that the blocks stay below ~4000
+  int zc = (int)((cols * nz + 3999) / 4000);
+  zc = zc < 16 ? 16 : zc;
+  zc = zc > nz ? nz : zc;
+  g.zc = zc > 0 ? zc : 1;
+  g.nzc = nz > 0 ? (nz + g.zc - 1) / g.zc : 0;
+  g.items = (int)(cols * g.nzc);
+  g.faces = !(P.periodic[0] && P.periodic[1] && P.periodic[2]);
+  return g;
+}
+
+// The first 24 coefficients of a phase's law row (isotropic: lambda, mu; cubic: the upper
+// triangle of the rotated Mandel stiffness, 21 entries), loaded together as vectors.
+template <typename T>
+__device__ __forceinline__ void load_law24(const T* __restrict__ lc, T c[24]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* v = reinterpret_cast<const float4*>(lc);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+      const float4 a = __ldg(v + i);
+      c[4 * i] = a.x; c[4 * i + 1] = a.y; c[4 * i + 2] = a.z; c[4 * i + 3] = a.w;
+    }
+  } else {
+    const double2* v = reinterpret_cast<const double2*>(lc);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const double2 a = __ldg(v + i);
+      c[2 * i] = a.x; c[2 * i + 1] = a.y;
+    }
+  }
+}
+
+// Small-strain elastic law from coefficients in registers: P as (11, 22, 33, 23, 13, 12).
+template <typename T>
+__device__ __forceinline__ void elastic_reg(int law, const T c[24], const T G[9], T s[6]) {
+  const T e00 = G[0], e11 = G[4], e22 = G[8];
+  const T e12 = T(0.5) * (G[5] + G[7]), e02 = T(0.5) * (G[2] + G[6]), e01 = T(0.5) * (G[1] + G[3]);
+  if (law == LAW_CUBIC) {
+    const T r2 = T(1.41421356237309504880), ir2 = T(0.70710678118654752440);
+    const T em[6] = {e00, e11, e22, r2 * e12, r2 * e02, r2 * e01};
+    T sm[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+      for (int b = a; b < 6; ++b) {
+        const T v = c[k++];
+        sm[a] += v * em[b];
+        if (b != a) sm[b] += v * em[a];
+      }
+    s[0] = sm[0]; s[1] = sm[1]; s[2] = sm[2];
+    s[3] = ir2 * sm[3]; s[4] = ir2 * sm[4]; s[5] = ir2 * sm[5];
+  } else {  // isotropic
+    const T mu2 = T(2) * c[1], tr = c[0] * (e00 + e11 + e22);
+    s[0] = tr + mu2 * e00; s[1] = tr + mu2 * e11; s[2] = tr + mu2 * e22;
+    s[3] = mu2 * e12; s[4] = mu2 * e02; s[5] = mu2 * e01;
+  }
+}
+
+template <typename T, int TETRA, bool LO>
+__global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, FusedGeom g) {
+  using NV = typename NodeV<T, LO>::t;
+  using T2 = typename V2<T>::t;
+  constexpr int NPP = TETRA ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char fsm[];
+  NV* su = reinterpret_cast<NV*>(fsm);                      // [2][3][FNY][FNX] node planes
+  T2* ss = reinterpret_cast<T2*>(su + 2 * 3 * FNY * FNX);   // [2][NPP][3][FY][FX] stress pairs
+  __shared__ double red[32];
+
+  const int tx = threadIdx.x % FX, ty = threadIdx.x / FX;
+  const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
+  const int N1 = P.N[0], N2 = P.N[1], N3 = P.N[2];
+  const long long nvox = (long long)n1 * n2 * n3;
+  const long long sy = P.sy, sz = P.sz;
+  const int item = blockIdx.x;
+  const int ix = item % g.ntx, iy = (item / g.ntx) % g.nty, iz = item / (g.ntx * g.nty);
+  const int X0 = g.a0[0] + ix * (FX - 1), Y0 = g.a0[1] + iy * (FY - 1);
+  const int Z0 = g.a0[2] + iz * g.zc, Z1 = min(Z0 + g.zc, g.a1[2]);
+  const int Xend = min(X0 + FX - 1, g.a1[0]), Yend = min(Y0 + FY - 1, g.a1[1]);
+
+  // this thread's voxel column (x, y) and node (x, y)
+  int vx = X0 - 1 + tx, vy = Y0 - 1 + ty;
+  const bool vin = (vx >= 0 || P.periodic[0]) && (vx < n1) && (vy >= 0 || P.periodic[1]) && (vy < n2);
+  if (vx < 0) vx += n1;
+  if (vy < 0) vy += n2;
+  const int mx = X0 - 1 + tx, my = Y0 - 1 + ty;
+  const bool node_out = tx >= 1 && ty >= 1 && mx < Xend && my < Yend;
+  // voxels this block counts in S_P and stores for the face kernel: the core [X0, Xend) of
+  // the tile, plus voxel 0 for the first tile of a non-periodic axis
+  const int ox_lo = X0 - ((ix == 0 && !P.periodic[0]) ? 1 : 0);
+  const int oy_lo = Y0 - ((iy == 0 && !P.periodic[1]) ? 1 : 0);
+  const bool own_xy = vin && mx >= ox_lo && mx < Xend && my >= oy_lo && my < Yend;
+  const bool xy_face = (!P.periodic[0] && (vx == 0 || vx == n1 - 1)) || (!P.periodic[1] && (vy == 0 || vy == n2 - 1));
+  const int phase_xy = vx + vy * (int)P.vy;
+
+  // the node slots this thread loads per plane: FNX x FNY nodes over FTHREADS threads
+  auto node_coord = [&](int slot, int* gx, int* gy) -> bool {
+    const int idx = threadIdx.x + slot * FTHREADS;
+    if (idx >= FNX * FNY) return false;
+    int x = X0 - 1 + idx % FNX, y = Y0 - 1 + idx / FNX;
+    if (x < 0) x += N1;  // only periodic axes reach x = -1 (non-periodic tiles start at X0 = 1)
+    if (y < 0) y += N2;
+    if (x >= N1) x -= N1;
+    if (y >= N2) y -= N2;
+    *gx = x;
+    *gy = y;
+    return true;
+  };
+  NV pre[2][3];
+  auto fetch_plane = [&](int z) {
+    if (z < 0) z += N3;
+    if (z >= N3) z -= N3;
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      int gx, gy;
+      if (node_coord(sl, &gx, &gy)) {
+        const long long at = gx + gy * sy + z * sz;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if constexpr (LO) pre[sl][c] = make_float2(__ldg(P.u[c] + at), __ldg(P.ulo[c] + at));
+          else pre[sl][c] = __ldg(P.u[c] + at);
+        }
+      }
+    }
+  };
+  auto store_plane = [&](int buf) {
+#pragma unroll
+    for (int sl = 0; sl < 2; ++sl) {
+      const int idx = threadIdx.x + sl * FTHREADS;
+      if (idx < FNX * FNY)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) su[(buf * 3 + c) * FNY * FNX + idx] = pre[sl][c];
+    }
+  };
+  // corners of the voxel (tx, ty): c = ox + 2 oy at the lower plane (lo) and upper plane
+  T ch[3][8], cl[3][8];
+  auto read_corners = [&](int buf, int oz) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const NV v = su[(buf * 3 + c) * FNY * FNX + (ty + (k >> 1)) * FNX + tx + (k & 1)];
+        ch[c][k + 4 * oz] = nv_hi(v);
+        cl[c][k + 4 * oz] = nv_lo(v);
+      }
+  };
+
+  T sp = T(0), sd = T(0);
+  double SP = 0.0, SD = 0.0;
+  int run = 0;
+
+  // phase of this thread's voxel in layer vz (prefetched one layer ahead)
+  auto phase_at = [&](int vz) -> int {
+    if (!vin) return 0;
+    if (vz < 0) vz += n3;
+    if (vz >= n3) return 0;
+    return P.phase[phase_xy + (long long)vz * P.vz];
+  };
+  // voxel layer vz from the corners in ch/cl: stresses into ss[buf], S_P, face layers
+  auto voxel_layer = [&](int vz, int buf, int ph) {
+    const bool zin = vz >= 0 && vz < n3;
+    const int vzz = vz < 0 ? vz + n3 : vz;
+    T Ps[NPP][6];
+#pragma unroll
+    for (int r = 0; r < NPP; ++r)
+#pragma unroll
+      for (int c = 0; c < 6; ++c) Ps[r][c] = T(0);
+    if (vin && (zin || P.periodic[2])) {
+      const int law = __ldg(P.law_id + ph);
+      T lc[24];
+      load_law24<T>(P.law_c + (size_t)ph * LAWC, lc);
+#pragma unroll
+      for (int r = 0; r < NPP; ++r) {
+        T Gf[9], Gt[9];
+        point_grad<T, TETRA, LO>(ch, cl, r, P.wgrad, Gf);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
+        if (P.quad) add_quad<T, TETRA>(P.hh, P.Qc, r, vx, vy, vzz, Gt);
+        elastic_reg<T>(law, lc, Gt, Ps[r]);
+      }
+      const bool own = own_xy && vz >= Z0 - (iz == 0 && !P.periodic[2] ? 1 : 0) && vz < Z1;
+      if (own) {
+        T spv = T(0);
+#pragma unroll
+        for (int r = 0; r < NPP; ++r)
+          spv += Ps[r][0] * Ps[r][0] + Ps[r][1] * Ps[r][1] + Ps[r][2] * Ps[r][2] +
+                 T(2) * (Ps[r][3] * Ps[r][3] + Ps[r][4] * Ps[r][4] + Ps[r][5] * Ps[r][5]);
+        sp += spv;
+        if (g.faces && (xy_face || (!P.periodic[2] && (vzz == 0 || vzz == n3 - 1)))) {
+          const long long v = phase_xy + (long long)vzz * P.vz;
+#pragma unroll
+          for (int r = 0; r < NPP; ++r) {
+            T* base = P.vs + (size_t)(r * 6) * nvox + v;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) base[c * nvox] = Ps[r][c];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NPP; ++r) {
+      T2* b = ss + (size_t)((buf * NPP + r) * 3) * FY * FX + ty * FX + tx;
+      T2 a0, a1, a2;
+      a0.x = Ps[r][0]; a0.y = Ps[r][1];  // 11, 22
+      a1.x = Ps[r][2]; a1.y = Ps[r][3];  // 33, 23
+      a2.x = Ps[r][4]; a2.y = Ps[r][5];  // 13, 12
+      b[0] = a0;
+      b[FY * FX] = a1;
+      b[2 * FY * FX] = a2;
+    }
+  };
+
+  // prologue: node planes Z0 - 1 and Z0, voxel layer Z0 - 1
+  int ph_next = phase_at(Z0 - 1);
+  fetch_plane(Z0 - 1);
+  store_plane(0);
+  fetch_plane(Z0);
+  store_plane(1);
+  __syncthreads();
+  read_corners(0, 0);
+  read_corners(1, 1);
+  __syncthreads();  // buffer 0 is refilled by the first step
+  {
+    const int ph = ph_next;
+    ph_next = phase_at(Z0);
+    voxel_layer(Z0 - 1, 0, ph);
+  }
+  if (Z0 + 1 <= Z1) fetch_plane(Z0 + 1);
+  for (int z = Z0; z < Z1; ++z) {
+    const int k = z - Z0;
+    // node plane z + 1 goes to buffer k & 1 (it held plane z - 1, read two barriers ago)
+    store_plane(k & 1);
+    // the lower corners of voxel layer z are the upper ones of layer z - 1
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ch[c][q] = ch[c][q + 4];
+        cl[c][q] = cl[c][q + 4];
+      }
+    __syncthreads();
+    if (z + 2 <= Z1) fetch_plane(z + 2);  // in flight during this layer
+    const int ph = ph_next;
+    if (z + 1 < Z1) ph_next = phase_at(z + 1);
+    read_corners(k & 1, 1);
+    voxel_layer(z, (k + 1) & 1, ph);
+    __syncthreads();
+    // D at node plane z from voxel layers z - 1 (buffer k & 1) and z (buffer (k + 1) & 1)
+    if (node_out) {
+      T val[8][6];
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+        const int r = TETRA ? ((((ox + oy + oz) & 1) != 0) ? 0 : 1) : 0;
+        const int buf = oz ? ((k + 1) & 1) : (k & 1);
+        const T2* b = ss + (size_t)((buf * NPP + r) * 3) * FY * FX + (ty - 1 + oy) * FX + (tx - 1 + ox);
+        const T2 a0 = b[0], a1 = b[FY * FX], a2 = b[2 * FY * FX];
+        val[o][0] = a0.x; val[o][1] = a0.y; val[o][2] = a1.x;
+        val[o][3] = a1.y; val[o][4] = a2.x; val[o][5] = a2.y;
+      }
+      T Dq[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          const int c = sym_index(i, q);
+          T s = T(0);
+#pragma unroll
+          for (int o = 0; o < 8; ++o) {
+            if ((o >> i) & 1) continue;
+            s += val[o | (1 << i)][c] - val[o][c];
+          }
+          Dq[q] += P.wdiv[i] * s;
+        }
+      const long long off = mx + my * sy + z * sz;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        P.D[q][off] = Dq[q];  // interior nodes transform every component (Table 1 ranges)
+        sd += Dq[q] * Dq[q];
+      }
+    }
+    if (++run == 16) {
+      SP += (double)sp;
+      SD += (double)sd;
+      sp = sd = T(0);
+      run = 0;
+    }
+  }
+  SP += (double)sp;
+  SD += (double)sd;
+  const double tsp = block_sum(SP, red);
+  const double tsd = block_sum(SD, red);
+  if (threadIdx.x == 0) {
+    P.partial[2 * blockIdx.x] = tsd;
+    P.partial[2 * blockIdx.x + 1] = tsp / NPP;
+  }
+}
+
+// Nodes on non-periodic faces (each once), with the ghost rules, from the boundary voxel
+// layers that k_residual_fused stored; one S_D partial per block (S_P slot zero).
+template <typename T, int TETRA>
+__global__ void __launch_bounds__(256) k_face_div(ResParams<T> P, FaceIdx fi) {
+  __shared__ double red[32];
+  double SD = 0.0;
+  int nface[3] = {P.n[0], P.n[1], P.n[2]};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < fi.count; t += gridDim.x * blockDim.x) {
+    int m[3];
+    if (!fi.at(t, nface, m)) continue;
+    T Dq[3] = {T(0), T(0), T(0)}, pq[3] = {T(0), T(0), T(0)};
+    node_div_general<T, TETRA, false, true>(P, m[0], m[1], m[2], Dq, pq);
+    SD += (double)store_node<T, false, false>(P, m[0], m[1], m[2], Dq, pq);
+  }
+  const double tot = block_sum(SD, red);
+  if (threadIdx.x == 0) {
+    P.partial[2 * blockIdx.x] = tot;
+    P.partial[2 * blockIdx.x + 1] = 0.0;
+  }
+}
+
+constexpr int kFaceBlocks = 152 * 2;
+
+template <typename T>
+static size_t fused_smem(int tetra) {
+  using NVs = typename NodeV<T, true>::t;  // same size as the FP64 node value
+  return (size_t)2 * 3 * FNY * FNX * sizeof(NVs) + (size_t)2 * (tetra ? 2 : 1) * 3 * FY * FX * 2 * sizeof(T);
+}
+
+// The fused path serves the solver's residual for problems whose every law is a
+// small-strain elastic one (isotropic or cubic: symmetric P, no internal variables), in the
+// plain (non-incremental) form without the test outputs.
+template <typename T>
+static bool fused_ok(const ResParams<T>& P, bool with_p) {
+  return !with_p && !P.inc && P.nst == 0 && P.sym && P.state == nullptr;
+}
+
+template <typename T>
+static int fused_blocks(const ResParams<T>& P) {
+  const FusedGeom g = fused_geom(P);
+  return g.items + (g.faces ? kFaceBlocks : 0);
+}
+
+template <typename T, int TETRA>
+static cudaError_t launch_fused_t(const ResParams<T>& P, cudaStream_t s, int* blocks_out) {
+  const FusedGeom g = fused_geom(P);
+  const bool lo = P.ulo[0] != nullptr;
+  const size_t smem = fused_smem<T>(TETRA);
+  if (g.items > 0) {
+    cudaError_t e = cudaSuccess;
+    if (lo) {
+      if constexpr (sizeof(T) == 4) {  // FP32 with a low part (the solver's fields)
+        auto kern = k_residual_fused<T, TETRA, true>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) kern<<<g.items, FTHREADS, smem, s>>>(P, g);
+      } else {
+        return cudaErrorInvalidValue;  // FP64 fields carry no low part
+      }
+    } else {
+      auto kern = k_residual_fused<T, TETRA, false>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) kern<<<g.items, FTHREADS, smem, s>>>(P, g);
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  int blocks = g.items;
+  if (g.faces) {
+    TileIdx tn;
+    FaceIdx fi;
+    interior_and_faces<T>(P, &tn, &fi);
+    ResParams<T> Pf = P;
+    Pf.partial = P.partial + 2 * (size_t)g.items;
+    k_face_div<T, TETRA><<<kFaceBlocks, 256, 0, s>>>(Pf, fi);
+    blocks += kFaceBlocks;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (blocks_out) *blocks_out = blocks;
+  return cudaSuccess;
+}
+
 template <typename T>
 int residual_blocks(const ResParams<T>& P, int tetra) {
   (void)tetra;
-  return RBLOCKS;
+  return fused_ok(P, false) ? fused_blocks(P) : RBLOCKS;
 }
 
 template <typename T, int TETRA, bool WITH_P, bool SYM>
@@ -1084,6 +1514,8 @@ static cudaError_t launch_res_s(const ResParams<T>& P, bool with_p, cudaStream_t
 
 template <typename T>
 cudaError_t launch_residual(const ResParams<T>& P, int tetra, bool with_p, cudaStream_t s, int* blocks_out) {
+  if (fused_ok(P, with_p))
+    return tetra ? launch_fused_t<T, 1>(P, s, blocks_out) : launch_fused_t<T, 0>(P, s, blocks_out);
   return tetra ? launch_res_s<T, 1>(P, with_p, s, blocks_out) : launch_res_s<T, 0>(P, with_p, s, blocks_out);
 }
 

@@ -156,6 +156,8 @@ RES_CASES = [
     ((36, 12, 9), [[["D", "N", "D"], ["N", "D", "D"]], [["P"] * 3] * 2, [["D", "N", "N"], ["N", "N", "D"]]], "HEX1"),
     ((16, 16, 16), axis_bc("P", "P", "P"), "TETRA2"),
     ((48, 36, 8), axis_bc("N", "D", "N"), "HEX1"),
+    ((96, 24, 36), axis_bc("P", "D", "N"), "TETRA2"),
+    ((72, 48, 36), axis_bc("D", "P", "P"), "HEX1"),
 ]
 
 
@@ -196,6 +198,41 @@ def test_residual_p_D_and_norms(precision, case):
         Gg = gp.get_voxel(F.FFTM_FIELD_GRAD)
         assert rel_l2(Pg, sym6(P_ref)) < TOL[precision]
         assert rel_l2(Gg, G_ref.reshape(G_ref.shape[0], 9, *G_ref.shape[3:])) < TOL[precision]
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", range(len(RES_CASES)))
+def test_solver_residual_D_and_norms(precision, case):
+    """The residual kernels the solver runs for elastic laws (gradient, law and divergence in
+    one pass; face nodes with the ghost rules), reached through fftm_residual_noalloc on
+    caller buffers, against the oracle's D and norms for every BC family of RES_CASES."""
+    torch = pytest.importorskip("torch")
+    from abi_helpers import node_from_abi, node_to_abi
+
+    n, bc, scheme = RES_CASES[case]
+    wl = _cubic_wl(n, bc, scheme)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, precision)
+    try:
+        rng = np.random.default_rng(case + 30)
+        u = 1e-3 * rng.standard_normal(pr.grid.node_shape)
+        for q in range(3):
+            u[q][~pr.grid.dof_mask(q)] = 0.0
+        _, D_ref, _, _, SD, SP = pr.residual(u, pr.grad_ustar())
+        tdt = torch.float64 if precision == "fp64" else torch.float32
+        u_dev = torch.from_numpy(node_to_abi(u).astype(gp.dtype)).cuda()
+        D_dev = torch.full(u_dev.shape, float("nan"), dtype=tdt, device="cuda")
+        norms = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+        F.fftm_residual_noalloc(gp.p, u_dev, D_dev, norms)
+        torch.cuda.synchronize()
+        D = node_from_abi(D_dev.cpu().numpy()).astype(np.float64)
+        nm = norms.cpu().numpy()
+        assert np.isfinite(D).all()
+        assert rel_l2(D, D_ref) < TOL[precision]
+        assert abs(nm[0] - SD) < 10 * TOL[precision] * SD
+        assert abs(nm[1] - SP) < TOL[precision] * SP
     finally:
         gp.close()
 
