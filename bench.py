@@ -402,7 +402,8 @@ def gpu_arm(args):
                        "iterations_per_step": iters, "anderson_steps_per_step": last["n_accelerated"],
                        "l2": "inputs larger than L2 (working set several GB; no flush needed)",
                        "parallelism": f"replicas x{dist.world}"},
-            "roofline": roofline, "gpu_launches": launches, "clocks": clk}
+            "roofline": roofline, "gpu_launches": launches, "clocks": clk,
+            "tuning": [t for t in F.fftm_tuning_table().splitlines() if t]}
 
     # ---- FP64 path beside it (same workload, device-resident) ----
     if args.fp64_steps > 0 and args.precision != "fp64":

@@ -237,6 +237,23 @@ enum fftm_field {
 /* Bytes of a field (dense layout above, problem precision). */
 int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
 
+/* Options of a problem (fftm_set_option):
+   FFTM_OPT_RESIDUAL_PASSES  how the solver evaluates the residual (rows a1-a4) of problems
+                             whose laws are all small-strain elastic: 1 = one pass over the
+                             grid (gradient, law and divergence fused, the voxel-point stresses
+                             kept on chip), 2 = two passes (stresses stored, then the
+                             divergence), 0 (default) = whichever the library measured faster
+                             for this grid shape on this GPU (timed once per shape and process;
+                             fftm_tuning_table lists the choices).  Both forms give the same D;
+                             problems with other laws always take two passes. */
+enum fftm_option { FFTM_OPT_RESIDUAL_PASSES = 0 };
+int fftm_set_option(fftm_problem* p, int option, int value);
+
+/* The launch-shape choices the library has measured in this process, one line per shape
+   ("key: choice (times)").  buf (HOST, may be NULL) receives up to len - 1 characters and a
+   terminating 0; *needed (may be NULL) the size the whole table needs. */
+int fftm_tuning_table(char* buf, size_t len, size_t* needed);
+
 /* Node dimensions N[3] of the problem's node fields (N_a = n_a + 1 on a non-periodic
    axis, n_a on a periodic one; Sec. 2.1), its precision (enum fftm_precision) and its
    CUDA device, so a caller can size, type and place the device buffers it passes to the

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <math_constants.h>
 
+#include <map>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -249,6 +250,7 @@ struct fftm_problem {
   uint16_t* phase = nullptr;
   int* law_id = nullptr;
   void* law_c = nullptr;
+  void* law_m = nullptr;  // elastic phases: the 6x6 Mandel stiffness in (2 x 2)-pair order, 36 per phase
   double* partial = nullptr;
   size_t partial_len = 0;
   double* dscal = nullptr;  // [0..1] norms, [2..9] anderson coef, [16..] stats
@@ -281,6 +283,8 @@ struct fftm_problem {
   size_t off_perm[3][3], off_tw[3][3], off_qw[3][3], off_S2[3][3], off_C2[3][3];
   int maxM[3], maxL[3];
   int cur = 0;  // ring slot holding the current u^f
+  int res_passes = 0;     // requested residual form: 0 tuned, 1 one pass, 2 two passes
+  int res_two_pass = -1;  // resolved form (-1: not yet)
   // per-kernel timing (fftm_set_profiling)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -492,6 +496,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   R.phase = p->phase;
   R.law_id = p->law_id;
   R.law_c = reinterpret_cast<const T*>(p->law_c);
+  R.law_m = reinterpret_cast<const T*>(p->law_m);
   for (int a = 0; a < 3; ++a) {
     R.n[a] = p->n[a];
     R.N[a] = p->N[a];
@@ -518,6 +523,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
       R.hi[q][a] = p->hi[q][a];
     }
   R.partial = p->partial;
+  R.two_pass = p->res_two_pass > 0 ? 1 : 0;
   R.vs = reinterpret_cast<T*>(p->vs);
   R.sym = p->sym;
   R.state = reinterpret_cast<T*>(p->state);
@@ -568,9 +574,92 @@ ResParams<T> commit_params(fftm_problem* p) {
   return R;
 }
 
+// ---- launch-shape tuning ----------------------------------------------------------------
+// Where a row of the path has several implementations with the same per-element arithmetic,
+// the library times them on the problem's own data the first time a problem of that shape
+// runs, keeps the fastest, and records the choice in a process-wide table keyed by the shape
+// (fftm_tuning_table prints it).
+std::mutex g_tune_mu;
+std::map<std::string, std::string> g_tune_table;  // key -> "choice (times)"
+std::map<std::string, int> g_tune_choice;
+
+std::string residual_key(const fftm_problem* p) {
+  char b[160];
+  std::snprintf(b, sizeof(b), "residual %s %s %dx%dx%d %c%c%c", p->esz == 8 ? "fp64" : "fp32",
+                p->tetra ? "TETRA2" : "HEX1", p->n[0], p->n[1], p->n[2], p->periodic[0] ? 'P' : 'B',
+                p->periodic[1] ? 'P' : 'B', p->periodic[2] ? 'P' : 'B');
+  return b;
+}
+
+// Milliseconds per launch of the residual in the given form (3 launches after one warm-up).
+template <typename T>
+double time_residual(fftm_problem* p, int slot, int two_pass) {
+  ResParams<T> R = res_params<T>(p, slot, nullptr, nullptr);
+  R.two_pass = two_pass;
+  cudaStream_t s = p->ctx->stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return -1.0;
+  }
+  double ms = -1.0;
+  if (launch_residual<T>(R, p->tetra, false, s, nullptr) == cudaSuccess) {
+    cudaEventRecord(e0, s);
+    bool ok = true;
+    for (int i = 0; i < 3 && ok; ++i) ok = launch_residual<T>(R, p->tetra, false, s, nullptr) == cudaSuccess;
+    cudaEventRecord(e1, s);
+    float t = 0.f;
+    if (ok && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+      ms = t / 3.0;
+  }
+  p->launches += 8;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+template <typename T>
+int resolve_residual_form(fftm_problem* p, int slot) {
+  if (p->res_passes == 1 || p->res_passes == 2) {
+    p->res_two_pass = p->res_passes == 2 ? 1 : 0;
+    return FFTM_OK;
+  }
+  ResParams<T> R = res_params<T>(p, slot, nullptr, nullptr);
+  if (!residual_one_pass<T>(R)) {
+    p->res_two_pass = 1;
+    return FFTM_OK;
+  }
+  const std::string key = residual_key(p);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_choice.find(key);
+    if (it != g_tune_choice.end()) {
+      p->res_two_pass = it->second;
+      return FFTM_OK;
+    }
+  }
+  const double t1 = time_residual<T>(p, slot, 0), t2 = time_residual<T>(p, slot, 1);
+  CU(cudaGetLastError());
+  const int two = (t1 < 0.0 || (t2 >= 0.0 && t2 < t1)) ? 1 : 0;
+  char b[160];
+  std::snprintf(b, sizeof(b), "%s (one pass %.4f ms, two passes %.4f ms)", two ? "two passes" : "one pass", t1, t2);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_choice[key] = two;
+    g_tune_table[key] = b;
+  }
+  p->res_two_pass = two;
+  return FFTM_OK;
+}
+
 // a1-a4: D (into the D slot of `slot`, or the test buffers) and the two norms.
 template <typename T>
 int run_residual(fftm_problem* p, int slot, bool test_outputs) {
+  if (!test_outputs && p->res_two_pass < 0) {
+    int rc = resolve_residual_form<T>(p, slot);
+    if (rc) return rc;
+  }
   T* D = nullptr;
   T* pp = nullptr;
   if (test_outputs) {
@@ -1038,6 +1127,7 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->phase);
   cudaFree(p->law_id);
   cudaFree(p->law_c);
+  cudaFree(p->law_m);
   cudaFree(p->partial);
   cudaFree(p->dscal);
   cudaFree(p->dint);
@@ -1259,6 +1349,38 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
       c[1] = m.params[1];
     }
   }
+  // the small-strain elastic phases' Mandel stiffness for the one-pass residual: float4 k = 3 bp + rp
+  // holds (C[2rp][2bp], C[2rp+1][2bp], C[2rp][2bp+1], C[2rp+1][2bp+1]) (isotropic: lambda 1 (x) 1 + 2 mu I)
+  std::vector<double> lm((size_t)desc->n_phases * 36, 0.0);
+  for (int i = 0; i < desc->n_phases; ++i) {
+    const fftm_material& m = desc->materials[i];
+    double Cm[6][6] = {};
+    if (m.law == FFTM_LAW_CUBIC_ELASTIC) {
+      double R[3][3];
+      quat_rot(m.quat, R);
+      cubic_mandel(m.params[0], m.params[1], m.params[2], R, Cm);
+    } else if (m.law == FFTM_LAW_ISO_ELASTIC) {
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Cm[a][b] = m.params[0];
+      for (int a = 0; a < 6; ++a) Cm[a][a] += 2.0 * m.params[1];
+    }
+    double* c = &lm[(size_t)i * 36];
+    for (int bp = 0; bp < 3; ++bp)
+      for (int rp = 0; rp < 3; ++rp) {
+        double* f = c + 4 * (3 * bp + rp);
+        f[0] = Cm[2 * rp][2 * bp];
+        f[1] = Cm[2 * rp + 1][2 * bp];
+        f[2] = Cm[2 * rp][2 * bp + 1];
+        f[3] = Cm[2 * rp + 1][2 * bp + 1];
+      }
+  }
+  CU(cudaMalloc(&p->law_m, lm.size() * p->esz));
+  if (p->esz == 8) {
+    CU(cudaMemcpy(p->law_m, lm.data(), lm.size() * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> lf(lm.begin(), lm.end());
+    CU(cudaMemcpy(p->law_m, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
+  }
   CU(cudaMalloc(&p->law_id, lid.size() * sizeof(int)));
   CU(cudaMemcpy(p->law_id, lid.data(), lid.size() * sizeof(int), cudaMemcpyHostToDevice));
   CU(cudaMalloc(&p->law_c, lc.size() * p->esz));
@@ -1379,6 +1501,33 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes) {
       return FFTM_OK;
     default: return set_err(FFTM_E_INVALID, "unknown field");
   }
+}
+
+int fftm_set_option(fftm_problem* p, int option, int value) {
+  if (!p) return set_err(FFTM_E_INVALID, "null problem");
+  switch (option) {
+    case FFTM_OPT_RESIDUAL_PASSES:
+      if (value < 0 || value > 2) return set_err(FFTM_E_INVALID, "residual passes: 0 (tuned), 1 or 2");
+      p->res_passes = value;
+      p->res_two_pass = value == 0 ? -1 : (value == 2 ? 1 : 0);
+      return FFTM_OK;
+    default: return set_err(FFTM_E_INVALID, "unknown option");
+  }
+}
+
+int fftm_tuning_table(char* buf, size_t len, size_t* needed) {
+  std::string out;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& kv : g_tune_table) out += kv.first + ": " + kv.second + "\n";
+  }
+  if (needed) *needed = out.size() + 1;
+  if (buf && len > 0) {
+    const size_t n = out.size() < len - 1 ? out.size() : len - 1;
+    std::memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return FFTM_OK;
 }
 
 int fftm_problem_layout(const fftm_problem* p, int N[3], int* precision, int* device) {

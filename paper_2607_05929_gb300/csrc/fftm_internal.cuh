@@ -72,6 +72,7 @@ struct ResParams {
   const uint16_t* phase;
   const int* law_id;  // per phase
   const T* law_c;     // per phase, LAWC coefficients
+  const T* law_m;     // per phase, the elastic Mandel stiffness as 9 (2 x 2) blocks (36 entries)
   int n[3], N[3];
   int periodic[3];
   long long sy, sz;  // node strides (x stride 1)
@@ -108,6 +109,7 @@ struct ResParams {
   T tr[3][2][3];
   T* vs;             // voxel-point stress buffer [r][c][voxel] (c < NC, see fftm_stencil.cu)
   int sym;           // 1: every law gives a symmetric P (6 stored components)
+  int two_pass;      // 1: evaluate the residual as two grid passes even where one pass serves
   double* partial;   // per block: S_D, S_P
 };
 
@@ -176,6 +178,10 @@ template <typename T>
 cudaError_t launch_residual(const ResParams<T>& P, int tetra, bool with_p, cudaStream_t s, int* blocks_out);
 template <typename T>
 int residual_blocks(const ResParams<T>& P, int tetra);
+// Whether the residual of these parameters has the one-pass form (small-strain elastic laws,
+// plain form) besides the two-pass one.
+template <typename T>
+bool residual_one_pass(const ResParams<T>& P);
 template <typename T>
 cudaError_t launch_green(const GreenParams<T>& P, cudaStream_t s);
 // a9: recompute the return (J2, crystal plasticity) at every voxel point from the

@@ -1147,14 +1147,93 @@ __device__ __forceinline__ void elastic_reg(int law, const T c[24], const T G[9]
   }
 }
 
+// Gradient at point r from the corner values of the lower (L, corners o < 4) and upper
+// (U, corners o >= 4) node planes, as point_grad forms it.  The FP32 variant takes (hi, lo)
+// pairs and uses packed FP32x2 arithmetic (one instruction per pair) with the same
+// differences, sums and rounding.
+template <int TETRA>
+__device__ __forceinline__ void grad_lu_f2(const float2 L[3][4], const float2 U[3][4], int r, const float* wg,
+                                           float G[9]) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int mask = TETRA ? ((1 << i) | (1 << ((i + 1) % 3))) : (1 << i);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float2 s = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        if ((o >> i) & 1) continue;
+        const int par = ((o & 1) + ((o >> 1) & 1) + ((o >> 2) & 1)) & 1;
+        if (TETRA && ((r == 0) != (par == 0))) continue;
+        const int o2 = o ^ mask;
+        const float2 a = o < 4 ? L[q][o] : U[q][o - 4];
+        const float2 b = o2 < 4 ? L[q][o2] : U[q][o2 - 4];
+        s = __fadd2_rn(s, __ffma2_rn(a, m1, b));  // + (u(o ^ mask) - u(o))
+      }
+      G[i * 3 + q] = wg[i] * (s.x + s.y);
+    }
+  }
+}
+
+template <typename T, int TETRA>
+__device__ __forceinline__ void grad_lu(const T L[3][4], const T U[3][4], int r, const T* wg, T G[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int mask = TETRA ? ((1 << i) | (1 << ((i + 1) % 3))) : (1 << i);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      T s = T(0);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) {
+        if ((o >> i) & 1) continue;
+        const int par = ((o & 1) + ((o >> 1) & 1) + ((o >> 2) & 1)) & 1;
+        if (TETRA && ((r == 0) != (par == 0))) continue;
+        const int o2 = o ^ mask;
+        s += (o2 < 4 ? L[q][o2] : U[q][o2 - 4]) - (o < 4 ? L[q][o] : U[q][o - 4]);
+      }
+      G[i * 3 + q] = wg[i] * s;
+    }
+  }
+}
+
+// Small-strain elastic law with the phase's full Mandel stiffness (9 blocks of 2 x 2, see
+// ResParams::law_m) and packed FP32x2 products: P as (11, 22, 33, 23, 13, 12).
+__device__ __forceinline__ void elastic_f2(const float4* __restrict__ M4, const float G[9], float s[6]) {
+  const float r2 = 1.41421356237309504880f, ir2 = 0.70710678118654752440f;
+  const float em[6] = {G[0], G[4], G[8], r2 * (0.5f * (G[5] + G[7])), r2 * (0.5f * (G[2] + G[6])),
+                       r2 * (0.5f * (G[1] + G[3]))};
+  float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+  for (int bp = 0; bp < 3; ++bp) {
+    const float2 e0 = make_float2(em[2 * bp], em[2 * bp]), e1 = make_float2(em[2 * bp + 1], em[2 * bp + 1]);
+#pragma unroll
+    for (int rp = 0; rp < 3; ++rp) {
+      const float4 c = __ldg(M4 + 3 * bp + rp);
+      acc[rp] = __ffma2_rn(make_float2(c.x, c.y), e0, acc[rp]);
+      acc[rp] = __ffma2_rn(make_float2(c.z, c.w), e1, acc[rp]);
+    }
+  }
+  s[0] = acc[0].x;
+  s[1] = acc[0].y;
+  s[2] = acc[1].x;
+  s[3] = ir2 * acc[1].y;
+  s[4] = ir2 * acc[2].x;
+  s[5] = ir2 * acc[2].y;
+}
+
+template <int V> struct Par { static constexpr int value = V; };
+
 template <typename T, int TETRA, bool LO>
 __global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, FusedGeom g) {
   using NV = typename NodeV<T, LO>::t;
   using T2 = typename V2<T>::t;
   constexpr int NPP = TETRA ? 2 : 1;
+  constexpr int PL = FNY * FNX;    // one component of one node plane
+  constexpr int SL = FY * FX;      // one stress pair of one point of one voxel layer
   extern __shared__ __align__(16) unsigned char fsm[];
   NV* su = reinterpret_cast<NV*>(fsm);                      // [2][3][FNY][FNX] node planes
-  T2* ss = reinterpret_cast<T2*>(su + 2 * 3 * FNY * FNX);   // [2][NPP][3][FY][FX] stress pairs
+  T2* ss = reinterpret_cast<T2*>(su + 2 * 3 * PL);          // [2][NPP][3][FY][FX] stress pairs
   __shared__ double red[32];
 
   const int tx = threadIdx.x % FX, ty = threadIdx.x / FX;
@@ -1182,29 +1261,32 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, 
   const bool own_xy = vin && mx >= ox_lo && mx < Xend && my >= oy_lo && my < Yend;
   const bool xy_face = (!P.periodic[0] && (vx == 0 || vx == n1 - 1)) || (!P.periodic[1] && (vy == 0 || vy == n2 - 1));
   const int phase_xy = vx + vy * (int)P.vy;
+  const int own_z0 = Z0 - (iz == 0 && !P.periodic[2] ? 1 : 0);
+  const long long node_xy = node_out ? mx + my * sy : 0;
 
   // the node slots this thread loads per plane: FNX x FNY nodes over FTHREADS threads
-  auto node_coord = [&](int slot, int* gx, int* gy) -> bool {
-    const int idx = threadIdx.x + slot * FTHREADS;
-    if (idx >= FNX * FNY) return false;
+  long long gxy[2];
+  bool gok[2];
+#pragma unroll
+  for (int sl = 0; sl < 2; ++sl) {
+    const int idx = threadIdx.x + sl * FTHREADS;
+    gok[sl] = idx < PL;
     int x = X0 - 1 + idx % FNX, y = Y0 - 1 + idx / FNX;
-    if (x < 0) x += N1;  // only periodic axes reach x = -1 (non-periodic tiles start at X0 = 1)
+    if (x < 0) x += N1;  // only periodic axes reach -1 (non-periodic tiles start at 1)
     if (y < 0) y += N2;
     if (x >= N1) x -= N1;
     if (y >= N2) y -= N2;
-    *gx = x;
-    *gy = y;
-    return true;
-  };
+    gxy[sl] = gok[sl] ? x + y * sy : 0;
+  }
   NV pre[2][3];
   auto fetch_plane = [&](int z) {
     if (z < 0) z += N3;
     if (z >= N3) z -= N3;
+    const long long zo = z * sz;
 #pragma unroll
     for (int sl = 0; sl < 2; ++sl) {
-      int gx, gy;
-      if (node_coord(sl, &gx, &gy)) {
-        const long long at = gx + gy * sy + z * sz;
+      if (gok[sl]) {
+        const long long at = gxy[sl] + zo;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if constexpr (LO) pre[sl][c] = make_float2(__ldg(P.u[c] + at), __ldg(P.ulo[c] + at));
@@ -1213,26 +1295,21 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, 
       }
     }
   };
-  auto store_plane = [&](int buf) {
+  auto store_plane = [&](auto par) {
+    constexpr int b = decltype(par)::value;
 #pragma unroll
-    for (int sl = 0; sl < 2; ++sl) {
-      const int idx = threadIdx.x + sl * FTHREADS;
-      if (idx < FNX * FNY)
+    for (int sl = 0; sl < 2; ++sl)
+      if (gok[sl])
 #pragma unroll
-        for (int c = 0; c < 3; ++c) su[(buf * 3 + c) * FNY * FNX + idx] = pre[sl][c];
-    }
+        for (int c = 0; c < 3; ++c) su[(b * 3 + c) * PL + threadIdx.x + sl * FTHREADS] = pre[sl][c];
   };
-  // corners of the voxel (tx, ty): c = ox + 2 oy at the lower plane (lo) and upper plane
-  T ch[3][8], cl[3][8];
-  auto read_corners = [&](int buf, int oz) {
+  NV* const su_me = su + ty * FNX + tx;
+  auto read4 = [&](auto par, NV (&cv)[3][4]) {
+    constexpr int b = decltype(par)::value;
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const NV v = su[(buf * 3 + c) * FNY * FNX + (ty + (k >> 1)) * FNX + tx + (k & 1)];
-        ch[c][k + 4 * oz] = nv_hi(v);
-        cl[c][k + 4 * oz] = nv_lo(v);
-      }
+      for (int k = 0; k < 4; ++k) cv[c][k] = su_me[(b * 3 + c) * PL + (k >> 1) * FNX + (k & 1)];
   };
 
   T sp = T(0), sd = T(0);
@@ -1246,8 +1323,11 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, 
     if (vz >= n3) return 0;
     return P.phase[phase_xy + (long long)vz * P.vz];
   };
-  // voxel layer vz from the corners in ch/cl: stresses into ss[buf], S_P, face layers
-  auto voxel_layer = [&](int vz, int buf, int ph) {
+  T2* const ss_me = ss + ty * FX + tx;
+  // voxel layer vz from the corner planes L (lower) and U (upper): stresses into stress
+  // buffer b, S_P, boundary layers to the stress buffer of the face kernel
+  auto voxel_layer = [&](auto par, int vz, int ph, const NV (&L)[3][4], const NV (&U)[3][4]) {
+    constexpr int b = decltype(par)::value;
     const bool zin = vz >= 0 && vz < n3;
     const int vzz = vz < 0 ? vz + n3 : vz;
     T Ps[NPP][6];
@@ -1256,20 +1336,32 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, 
 #pragma unroll
       for (int c = 0; c < 6; ++c) Ps[r][c] = T(0);
     if (vin && (zin || P.periodic[2])) {
-      const int law = __ldg(P.law_id + ph);
-      T lc[24];
-      load_law24<T>(P.law_c + (size_t)ph * LAWC, lc);
+      if constexpr (LO) {  // FP32 hi + lo fields: packed FP32x2 gradient and law
+        const float4* M4 = reinterpret_cast<const float4*>(P.law_m + (size_t)ph * 36);
 #pragma unroll
-      for (int r = 0; r < NPP; ++r) {
-        T Gf[9], Gt[9];
-        point_grad<T, TETRA, LO>(ch, cl, r, P.wgrad, Gf);
+        for (int r = 0; r < NPP; ++r) {
+          float Gf[9], Gt[9];
+          grad_lu_f2<TETRA>(L, U, r, P.wgrad, Gf);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
-        if (P.quad) add_quad<T, TETRA>(P.hh, P.Qc, r, vx, vy, vzz, Gt);
-        elastic_reg<T>(law, lc, Gt, Ps[r]);
+          for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
+          if (P.quad) add_quad<T, TETRA>(P.hh, P.Qc, r, vx, vy, vzz, Gt);
+          elastic_f2(M4, Gt, Ps[r]);
+        }
+      } else {
+        const int law = __ldg(P.law_id + ph);
+        T lc[24];
+        load_law24<T>(P.law_c + (size_t)ph * LAWC, lc);
+#pragma unroll
+        for (int r = 0; r < NPP; ++r) {
+          T Gf[9], Gt[9];
+          grad_lu<T, TETRA>(L, U, r, P.wgrad, Gf);
+#pragma unroll
+          for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
+          if (P.quad) add_quad<T, TETRA>(P.hh, P.Qc, r, vx, vy, vzz, Gt);
+          elastic_reg<T>(law, lc, Gt, Ps[r]);
+        }
       }
-      const bool own = own_xy && vz >= Z0 - (iz == 0 && !P.periodic[2] ? 1 : 0) && vz < Z1;
-      if (own) {
+      if (own_xy && vz >= own_z0 && vz < Z1) {
         T spv = T(0);
 #pragma unroll
         for (int r = 0; r < NPP; ++r)
@@ -1289,92 +1381,95 @@ __global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, 
     }
 #pragma unroll
     for (int r = 0; r < NPP; ++r) {
-      T2* b = ss + (size_t)((buf * NPP + r) * 3) * FY * FX + ty * FX + tx;
       T2 a0, a1, a2;
       a0.x = Ps[r][0]; a0.y = Ps[r][1];  // 11, 22
       a1.x = Ps[r][2]; a1.y = Ps[r][3];  // 33, 23
       a2.x = Ps[r][4]; a2.y = Ps[r][5];  // 13, 12
-      b[0] = a0;
-      b[FY * FX] = a1;
-      b[2 * FY * FX] = a2;
+      ss_me[((b * NPP + r) * 3 + 0) * SL] = a0;
+      ss_me[((b * NPP + r) * 3 + 1) * SL] = a1;
+      ss_me[((b * NPP + r) * 3 + 2) * SL] = a2;
+    }
+  };
+  const T2* const ss_nb = ss + (ty > 0 ? ty - 1 : 0) * FX + (tx > 0 ? tx - 1 : 0);
+  // D at node plane z from the voxel layers below (stress buffer bl) and above (bu)
+  auto node_div = [&](auto parl, int z) {
+    constexpr int bl = decltype(parl)::value, bu = 1 - bl;
+    T val[8][6];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
+      const int r = TETRA ? ((((ox + oy + oz) & 1) != 0) ? 0 : 1) : 0;
+      const int b = oz ? bu : bl;
+      const T2* p = ss_nb + ((b * NPP + r) * 3) * SL + oy * FX + ox;
+      const T2 a0 = p[0], a1 = p[SL], a2 = p[2 * SL];
+      val[o][0] = a0.x; val[o][1] = a0.y; val[o][2] = a1.x;
+      val[o][3] = a1.y; val[o][4] = a2.x; val[o][5] = a2.y;
+    }
+    T Dq[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int c = sym_index(i, q);
+        T s = T(0);
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          if ((o >> i) & 1) continue;
+          s += val[o | (1 << i)][c] - val[o][c];
+        }
+        Dq[q] += P.wdiv[i] * s;
+      }
+    const long long off = node_xy + z * sz;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      P.D[q][off] = Dq[q];  // interior nodes transform every component (Table 1 ranges)
+      sd += Dq[q] * Dq[q];
     }
   };
 
-  // prologue: node planes Z0 - 1 and Z0, voxel layer Z0 - 1
-  int ph_next = phase_at(Z0 - 1);
-  fetch_plane(Z0 - 1);
-  store_plane(0);
-  fetch_plane(Z0);
-  store_plane(1);
-  __syncthreads();
-  read_corners(0, 0);
-  read_corners(1, 1);
-  __syncthreads();  // buffer 0 is refilled by the first step
-  {
-    const int ph = ph_next;
-    ph_next = phase_at(Z0);
-    voxel_layer(Z0 - 1, 0, ph);
-  }
-  if (Z0 + 1 <= Z1) fetch_plane(Z0 + 1);
-  for (int z = Z0; z < Z1; ++z) {
-    const int k = z - Z0;
-    // node plane z + 1 goes to buffer k & 1 (it held plane z - 1, read two barriers ago)
-    store_plane(k & 1);
-    // the lower corners of voxel layer z are the upper ones of layer z - 1
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        ch[c][q] = ch[c][q + 4];
-        cl[c][q] = cl[c][q + 4];
-      }
+  // one z step: node plane z + 1 into node buffer B, voxel layer z from (Lo, Up) into
+  // stress buffer 1 - B, D at node plane z (stress buffers B below, 1 - B above)
+  NV cA[3][4], cB[3][4];
+  int ph_next = 0;
+  auto step = [&](auto par, int z, const NV (&Lo)[3][4], NV (&Up)[3][4]) {
+    constexpr int B = decltype(par)::value;
+    store_plane(Par<B>{});
     __syncthreads();
     if (z + 2 <= Z1) fetch_plane(z + 2);  // in flight during this layer
     const int ph = ph_next;
     if (z + 1 < Z1) ph_next = phase_at(z + 1);
-    read_corners(k & 1, 1);
-    voxel_layer(z, (k + 1) & 1, ph);
+    read4(Par<B>{}, Up);
+    voxel_layer(Par<1 - B>{}, z, ph, Lo, Up);
     __syncthreads();
-    // D at node plane z from voxel layers z - 1 (buffer k & 1) and z (buffer (k + 1) & 1)
-    if (node_out) {
-      T val[8][6];
-#pragma unroll
-      for (int o = 0; o < 8; ++o) {
-        const int ox = o & 1, oy = (o >> 1) & 1, oz = o >> 2;
-        const int r = TETRA ? ((((ox + oy + oz) & 1) != 0) ? 0 : 1) : 0;
-        const int buf = oz ? ((k + 1) & 1) : (k & 1);
-        const T2* b = ss + (size_t)((buf * NPP + r) * 3) * FY * FX + (ty - 1 + oy) * FX + (tx - 1 + ox);
-        const T2 a0 = b[0], a1 = b[FY * FX], a2 = b[2 * FY * FX];
-        val[o][0] = a0.x; val[o][1] = a0.y; val[o][2] = a1.x;
-        val[o][3] = a1.y; val[o][4] = a2.x; val[o][5] = a2.y;
-      }
-      T Dq[3] = {T(0), T(0), T(0)};
-#pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const int c = sym_index(i, q);
-          T s = T(0);
-#pragma unroll
-          for (int o = 0; o < 8; ++o) {
-            if ((o >> i) & 1) continue;
-            s += val[o | (1 << i)][c] - val[o][c];
-          }
-          Dq[q] += P.wdiv[i] * s;
-        }
-      const long long off = mx + my * sy + z * sz;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        P.D[q][off] = Dq[q];  // interior nodes transform every component (Table 1 ranges)
-        sd += Dq[q] * Dq[q];
-      }
-    }
+    if (node_out) node_div(Par<B>{}, z);
     if (++run == 16) {
       SP += (double)sp;
       SD += (double)sd;
       sp = sd = T(0);
       run = 0;
     }
+  };
+
+  // prologue: node planes Z0 - 1 (buffer 0) and Z0 (buffer 1), voxel layer Z0 - 1 (stress 0)
+  ph_next = phase_at(Z0 - 1);
+  fetch_plane(Z0 - 1);
+  store_plane(Par<0>{});
+  fetch_plane(Z0);
+  store_plane(Par<1>{});
+  __syncthreads();
+  read4(Par<0>{}, cB);
+  read4(Par<1>{}, cA);
+  __syncthreads();  // buffer 0 is refilled by the first step
+  {
+    const int ph = ph_next;
+    ph_next = phase_at(Z0);
+    voxel_layer(Par<0>{}, Z0 - 1, ph, cB, cA);
+  }
+  if (Z0 + 1 <= Z1) fetch_plane(Z0 + 1);
+  // steps alternate buffers; the corners of plane z stay in registers (cA, cB in turn)
+  for (int z = Z0; z < Z1; z += 2) {
+    step(Par<0>{}, z, cA, cB);
+    if (z + 1 < Z1) step(Par<1>{}, z + 1, cB, cA);
   }
   SP += (double)sp;
   SD += (double)sd;
@@ -1420,7 +1515,7 @@ static size_t fused_smem(int tetra) {
 // plain (non-incremental) form without the test outputs.
 template <typename T>
 static bool fused_ok(const ResParams<T>& P, bool with_p) {
-  return !with_p && !P.inc && P.nst == 0 && P.sym && P.state == nullptr;
+  return !with_p && !P.inc && P.nst == 0 && P.sym && P.state == nullptr && !P.two_pass;
 }
 
 template <typename T>
@@ -1523,6 +1618,15 @@ template cudaError_t launch_residual<float>(const ResParams<float>&, int, bool, 
 template cudaError_t launch_residual<double>(const ResParams<double>&, int, bool, cudaStream_t, int*);
 template int residual_blocks<float>(const ResParams<float>&, int);
 template int residual_blocks<double>(const ResParams<double>&, int);
+
+template <typename T>
+bool residual_one_pass(const ResParams<T>& P) {
+  ResParams<T> Q = P;
+  Q.two_pass = 0;
+  return fused_ok(Q, false);
+}
+template bool residual_one_pass<float>(const ResParams<float>&);
+template bool residual_one_pass<double>(const ResParams<double>&);
 
 // ---- per-voxel evaluation shared by the output and statistics kernels ----
 template <typename T, int TETRA, bool LO>

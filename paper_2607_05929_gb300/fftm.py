@@ -31,6 +31,7 @@ FFTM_GREEN_B0, FFTM_GREEN_MU0 = 0, 1
 FFTM_FP64, FFTM_FP32, FFTM_FP32_TC = 0, 1, 2
 FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
 FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D, FFTM_FIELD_STATE = 0, 1, 2, 3, 4, 5
+FFTM_OPT_RESIDUAL_PASSES = 0
 FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP_GREEN_UPDATE = 0, 1, 2, 3, 4
 
 # every symbol include/fftm.h declares
@@ -38,7 +39,7 @@ EXPORTS = [
     "fftm_last_error", "fftm_version", "fftm_ctx_create", "fftm_ctx_destroy",
     "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
     "fftm_set_phase", "fftm_set_load", "fftm_get_load", "fftm_solve_step", "fftm_field_bytes",
-    "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_apply", "fftm_kernel_launches",
+    "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_set_option", "fftm_tuning_table", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
     "fftm_server_inject_start_failures",
@@ -127,6 +128,8 @@ def load_library(path=LIB_PATH):
                             ctypes.c_int),
         "fftm_field_bytes": ([vp, ctypes.c_int, P(ctypes.c_size_t)], ctypes.c_int),
         "fftm_problem_layout": ([vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)], ctypes.c_int),
+        "fftm_set_option": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "fftm_tuning_table": ([ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)], ctypes.c_int),
         "fftm_get_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "fftm_set_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "fftm_apply": ([vp, ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
@@ -324,6 +327,19 @@ def fftm_problem_layout(p):
     prec, dev = ctypes.c_int(), ctypes.c_int()
     _check(load_library().fftm_problem_layout(p, N, ctypes.byref(prec), ctypes.byref(dev)))
     return tuple(N[:]), prec.value, dev.value
+
+
+def fftm_set_option(p, option, value):
+    return _check(load_library().fftm_set_option(p, int(option), int(value)))
+
+
+def fftm_tuning_table():
+    """The launch-shape choices measured in this process, as text."""
+    need = ctypes.c_size_t()
+    _check(load_library().fftm_tuning_table(None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(load_library().fftm_tuning_table(buf, need.value, None))
+    return buf.value.decode()
 
 
 def _ptr_of(buf):

@@ -202,12 +202,14 @@ def test_residual_p_D_and_norms(precision, case):
         gp.close()
 
 
+@pytest.mark.parametrize("passes", [1, 2])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", range(len(RES_CASES)))
-def test_solver_residual_D_and_norms(precision, case):
-    """The residual kernels the solver runs for elastic laws (gradient, law and divergence in
-    one pass; face nodes with the ghost rules), reached through fftm_residual_noalloc on
-    caller buffers, against the oracle's D and norms for every BC family of RES_CASES."""
+def test_solver_residual_D_and_norms(precision, case, passes):
+    """The residual kernels the solver runs for elastic laws, in both forms (gradient, law and
+    divergence in one pass with face nodes by the ghost rules; or stresses stored, then the
+    divergence), reached through fftm_residual_noalloc on caller buffers, against the oracle's
+    D and norms for every BC family of RES_CASES."""
     torch = pytest.importorskip("torch")
     from abi_helpers import node_from_abi, node_to_abi
 
@@ -215,6 +217,7 @@ def test_solver_residual_D_and_norms(precision, case):
     wl = _cubic_wl(n, bc, scheme)
     pr = Problem(wl)
     gp = GpuProblem(wl, precision)
+    F.fftm_set_option(gp.p, F.FFTM_OPT_RESIDUAL_PASSES, passes)
     try:
         rng = np.random.default_rng(case + 30)
         u = 1e-3 * rng.standard_normal(pr.grid.node_shape)
@@ -320,6 +323,28 @@ def test_solve_step_fp64_matches_oracle(name):
         assert np.allclose(r["mean_P"], ref_mean, rtol=1e-9, atol=1e-15)
     finally:
         gp.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_both_residual_forms_give_the_same_solve(precision):
+    """One pass and two passes: the same D per node, so the same iterates, iteration counts and
+    Anderson decisions; the norms differ only by summation order."""
+    wl = SOLVE_CASES["voronoi_tet"]()
+    wl.tol = 1e-8 if precision == "fp64" else 1e-6
+    runs = []
+    for passes in (1, 2):
+        gp = GpuProblem(wl, precision)
+        try:
+            F.fftm_set_option(gp.p, F.FFTM_OPT_RESIDUAL_PASSES, passes)
+            st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+            runs.append((r, eh, ah, gp.get_node(F.FFTM_FIELD_U)))
+        finally:
+            gp.close()
+    (r1, e1, a1, u1), (r2, e2, a2, u2) = runs
+    assert r1["converged"] and r2["converged"]
+    assert r1["iterations"] == r2["iterations"] and list(a1) == list(a2)
+    assert np.allclose(e1, e2, rtol=1e-5 if precision == "fp32" else 1e-12, atol=0.0)
+    assert rel_l2(u1, u2) < (1e-6 if precision == "fp32" else 1e-13)
 
 
 @pytest.mark.parametrize("name", ["sphere32_hex", "voronoi_tet", "voronoi_hex_mu0", "xlam_tet"])
