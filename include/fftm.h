@@ -245,8 +245,10 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
                              divergence), 0 (default) = whichever the library measured faster
                              for this grid shape on this GPU (timed once per shape and process;
                              fftm_tuning_table lists the choices).  Both forms give the same D;
-                             problems with other laws always take two passes. */
-enum fftm_option { FFTM_OPT_RESIDUAL_PASSES = 0 };
+                             problems with other laws always take two passes.
+   FFTM_OPT_RESIDUAL_TILE    the one-pass form's voxel tile height: 8 or 16 rows of 32
+                             voxels per thread block, or 0 (default) = measured, as above. */
+enum fftm_option { FFTM_OPT_RESIDUAL_PASSES = 0, FFTM_OPT_RESIDUAL_TILE = 1 };
 int fftm_set_option(fftm_problem* p, int option, int value);
 
 /* The launch-shape choices the library has measured in this process, one line per shape

@@ -285,6 +285,8 @@ struct fftm_problem {
   int cur = 0;  // ring slot holding the current u^f
   int res_passes = 0;     // requested residual form: 0 tuned, 1 one pass, 2 two passes
   int res_two_pass = -1;  // resolved form (-1: not yet)
+  int res_tile = 0;       // requested one-pass tile height: 0 tuned, 8 or 16
+  int res_fy = 8;         // resolved tile height
   // per-kernel timing (fftm_set_profiling)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -524,6 +526,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
     }
   R.partial = p->partial;
   R.two_pass = p->res_two_pass > 0 ? 1 : 0;
+  R.fused_fy = p->res_fy;
   R.vs = reinterpret_cast<T*>(p->vs);
   R.sym = p->sym;
   R.state = reinterpret_cast<T*>(p->state);
@@ -593,9 +596,10 @@ std::string residual_key(const fftm_problem* p) {
 
 // Milliseconds per launch of the residual in the given form (3 launches after one warm-up).
 template <typename T>
-double time_residual(fftm_problem* p, int slot, int two_pass) {
+double time_residual(fftm_problem* p, int slot, int two_pass, int fy) {
   ResParams<T> R = res_params<T>(p, slot, nullptr, nullptr);
   R.two_pass = two_pass;
+  R.fused_fy = fy;
   cudaStream_t s = p->ctx->stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
@@ -619,15 +623,19 @@ double time_residual(fftm_problem* p, int slot, int two_pass) {
   return ms;
 }
 
+// The residual's form: one pass with a tile of 8 or 16 voxel rows, or two passes; as
+// requested, else the fastest measured for the problem's grid shape (once per process).
 template <typename T>
 int resolve_residual_form(fftm_problem* p, int slot) {
-  if (p->res_passes == 1 || p->res_passes == 2) {
-    p->res_two_pass = p->res_passes == 2 ? 1 : 0;
+  ResParams<T> R = res_params<T>(p, slot, nullptr, nullptr);
+  const bool one_ok = residual_one_pass<T>(R);
+  if (!one_ok || p->res_passes == 2) {
+    p->res_two_pass = 1;
     return FFTM_OK;
   }
-  ResParams<T> R = res_params<T>(p, slot, nullptr, nullptr);
-  if (!residual_one_pass<T>(R)) {
-    p->res_two_pass = 1;
+  if (p->res_passes == 1 && p->res_tile != 0) {
+    p->res_two_pass = 0;
+    p->res_fy = p->res_tile;
     return FFTM_OK;
   }
   const std::string key = residual_key(p);
@@ -635,21 +643,30 @@ int resolve_residual_form(fftm_problem* p, int slot) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_choice.find(key);
     if (it != g_tune_choice.end()) {
-      p->res_two_pass = it->second;
+      const int c = it->second;  // 0: one pass, fy 8; 1: one pass, fy 16; 2: two passes
+      p->res_two_pass = (p->res_passes == 1) ? 0 : (c == 2 ? 1 : 0);
+      p->res_fy = c == 1 ? 16 : 8;
       return FFTM_OK;
     }
   }
-  const double t1 = time_residual<T>(p, slot, 0), t2 = time_residual<T>(p, slot, 1);
+  const double t8 = time_residual<T>(p, slot, 0, 8), t16 = time_residual<T>(p, slot, 0, 16);
+  const double t2 = p->res_passes == 1 ? -1.0 : time_residual<T>(p, slot, 1, 8);
   CU(cudaGetLastError());
-  const int two = (t1 < 0.0 || (t2 >= 0.0 && t2 < t1)) ? 1 : 0;
-  char b[160];
-  std::snprintf(b, sizeof(b), "%s (one pass %.4f ms, two passes %.4f ms)", two ? "two passes" : "one pass", t1, t2);
+  int c = 0;
+  double best = t8;
+  if (t16 >= 0.0 && (best < 0.0 || t16 < best)) c = 1, best = t16;
+  if (t2 >= 0.0 && (best < 0.0 || t2 < best)) c = 2, best = t2;
+  static const char* names[3] = {"one pass, 8-row tiles", "one pass, 16-row tiles", "two passes"};
+  char b[200];
+  std::snprintf(b, sizeof(b), "%s (one pass 8 rows %.4f ms, 16 rows %.4f ms; two passes %.4f ms)", names[c], t8, t16,
+                t2);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_choice[key] = two;
+    g_tune_choice[key] = c;
     g_tune_table[key] = b;
   }
-  p->res_two_pass = two;
+  p->res_two_pass = c == 2 ? 1 : 0;
+  p->res_fy = c == 1 ? 16 : 8;
   return FFTM_OK;
 }
 
@@ -1510,6 +1527,13 @@ int fftm_set_option(fftm_problem* p, int option, int value) {
       if (value < 0 || value > 2) return set_err(FFTM_E_INVALID, "residual passes: 0 (tuned), 1 or 2");
       p->res_passes = value;
       p->res_two_pass = value == 0 ? -1 : (value == 2 ? 1 : 0);
+      if (value == 1 && p->res_tile == 0) p->res_two_pass = -1;  // the tile height is still tuned
+      return FFTM_OK;
+    case FFTM_OPT_RESIDUAL_TILE:
+      if (value != 0 && value != 8 && value != 16) return set_err(FFTM_E_INVALID, "residual tile: 0 (tuned), 8 or 16");
+      p->res_tile = value;
+      if (value) p->res_fy = value;
+      p->res_two_pass = p->res_passes == 2 ? 1 : ((p->res_passes == 1 && value) ? 0 : -1);
       return FFTM_OK;
     default: return set_err(FFTM_E_INVALID, "unknown option");
   }

@@ -110,6 +110,7 @@ struct ResParams {
   T* vs;             // voxel-point stress buffer [r][c][voxel] (c < NC, see fftm_stencil.cu)
   int sym;           // 1: every law gives a symmetric P (6 stored components)
   int two_pass;      // 1: evaluate the residual as two grid passes even where one pass serves
+  int fused_fy;      // voxel tile height of the one-pass residual (8 or 16)
   double* partial;   // per block: S_D, S_P
 };
 

@@ -1055,7 +1055,7 @@ static void interior_and_faces(const ResParams<T>& P, TileIdx* ti, FaceIdx* fi) 
 // nodes it owns see all their voxels; the stresses never leave the SM.  Nodes on
 // non-periodic faces take the ghost rules in k_face_div, which reads the stresses of the
 // boundary voxel layers that this kernel stores to the voxel-point buffer.
-constexpr int FX = 32, FY = 8, FNX = FX + 1, FNY = FY + 1, FTHREADS = FX * FY;
+constexpr int FX = 32, FNX = FX + 1;  // voxel tile width in x (one warp); tile height FY is 8 or 16
 
 // u^f at a node in shared memory: (hi, lo) in FP32, the value in FP64
 template <typename T, bool LO> struct NodeV { using t = T; };
@@ -1071,6 +1071,7 @@ __device__ __forceinline__ double nv_lo(double) { return 0.0; }
 // (every node on a periodic axis, [1, n) on a non-periodic one), tiles of FX-1 (x) and
 // FY-1 (y) nodes, chunks of zc node planes in z.
 struct FusedGeom {
+  int fy;  // voxel tile height (8 or 16)
   int a0[3], a1[3];
   int ntx, nty, nzc, zc;
   int items;
@@ -1080,6 +1081,8 @@ struct FusedGeom {
 template <typename T>
 static FusedGeom fused_geom(const ResParams<T>& P) {
   FusedGeom g;
+  g.fy = P.fused_fy == 16 ? 16 : 8;
+  const int FY = g.fy;
   for (int a = 0; a < 3; ++a) {
     g.a0[a] = P.periodic[a] ? 0 : 1;
     g.a1[a] = P.n[a];
@@ -1224,8 +1227,9 @@ __device__ __forceinline__ void elastic_f2(const float4* __restrict__ M4, const 
 
 template <int V> struct Par { static constexpr int value = V; };
 
-template <typename T, int TETRA, bool LO>
-__global__ void __launch_bounds__(FTHREADS, 2) k_residual_fused(ResParams<T> P, FusedGeom g) {
+template <typename T, int TETRA, bool LO, int FY>
+__global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T> P, FusedGeom g) {
+  constexpr int FNY = FY + 1, FTHREADS = FX * FY;
   using NV = typename NodeV<T, LO>::t;
   using T2 = typename V2<T>::t;
   constexpr int NPP = TETRA ? 2 : 1;
@@ -1505,9 +1509,18 @@ __global__ void __launch_bounds__(256) k_face_div(ResParams<T> P, FaceIdx fi) {
 constexpr int kFaceBlocks = 152 * 2;
 
 template <typename T>
-static size_t fused_smem(int tetra) {
+static size_t fused_smem(int tetra, int fy) {
   using NVs = typename NodeV<T, true>::t;  // same size as the FP64 node value
-  return (size_t)2 * 3 * FNY * FNX * sizeof(NVs) + (size_t)2 * (tetra ? 2 : 1) * 3 * FY * FX * 2 * sizeof(T);
+  return (size_t)2 * 3 * (fy + 1) * FNX * sizeof(NVs) + (size_t)2 * (tetra ? 2 : 1) * 3 * fy * FX * 2 * sizeof(T);
+}
+
+template <typename T, int TETRA, bool LO, int FY>
+static cudaError_t launch_fused_kernel(const ResParams<T>& P, const FusedGeom& g, cudaStream_t s) {
+  auto kern = k_residual_fused<T, TETRA, LO, FY>;
+  const size_t smem = fused_smem<T>(TETRA, FY);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) kern<<<g.items, FX * FY, smem, s>>>(P, g);
+  return e;
 }
 
 // The fused path serves the solver's residual for problems whose every law is a
@@ -1528,21 +1541,16 @@ template <typename T, int TETRA>
 static cudaError_t launch_fused_t(const ResParams<T>& P, cudaStream_t s, int* blocks_out) {
   const FusedGeom g = fused_geom(P);
   const bool lo = P.ulo[0] != nullptr;
-  const size_t smem = fused_smem<T>(TETRA);
   if (g.items > 0) {
     cudaError_t e = cudaSuccess;
     if (lo) {
       if constexpr (sizeof(T) == 4) {  // FP32 with a low part (the solver's fields)
-        auto kern = k_residual_fused<T, TETRA, true>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) kern<<<g.items, FTHREADS, smem, s>>>(P, g);
+        e = g.fy == 16 ? launch_fused_kernel<T, TETRA, true, 16>(P, g, s) : launch_fused_kernel<T, TETRA, true, 8>(P, g, s);
       } else {
         return cudaErrorInvalidValue;  // FP64 fields carry no low part
       }
     } else {
-      auto kern = k_residual_fused<T, TETRA, false>;
-      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) kern<<<g.items, FTHREADS, smem, s>>>(P, g);
+      e = g.fy == 16 ? launch_fused_kernel<T, TETRA, false, 16>(P, g, s) : launch_fused_kernel<T, TETRA, false, 8>(P, g, s);
     }
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();

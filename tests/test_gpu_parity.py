@@ -202,10 +202,10 @@ def test_residual_p_D_and_norms(precision, case):
         gp.close()
 
 
-@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("passes,tile", [(1, 8), (1, 16), (2, 0)])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("case", range(len(RES_CASES)))
-def test_solver_residual_D_and_norms(precision, case, passes):
+def test_solver_residual_D_and_norms(precision, case, passes, tile):
     """The residual kernels the solver runs for elastic laws, in both forms (gradient, law and
     divergence in one pass with face nodes by the ghost rules; or stresses stored, then the
     divergence), reached through fftm_residual_noalloc on caller buffers, against the oracle's
@@ -218,6 +218,7 @@ def test_solver_residual_D_and_norms(precision, case, passes):
     pr = Problem(wl)
     gp = GpuProblem(wl, precision)
     F.fftm_set_option(gp.p, F.FFTM_OPT_RESIDUAL_PASSES, passes)
+    F.fftm_set_option(gp.p, F.FFTM_OPT_RESIDUAL_TILE, tile)
     try:
         rng = np.random.default_rng(case + 30)
         u = 1e-3 * rng.standard_normal(pr.grid.node_shape)
@@ -332,19 +333,21 @@ def test_both_residual_forms_give_the_same_solve(precision):
     wl = SOLVE_CASES["voronoi_tet"]()
     wl.tol = 1e-8 if precision == "fp64" else 1e-6
     runs = []
-    for passes in (1, 2):
+    for passes, tile in ((1, 8), (1, 16), (2, 0)):
         gp = GpuProblem(wl, precision)
         try:
             F.fftm_set_option(gp.p, F.FFTM_OPT_RESIDUAL_PASSES, passes)
+            F.fftm_set_option(gp.p, F.FFTM_OPT_RESIDUAL_TILE, tile)
             st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
             runs.append((r, eh, ah, gp.get_node(F.FFTM_FIELD_U)))
         finally:
             gp.close()
-    (r1, e1, a1, u1), (r2, e2, a2, u2) = runs
-    assert r1["converged"] and r2["converged"]
-    assert r1["iterations"] == r2["iterations"] and list(a1) == list(a2)
-    assert np.allclose(e1, e2, rtol=1e-5 if precision == "fp32" else 1e-12, atol=0.0)
-    assert rel_l2(u1, u2) < (1e-6 if precision == "fp32" else 1e-13)
+    r1, e1, a1, u1 = runs[0]
+    for r2, e2, a2, u2 in runs[1:]:
+        assert r1["converged"] and r2["converged"]
+        assert r1["iterations"] == r2["iterations"] and list(a1) == list(a2)
+        assert np.allclose(e1, e2, rtol=1e-5 if precision == "fp32" else 1e-12, atol=0.0)
+        assert rel_l2(u1, u2) < (1e-6 if precision == "fp32" else 1e-13)
 
 
 @pytest.mark.parametrize("name", ["sphere32_hex", "voronoi_tet", "voronoi_hex_mu0", "xlam_tet"])
