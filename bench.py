@@ -58,12 +58,14 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--grains", type=int, default=500)
-    ap.add_argument("--precision", choices=["fp32", "fp32_tc", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp32_tc", "fp32_tf32", "fp64"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed beside (0 = skip)")
     ap.add_argument("--tc-steps", type=int, default=3,
                     help="tensor-core (FP32_TC) path steps timed beside the FP32 path (0 = skip)")
+    ap.add_argument("--tf32-steps", type=int, default=3,
+                    help="TF32 tensor-core (FP32_TF32) path steps timed beside the FP32 path (0 = skip)")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream (mixed sizes/BCs/laws, Poisson arrivals): solves/s and p50/p99 latency")
     ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream (--serve)")
@@ -437,6 +439,28 @@ def gpu_arm(args):
         line["fp32_tc_path"] = {"value": utc / stc, "unit": UNIT, "iterations_per_step": last["iterations"],
                                 "steps": args.tc_steps, "ms_per_step": 1000.0 * stc / args.tc_steps,
                                 "note": "per-axis transforms as tcgen05 BF16 contractions, FP32 fields and residual"}
+        F.fftm_problem_destroy(prob)
+        prob = make(args.precision)
+
+    # ---- TF32 tensor-core transforms beside it (the precision form, same workload) ----
+    if args.tf32_steps > 0 and args.precision == "fp32":
+        F.fftm_problem_destroy(prob)
+        prob = make("fp32_tf32")
+        step()  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        F.fftm_set_profiling(prob, True)
+        e0.record(stream)
+        utf = sum(step() for _ in range(args.tf32_steps))
+        e1.record(stream)
+        e1.synchronize()
+        stf = e0.elapsed_time(e1) / 1000.0
+        kt = F.fftm_kernel_times(prob)
+        F.fftm_set_profiling(prob, False)
+        line["fp32_tf32_path"] = {"value": utf / stf, "unit": UNIT, "iterations_per_step": last["iterations"],
+                                  "steps": args.tf32_steps, "ms_per_step": 1000.0 * stf / args.tf32_steps,
+                                  "ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()},
+                                  "note": "per-axis transforms as tcgen05 TF32 contractions, FP32 fields and residual"}
         F.fftm_problem_destroy(prob)
         prob = make(args.precision)
 

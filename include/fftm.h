@@ -69,7 +69,12 @@ enum fftm_green { FFTM_GREEN_B0 = 0, FFTM_GREEN_MU0 = 1 };
    and FP32 accumulation (transform lengths up to 288 node positions along x, the
    range's first node mod 4 included, and 352 along y and z; FFTM_E_UNSUPPORTED
    beyond). */
-enum fftm_precision { FFTM_FP64 = 0, FFTM_FP32 = 1, FFTM_FP32_TC = 2 };
+/* FFTM_FP32_TF32: FP32 fields and residual, per-axis transforms as dense matrix
+   contractions on the tensor cores with TF32 operands (tcgen05 kind::tf32: the FP32
+   fields and FP32 matrices are read as stored, the products carry 10-bit significands,
+   FP32 accumulation), lengths up to 384 node positions per axis (FFTM_E_UNSUPPORTED
+   beyond). */
+enum fftm_precision { FFTM_FP64 = 0, FFTM_FP32 = 1, FFTM_FP32_TC = 2, FFTM_FP32_TF32 = 3 };
 enum fftm_law {
   FFTM_LAW_ISO_ELASTIC = 0,   /* params: lambda, mu                          */
   FFTM_LAW_CUBIC_ELASTIC = 1, /* params: C11, C12, C44; quat = orientation     */

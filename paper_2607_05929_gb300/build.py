@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libfftm.so")
-HEADERS = [os.path.join(CSRC, "fftm_internal.cuh"), os.path.join(ROOT, "include", "fftm.h"),
-           os.path.join(ROOT, "include", "fftm_server.h")]
+HEADERS = ([os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cuh")] +
+           [os.path.join(ROOT, "include", "fftm.h"), os.path.join(ROOT, "include", "fftm_server.h")])
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -275,6 +275,7 @@ struct fftm_problem {
   int inc_ok = 0;           // incremental residual after a commit (J2 with linear small-strain laws)
   // tensor-core transforms (FFTM_FP32_TC): BF16 matrices, Kp x Kp per component and axis
   int tc = 0;
+  int tf = 0;  // FFTM_FP32_TF32: FP32 matrices, TF32 contractions (same offsets tables)
   void* tcmat = nullptr;
   int* tc_err = nullptr;  // timeout flag of the tensor-core passes
   size_t off_tcf[3][3], off_tci[3][3];
@@ -480,6 +481,53 @@ TcPassParams tc_params(fftm_problem* p, int axis, int inverse, int fused, int in
 int launch_tc(fftm_problem* p, const TcPassParams& P) {
   ProfScope ps(p, P.axis == 0 ? FFTM_KCAT_PASS_X : (P.axis == 1 ? FFTM_KCAT_PASS_Y : FFTM_KCAT_PASS_Z));
   CU(launch_pass_tc(P, p->ctx->stream));
+  p->launches++;
+  return FFTM_OK;
+}
+
+// One TF32 tensor-core pass along `axis`: mode 0 plain (scale 1; the inverse matrices carry
+// the normalisation), 1 x inverse accumulated onto a base field, 2 z forward times the Green
+// factor.
+TfPassParams tf_params(fftm_problem* p, int axis, int inverse, int mode, int in_set, int out_set) {
+  TfPassParams P;
+  std::memset(&P, 0, sizeof(P));
+  const char* base = reinterpret_cast<const char*>(p->tcmat);
+  for (int q = 0; q < 3; ++q) {
+    P.in[q] = field_ptr<float>(p, in_set, q);
+    P.out[q] = field_ptr<float>(p, out_set, q);
+    P.lo[q] = p->plans[q][axis].lo;
+    P.L[q] = p->plans[q][axis].L;
+    P.Kp[q] = p->tcKp[q][axis];
+    P.A[q] = reinterpret_cast<const float*>(base + (inverse ? p->off_tci[q][axis] : p->off_tcf[q][axis]));
+    P.scale[q] = 1.f;
+    for (int a = 0; a < 3; ++a) {
+      P.S2[q][a] = tptr<float>(p, p->off_S2[q][a]);
+      P.C2[q][a] = tptr<float>(p, p->off_C2[q][a]);
+      P.flo[q][a] = p->plans[q][a].lo;
+      P.fL[q][a] = p->plans[q][a].L;
+    }
+    P.gscale[q] = 1.f;
+  }
+  P.axis = axis;
+  P.mode = mode;
+  for (int a = 0; a < 3; ++a) {
+    P.N[a] = p->N[a];
+    P.hf[a] = (float)(4.0 / (p->h[a] * p->h[a]));
+  }
+  P.stride[0] = 1;
+  P.stride[1] = p->sy;
+  P.stride[2] = p->sz;
+  const double lam0 = p->desc.green == FFTM_GREEN_MU0 ? 0.0 : p->desc.lambda0;
+  P.two_mu0 = (float)(2.0 * p->desc.mu0);
+  P.lam0 = (float)lam0;
+  P.tetra = p->tetra;
+  P.err = p->tc_err;
+  return P;
+}
+
+int launch_tf(fftm_problem* p, const TfPassParams& P) {
+  ProfScope ps(p, P.axis == 0 ? FFTM_KCAT_PASS_X : (P.axis == 1 ? FFTM_KCAT_PASS_Y : FFTM_KCAT_PASS_Z));
+  CU(launch_pass_tf32(P, p->ctx->stream));
   p->launches++;
   return FFTM_OK;
 }
@@ -720,6 +768,26 @@ template <typename T>
 int green_apply(fftm_problem* p, int in_set, int base_set, int base_lo_set, int out_set, int out_lo_set,
                 bool negate) {
   int rc;
+  if (p->tf) {
+    if ((rc = launch_tf(p, tf_params(p, 0, 0, 0, in_set, SET_WORK)))) return rc;
+    if ((rc = launch_tf(p, tf_params(p, 1, 0, 0, SET_WORK, SET_WORK)))) return rc;
+    {
+      TfPassParams P = tf_params(p, 2, 0, 2, SET_WORK, SET_WORK);
+      if (negate)
+        for (int q = 0; q < 3; ++q) P.gscale[q] = -1.f;
+      if ((rc = launch_tf(p, P))) return rc;
+    }
+    if ((rc = launch_tf(p, tf_params(p, 2, 1, 0, SET_WORK, SET_WORK)))) return rc;
+    if ((rc = launch_tf(p, tf_params(p, 1, 1, 0, SET_WORK, SET_WORK)))) return rc;
+    TfPassParams P = tf_params(p, 0, 1, base_set >= 0 ? 1 : 0, SET_WORK, out_set);
+    if (base_set >= 0)
+      for (int q = 0; q < 3; ++q) {
+        P.base[q] = field_ptr<float>(p, base_set, q);
+        P.base_lo[q] = base_lo_set >= 0 ? field_ptr<float>(p, base_lo_set, q) : nullptr;
+        P.out_lo[q] = out_lo_set >= 0 ? field_ptr<float>(p, out_lo_set, q) : nullptr;
+      }
+    return launch_tf(p, P);
+  }
   if (p->tc) {
     if ((rc = launch_tc(p, tc_params(p, 0, 0, 0, in_set, SET_WORK)))) return rc;
     if ((rc = launch_tc(p, tc_params(p, 1, 0, 0, SET_WORK, SET_WORK)))) return rc;
@@ -977,7 +1045,7 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     nacc += acc[i];
   }
   rep->n_accelerated = nacc;
-  if (p->tc) {  // a tensor-core pass that gave up on a barrier leaves its result undefined
+  if (p->tc || p->tf) {  // a tensor-core pass that gave up on a barrier leaves its result undefined
     int e = 0;
     CU(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
@@ -1045,8 +1113,13 @@ int validate(const fftm_problem_desc* d) {
   if (d->scheme != FFTM_HEX1 && d->scheme != FFTM_TETRA2) return set_err(FFTM_E_INVALID, "bad scheme");
   if (d->green != FFTM_GREEN_B0 && d->green != FFTM_GREEN_MU0) return set_err(FFTM_E_INVALID, "bad green");
   if (!(d->mu0 > 0.0) || !(d->lambda0 >= 0.0)) return set_err(FFTM_E_INVALID, "need mu0 > 0, lambda0 >= 0");
-  if (d->precision != FFTM_FP64 && d->precision != FFTM_FP32 && d->precision != FFTM_FP32_TC)
+  if (d->precision != FFTM_FP64 && d->precision != FFTM_FP32 && d->precision != FFTM_FP32_TC &&
+      d->precision != FFTM_FP32_TF32)
     return set_err(FFTM_E_INVALID, "bad precision");
+  if (d->precision == FFTM_FP32_TF32)
+    for (int a = 0; a < 3; ++a)
+      if (d->n[a] + 1 > 384)
+        return set_err(FFTM_E_UNSUPPORTED, "TF32 tensor-core transforms need n <= 383 per axis");
   if (d->precision == FFTM_FP32_TC)
     for (int a = 0; a < 3; ++a)
       if (d->n[a] + 1 > 384) return set_err(FFTM_E_UNSUPPORTED, "tensor-core transforms need n <= 383 per axis");
@@ -1332,6 +1405,45 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
       }
     CU(cudaMalloc(&p->tcmat, mats.size() * sizeof(uint16_t)));
     CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    CU(cudaMalloc(&p->tc_err, sizeof(int)));
+    CU(cudaMemset(p->tc_err, 0, sizeof(int)));
+  }
+  if (desc->precision == FFTM_FP32_TF32) {
+    p->tf = 1;
+    std::vector<float> mats;
+    // R x Kp zero-padded (R = Kp, on the x axis Kp rounded up to 128), in 32-column chunks in
+    // the K-major core-matrix order of FP32 elements: element (m, jj) of chunk c at
+    // c R 32 + (m>>3) 256 + (jj>>2) 32 + (m&7) 4 + (jj&3).  On the x axis rows and columns are
+    // shifted by lo - xb, xb = lo rounded down to a multiple of 4 (aligned 16-byte copies).
+    auto put_mat = [&](const std::vector<double>& M, int L, int Kp, int R, int sh) {
+      size_t off = (mats.size() + 31) & ~(size_t)31;  // 128-byte aligned
+      mats.resize(off + (size_t)R * Kp, 0.f);
+      for (int r0 = 0; r0 < L; ++r0)
+        for (int c0 = 0; c0 < L; ++c0) {
+          const int m = r0 + sh, c = c0 + sh;
+          const int ch = c / 32, jj = c % 32;
+          const size_t at = (size_t)ch * R * 32 + (size_t)(m >> 3) * 256 + (jj >> 2) * 32 + (m & 7) * 4 + (jj & 3);
+          mats[off + at] = (float)M[(size_t)r0 * L + c0];
+        }
+      return off * sizeof(float);
+    };
+    for (int q = 0; q < 3; ++q)
+      for (int a = 0; a < 3; ++a) {
+        std::vector<double> F, I;
+        int L;
+        dense_forward(p->kind[q][a], p->n[a], &F, &L);
+        dense_inverse(p->kind[q][a], p->n[a], &I);
+        const int col0 = a == 0 ? (p->plans[q][a].lo & 3) : 0;
+        const int Kp = (L + col0 + 31) / 32 * 32;
+        if (!pass_tf32_fits(Kp, a))
+          return set_err(FFTM_E_UNSUPPORTED, "TF32 tensor-core transforms need lengths up to 384 per axis");
+        p->tcKp[q][a] = Kp;
+        const int R = pass_tf32_rows(Kp, a);
+        p->off_tcf[q][a] = put_mat(F, L, Kp, R, col0);
+        p->off_tci[q][a] = put_mat(I, L, Kp, R, col0);
+      }
+    CU(cudaMalloc(&p->tcmat, mats.size() * sizeof(float)));
+    CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(float), cudaMemcpyHostToDevice));
     CU(cudaMalloc(&p->tc_err, sizeof(int)));
     CU(cudaMemset(p->tc_err, 0, sizeof(int)));
   }
@@ -1709,13 +1821,15 @@ static int apply_t(fftm_problem* p, int op, double* norms) {
     }
     case FFTM_OP_DT_FORWARD:
       for (int a = 0; a < 3 && !rc; ++a)
-        rc = p->tc ? launch_tc(p, tc_params(p, a, 0, 0, SET_WORK, SET_WORK))
-                   : run_pass<T>(p, a, 0, 0, SET_WORK, SET_WORK, false);
+        rc = p->tf ? launch_tf(p, tf_params(p, a, 0, 0, SET_WORK, SET_WORK))
+             : p->tc ? launch_tc(p, tc_params(p, a, 0, 0, SET_WORK, SET_WORK))
+                     : run_pass<T>(p, a, 0, 0, SET_WORK, SET_WORK, false);
       break;
     case FFTM_OP_DT_INVERSE:
       for (int a = 2; a >= 0 && !rc; --a)
-        rc = p->tc ? launch_tc(p, tc_params(p, a, 1, 0, SET_WORK, SET_WORK))
-                   : run_pass<T>(p, a, 1, 0, SET_WORK, SET_WORK, true);
+        rc = p->tf ? launch_tf(p, tf_params(p, a, 1, 0, SET_WORK, SET_WORK))
+             : p->tc ? launch_tc(p, tc_params(p, a, 1, 0, SET_WORK, SET_WORK))
+                     : run_pass<T>(p, a, 1, 0, SET_WORK, SET_WORK, true);
       break;
     case FFTM_OP_GREEN: {
       PassParams<T> P = pass_params<T>(p, 2, 0, 0, SET_WORK, SET_WORK);
@@ -1756,7 +1870,7 @@ static int apply_t(fftm_problem* p, int op, double* norms) {
   }
   if (rc) return rc;
   CU(cudaStreamSynchronize(s));
-  if (p->tc) {
+  if (p->tc || p->tf) {
     int e = 0;
     CU(cudaMemcpy(&e, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {

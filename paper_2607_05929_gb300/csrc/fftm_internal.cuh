@@ -157,6 +157,39 @@ bool pass_tc_fits(int Kp, int axis);
 // Rows of one matrix in the tensor-core chunk layout (x: Kp padded to a multiple of 128).
 int pass_tc_rows(int Kp, int axis);
 
+// One axis pass as a dense contraction on the tensor cores with TF32 operands (tcgen05
+// kind::tf32, FP32 data read as is, FP32 accumulation in TMEM).  A: the R x Kp transform
+// matrix (zero-padded; Kp = L rounded up to 32, on x after the shift by lo mod 4; R = Kp,
+// on x Kp rounded up to 128) in 32-column chunks, each in the K-major core-matrix order of
+// FP32 elements: element (m, jj) of chunk c at c R 32 + (m>>3) 256 + (jj>>2) 32 + (m&7) 4
+// + (jj&3).  mode 0: out = scale T in; mode 1 (x axis): out = base + scale T in, as an
+// unevaluated hi + lo pair when out_lo is set; mode 2 (z axis): the forward result times the
+// B0 / 2 mu0 Green factor -gscale / den (0 where den is null).
+struct TfPassParams {
+  const float* in[3];
+  float* out[3];
+  const float* base[3];
+  const float* base_lo[3];
+  float* out_lo[3];
+  int axis, mode;
+  int N[3];
+  long long stride[3];
+  int lo[3], L[3], Kp[3];
+  const float* A[3];
+  float scale[3];
+  const float* S2[3][3];
+  const float* C2[3][3];
+  int flo[3][3], fL[3][3];
+  float hf[3];
+  float two_mu0, lam0;
+  int tetra;
+  float gscale[3];
+  int* err;  // set to 1 by a CTA whose bounded wait on the tensor-core pipeline gave up
+};
+cudaError_t launch_pass_tf32(const TfPassParams& P, cudaStream_t s);
+bool pass_tf32_fits(int Kp, int axis);
+int pass_tf32_rows(int Kp, int axis);
+
 // Green factor on a spectral field (standalone step).
 template <typename T>
 struct GreenParams {

@@ -1,0 +1,611 @@
+// Axis passes of the 3D transforms as dense contractions on the 5th-generation tensor cores
+// with TF32 operands: the FP32 fields and FP32 transform matrices are read as they are
+// stored and multiplied by tcgen05.mma kind::tf32 (10-bit significands in the products,
+// FP32 accumulation in TMEM).  The precision form of the transforms (Table 1 as dense
+// matrices, Sec. 2.7.2); the residual that decides convergence stays in FP32.
+//
+// Every 1D transform of Table 1 and its inverse is a real L x L matrix T over the
+// transform's node range (periodic axes in halfcomplex order).  A tile is 128 pencils of one
+// component.  y and z axes (pencils are the contiguous direction):
+//     D[p][k] = sum_j S[p][j] T[k][j]
+// with the tile S as the A operand (M = 128 pencils) and T as the B operand (N = the padded
+// output length, up to 256 per instruction), both K-major (the producers transpose 4 x 4
+// blocks of the tile in registers); TMEM lanes are pencils and one store writes 32
+// consecutive pencils.  x axis (pencils are rows of memory):
+//     D[k][p] = sum_j T[k][j] S[p][j]
+// with T as the A operand (M = outputs in blocks of 128) and S as the B operand (N = 128
+// pencils, K-major); TMEM lanes are outputs and a warp stores 32 consecutive nodes of a row.
+//
+// The contraction dimension streams through a ring of shared-memory stages, each holding
+// 32 K-columns of the tile (filled by seven producer warps: 16-byte cp.async copies on x,
+// transposed 4 x 4 blocks on y and z) and of the matrix (one bulk copy).  One thread issues the MMAs
+// of a stage as soon as both halves have landed and releases the stage when they have read
+// it; eight epilogue warps drain the TMEM accumulators (two, alternating, when they fit)
+// while the next tile is contracted.  Every wait is bounded: past the limit the CTA records
+// an error in P.err, lets its copies and MMAs finish, frees its TMEM and returns.
+#include "fftm_internal.cuh"
+#include "fftm_umma.cuh"
+
+namespace fftm {
+
+constexpr int TF_P = 128;      // pencils per tile
+constexpr int TF_KC = 32;      // K columns per stage (four MMA k-steps of 8)
+constexpr int TF_EPI = 256;    // epilogue threads (warps 0-7)
+constexpr int TF_PROD = 224;   // producer threads (warps 8-14)
+constexpr int TF_THREADS = TF_EPI + TF_PROD + 32;  // warp 15: matrix copies and MMAs (lane 0)
+constexpr int TF_MAXST = 8;
+constexpr int TF_LAG = 2;      // stages a producer keeps in flight before completing the oldest
+constexpr int TF_TMEM_COLS = 512;
+constexpr uint32_t TF_TILE_BYTES = TF_P * TF_KC * 4;
+
+// Instruction descriptor, kind::tf32: F32 accumulator, TF32 A and B, both K-major,
+// N >> 3, M >> 4.
+__device__ __forceinline__ uint32_t tf_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TF_P >> 4) << 24);
+}
+
+__device__ __forceinline__ void tf_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void st_zero16(uint32_t saddr) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(saddr), "r"(0u) : "memory");
+}
+
+// Shared-memory geometry for a padded transform length Kp (a multiple of 32).
+struct TfGeom {
+  int mp;            // matrix rows (x: Kp rounded up to 128; y, z: Kp)
+  uint32_t stage;    // bytes of one stage: tile part, then matrix part (mp x 32 FP32)
+  int nst;           // stages
+  int acc_cols;      // TMEM columns of one accumulator
+  __host__ __device__ static TfGeom make(int Kp, int axis) {
+    TfGeom g;
+    g.mp = axis == 0 ? (Kp + 127) / 128 * 128 : Kp;
+    g.stage = (TF_TILE_BYTES + (uint32_t)g.mp * TF_KC * 4 + 1023u) & ~1023u;
+    const long long room = (long long)kMaxDynSmem - 2048;
+    g.nst = (int)(room / g.stage);
+    if (g.nst > TF_MAXST) g.nst = TF_MAXST;
+    g.acc_cols = axis == 0 ? g.mp : Kp;
+    return g;
+  }
+  __host__ __device__ size_t smem() const { return 2048 + (size_t)nst * stage; }
+};
+
+// ---- tiles ------------------------------------------------------------------------------
+// x axis: runs of 128 consecutive (y, z) rows of the whole grid; y and z axes: runs of 128
+// pencils along x within the component's x node range (from a multiple of 8), for every z
+// (y pass) or for every y of the component's y range (z passes).
+struct TfTile {
+  int q, L, lo, Kp, npen, row0, x0, other;
+  long long base0, estride;
+};
+
+template <int AXIS>
+__device__ __forceinline__ int tf_comp_tiles(const TfPassParams& P, int q, int* ntx_out) {
+  if (AXIS == 0) {
+    *ntx_out = 1;
+    return (P.N[1] * P.N[2] + TF_P - 1) / TF_P;
+  }
+  const int xb = P.flo[q][0] & ~7, xe = P.flo[q][0] + P.fL[q][0];
+  const int ntx = (xe - xb + TF_P - 1) / TF_P;
+  *ntx_out = ntx;
+  const int nother = AXIS == 1 ? P.N[2] : P.fL[q][1];
+  return ntx * nother;
+}
+
+template <int AXIS>
+__device__ __forceinline__ TfTile tf_tile_of(const TfPassParams& P, int t) {
+  TfTile T;
+  int q = 0, ntx = 1, nt = tf_comp_tiles<AXIS>(P, 0, &ntx);
+  while (t >= nt && q < 2) {
+    t -= nt;
+    ++q;
+    nt = tf_comp_tiles<AXIS>(P, q, &ntx);
+  }
+  T.q = q;
+  T.L = P.L[q];
+  T.lo = P.lo[q];
+  T.Kp = P.Kp[q];
+  T.row0 = T.x0 = T.other = 0;
+  T.base0 = 0;
+  T.estride = 1;
+  if (AXIS == 0) {
+    T.row0 = t * TF_P;
+    T.npen = min(TF_P, P.N[1] * P.N[2] - T.row0);
+  } else {
+    const int xb = P.flo[q][0] & ~7, xe = P.flo[q][0] + P.fL[q][0];
+    const int xt = t % ntx, o = t / ntx;
+    T.other = AXIS == 1 ? o : P.flo[q][1] + o;
+    T.x0 = xb + xt * TF_P;
+    T.npen = min(T.x0 + TF_P, xe) - T.x0;
+    T.base0 = T.x0 + (long long)T.other * (AXIS == 1 ? P.stride[2] : P.stride[1]);
+    T.estride = AXIS == 1 ? P.stride[1] : P.stride[2];
+  }
+  return T;
+}
+
+template <int AXIS>
+__device__ __forceinline__ int tf_total_tiles(const TfPassParams& P) {
+  int n = 0, ntx;
+  for (int q = 0; q < 3; ++q) n += tf_comp_tiles<AXIS>(P, q, &ntx);
+  return n;
+}
+
+// ---- producers ---------------------------------------------------------------------------
+// The tile part of a stage holds 128 rows (pencils) x 32 K values in the K-major core-matrix
+// order: element (p, k) at (p>>3) 1024 + (k>>2) 128 + (p&7) 16 + (k&3) 4 bytes (LBO = 128
+// along K, SBO = 1024 per 8 rows), zero where it falls outside the array or the tile.
+//  x axis: 1024 pieces (row p, group g) of 4 consecutive x, copied with 16-byte cp.async.
+//  y, z axes: 256 blocks (pencil group pg, row group kq) of 4 pencils x 4 rows, loaded as
+//    four 16-byte rows and transposed in registers (each pencil's 4 K values in one store).
+__device__ __forceinline__ void tf_stage_x(const TfPassParams& P, const TfTile& T, int c, uint32_t sdst, int ptid) {
+  const float* __restrict__ in = P.in[T.q];
+  const long long PX = P.stride[1];  // row pitch (a multiple of 8, >= N1)
+  const int N2 = P.N[1];
+  const long long sy = P.stride[1], sz = P.stride[2];
+  const int xb = T.lo & ~3;
+  for (int i = ptid; i < TF_P * 8; i += TF_PROD) {
+    const int p = i >> 3, gq = i & 7;
+    const int x = xb + TF_KC * c + 4 * gq;
+    const uint32_t d = sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)gq * 128u + (uint32_t)(p & 7) * 16u;
+    if (p < T.npen && x < PX) {
+      const int r = T.row0 + p;
+      cp_async16(d, in + (long long)(r % N2) * sy + (long long)(r / N2) * sz + x);
+    } else {
+      st_zero16(d);
+    }
+  }
+}
+
+constexpr int TF_BLK = 2;  // 4 x 4 blocks per producer thread and stage (256 blocks, 224 threads)
+
+struct TfBlocks {
+  float4 v[TF_BLK][4];
+};
+
+template <int AXIS>
+__device__ __forceinline__ void tf_load_yz(const TfPassParams& P, const TfTile& T, int c, int ptid, TfBlocks& B) {
+  const float* __restrict__ in = P.in[T.q];
+  const long long PX = P.stride[1];
+  const int Nax = P.N[AXIS];
+#pragma unroll
+  for (int b = 0; b < TF_BLK; ++b) {
+    const int i = ptid + b * TF_PROD;
+    const int pg = i & 31, kq = i >> 5;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int row = T.lo + TF_KC * c + 4 * kq + r;
+      const bool ok = i < 256 && row < Nax && T.x0 + 4 * pg < PX;
+      B.v[b][r] = ok ? __ldg(reinterpret_cast<const float4*>(in + T.base0 + (long long)row * T.estride + 4 * pg))
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+__device__ __forceinline__ void tf_store_yz(uint32_t sdst, int ptid, const TfBlocks& B) {
+#pragma unroll
+  for (int b = 0; b < TF_BLK; ++b) {
+    const int i = ptid + b * TF_PROD;
+    if (i >= 256) continue;
+    const int pg = i & 31, kq = i >> 5;
+    const float4* v = B.v[b];
+    const float4 w[4] = {make_float4(v[0].x, v[1].x, v[2].x, v[3].x), make_float4(v[0].y, v[1].y, v[2].y, v[3].y),
+                         make_float4(v[0].z, v[1].z, v[2].z, v[3].z), make_float4(v[0].w, v[1].w, v[2].w, v[3].w)};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int p = 4 * pg + e;
+      const uint32_t d = sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)kq * 128u + (uint32_t)(p & 7) * 16u;
+      asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(d), "f"(w[e].x), "f"(w[e].y), "f"(w[e].z),
+                   "f"(w[e].w)
+                   : "memory");
+    }
+  }
+}
+
+// ---- barriers ----------------------------------------------------------------------------
+struct TfBars {
+  uint64_t* full;       // [nst] TF_PROD arrivals + 1 (matrix copy, transaction bytes)
+  uint64_t* empty;      // [nst] 1 (MMA commit): the stage has been read
+  uint64_t* acc_full;   // [2]   1 (MMA commit): the tile's contraction is done
+  uint64_t* acc_empty;  // [2]   TF_EPI arrivals: the accumulator has been drained
+  uint64_t* done;       // 1     (MMA commit): every MMA of the CTA has completed
+};
+
+// ---- the MMA thread (warp 15, lane 0): matrix copies ahead, MMAs as stages land -----------
+template <int AXIS>
+__device__ void tf_mma_thread(const TfPassParams& P, const TfGeom& g, unsigned char* stages, const TfBars& B,
+                              uint32_t tmem, int nacc, int my_tiles, volatile int* abort) {
+  // chunk sequence: tile i, chunk c; loader position (li, lc), consumer position (ci, cc)
+  int li = 0, lc = 0, ci = 0, cc = 0, cstarted = 0;
+  long long nl = 0, nc = 0;  // chunks loaded, consumed
+  TfTile LT, CT;
+  if (my_tiles > 0) {
+    LT = tf_tile_of<AXIS>(P, blockIdx.x);
+    CT = LT;
+  }
+  long long idle = 0;
+  while (ci < my_tiles) {
+    bool progress = false;
+    // -- loader: the next matrix chunk once its stage has been released
+    if (li < my_tiles && nl < nc + g.nst) {
+      const int s = (int)(nl % g.nst);
+      const long long u = nl / g.nst;
+      if (u == 0 || bar_test(&B.empty[s], (uint32_t)((u - 1) & 1))) {
+        const TfGeom tg = TfGeom::make(LT.Kp, AXIS);
+        const uint32_t mbytes = (uint32_t)tg.mp * TF_KC * 4;
+        bulk_load(stages + (size_t)s * g.stage + TF_TILE_BYTES,
+                  reinterpret_cast<const unsigned char*>(P.A[LT.q]) + (size_t)lc * mbytes, mbytes, &B.full[s]);
+        ++nl;
+        progress = true;
+        if (++lc == LT.Kp / TF_KC) {
+          lc = 0;
+          if (++li < my_tiles) LT = tf_tile_of<AXIS>(P, blockIdx.x + li * gridDim.x);
+        }
+      }
+    }
+    // -- consumer: a tile starts once its accumulator is free
+    const int a = ci % nacc;
+    if (!cstarted) {
+      if (ci < nacc || bar_test(&B.acc_empty[a], (uint32_t)(((ci / nacc) - 1) & 1))) {
+        cstarted = 1;
+        progress = true;
+      }
+    }
+    if (cstarted && nc < nl) {
+      const int s = (int)(nc % g.nst);
+      if (bar_test(&B.full[s], (uint32_t)((nc / g.nst) & 1))) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        const TfGeom cg = TfGeom::make(CT.Kp, AXIS);
+        const uint32_t acc = tmem + (uint32_t)(a * 256);
+        const uint32_t st = smem_u32(stages + (size_t)s * g.stage);
+        const uint32_t sm = st + TF_TILE_BYTES;
+#pragma unroll
+        for (int ks = 0; ks < TF_KC / 8; ++ks) {
+          const uint32_t accum = (cc > 0 || ks > 0) ? 1u : 0u;
+          if (AXIS == 0) {
+            // D[m][p] += T[m][k] S[p][k]: A = matrix (K-major, blocks of 128 rows), B = tile
+            // (K-major, N = 128): a k-step of 8 is two core matrices along K
+            const uint64_t db = smem_desc(st + (uint32_t)ks * 256u, 128, 1024);
+            for (int mb = 0; mb < cg.mp / 128; ++mb) {
+              const uint64_t da = smem_desc(sm + (uint32_t)mb * 16u * 1024u + (uint32_t)ks * 256u, 128, 1024);
+              tf_mma(acc + mb * 128, da, db, tf_idesc(TF_P), accum);
+            }
+          } else {
+            // D[p][k] += S[p][j] T[k][j]: A = tile (K-major, M = 128 pencils), B = matrix
+            // (K-major, N = outputs in blocks of up to 256)
+            const uint64_t da = smem_desc(st + (uint32_t)ks * 256u, 128, 1024);
+            for (int n0 = 0; n0 < CT.Kp; n0 += 256) {
+              const int nn = CT.Kp - n0 < 256 ? CT.Kp - n0 : 256;
+              const uint64_t db = smem_desc(sm + (uint32_t)(n0 / 8) * 1024u + (uint32_t)ks * 256u, 128, 1024);
+              tf_mma(acc + n0, da, db, tf_idesc(nn), accum);
+            }
+          }
+        }
+        mma_commit(&B.empty[s]);
+        ++nc;
+        progress = true;
+        if (++cc == CT.Kp / TF_KC) {
+          mma_commit(&B.acc_full[a]);
+          cc = 0;
+          cstarted = 0;
+          if (++ci < my_tiles) CT = tf_tile_of<AXIS>(P, blockIdx.x + ci * gridDim.x);
+        }
+      }
+    }
+    if (progress) {
+      idle = 0;
+    } else if (++idle > 64) {
+      __nanosleep(64);
+      if (idle > UM_SPIN || ((idle & 255) == 0 && *abort)) {
+        *abort = 1;
+        break;
+      }
+    }
+  }
+  // copies still in flight (only after an abort) land, and every MMA completes, before the
+  // CTA frees its TMEM and exits
+  for (long long k = nc; k < nl; ++k) {
+    const int s = (int)(k % g.nst);
+    for (long long it = 0; it < UM_SPIN && !bar_test(&B.full[s], (uint32_t)((k / g.nst) & 1)); ++it) {
+      if (*abort && it > 4096) break;  // a stage whose producers gave up never completes
+      __nanosleep(64);
+    }
+  }
+  if (nc > 0) {
+    mma_commit(B.done);
+    for (long long it = 0; it < UM_SPIN && !bar_test(B.done, 0u); ++it) __nanosleep(64);
+  }
+}
+
+// ---- Green factor along one z line (z forward pass, mode 2) -------------------------------
+// With (kx, ky) fixed the B0 / 2 mu0 denominator 2 mu0 (a0 + a1 + a2) + lam0 a_q is
+// alpha cz + beta sz (each a_i a sum of monomials in the squared sines and cosines, linear in
+// cz and sz); a monomial with a zero factor stays exactly zero, so null denominators stay
+// exact zeros.
+struct TfGreenLine {
+  float alpha, beta, g;
+  __device__ __forceinline__ float at(float sz, float cz) const {
+    const float den = fmaf(alpha, cz, beta * sz);
+    return den > 0.f ? __fdividef(g, den) : 0.f;
+  }
+};
+
+__device__ __forceinline__ TfGreenLine tf_green_line(const TfPassParams& P, int q, int kx, int ky) {
+  const float sx = P.S2[q][0][kx], cx = P.C2[q][0][kx];
+  const float sy = P.S2[q][1][ky], cy = P.C2[q][1][ky];
+  const float t = P.tetra ? 1.f : 0.f;
+  const float c00 = P.hf[0] * sx * cy, c01 = t * P.hf[0] * cx * sy;
+  const float c10 = P.hf[1] * cx * sy, c11 = t * P.hf[1] * sx * cy;
+  const float c20 = t * P.hf[2] * sx * sy, c21 = P.hf[2] * cx * cy;
+  const float aqc = q == 0 ? c00 : (q == 1 ? c10 : c20);
+  const float aqs = q == 0 ? c01 : (q == 1 ? c11 : c21);
+  TfGreenLine G;
+  G.alpha = P.two_mu0 * (c00 + c10 + c20) + P.lam0 * aqc;
+  G.beta = P.two_mu0 * (c01 + c11 + c21) + P.lam0 * aqs;
+  G.g = -P.gscale[q];
+  return G;
+}
+
+// ---- the epilogue (warps 0-7) --------------------------------------------------------------
+// Warp w reads TMEM lanes 32 (w % 4) .. + 31 and takes half h = w / 4 of the accumulator's
+// columns (x: of its M blocks).
+template <int AXIS>
+__device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTile& T, uint32_t acc, int warp,
+                                              int lane) {
+  const int q = T.q, L = T.L, Kp = T.Kp, npen = T.npen;
+  float* __restrict__ out = P.out[q];
+  const float sc = P.scale[q];
+  const int gq = warp & 3, h = warp >> 2;
+  const uint32_t lane_base = (uint32_t)(gq * 32) << 16;
+  if (AXIS == 0) {
+    // lanes are outputs: M index m <-> node x = xb + m; a warp writes 32 consecutive nodes of
+    // one row per store
+    const float* __restrict__ bh = P.base[q];
+    const float* __restrict__ bl = P.base_lo[q];
+    float* __restrict__ ol = P.out_lo[q];
+    const int mp = (Kp + 127) / 128 * 128, xb = T.lo & ~3;
+    const int N2 = P.N[1];
+    const long long sy = P.stride[1], wrap = P.stride[2] - (long long)(N2 - 1) * P.stride[1];
+    for (int mb = h; mb < mp / 128; mb += 2) {
+      const int x = xb + mb * 128 + gq * 32 + lane;
+      const bool ok = x >= T.lo && x < T.lo + L;
+      for (int p0 = 0; p0 < npen; p0 += 32) {
+        float v[32];
+        tmem_ld32(acc + lane_base + (uint32_t)(mb * 128 + p0), v);
+        if (!ok) continue;
+        // row r = row0 + p0 + u of the grid's (y, z) rows: its offset advances by sy, or
+        // wraps to the next z plane
+        int r = T.row0 + p0, y = r % N2;
+        long long row = (long long)y * sy + (long long)(r / N2) * P.stride[2];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          if (p0 + u >= npen) break;
+          const long long at = row + x;
+          row += (++y == N2) ? wrap : sy;
+          if (y == N2) y = 0;
+          const float val = sc * v[u];
+          if (P.mode != 1 || bh == nullptr) {
+            out[at] = val;
+          } else if (ol == nullptr) {
+            out[at] = bh[at] + val;
+          } else {  // (hi, lo) = (bh, bl) + val with an error-free sum of the high parts
+            const float a = bh[at];
+            const float s1 = a + val;
+            const float bs = s1 - a;
+            const float er = (a - (s1 - bs)) + (val - bs);
+            const float tt = bl[at] + er;
+            const float hsum = s1 + tt;
+            out[at] = hsum;
+            ol[at] = tt - (hsum - s1);
+          }
+        }
+      }
+    }
+  } else {
+    // lanes are pencils (consecutive in memory): one coalesced store per output
+    const int p = gq * 32 + lane;
+    const bool live = p < npen;
+    const long long rowbase = T.base0 + p + (long long)T.lo * T.estride;
+    const bool green = AXIS == 2 && P.mode == 2;
+    TfGreenLine G;
+    G.alpha = G.beta = 0.f;
+    G.g = 0.f;
+    bool gl = false;
+    if (green) {
+      const int kx = T.x0 + p - P.flo[q][0], ky = T.other - P.flo[q][1];
+      gl = live && kx >= 0 && kx < P.fL[q][0] && ky >= 0 && ky < P.fL[q][1];
+      G = tf_green_line(P, q, gl ? kx : 0, gl ? ky : 0);
+    }
+    const float* __restrict__ Sz = P.S2[q][2];
+    const float* __restrict__ Cz = P.C2[q][2];
+    const int half = Kp / 2;  // a multiple of 16
+    for (int c0 = h * half; c0 < (h + 1) * half; c0 += 16) {
+      float v[16];
+      tmem_ld16(acc + lane_base + (uint32_t)c0, v);  // warp-collective: every lane takes part
+      if (!live) continue;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int k = c0 + i;
+        if (k >= L) break;
+        float val = sc * v[i];
+        if (green) val = gl ? val * G.at(__ldg(Sz + k), __ldg(Cz + k)) : 0.f;
+        out[rowbase + (long long)k * T.estride] = val;
+      }
+    }
+  }
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_constant__ TfPassParams P, int maxKp) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const TfGeom g = TfGeom::make(maxKp, AXIS);
+  // fixed region (2 KB): barriers, TMEM slot, abort flag; the stages follow
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+  TfBars B;
+  B.full = bars;
+  B.empty = bars + TF_MAXST;
+  B.acc_full = bars + 2 * TF_MAXST;
+  B.acc_empty = bars + 2 * TF_MAXST + 2;
+  B.done = bars + 2 * TF_MAXST + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TF_MAXST + 5);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  unsigned char* stages = smem + 2048;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = tf_total_tiles<AXIS>(P);
+  const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int nacc = 2 * g.acc_cols <= TF_TMEM_COLS ? 2 : 1;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TF_TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < TF_MAXST; ++s) {
+      bar_init(&B.full[s], TF_PROD + 1);
+      bar_init(&B.empty[s], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bar_init(&B.acc_full[i], 1);
+      bar_init(&B.acc_empty[i], TF_EPI);
+    }
+    bar_init(B.done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp >= TF_EPI / 32 && warp < (TF_EPI + TF_PROD) / 32) {
+    // ---- producers: the tile part of every stage ----
+    const int ptid = tid - TF_EPI;
+    long long seq = 0;
+    if (AXIS == 0) {
+      // cp.async copies, TF_LAG stages in flight per thread before the oldest is published
+      long long arrived = 0;
+      bool ok = true;
+      for (int i = 0; i < my_tiles && ok; ++i) {
+        const TfTile T = tf_tile_of<AXIS>(P, blockIdx.x + i * gridDim.x);
+        for (int c = 0; c < T.Kp / TF_KC; ++c) {
+          const int s = (int)(seq % g.nst);
+          const long long u = seq / g.nst;
+          if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) {
+            ok = false;
+            break;
+          }
+          tf_stage_x(P, T, c, smem_u32(stages + (size_t)s * g.stage), ptid);
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+          ++seq;
+          if (seq - arrived > TF_LAG) {  // the oldest stage of this thread has landed: publish it
+            asm volatile("cp.async.wait_group %0;\n" ::"n"(TF_LAG) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            bar_arrive(&B.full[(int)(arrived % g.nst)]);
+            ++arrived;
+          }
+        }
+      }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      for (; arrived < seq; ++arrived) bar_arrive(&B.full[(int)(arrived % g.nst)]);
+    } else {
+      // register blocks, the next stage's loads in flight while this one is transposed
+      TfBlocks cur, nxt;
+      int ti = 0, c = 0;
+      TfTile T;
+      if (my_tiles > 0) {
+        T = tf_tile_of<AXIS>(P, blockIdx.x);
+        tf_load_yz<AXIS>(P, T, 0, ptid, cur);
+      }
+      while (ti < my_tiles) {
+        const int s = (int)(seq % g.nst);
+        const long long u = seq / g.nst;
+        // position of the next stage
+        int nti = ti, nc = c + 1;
+        TfTile NT = T;
+        if (nc == T.Kp / TF_KC) {
+          nc = 0;
+          if (++nti < my_tiles) NT = tf_tile_of<AXIS>(P, blockIdx.x + nti * gridDim.x);
+        }
+        if (nti < my_tiles) tf_load_yz<AXIS>(P, NT, nc, ptid, nxt);
+        if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) break;
+        tf_store_yz(smem_u32(stages + (size_t)s * g.stage), ptid, cur);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        bar_arrive(&B.full[s]);
+        ++seq;
+        cur = nxt;
+        ti = nti;
+        c = nc;
+        T = NT;
+      }
+    }
+  } else if (warp == (TF_EPI + TF_PROD) / 32) {
+    // ---- warp 15: lane 0 copies the matrix chunks and issues the MMAs ----
+    if (lane == 0) tf_mma_thread<AXIS>(P, g, stages, B, tmem, nacc, my_tiles, abort);
+    __syncwarp();
+  } else {
+    // ---- epilogue warps 0-7 ----
+    uint32_t acc_uses[2] = {0u, 0u};
+    for (int i = 0; i < my_tiles; ++i) {
+      const int a = i % nacc;
+      const uint32_t acc = tmem + (uint32_t)(a * 256);
+      const TfTile T = tf_tile_of<AXIS>(P, blockIdx.x + i * gridDim.x);
+      if (!bar_wait(&B.acc_full[a], acc_uses[a] & 1, abort)) break;
+      ++acc_uses[a];
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      tf_store_tile<AXIS>(P, T, acc, warp, lane);
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      bar_arrive(&B.acc_empty[a]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (tid == 0 && *abort) atomicExch(P.err, 1);
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TF_TMEM_COLS));
+}
+
+template <int AXIS>
+static cudaError_t launch_tf32_one(const TfPassParams& P, int maxKp, cudaStream_t s) {
+  const size_t smem = TfGeom::make(maxKp, AXIS).smem();
+  auto kern = k_pass_tf32<AXIS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // one persistent CTA per SM (each holds all 512 TMEM columns)
+  kern<<<dim3((unsigned)(sms > 0 ? sms : 152)), TF_THREADS, smem, s>>>(P, maxKp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_tf32(const TfPassParams& P, cudaStream_t s) {
+  int maxKp = 0;
+  for (int q = 0; q < 3; ++q) {
+    if (!pass_tf32_fits(P.Kp[q], P.axis)) return cudaErrorInvalidValue;
+    maxKp = maxKp > P.Kp[q] ? maxKp : P.Kp[q];
+  }
+  if (P.mode == 1 && P.axis != 0) return cudaErrorInvalidValue;
+  if (P.mode == 2 && P.axis != 2) return cudaErrorInvalidValue;
+  if (P.axis == 0) return launch_tf32_one<0>(P, maxKp, s);
+  if (P.axis == 1) return launch_tf32_one<1>(P, maxKp, s);
+  return launch_tf32_one<2>(P, maxKp, s);
+}
+
+bool pass_tf32_fits(int Kp, int axis) {
+  if (Kp < TF_KC || Kp % TF_KC != 0) return false;
+  const TfGeom g = TfGeom::make(Kp, axis);
+  // the accumulator fits TMEM (x: Mp / 128 blocks of 128 columns; y, z: Kp columns) and the
+  // ring has at least TF_LAG + 1 stages (the producers keep TF_LAG in flight)
+  return g.acc_cols <= TF_TMEM_COLS && g.nst >= TF_LAG + 1 && g.smem() <= (size_t)kMaxDynSmem;
+}
+
+int pass_tf32_rows(int Kp, int axis) { return TfGeom::make(Kp, axis).mp; }
+
+}  // namespace fftm

@@ -28,7 +28,7 @@ FFTM_E_TIMEOUT = -6
 FFTM_BC_PERIODIC, FFTM_BC_DIRICHLET, FFTM_BC_NEUMANN = 0, 1, 2
 FFTM_HEX1, FFTM_TETRA2 = 0, 1
 FFTM_GREEN_B0, FFTM_GREEN_MU0 = 0, 1
-FFTM_FP64, FFTM_FP32, FFTM_FP32_TC = 0, 1, 2
+FFTM_FP64, FFTM_FP32, FFTM_FP32_TC, FFTM_FP32_TF32 = 0, 1, 2, 3
 FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
 FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D, FFTM_FIELD_STATE = 0, 1, 2, 3, 4, 5
 FFTM_OPT_RESIDUAL_PASSES, FFTM_OPT_RESIDUAL_TILE = 0, 1
@@ -214,7 +214,7 @@ def make_desc(n, phase, materials, bc, scheme="HEX1", green="B0", lambda0=0.0, m
     d.lambda0 = float(lambda0)
     d.mu0 = float(mu0)
     d.precision = {"fp64": FFTM_FP64, "fp32": FFTM_FP32, "float32": FFTM_FP32,
-                   "fp32_tc": FFTM_FP32_TC}[precision]
+                   "fp32_tc": FFTM_FP32_TC, "fp32_tf32": FFTM_FP32_TF32}[precision]
     d.tol = float(tol)
     d.max_iter = int(max_iter)
     d.anderson_depth = int(anderson_depth)

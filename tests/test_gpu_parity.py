@@ -508,3 +508,73 @@ def test_tc_solve_matches_fp64_oracle(name):
         assert rel_l2(sym6(_strain(Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:]))), sym6(_strain(pr.last["G"]))) < 1e-5
     finally:
         gp.close()
+
+
+# ---- tensor-core transforms with TF32 operands (FFTM_FP32_TF32) ----
+TF32_TOL = 2e-3  # TF32 products: 11-bit significands, FP32 accumulation
+
+
+@pytest.mark.parametrize("case", range(len(TC_DT_CASES)))
+def test_tf32_dt_forward_and_round_trip(case):
+    n, kinds = TC_DT_CASES[case]
+    wl = _wl(n, _bc_for(*kinds, mix=True))
+    g = Grid(wl.n, wl.bc)
+    gp = GpuProblem(wl, "fp32_tf32")
+    try:
+        rng = np.random.default_rng(case)
+        x = rng.standard_normal(g.node_shape)
+        for q in range(3):
+            x[q][~g.dof_mask(q)] = 0.0
+        gp.set_node(F.FFTM_FIELD_WORK, x)
+        F.fftm_apply(gp.p, F.FFTM_OP_DT_FORWARD)
+        got = gp.get_node(F.FFTM_FIELD_WORK)
+        for q in range(3):
+            ref = oracle_r2r_forward(x[q], g.kind[q], g.n, g.N)
+            assert rel_l2(got[q], ref) < TF32_TOL, (q, g.kind[q])
+        F.fftm_apply(gp.p, F.FFTM_OP_DT_INVERSE)
+        back = gp.get_node(F.FFTM_FIELD_WORK)
+        assert rel_l2(back, x) < TF32_TOL
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("case", [0, 1, 2, 4])
+def test_tf32_green_update(case):
+    n, bc, scheme = RES_CASES[case]
+    wl = _cubic_wl(n, bc, scheme)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, "fp32_tf32")
+    try:
+        rng = np.random.default_rng(case + 20)
+        u = np.zeros(pr.grid.node_shape)
+        for q in range(3):
+            u[q] = rng.standard_normal() * np.sin(np.linspace(0, np.pi, pr.grid.N[0]))[:, None, None]
+            u[q][~pr.grid.dof_mask(q)] = 0.0
+        p = pr.residual(u, 0 * pr.grad_ustar())[0]
+        gp.set_node(F.FFTM_FIELD_WORK, p)
+        F.fftm_apply(gp.p, F.FFTM_OP_GREEN_UPDATE)
+        got = gp.get_node(F.FFTM_FIELD_U)
+        assert rel_l2(got, pr.green_update(p)) < 3 * TF32_TOL
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("name", ["sphere32_hex", "voronoi_tet", "voronoi_hex_mu0"])
+def test_tf32_solve_matches_fp64_oracle(name):
+    """The precision form: TF32 transforms, FP32 fields and residual at tolerance 1e-6 reach the
+    oracle's fields to 1e-5 relative L2 within +-2 of its iteration count."""
+    wl = SOLVE_CASES[name]()
+    wl.tol = 1e-6
+    pr = Problem(wl)
+    uf, rep = pr.solve_step()
+    gp = GpuProblem(wl, "fp32_tf32")
+    try:
+        st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+        assert r["converged"], r
+        assert abs(r["iterations"] - rep.iterations) <= 2, (r["iterations"], rep.iterations)
+        Pg = gp.get_voxel(F.FFTM_FIELD_STRESS)
+        Gg = gp.get_voxel(F.FFTM_FIELD_GRAD)
+        assert rel_l2(Pg, sym6(pr.last["P"])) < 1e-5
+        assert rel_l2(sym6(_strain(Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:]))), sym6(_strain(pr.last["G"]))) < 1e-5
+    finally:
+        gp.close()
