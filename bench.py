@@ -66,6 +66,13 @@ def parse_args(argv=None):
                     help="tensor-core (FP32_TC) path steps timed beside the FP32 path (0 = skip)")
     ap.add_argument("--tf32-steps", type=int, default=3,
                     help="TF32 tensor-core (FP32_TF32) path steps timed beside the FP32 path (0 = skip)")
+    ap.add_argument("--workload", choices=["polycrystal", "sphere_inclusion", "sphere_bending", "cp_torsion_bending"],
+                    default="polycrystal",
+                    help="polycrystal: the headline step; the others print one line per precision arm for the "
+                         "32^3 sphere inclusion (FP64, tol 1e-8), the 128^3 J2 sphere composite under 20 bending "
+                         "steps and the 128^3 crystal-plasticity polycrystal under 30 torsion-bending increments")
+    ap.add_argument("--arms", default="",
+                    help="comma-separated precisions of a --workload scenario (default: per scenario)")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream (mixed sizes/BCs/laws, Poisson arrivals): solves/s and p50/p99 latency")
     ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream (--serve)")
@@ -587,12 +594,95 @@ def serve_arm(args):
     return 0
 
 
+def scenario(name, n=None):
+    """(workload, loads, default arms, description) of a --workload scenario."""
+    import synthetic as syn
+
+    if name == "sphere_inclusion":
+        wl = syn.sphere_inclusion_32(n=n or 32)
+        return wl, [(wl.A, wl.b, wl.Q)], ["fp64", "fp32"], (
+            f"sphere_inclusion_{wl.n[0]}: {wl.n[0]}^3, centred sphere r = n/4, E 1 / 10, nu 0.3, HEX1, B0, "
+            "x Dirichlet / y Neumann / z periodic, eps_xx = 1e-3, tol 1e-8")
+    if name == "sphere_bending":
+        wl, loads = syn.sphere_composite_bending(n or 128)
+        return wl, loads, ["fp64", "fp32", "fp32_tf32", "fp32_tc"], (
+            f"sphere_composite_bending_{wl.n[0]}: {wl.n[0]}^3, random spheres 30 %, r in [4, 10], J2 matrix "
+            "(E 200 GPa, nu 0.3, sigma_y 0.3 GPa, H 2 GPa), elastic particles, HEX1, B0, 20 bending steps "
+            "(theta up to 0.012), x Dirichlet / y, z Neumann, tol 1e-6")
+    if name == "cp_torsion_bending":
+        wl, loads = syn.cp_polycrystal_torsion_bending(n or 128)
+        return wl, loads, ["fp32", "fp32_tf32"], (
+            f"cp_polycrystal_torsion_bending_{wl.n[0]}: {wl.n[0]}^3, 200-grain Voronoi FCC crystal plasticity "
+            "(12 {111}<110> systems, n 20, gdot0 1e-3/s, Voce 30/90/300 MPa), TETRA2, B0, 30 torsion-bending "
+            "increments (phi 0.05, theta 0.02), x Dirichlet / y, z Neumann, tol 1e-6, finite strain")
+    raise ValueError(name)
+
+
+def scenario_arm(args):
+    """A whole load history of one scenario per precision arm on one GPU: voxel-iterations/s over
+    the history (CUDA events on the library's stream), iterations per step, and each FP32 arm's
+    final stresses against the FP64 arm's (relative L2) when both ran."""
+    import torch
+
+    from paper_2607_05929_gb300 import build as libbuild
+    from paper_2607_05929_gb300 import fftm as F
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the GPU arm has no CPU fallback")
+    wl, loads, arms, desc = scenario(args.workload, args.n if args.n != 256 else None)
+    if args.arms:
+        arms = [a.strip() for a in args.arms.split(",") if a.strip()]
+    libbuild.build()
+    F.load_library()
+    stream = torch.cuda.Stream()
+    ctx = F.fftm_ctx_create(0, stream)
+    mats = [(m.law, m.params, m.quat) for m in wl.materials]
+    nvox = wl.n[0] * wl.n[1] * wl.n[2]
+    npp = 2 if wl.scheme == "TETRA2" else 1
+    results = {}
+    for prec in arms:
+        d, keep = F.make_desc(wl.n, wl.phase, mats, wl.bc, scheme=wl.scheme, green=wl.green, lambda0=wl.lambda0,
+                              mu0=wl.mu0, precision=prec, tol=wl.tol, max_iter=wl.max_iter, h=wl.h)
+        p = F.fftm_problem_create(ctx, d)
+        its, accs, conv = [], [], []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for A, b, Q in loads:
+            F.fftm_set_load(p, A, b, Q)
+            st, r, _, _ = F.fftm_solve_step(p)
+            its.append(r["iterations"])
+            accs.append(r["n_accelerated"])
+            conv.append(bool(r["converged"]))
+        e1.record(stream)
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1000.0
+        nb = F.fftm_field_bytes(p, F.FFTM_FIELD_STRESS)
+        S = np.zeros(nb // (8 if prec == "fp64" else 4), dtype=np.float64 if prec == "fp64" else np.float32)
+        F.fftm_get_field(p, F.FFTM_FIELD_STRESS, S)
+        F.fftm_problem_destroy(p)
+        results[prec] = S.astype(np.float64)
+        line = {"metric": METRIC, "value": nvox * sum(its) / sec, "unit": UNIT, "n_gpus": 1,
+                "higher_is_better": True, "dtype": "f64" if prec == "fp64" else "f32", "data": "synthetic",
+                "precision": prec, "seconds": sec, "steps": len(loads), "iterations_total": int(sum(its)),
+                "iterations_per_step": its, "anderson_steps_per_step": accs, "all_converged": all(conv),
+                "voxel_points": nvox * npp, "config": {"workload": desc}}
+        if "fp64" in results and prec != "fp64":
+            ref = results["fp64"]
+            line["final_stress_rel_l2_vs_fp64"] = float(np.linalg.norm(results[prec] - ref) / np.linalg.norm(ref))
+        print(json.dumps(line), flush=True)
+    F.fftm_ctx_destroy(ctx)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return reference_arm(args)
     if args.serve:
         return serve_arm(args)
+    if args.workload != "polycrystal":
+        return scenario_arm(args)
     return gpu_arm(args)
 
 

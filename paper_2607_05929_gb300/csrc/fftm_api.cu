@@ -217,6 +217,19 @@ void dense_inverse(int kind, int n, std::vector<double>* M) {
     }
 }
 
+// Round to TF32 (10 explicit significand bits; nearest, ties to even) from FP64 through FP32,
+// so that the tensor cores read the matrix entries exactly.
+float to_tf32(double d) {
+  const float f = (float)d;
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  b += 0xFFFu + ((b >> 13) & 1u);
+  b &= ~0x1FFFu;
+  float r;
+  std::memcpy(&r, &b, 4);
+  return r;
+}
+
 // Round to BF16 (nearest, ties to even) from FP64 through FP32.
 uint16_t to_bf16(double d) {
   const float f = (float)d;
@@ -1423,7 +1436,7 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
           const int m = r0 + sh, c = c0 + sh;
           const int ch = c / 32, jj = c % 32;
           const size_t at = (size_t)ch * R * 32 + (size_t)(m >> 3) * 256 + (jj >> 2) * 32 + (m & 7) * 4 + (jj & 3);
-          mats[off + at] = (float)M[(size_t)r0 * L + c0];
+          mats[off + at] = to_tf32(M[(size_t)r0 * L + c0]);
         }
       return off * sizeof(float);
     };

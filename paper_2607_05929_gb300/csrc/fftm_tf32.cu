@@ -17,8 +17,9 @@
 // pencils, K-major); TMEM lanes are outputs and a warp stores 32 consecutive nodes of a row.
 //
 // The contraction dimension streams through a ring of shared-memory stages, each holding
-// 32 K-columns of the tile (filled by seven producer warps: 16-byte cp.async copies on x,
-// transposed 4 x 4 blocks on y and z) and of the matrix (one bulk copy).  One thread issues the MMAs
+// 32 K-columns of the tile (filled by seven producer warps from 16-byte loads, transposed in
+// 4 x 4 blocks on y and z and rounded to the nearest TF32) and of the matrix (one bulk copy,
+// entries rounded to TF32 on the host).  One thread issues the MMAs
 // of a stage as soon as both halves have landed and releases the stage when they have read
 // it; eight epilogue warps drain the TMEM accumulators (two, alternating, when they fit)
 // while the next tile is contracted.  Every wait is bounded: past the limit the CTA records
@@ -34,7 +35,6 @@ constexpr int TF_EPI = 256;    // epilogue threads (warps 0-7)
 constexpr int TF_PROD = 224;   // producer threads (warps 8-14)
 constexpr int TF_THREADS = TF_EPI + TF_PROD + 32;  // warp 15: matrix copies and MMAs (lane 0)
 constexpr int TF_MAXST = 8;
-constexpr int TF_LAG = 2;      // stages a producer keeps in flight before completing the oldest
 constexpr int TF_TMEM_COLS = 512;
 constexpr uint32_t TF_TILE_BYTES = TF_P * TF_KC * 4;
 
@@ -51,12 +51,6 @@ __device__ __forceinline__ void tf_mma(uint32_t tmem, uint64_t da, uint64_t db, 
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void st_zero16(uint32_t saddr) {
-  asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};\n" ::"r"(saddr), "r"(0u) : "memory");
-}
 
 // Shared-memory geometry for a padded transform length Kp (a multiple of 32).
 struct TfGeom {
@@ -144,66 +138,89 @@ __device__ __forceinline__ int tf_total_tiles(const TfPassParams& P) {
 //  x axis: 1024 pieces (row p, group g) of 4 consecutive x, copied with 16-byte cp.async.
 //  y, z axes: 256 blocks (pencil group pg, row group kq) of 4 pencils x 4 rows, loaded as
 //    four 16-byte rows and transposed in registers (each pencil's 4 K values in one store).
-__device__ __forceinline__ void tf_stage_x(const TfPassParams& P, const TfTile& T, int c, uint32_t sdst, int ptid) {
-  const float* __restrict__ in = P.in[T.q];
-  const long long PX = P.stride[1];  // row pitch (a multiple of 8, >= N1)
-  const int N2 = P.N[1];
-  const long long sy = P.stride[1], sz = P.stride[2];
-  const int xb = T.lo & ~3;
-  for (int i = ptid; i < TF_P * 8; i += TF_PROD) {
-    const int p = i >> 3, gq = i & 7;
-    const int x = xb + TF_KC * c + 4 * gq;
-    const uint32_t d = sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)gq * 128u + (uint32_t)(p & 7) * 16u;
-    if (p < T.npen && x < PX) {
-      const int r = T.row0 + p;
-      cp_async16(d, in + (long long)(r % N2) * sy + (long long)(r / N2) * sz + x);
-    } else {
-      st_zero16(d);
-    }
-  }
-}
+constexpr int TF_XPC = 5;  // x axis: 16-byte pieces per producer thread and stage (1024 pieces, 224 threads)
 
 constexpr int TF_BLK = 2;  // 4 x 4 blocks per producer thread and stage (256 blocks, 224 threads)
 
+// FP32 -> the nearest TF32 value (ties away from zero), kept in an FP32 register
+__device__ __forceinline__ float tf32r(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 struct TfBlocks {
-  float4 v[TF_BLK][4];
+  float4 v[8];  // y, z: TF_BLK blocks of 4 rows; x: TF_XPC pieces
 };
 
 template <int AXIS>
-__device__ __forceinline__ void tf_load_yz(const TfPassParams& P, const TfTile& T, int c, int ptid, TfBlocks& B) {
+__device__ __forceinline__ void tf_load(const TfPassParams& P, const TfTile& T, int c, int ptid, TfBlocks& B) {
   const float* __restrict__ in = P.in[T.q];
-  const long long PX = P.stride[1];
-  const int Nax = P.N[AXIS];
+  const long long PX = P.stride[1];  // row pitch (a multiple of 8, >= N1)
+  if (AXIS == 0) {
+    const int N2 = P.N[1];
+    const long long sy = P.stride[1], sz = P.stride[2];
+    const int xb = T.lo & ~3;
 #pragma unroll
-  for (int b = 0; b < TF_BLK; ++b) {
-    const int i = ptid + b * TF_PROD;
-    const int pg = i & 31, kq = i >> 5;
+    for (int k = 0; k < TF_XPC; ++k) {
+      const int i = ptid + k * TF_PROD;
+      const int p = i >> 3, gq = i & 7;
+      const int x = xb + TF_KC * c + 4 * gq;
+      const int r = T.row0 + p;
+      const bool ok = i < TF_P * 8 && p < T.npen && x < PX;
+      B.v[k] = ok ? __ldg(reinterpret_cast<const float4*>(in + (long long)(r % N2) * sy + (long long)(r / N2) * sz + x))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else {
+    const int Nax = P.N[AXIS];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int row = T.lo + TF_KC * c + 4 * kq + r;
-      const bool ok = i < 256 && row < Nax && T.x0 + 4 * pg < PX;
-      B.v[b][r] = ok ? __ldg(reinterpret_cast<const float4*>(in + T.base0 + (long long)row * T.estride + 4 * pg))
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int b = 0; b < TF_BLK; ++b) {
+      const int i = ptid + b * TF_PROD;
+      const int pg = i & 31, kq = i >> 5;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = T.lo + TF_KC * c + 4 * kq + r;
+        const bool ok = i < 256 && row < Nax && T.x0 + 4 * pg < PX;
+        B.v[4 * b + r] = ok ? __ldg(reinterpret_cast<const float4*>(in + T.base0 + (long long)row * T.estride + 4 * pg))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
   }
 }
 
-__device__ __forceinline__ void tf_store_yz(uint32_t sdst, int ptid, const TfBlocks& B) {
+__device__ __forceinline__ void st_shared4(uint32_t d, float a, float b, float c, float e) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(d), "f"(a), "f"(b), "f"(c), "f"(e) : "memory");
+}
+
+// Stores a stage's tile part, every value rounded to the nearest TF32 (the tensor cores would
+// drop the low bits instead).
+template <int AXIS>
+__device__ __forceinline__ void tf_store(uint32_t sdst, int ptid, const TfBlocks& B) {
+  if (AXIS == 0) {
 #pragma unroll
-  for (int b = 0; b < TF_BLK; ++b) {
-    const int i = ptid + b * TF_PROD;
-    if (i >= 256) continue;
-    const int pg = i & 31, kq = i >> 5;
-    const float4* v = B.v[b];
-    const float4 w[4] = {make_float4(v[0].x, v[1].x, v[2].x, v[3].x), make_float4(v[0].y, v[1].y, v[2].y, v[3].y),
-                         make_float4(v[0].z, v[1].z, v[2].z, v[3].z), make_float4(v[0].w, v[1].w, v[2].w, v[3].w)};
+    for (int k = 0; k < TF_XPC; ++k) {
+      const int i = ptid + k * TF_PROD;
+      if (i >= TF_P * 8) continue;
+      const int p = i >> 3, gq = i & 7;
+      const float4 v = B.v[k];
+      st_shared4(sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)gq * 128u + (uint32_t)(p & 7) * 16u, tf32r(v.x),
+                 tf32r(v.y), tf32r(v.z), tf32r(v.w));
+    }
+  } else {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int p = 4 * pg + e;
-      const uint32_t d = sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)kq * 128u + (uint32_t)(p & 7) * 16u;
-      asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(d), "f"(w[e].x), "f"(w[e].y), "f"(w[e].z),
-                   "f"(w[e].w)
-                   : "memory");
+    for (int b = 0; b < TF_BLK; ++b) {
+      const int i = ptid + b * TF_PROD;
+      if (i >= 256) continue;
+      const int pg = i & 31, kq = i >> 5;
+      const float4* v = B.v + 4 * b;
+      const float4 w[4] = {make_float4(v[0].x, v[1].x, v[2].x, v[3].x), make_float4(v[0].y, v[1].y, v[2].y, v[3].y),
+                           make_float4(v[0].z, v[1].z, v[2].z, v[3].z), make_float4(v[0].w, v[1].w, v[2].w, v[3].w)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int p = 4 * pg + e;
+        st_shared4(sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)kq * 128u + (uint32_t)(p & 7) * 16u,
+                   tf32r(w[e].x), tf32r(w[e].y), tf32r(w[e].z), tf32r(w[e].w));
+      }
     }
   }
 }
@@ -485,66 +502,36 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
   const uint32_t tmem = *tmem_slot;
 
   if (warp >= TF_EPI / 32 && warp < (TF_EPI + TF_PROD) / 32) {
-    // ---- producers: the tile part of every stage ----
+    // ---- producers: the tile part of every stage, the next stage's loads in flight while
+    // this one is rounded and stored ----
     const int ptid = tid - TF_EPI;
     long long seq = 0;
-    if (AXIS == 0) {
-      // cp.async copies, TF_LAG stages in flight per thread before the oldest is published
-      long long arrived = 0;
-      bool ok = true;
-      for (int i = 0; i < my_tiles && ok; ++i) {
-        const TfTile T = tf_tile_of<AXIS>(P, blockIdx.x + i * gridDim.x);
-        for (int c = 0; c < T.Kp / TF_KC; ++c) {
-          const int s = (int)(seq % g.nst);
-          const long long u = seq / g.nst;
-          if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) {
-            ok = false;
-            break;
-          }
-          tf_stage_x(P, T, c, smem_u32(stages + (size_t)s * g.stage), ptid);
-          asm volatile("cp.async.commit_group;\n" ::: "memory");
-          ++seq;
-          if (seq - arrived > TF_LAG) {  // the oldest stage of this thread has landed: publish it
-            asm volatile("cp.async.wait_group %0;\n" ::"n"(TF_LAG) : "memory");
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            bar_arrive(&B.full[(int)(arrived % g.nst)]);
-            ++arrived;
-          }
-        }
+    TfBlocks cur, nxt;
+    int ti = 0, c = 0;
+    TfTile T;
+    if (my_tiles > 0) {
+      T = tf_tile_of<AXIS>(P, blockIdx.x);
+      tf_load<AXIS>(P, T, 0, ptid, cur);
+    }
+    while (ti < my_tiles) {
+      const int s = (int)(seq % g.nst);
+      const long long u = seq / g.nst;
+      int nti = ti, nc = c + 1;  // position of the next stage
+      TfTile NT = T;
+      if (nc == T.Kp / TF_KC) {
+        nc = 0;
+        if (++nti < my_tiles) NT = tf_tile_of<AXIS>(P, blockIdx.x + nti * gridDim.x);
       }
-      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      if (nti < my_tiles) tf_load<AXIS>(P, NT, nc, ptid, nxt);
+      if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) break;
+      tf_store<AXIS>(smem_u32(stages + (size_t)s * g.stage), ptid, cur);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      for (; arrived < seq; ++arrived) bar_arrive(&B.full[(int)(arrived % g.nst)]);
-    } else {
-      // register blocks, the next stage's loads in flight while this one is transposed
-      TfBlocks cur, nxt;
-      int ti = 0, c = 0;
-      TfTile T;
-      if (my_tiles > 0) {
-        T = tf_tile_of<AXIS>(P, blockIdx.x);
-        tf_load_yz<AXIS>(P, T, 0, ptid, cur);
-      }
-      while (ti < my_tiles) {
-        const int s = (int)(seq % g.nst);
-        const long long u = seq / g.nst;
-        // position of the next stage
-        int nti = ti, nc = c + 1;
-        TfTile NT = T;
-        if (nc == T.Kp / TF_KC) {
-          nc = 0;
-          if (++nti < my_tiles) NT = tf_tile_of<AXIS>(P, blockIdx.x + nti * gridDim.x);
-        }
-        if (nti < my_tiles) tf_load_yz<AXIS>(P, NT, nc, ptid, nxt);
-        if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) break;
-        tf_store_yz(smem_u32(stages + (size_t)s * g.stage), ptid, cur);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        bar_arrive(&B.full[s]);
-        ++seq;
-        cur = nxt;
-        ti = nti;
-        c = nc;
-        T = NT;
-      }
+      bar_arrive(&B.full[s]);
+      ++seq;
+      cur = nxt;
+      ti = nti;
+      c = nc;
+      T = NT;
     }
   } else if (warp == (TF_EPI + TF_PROD) / 32) {
     // ---- warp 15: lane 0 copies the matrix chunks and issues the MMAs ----
@@ -602,8 +589,8 @@ bool pass_tf32_fits(int Kp, int axis) {
   if (Kp < TF_KC || Kp % TF_KC != 0) return false;
   const TfGeom g = TfGeom::make(Kp, axis);
   // the accumulator fits TMEM (x: Mp / 128 blocks of 128 columns; y, z: Kp columns) and the
-  // ring has at least TF_LAG + 1 stages (the producers keep TF_LAG in flight)
-  return g.acc_cols <= TF_TMEM_COLS && g.nst >= TF_LAG + 1 && g.smem() <= (size_t)kMaxDynSmem;
+  // ring has at least three stages
+  return g.acc_cols <= TF_TMEM_COLS && g.nst >= 3 && g.smem() <= (size_t)kMaxDynSmem;
 }
 
 int pass_tf32_rows(int Kp, int axis) { return TfGeom::make(Kp, axis).mp; }

@@ -37,4 +37,5 @@ from .workloads import (  # noqa: F401
     bending_load,
     torsion_bending_load,
     sphere_composite_bending,
+    cp_polycrystal_torsion_bending,
 )

@@ -190,3 +190,30 @@ def sphere_composite_bending(n=128, fraction=0.30, r_min=4.0, r_max=10.0, seed=4
     loads = [bending_load(nn, wl.h, k * theta_max / steps) for k in range(1, steps + 1)]
     wl.A, wl.b, wl.Q = loads[0]
     return wl, loads
+
+
+CP_FCC_PARAMS = (168.0, 121.0, 75.0, 1e-3, 20.0, 0.03, 0.09, 0.3, 1.0)  # C11 C12 C44 gdot0 n tau0 tau_inf h0 dt
+
+
+def cp_polycrystal_torsion_bending(n=128, grains=200, seed_geom=5, seed_orient=6, increments=30, phi_final=0.05,
+                                   theta_final=0.02, scheme="TETRA2", tol=1e-6):
+    """Finite-strain FCC crystal plasticity (power-law slip n = 20, gdot0 = 1e-3/s, Voce hardening
+    tau0 = 30 MPa, tau_inf = 90 MPa, h0 = 300 MPa; C11/C12/C44 = 168/121/75 GPa; one increment of
+    1 s per load step) on a Voronoi polycrystal (grain seeds uniform in the box, seed 5; orientations
+    uniform on SO(3), seed 6).  x = 0 at rest, the x = L1 face turned by the torsion-bending rotation
+    R_3(theta) R_1(phi) with (phi, theta) = k (phi_final, theta_final) / increments, k = 1..increments;
+    y and z traction-free; B0 with lambda0 = C12, mu0 = (C44 + (C11 - C12)/2)/2.
+    Returns (workload, loads)."""
+    nn = (n, n, n) if np.isscalar(n) else tuple(n)
+    phase, _ = voronoi(nn, grains, seed_geom)
+    quats = shoemake_quaternions(grains, seed_orient)
+    mats = [Material(CP_FCC, CP_FCC_PARAMS, tuple(q)) for q in quats]
+    C11, C12, C44 = CP_FCC_PARAMS[:3]
+    wl = Workload(name=f"cp_polycrystal_torsion_bending_{nn[0]}", n=nn, phase=phase, materials=mats,
+                  bc=axis_bc("D", "N", "N"), scheme=scheme, green="B0", lambda0=C12,
+                  mu0=0.5 * (C44 + 0.5 * (C11 - C12)), tol=tol, max_iter=3000)
+    loads = [torsion_bending_load(nn, wl.h, k * phi_final / increments, k * theta_final / increments)
+             for k in range(1, increments + 1)]
+    wl.A, wl.b, wl.Q = loads[0]
+    return wl, loads
+

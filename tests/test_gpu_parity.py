@@ -511,7 +511,8 @@ def test_tc_solve_matches_fp64_oracle(name):
 
 
 # ---- tensor-core transforms with TF32 operands (FFTM_FP32_TF32) ----
-TF32_TOL = 2e-3  # TF32 products: 11-bit significands, FP32 accumulation
+TF32_TOL = 2e-3  # one 3D transform with TF32 products (11-bit significands), FP32 accumulation
+TF32_RT_TOL = 5e-3  # forward and inverse: six axis passes
 
 
 @pytest.mark.parametrize("case", range(len(TC_DT_CASES)))
@@ -533,7 +534,7 @@ def test_tf32_dt_forward_and_round_trip(case):
             assert rel_l2(got[q], ref) < TF32_TOL, (q, g.kind[q])
         F.fftm_apply(gp.p, F.FFTM_OP_DT_INVERSE)
         back = gp.get_node(F.FFTM_FIELD_WORK)
-        assert rel_l2(back, x) < TF32_TOL
+        assert rel_l2(back, x) < TF32_RT_TOL
     finally:
         gp.close()
 
