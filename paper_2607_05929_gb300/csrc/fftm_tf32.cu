@@ -398,28 +398,49 @@ __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTil
         if (!ok) continue;
         // row r = row0 + p0 + u of the grid's (y, z) rows: its offset advances by sy, or
         // wraps to the next z plane
-        int r = T.row0 + p0, y = r % N2;
-        long long row = (long long)y * sy + (long long)(r / N2) * P.stride[2];
+        int y = (T.row0 + p0) % N2;
+        int row = y * (int)sy + ((T.row0 + p0) / N2) * (int)P.stride[2];  // within one component array
+        const int wr = (int)wrap, syi = (int)sy;
+        int at[32];
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
-          if (p0 + u >= npen) break;
-          const long long at = row + x;
-          row += (++y == N2) ? wrap : sy;
+          at[u] = row + x;
+          row += (++y == N2) ? wr : syi;
           if (y == N2) y = 0;
-          const float val = sc * v[u];
-          if (P.mode != 1 || bh == nullptr) {
-            out[at] = val;
-          } else if (ol == nullptr) {
-            out[at] = bh[at] + val;
-          } else {  // (hi, lo) = (bh, bl) + val with an error-free sum of the high parts
-            const float a = bh[at];
-            const float s1 = a + val;
-            const float bs = s1 - a;
-            const float er = (a - (s1 - bs)) + (val - bs);
-            const float tt = bl[at] + er;
-            const float hsum = s1 + tt;
-            out[at] = hsum;
-            ol[at] = tt - (hsum - s1);
+        }
+        const bool acc_mode = P.mode == 1 && bh != nullptr;
+        if (!acc_mode) {
+#pragma unroll
+          for (int u = 0; u < 32; ++u)
+            if (p0 + u < npen) out[at[u]] = sc * v[u];
+        } else {
+#pragma unroll
+          for (int h16 = 0; h16 < 32; h16 += 16) {
+            // the base values of 16 rows are loaded before the first sum (loads in flight together)
+            float a[16], b[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const bool live = p0 + h16 + u < npen;
+              a[u] = live ? bh[at[h16 + u]] : 0.f;
+              b[u] = (live && ol) ? bl[at[h16 + u]] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              if (p0 + h16 + u >= npen) continue;
+              const int o = at[h16 + u];
+              const float val = sc * v[h16 + u];
+              if (ol == nullptr) {
+                out[o] = a[u] + val;
+              } else {  // (hi, lo) = (bh, bl) + val with an error-free sum of the high parts
+                const float s1 = a[u] + val;
+                const float bs = s1 - a[u];
+                const float er = (a[u] - (s1 - bs)) + (val - bs);
+                const float tt = b[u] + er;
+                const float hsum = s1 + tt;
+                out[o] = hsum;
+                ol[o] = tt - (hsum - s1);
+              }
+            }
           }
         }
       }
@@ -443,15 +464,24 @@ __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTil
     const float* __restrict__ Cz = P.C2[q][2];
     const int half = Kp / 2;  // a multiple of 16
     for (int c0 = h * half; c0 < (h + 1) * half; c0 += 16) {
+      float zs[16], zc[16];
+      if (green) {  // the z factors of these 16 outputs, loaded before the TMEM read
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int k = min(c0 + i, L - 1);
+          zs[i] = __ldg(Sz + k);
+          zc[i] = __ldg(Cz + k);
+        }
+      }
       float v[16];
       tmem_ld16(acc + lane_base + (uint32_t)c0, v);  // warp-collective: every lane takes part
       if (!live) continue;
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int k = c0 + i;
-        if (k >= L) break;
+        if (k >= L) continue;
         float val = sc * v[i];
-        if (green) val = gl ? val * G.at(__ldg(Sz + k), __ldg(Cz + k)) : 0.f;
+        if (green) val = gl ? val * G.at(zs[i], zc[i]) : 0.f;
         out[rowbase + (long long)k * T.estride] = val;
       }
     }

@@ -110,3 +110,41 @@ def test_admission_respects_the_memory_budget_and_refuses_oversize():
             F.fftm_server_submit(srv, big[0], loads)  # far more than the budget
     finally:
         F.fftm_server_destroy(srv)
+
+
+def test_served_results_match_the_fp64_oracle():
+    """Every small served request, solved in the mix on four slots, against the FP64 oracle run
+    through the same load steps: the mean stress of the last step to 1e-5 relative, the final
+    u^f to 3e-5 (at tolerance 1e-6 each side's u^f lies within ~4e-6 of the converged field,
+    measured on these requests), the iteration count within +-2 per load step."""
+    from oracle.solver import Problem
+
+    reqs = _requests(6, max_side=32)
+    mixed, u_mixed = _run(reqs, 4, False)
+    for i, (wl, loads) in enumerate(reqs):
+        pr = Problem(wl)
+        iters = 0
+        for A, b, Q in loads:
+            _, rep = pr.solve_step(A=A, b=b, Q=Q, tol=wl.tol)
+            assert rep.converged
+            iters += rep.iterations
+        r = mixed[i]
+        assert r["status"] == F.FFTM_OK and r["converged_steps"] == len(loads), r
+        assert abs(r["iterations"] - iters) <= 2 * len(loads), (i, r["iterations"], iters)
+        u = np.asarray(u_mixed[i], dtype=np.float64).transpose(0, 3, 2, 1)
+        assert np.linalg.norm(u - pr.uf) <= 3e-5 * np.linalg.norm(pr.uf), i
+        Pm = pr.last["P"].mean(axis=(0, 3, 4, 5))
+        ref = np.array([Pm[0, 0], Pm[1, 1], Pm[2, 2], Pm[1, 2], Pm[0, 2], Pm[0, 1]])
+        assert np.linalg.norm(r["mean_P"] - ref) <= 1e-5 * np.linalg.norm(ref), (i, r["mean_P"], ref)
+
+
+def test_server_runs_on_the_workers_that_started():
+    """One of two workers fails at start (injected on the host): the server keeps serving on
+    the other, and every result is still correct."""
+    reqs = _requests(2)
+    F.fftm_server_inject_start_failures(1)
+    try:
+        res, _ = _run(reqs, 2, False)
+    finally:
+        F.fftm_server_inject_start_failures(0)
+    assert all(r["status"] == F.FFTM_OK for r in res.values())
