@@ -252,8 +252,16 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
                              fftm_tuning_table lists the choices).  Both forms give the same D;
                              problems with other laws always take two passes.
    FFTM_OPT_RESIDUAL_TILE    the one-pass form's voxel tile height: 8 or 16 rows of 32
-                             voxels per thread block, or 0 (default) = measured, as above. */
-enum fftm_option { FFTM_OPT_RESIDUAL_PASSES = 0, FFTM_OPT_RESIDUAL_TILE = 1 };
+                             voxels per thread block, or 0 (default) = measured, as above.
+   FFTM_OPT_DEVICE_LOOP      1 (default): the convergence test of each iteration (Eq.
+                             equilibrium_condition against tol, the iteration limit, non-finite
+                             norms) runs on the device; the host enqueues the iterations in
+                             chunks of four and waits once per chunk, and the launches of a chunk
+                             that follow the iteration that stopped the step do nothing.  0: the
+                             host reads the norms after every residual.  Loads with a
+                             normal-mixed part always take the host path (their free strain
+                             components are updated on the host).  Both give the same iterates. */
+enum fftm_option { FFTM_OPT_RESIDUAL_PASSES = 0, FFTM_OPT_RESIDUAL_TILE = 1, FFTM_OPT_DEVICE_LOOP = 2 };
 int fftm_set_option(fftm_problem* p, int option, int value);
 
 /* The launch-shape choices the library has measured in this process, one line per shape

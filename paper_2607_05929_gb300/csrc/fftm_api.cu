@@ -305,8 +305,16 @@ struct fftm_problem {
   bool prof = false;
   std::vector<cudaEvent_t> ev;
   std::vector<int> ev_free;
-  struct Pending { int cat, a, b; };
+  struct Pending { int cat, a, b, m, post; };
   std::vector<Pending> pending;
+  int prof_m = -1, prof_post = 0;  // iteration tag of the launches being enqueued (device loop)
+  // device-decided load steps (every load without a normal-mixed part): the convergence test
+  // runs on the device and the host waits once per chunk of iterations
+  int dev_loop = 1;                // FFTM_OPT_DEVICE_LOOP
+  int* dctl = nullptr;             // control block of k_check: stop, next iteration, last checked
+  double* derr = nullptr;          // per-iteration errors of the step (device)
+  int derr_len = 0;
+  const int* stop = nullptr;       // dctl while a device-decided step is being enqueued, else null
   double prof_ms[FFTM_KCAT_COUNT] = {0, 0, 0, 0, 0, 0};
   long long prof_cnt[FFTM_KCAT_COUNT] = {0, 0, 0, 0, 0, 0};
 };
@@ -355,15 +363,19 @@ struct ProfScope {
     const int b = ev_get(p);
     if (b < 0) return;
     cudaEventRecord(p->ev[b], p->ctx->stream);
-    p->pending.push_back({cat, a, b});
+    p->pending.push_back({cat, a, b, p->prof_m, p->prof_post});
   }
 };
 
-// Accumulate the elapsed times of completed event pairs (call after a stream sync).
-void prof_flush(fftm_problem* p) {
+// Accumulate the elapsed times of completed event pairs (call after a stream sync).  In a
+// device-decided step, launches enqueued past the iteration the step stopped at did no work:
+// with m_last >= 0 only the pairs of iterations up to it count (for the last iteration, only
+// its residual and check).
+void prof_flush(fftm_problem* p, int m_last = -1) {
   for (const auto& e : p->pending) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, p->ev[e.a], p->ev[e.b]) == cudaSuccess) {
+    const bool count = m_last < 0 || e.m < 0 || e.m < m_last || (e.m == m_last && !e.post);
+    if (count && cudaEventElapsedTime(&ms, p->ev[e.a], p->ev[e.b]) == cudaSuccess) {
       p->prof_ms[e.cat] += ms;
       p->prof_cnt[e.cat] += 1;
     }
@@ -434,6 +446,7 @@ PassParams<T> pass_params(fftm_problem* p, int axis, int inverse, int fused, int
   P.lam0 = T(lam0);
   P.tetra = p->tetra;
   for (int q = 0; q < 3; ++q) P.gscale[q] = T(1.0 / (axis_norm(p, q, 0) * axis_norm(p, q, 1) * axis_norm(p, q, 2)));
+  P.stop = p->stop;
   return P;
 }
 
@@ -488,6 +501,7 @@ TcPassParams tc_params(fftm_problem* p, int axis, int inverse, int fused, int in
   P.lam0 = (float)lam0;
   P.tetra = p->tetra;
   P.err = p->tc_err;
+  P.stop = p->stop;
   return P;
 }
 
@@ -535,6 +549,7 @@ TfPassParams tf_params(fftm_problem* p, int axis, int inverse, int mode, int in_
   P.lam0 = (float)lam0;
   P.tetra = p->tetra;
   P.err = p->tc_err;
+  P.stop = p->stop;
   return P;
 }
 
@@ -586,6 +601,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
       R.hi[q][a] = p->hi[q][a];
     }
   R.partial = p->partial;
+  R.stop = p->stop;
   R.two_pass = p->res_two_pass > 0 ? 1 : 0;
   R.fused_fy = p->res_fy;
   R.vs = reinterpret_cast<T*>(p->vs);
@@ -769,8 +785,12 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
   int blocks = 0;
   ProfScope ps(p, test_outputs ? FFTM_KCAT_OTHER : FFTM_KCAT_RESIDUAL);
   CU(launch_residual<T>(R, p->tetra, test_outputs, p->ctx->stream, &blocks));
-  CU(launch_reduce_norms(p->partial, blocks, 2, p->dscal, p->ctx->stream));
+  CU(launch_reduce_norms(p->partial, blocks, 2, p->dscal, p->ctx->stream, p->stop));
   p->launches += 2;
+  if (p->stop && !test_outputs) {  // the convergence test on the device
+    CU(launch_check(p->dscal, p->dctl, p->derr, p->desc.tol, p->desc.max_iter, p->h[0], p->ctx->stream));
+    p->launches += 1;
+  }
   return FFTM_OK;
 }
 
@@ -892,6 +912,111 @@ double mixed_error(const double sig[3][3], int mask) {
   return std::sqrt(f / tot);
 }
 
+// The update that follows the residual of iteration m (a5-a8): u^{m+1} into the next ring slot,
+// either u^m - Gamma(D^m) or, on an Anderson iteration with a full history, the mix of the
+// stored couples minus Gamma of the mixed residual.  In a device-decided step the launches
+// carry the stop flag and the Anderson flag goes to the iteration the device checked last.
+template <typename T>
+int update_after(fftm_problem* p, int m, int cur0) {
+  cudaStream_t s = p->ctx->stream;
+  const bool lo = p->esz == 4;
+  const int depth = p->desc.anderson_depth, period = p->desc.anderson_period;
+  const long long cnt = p->comp_stride;
+  const int sm = (cur0 + m) % NSLOT, sn = (cur0 + m + 1) % NSLOT;
+  // couples k = m - depth + 1 .. m (k >= 1) are in slots (cur0 + k) % NSLOT
+  const int have = std::min(m, depth);
+  const bool accel = depth > 0 && (m % period == period - 1) && have == depth;
+  if (accel) {
+    const T* Ds[4][3];
+    const T* uh[4][3];
+    const T* ul[4][3];
+    for (int j = 0; j < 4; ++j) {
+      const int k = m - depth + 1 + std::min(j, depth - 1);
+      const int sk = (cur0 + k) % NSLOT;
+      for (int q = 0; q < 3; ++q) {
+        Ds[j][q] = field_ptr<T>(p, SET_D + sk, q);
+        uh[j][q] = field_ptr<T>(p, SET_UH + sk, q);
+        ul[j][q] = lo ? field_ptr<T>(p, SET_UL + sk, q) : nullptr;
+      }
+    }
+    {
+      const int gb = gram_blocks(cnt);
+      ProfScope ps(p, FFTM_KCAT_ANDERSON);
+      CU(launch_gram<T>(Ds, depth, cnt, p->partial, gb, s, p->stop));
+      if (p->stop)
+        CU(launch_anderson_solve(p->partial, gb, depth, 1e-8, p->dscal + 2, p->dint, s, p->dctl));
+      else
+        CU(launch_anderson_solve(p->partial, gb, depth, 1e-8, p->dscal + 2, p->dint + m, s));
+      T* work[3];
+      T* bh[3];
+      T* bl[3];
+      set_ptrs<T>(p, SET_WORK, work);
+      set_ptrs<T>(p, SET_BH, bh);
+      if (lo) set_ptrs<T>(p, SET_BL, bl);
+      CU(launch_combine<T>(work, bh, lo ? bl : nullptr, Ds, uh, ul, depth, p->dscal + 2, cnt, s, p->stop));
+      p->launches += 3;
+    }
+    return green_apply<T>(p, SET_WORK, SET_BH, lo ? SET_BL : -1, SET_UH + sn, lo ? SET_UL + sn : -1, true);
+  }
+  return green_apply<T>(p, SET_D + sm, SET_UH + sm, lo ? SET_UL + sm : -1, SET_UH + sn, lo ? SET_UL + sn : -1,
+                        true);
+}
+
+// A load step whose convergence test runs on the device (every load without a normal-mixed
+// part): the host enqueues iterations in chunks (residual, reduction, k_check, update), every
+// launch after the test stops the step does nothing, and the host waits once per chunk.
+// Returns the last checked iteration in *m_out and the stop code in *stop_out.
+constexpr int kDevChunk = 4;
+
+template <typename T>
+int device_loop(fftm_problem* p, int cur0, int* m_out, int* stop_out) {
+  cudaStream_t s = p->ctx->stream;
+  const int max_iter = p->desc.max_iter;
+  if (p->derr_len < max_iter + 1) {
+    if (p->derr) cudaFree(p->derr);
+    p->derr = nullptr;
+    CU(cudaMalloc(&p->derr, (max_iter + 1) * sizeof(double)));
+    p->derr_len = max_iter + 1;
+  }
+  if (!p->dctl) CU(cudaMalloc(&p->dctl, 4 * sizeof(int)));
+  CU(cudaMemsetAsync(p->dctl, 0, 4 * sizeof(int), s));
+  if (p->res_two_pass < 0) {  // the residual's form is measured before anything is enqueued
+    int rc = resolve_residual_form<T>(p, cur0 % NSLOT);
+    if (rc) return rc;
+  }
+  int* hctl = reinterpret_cast<int*>(p->hpin + 40);
+  int stop = 0, mlast = 0;
+  p->stop = p->dctl;
+  int rc = FFTM_OK;
+  for (int m0 = 0; m0 <= max_iter && !rc; m0 += kDevChunk) {
+    for (int m = m0; m < m0 + kDevChunk && m <= max_iter && !rc; ++m) {
+      p->prof_m = m;
+      p->prof_post = 0;
+      rc = run_residual<T>(p, (cur0 + m) % NSLOT, false);
+      if (rc || m >= max_iter) break;
+      p->prof_post = 1;
+      rc = update_after<T>(p, m, cur0);
+    }
+    if (rc) break;
+    if (cudaMemcpyAsync(hctl, p->dctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = set_err(FFTM_E_CUDA, std::string("device-decided step: ") + cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    stop = hctl[0];
+    mlast = hctl[2];
+    prof_flush(p, stop ? mlast : -1);
+    if (stop) break;
+  }
+  p->stop = nullptr;
+  p->prof_m = -1;
+  p->prof_post = 0;
+  if (rc) return rc;
+  *m_out = mlast;
+  *stop_out = stop;
+  return FFTM_OK;
+}
+
 // Algorithm 1 for one load step.  The update of iteration m is
 //   u^{m+1} = u^m - Gamma(D^m)                                 (plain step)
 //   u^{m+1} = sum_k c_k u^k - Gamma(sum_k c_k D^k)             (Anderson step)
@@ -918,6 +1043,18 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
   const int cur0 = p->cur;
   int m = 0, converged = 0;
   double err = 0.0;
+  if (p->dev_loop && !p->load.mixed) {
+    int stop = 0;
+    int rc = device_loop<T>(p, cur0, &m, &stop);
+    if (rc) return rc;
+    std::vector<double> eh(m + 1);
+    CU(cudaMemcpy(eh.data(), p->derr, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int i = 0; i <= m && err_hist && i < hist_len; ++i) err_hist[i] = eh[i];
+    err = eh[m];
+    p->cur = (cur0 + m) % NSLOT;
+    if (stop == 2) return set_err(FFTM_E_DIVERGED, "non-finite equilibrium norm");
+    converged = stop == 1;
+  } else
   for (m = 0;; ++m) {
     const int sm = (cur0 + m) % NSLOT;
     int rc = run_residual<T>(p, sm, false);
@@ -961,42 +1098,7 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
         for (int j = 0; j < 3; ++j) p->load.A[i][j] += d[i][j];
     }
     if (m >= max_iter) break;
-    const int sn = (cur0 + m + 1) % NSLOT;
-    // couples k = m - depth + 1 .. m (k >= 1) are in slots (cur0 + k) % NSLOT
-    const int have = std::min(m, depth);
-    const bool accel = depth > 0 && (m % period == period - 1) && have == depth;
-    if (accel) {
-      const T* Ds[4][3];
-      const T* uh[4][3];
-      const T* ul[4][3];
-      for (int j = 0; j < 4; ++j) {
-        const int k = m - depth + 1 + std::min(j, depth - 1);
-        const int sk = (cur0 + k) % NSLOT;
-        for (int q = 0; q < 3; ++q) {
-          Ds[j][q] = field_ptr<T>(p, SET_D + sk, q);
-          uh[j][q] = field_ptr<T>(p, SET_UH + sk, q);
-          ul[j][q] = lo ? field_ptr<T>(p, SET_UL + sk, q) : nullptr;
-        }
-      }
-      {
-      const int gb = gram_blocks(cnt);
-      ProfScope ps(p, FFTM_KCAT_ANDERSON);
-      CU(launch_gram<T>(Ds, depth, cnt, p->partial, gb, s));
-      CU(launch_anderson_solve(p->partial, gb, depth, 1e-8, p->dscal + 2, p->dint + m, s));
-      T* work[3];
-      T* bh[3];
-      T* bl[3];
-      set_ptrs<T>(p, SET_WORK, work);
-      set_ptrs<T>(p, SET_BH, bh);
-      if (lo) set_ptrs<T>(p, SET_BL, bl);
-      CU(launch_combine<T>(work, bh, lo ? bl : nullptr, Ds, uh, ul, depth, p->dscal + 2, cnt, s));
-      p->launches += 3;
-      }
-      rc = green_apply<T>(p, SET_WORK, SET_BH, lo ? SET_BL : -1, SET_UH + sn, lo ? SET_UL + sn : -1, true);
-    } else {
-      rc = green_apply<T>(p, SET_D + sm, SET_UH + sm, lo ? SET_UL + sm : -1, SET_UH + sn, lo ? SET_UL + sn : -1,
-                          true);
-    }
+    rc = update_after<T>(p, m, cur0);
     if (rc) return rc;
   }
   // report
@@ -1234,6 +1336,8 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->partial);
   cudaFree(p->dscal);
   cudaFree(p->dint);
+  cudaFree(p->dctl);
+  cudaFree(p->derr);
   cudaFree(p->scratch);
   cudaFree(p->vs);
   cudaFree(p->vs_test);
@@ -1653,6 +1757,10 @@ int fftm_set_option(fftm_problem* p, int option, int value) {
       p->res_passes = value;
       p->res_two_pass = value == 0 ? -1 : (value == 2 ? 1 : 0);
       if (value == 1 && p->res_tile == 0) p->res_two_pass = -1;  // the tile height is still tuned
+      return FFTM_OK;
+    case FFTM_OPT_DEVICE_LOOP:
+      if (value != 0 && value != 1) return set_err(FFTM_E_INVALID, "device loop: 0 or 1");
+      p->dev_loop = value;
       return FFTM_OK;
     case FFTM_OPT_RESIDUAL_TILE:
       if (value != 0 && value != 8 && value != 16) return set_err(FFTM_E_INVALID, "residual tile: 0 (tuned), 8 or 16");

@@ -405,6 +405,7 @@ constexpr int PASS_THREADS = 512;
 
 template <typename T, int AXIS, int FUSED>
 __global__ void __launch_bounds__(PASS_THREADS) k_pass(PassParams<T> P) {
+  if (P.stop && *P.stop) return;
   constexpr int TP = TileCfg<T>::TP;
   constexpr int PC = TileCfg<T>::PC;
   constexpr int SP = TileCfg<T>::SP;

@@ -60,6 +60,7 @@ struct PassParams {
   T two_mu0, lam0;
   int tetra;
   T gscale[3];        // inverse-transform normalisation folded into the Green factor
+  const int* stop;    // device flag: nonzero once the load step has stopped (the launch does nothing)
 };
 
 // Stencil + law + divergence (one fixed-point residual evaluation).
@@ -112,6 +113,7 @@ struct ResParams {
   int two_pass;      // 1: evaluate the residual as two grid passes even where one pass serves
   int fused_fy;      // voxel tile height of the one-pass residual (8 or 16)
   double* partial;   // per block: S_D, S_P
+  const int* stop;   // device flag: nonzero once the load step has stopped (the launch does nothing)
 };
 
 constexpr int LAWC = 40;
@@ -150,6 +152,7 @@ struct TcPassParams {
   int tetra;
   float gscale[3];
   int* err;  // set to 1 by a CTA whose wait on the tensor cores timed out
+  const int* stop;  // device flag: nonzero once the load step has stopped (the launch does nothing)
 };
 cudaError_t launch_pass_tc(const TcPassParams& P, cudaStream_t s);
 // Whether a transform of padded length Kp along `axis` fits one tensor-core CTA.
@@ -185,6 +188,7 @@ struct TfPassParams {
   int tetra;
   float gscale[3];
   int* err;  // set to 1 by a CTA whose bounded wait on the tensor-core pipeline gave up
+  const int* stop;  // device flag: nonzero once the load step has stopped (the launch does nothing)
 };
 cudaError_t launch_pass_tf32(const TfPassParams& P, cudaStream_t s);
 bool pass_tf32_fits(int Kp, int axis);
@@ -229,7 +233,14 @@ cudaError_t launch_commit(const ResParams<T>& P, int tetra, T* out, cudaStream_t
 template <typename T>
 cudaError_t launch_state_io(const ResParams<T>& P, int tetra, T* out, const T* in, cudaStream_t s);
 
-cudaError_t launch_reduce_norms(const double* partial, int nblocks, int nvals, double* out, cudaStream_t s);
+cudaError_t launch_reduce_norms(const double* partial, int nblocks, int nvals, double* out, cudaStream_t s,
+                                const int* stop = nullptr);
+// Control block of a load step whose convergence is decided on the device (Algorithm 1's
+// test, Eq. equilibrium_condition): ctl[0] stop (0 running, 1 converged, 2 diverged,
+// 3 iteration limit), ctl[1] the iteration to check next, ctl[2] the iteration checked last.
+// k_check reads S_D, S_P from sums, records err at err_hist[m] and stops the step or moves on.
+cudaError_t launch_check(const double* sums, int* ctl, double* err_hist, double tol, int max_iter, double h1,
+                         cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_axpy_fields(T* const dst[3], const T* const a[3], const T* const b[3], T alpha,
@@ -240,14 +251,16 @@ cudaError_t launch_copy_fields(T* const dst[3], const T* const src[3], long long
 // right-hand side <D_k - D_last, D_last>, per block (9 doubles).
 template <typename T>
 cudaError_t launch_gram(const T* const D[4][3], int m, long long count, double* partial, int nblocks,
-                        cudaStream_t s);
+                        cudaStream_t s, const int* stop = nullptr);
+// accepted: the step's flag array, indexed by ctl[2] when ctl is given (device-decided loop),
+// else accepted[0].
 cudaError_t launch_anderson_solve(const double* partial, int nblocks, int m, double pivot_tol, double* coef,
-                                  int* accepted, cudaStream_t s);
+                                  int* accepted, cudaStream_t s, const int* ctl = nullptr);
 // Dbar = sum c_k D_k -> dst;  ubar = u_last + sum_k c_k (u_k - u_last) -> (bh, bl)
 template <typename T>
 cudaError_t launch_combine(T* const dst[3], T* const bh[3], T* const bl[3], const T* const D[4][3],
                            const T* const uh[4][3], const T* const ul[4][3], int m, const double* coef,
-                           long long count, cudaStream_t s);
+                           long long count, cudaStream_t s, const int* stop = nullptr);
 template <typename T>
 cudaError_t launch_voxel_fields(const ResParams<T>& P, int tetra, T* grad_out, T* stress_out, cudaStream_t s);
 template <typename T>

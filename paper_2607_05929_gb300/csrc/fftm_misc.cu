@@ -12,12 +12,16 @@
 // normal equations of the differences D_k - D_last are accumulated in FP64
 // and solved by Cholesky in FP64 by one thread; a pivot below `pivot_tol`
 // times its diagonal entry rejects the step (c = e_last).
+#include <math_constants.h>
+
 #include "fftm_internal.cuh"
 
 namespace fftm {
 
 // Sum `nvals` doubles over `nblocks` rows (fixed order: deterministic).
-__global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nvals, double* __restrict__ out) {
+__global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nvals, double* __restrict__ out,
+                         const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ double red[256];
   for (int v = 0; v < nvals; ++v) {
     double s = 0.0;
@@ -33,8 +37,33 @@ __global__ void k_reduce(const double* __restrict__ partial, int nblocks, int nv
   }
 }
 
-cudaError_t launch_reduce_norms(const double* partial, int nblocks, int nvals, double* out, cudaStream_t s) {
-  k_reduce<<<1, 256, 0, s>>>(partial, nblocks, nvals, out);
+cudaError_t launch_reduce_norms(const double* partial, int nblocks, int nvals, double* out, cudaStream_t s,
+                                const int* stop) {
+  k_reduce<<<1, 256, 0, s>>>(partial, nblocks, nvals, out, stop);
+  return cudaGetLastError();
+}
+
+// The convergence test of Algorithm 1 on the device: err = h1 sqrt(S_D / S_P) (Eq.
+// equilibrium_condition; +inf while S_P is 0 under a non-zero S_D, which only means "not yet"),
+// recorded at err_hist[m]; the step stops when err < tol (1), on a non-finite norm (2) or at the
+// iteration limit (3), else the next iteration is m + 1.
+__global__ void k_check(const double* __restrict__ sums, int* __restrict__ ctl, double* __restrict__ err_hist,
+                        double tol, int max_iter, double h1) {
+  if (ctl[0]) return;
+  const int m = ctl[1];
+  const double sd = sums[0], sp = sums[1];
+  const double err = sp > 0.0 ? h1 * sqrt(sd / sp) : (sd == 0.0 ? 0.0 : CUDART_INF);
+  err_hist[m] = err;
+  ctl[2] = m;
+  if (isnan(err) || isinf(sd) || isinf(sp) || isnan(sd) || isnan(sp)) ctl[0] = 2;
+  else if (err < tol) ctl[0] = 1;
+  else if (m >= max_iter) ctl[0] = 3;
+  else ctl[1] = m + 1;
+}
+
+cudaError_t launch_check(const double* sums, int* ctl, double* err_hist, double tol, int max_iter, double h1,
+                         cudaStream_t s) {
+  k_check<<<1, 1, 0, s>>>(sums, ctl, err_hist, tol, max_iter, h1);
   return cudaGetLastError();
 }
 
@@ -111,7 +140,9 @@ struct DotAcc<float> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_gram(GramArgs<T> A, int m, long long count, double* __restrict__ partial) {
+__global__ void __launch_bounds__(256) k_gram(GramArgs<T> A, int m, long long count, double* __restrict__ partial,
+                                              const int* __restrict__ stop) {
+  if (stop && *stop) return;
   __shared__ double red[8][9];
   DotAcc<T> acc[9];
   const int L = m - 1;
@@ -156,11 +187,11 @@ __global__ void __launch_bounds__(256) k_gram(GramArgs<T> A, int m, long long co
 
 template <typename T>
 cudaError_t launch_gram(const T* const D[4][3], int m, long long count, double* partial, int nblocks,
-                        cudaStream_t s) {
+                        cudaStream_t s, const int* stop) {
   GramArgs<T> A;
   for (int j = 0; j < 4; ++j)
     for (int c = 0; c < 3; ++c) A.D[j][c] = (j < m) ? D[j][c] : D[0][c];
-  k_gram<T><<<nblocks, 256, 0, s>>>(A, m, count, partial);
+  k_gram<T><<<nblocks, 256, 0, s>>>(A, m, count, partial, stop);
   return cudaGetLastError();
 }
 
@@ -168,7 +199,9 @@ cudaError_t launch_gram(const T* const D[4][3], int m, long long count, double* 
 // c_k = gamma_k (k < last), c_last = 1 - sum gamma.  A pivot below pivot_tol
 // times its diagonal entry rejects the step: c = e_last.
 __global__ void k_anderson_solve(const double* __restrict__ partial, int nblocks, int m, double pivot_tol,
-                                 double* __restrict__ coef, int* __restrict__ accepted) {
+                                 double* __restrict__ coef, int* __restrict__ accepted, const int* __restrict__ ctl) {
+  if (ctl && ctl[0]) return;
+  if (ctl) accepted += ctl[2];
   __shared__ double g[9];
   if (threadIdx.x < 9) {
     double t = 0.0;
@@ -223,8 +256,8 @@ __global__ void k_anderson_solve(const double* __restrict__ partial, int nblocks
 }
 
 cudaError_t launch_anderson_solve(const double* partial, int nblocks, int m, double pivot_tol, double* coef,
-                                  int* accepted, cudaStream_t s) {
-  k_anderson_solve<<<1, 32, 0, s>>>(partial, nblocks, m, pivot_tol, coef, accepted);
+                                  int* accepted, cudaStream_t s, const int* ctl) {
+  k_anderson_solve<<<1, 32, 0, s>>>(partial, nblocks, m, pivot_tol, coef, accepted, ctl);
   return cudaGetLastError();
 }
 
@@ -244,7 +277,9 @@ struct CombArgs {
 // loaded before the first store, so that the loads of all three components are in
 // flight together (the output arrays may alias nothing the compiler can see).
 template <typename T, bool LO>
-__global__ void k_combine(CombArgs<T> A, int m, const double* __restrict__ coef, long long count) {
+__global__ void k_combine(CombArgs<T> A, int m, const double* __restrict__ coef, long long count,
+                          const int* __restrict__ stop) {
+  if (stop && *stop) return;
   T c[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) c[j] = (j < m) ? (T)coef[j] : T(0);
@@ -300,7 +335,7 @@ __global__ void k_combine(CombArgs<T> A, int m, const double* __restrict__ coef,
 template <typename T>
 cudaError_t launch_combine(T* const dst[3], T* const bh[3], T* const bl[3], const T* const D[4][3],
                            const T* const uh[4][3], const T* const ul[4][3], int m, const double* coef,
-                           long long count, cudaStream_t s) {
+                           long long count, cudaStream_t s, const int* stop) {
   CombArgs<T> A;
   const bool lo = bl != nullptr && bl[0] != nullptr;
   for (int q = 0; q < 3; ++q) {
@@ -314,8 +349,8 @@ cudaError_t launch_combine(T* const dst[3], T* const bh[3], T* const bl[3], cons
       A.ul[j][q] = lo ? ul[jj][q] : nullptr;
     }
   }
-  if (lo) k_combine<T, true><<<152 * 8, 256, 0, s>>>(A, m, coef, count);
-  else k_combine<T, false><<<152 * 8, 256, 0, s>>>(A, m, coef, count);
+  if (lo) k_combine<T, true><<<152 * 8, 256, 0, s>>>(A, m, coef, count, stop);
+  else k_combine<T, false><<<152 * 8, 256, 0, s>>>(A, m, coef, count, stop);
   return cudaGetLastError();
 }
 
@@ -385,10 +420,11 @@ cudaError_t launch_mask(T* const f[3], const int lo[3][3], const int hi[3][3], i
   template cudaError_t launch_copy_fields<T>(T* const[3], const T* const[3], long long, cudaStream_t);            \
   template cudaError_t launch_axpy_fields<T>(T* const[3], const T* const[3], const T* const[3], T, long long,     \
                                              cudaStream_t);                                                        \
-  template cudaError_t launch_gram<T>(const T* const[4][3], int, long long, double*, int, cudaStream_t);          \
+  template cudaError_t launch_gram<T>(const T* const[4][3], int, long long, double*, int, cudaStream_t,           \
+                                      const int*);                                                                 \
   template cudaError_t launch_combine<T>(T* const[3], T* const[3], T* const[3], const T* const[4][3],             \
                                          const T* const[4][3], const T* const[4][3], int, const double*,          \
-                                         long long, cudaStream_t);                                                 \
+                                         long long, cudaStream_t, const int*);                                     \
   template cudaError_t launch_pack<T>(const T* const[3], T*, int, int, int, long long, long long, int,            \
                                       cudaStream_t);                                                               \
   template cudaError_t launch_mask<T>(T* const[3], const int[3][3], const int[3][3], int, int, int, long long,    \

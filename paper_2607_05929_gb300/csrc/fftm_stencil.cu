@@ -641,6 +641,7 @@ __device__ __forceinline__ int sym_index(int i, int q) {
 
 template <typename T, int TETRA, bool WITH_P, bool LO, bool SYM, int SL>
 __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti) {
+  if (P.stop && *P.stop) return;
   constexpr bool J2 = (SL & 1) != 0;
   constexpr int NPP = TETRA ? 2 : 1;
   constexpr int NC = SYM ? 6 : 9;
@@ -753,6 +754,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
 // gradient increment; J2: j2_inc).  S_P still takes the full P.
 template <typename T, int TETRA, bool LO, bool SYM>
 __global__ void __launch_bounds__(RTX * RTY) k_stress_inc(ResParams<T> P, TileIdx ti) {
+  if (P.stop && *P.stop) return;
   constexpr int NPP = TETRA ? 2 : 1;
   constexpr int NC = SYM ? 6 : 9;
   __shared__ double red[32];
@@ -932,6 +934,7 @@ __device__ __forceinline__ T store_node(const ResParams<T>& P, int mx, int my, i
 // Interior nodes: all 8 neighbouring voxels exist (or wrap); plain differences.
 template <typename T, int TETRA, bool WITH_P, bool SYM, bool INC>
 __global__ void __launch_bounds__(RTX * RTY) k_div(ResParams<T> P, TileIdx ti, FaceIdx fi) {
+  if (P.stop && *P.stop) return;
   constexpr int NC = SYM ? 6 : 9;
   constexpr int NCT = WITH_P ? NC + 9 : NC;
   __shared__ double red[32];
@@ -1229,6 +1232,7 @@ template <int V> struct Par { static constexpr int value = V; };
 
 template <typename T, int TETRA, bool LO, int FY>
 __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T> P, FusedGeom g) {
+  if (P.stop && *P.stop) return;
   constexpr int FNY = FY + 1, FTHREADS = FX * FY;
   using NV = typename NodeV<T, LO>::t;
   using T2 = typename V2<T>::t;
@@ -1489,6 +1493,7 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
 // layers that k_residual_fused stored; one S_D partial per block (S_P slot zero).
 template <typename T, int TETRA>
 __global__ void __launch_bounds__(256) k_face_div(ResParams<T> P, FaceIdx fi) {
+  if (P.stop && *P.stop) return;
   __shared__ double red[32];
   double SD = 0.0;
   int nface[3] = {P.n[0], P.n[1], P.n[2]};

@@ -607,6 +607,7 @@ __device__ __forceinline__ void green_tile(const TcPassParams& P, const Tile& T,
 
 template <int AXIS, int FUSED>
 __global__ void __launch_bounds__(UM_THREADS, 1) k_pass_umma(TcPassParams P, int maxKp) {
+  if (P.stop && *P.stop) return;  // before any TMEM allocation or barrier
   extern __shared__ __align__(1024) unsigned char smem[];
   const UmGeom g = um_geom(maxKp, AXIS);
   unsigned char* const sA[2] = {smem, smem + g.a_bytes};

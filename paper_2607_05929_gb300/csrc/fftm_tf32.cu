@@ -490,6 +490,7 @@ __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTil
 
 template <int AXIS>
 __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_constant__ TfPassParams P, int maxKp) {
+  if (P.stop && *P.stop) return;  // before any TMEM allocation or barrier
   extern __shared__ __align__(1024) unsigned char smem[];
   const TfGeom g = TfGeom::make(maxKp, AXIS);
   // fixed region (2 KB): barriers, TMEM slot, abort flag; the stages follow

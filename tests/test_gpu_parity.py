@@ -350,6 +350,42 @@ def test_both_residual_forms_give_the_same_solve(precision):
         assert rel_l2(u1, u2) < (1e-6 if precision == "fp32" else 1e-13)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tf32"])
+@pytest.mark.parametrize("name", ["sphere16_hex", "voronoi_tet"])
+def test_device_decided_step_equals_the_host_loop(precision, name):
+    """The convergence test on the device (iterations enqueued in chunks, launches after the
+    stopping iteration doing nothing) gives the host loop's iterates exactly: the same iteration
+    count, Anderson steps, error history and fields, bit for bit."""
+    wl = SOLVE_CASES[name]()
+    wl.tol = 1e-8 if precision == "fp64" else 1e-6
+    runs = []
+    for dev in (1, 0):
+        gp = GpuProblem(wl, precision)
+        try:
+            F.fftm_set_option(gp.p, F.FFTM_OPT_DEVICE_LOOP, dev)
+            st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+            runs.append((st, r, eh, ah, gp.get_node(F.FFTM_FIELD_U), gp.get_voxel(F.FFTM_FIELD_STRESS)))
+        finally:
+            gp.close()
+    (s1, r1, e1, a1, u1, P1), (s2, r2, e2, a2, u2, P2) = runs
+    assert s1 == s2 == F.FFTM_OK and r1["converged"] and r2["converged"]
+    assert r1["iterations"] == r2["iterations"] and list(a1) == list(a2)
+    assert np.array_equal(e1, e2) and r1["err"] == r2["err"]
+    assert np.array_equal(u1, u2) and np.array_equal(P1, P2)
+    assert np.array_equal(r1["mean_P"], r2["mean_P"])
+
+
+def test_device_decided_step_stops_at_the_iteration_limit():
+    wl = SOLVE_CASES["sphere16_hex"]()
+    gp = GpuProblem(wl, "fp64", max_iter=6)
+    try:
+        st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=8)
+        assert st == F.FFTM_NOT_CONVERGED and not r["converged"] and r["iterations"] == 6
+        assert len(eh) == 7 and np.all(np.isfinite(eh))
+    finally:
+        gp.close()
+
+
 @pytest.mark.parametrize("name", ["sphere32_hex", "voronoi_tet", "voronoi_hex_mu0", "xlam_tet"])
 def test_solve_step_fp32_vs_fp64_oracle(name):
     wl = SOLVE_CASES[name]()
