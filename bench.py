@@ -73,6 +73,8 @@ def parse_args(argv=None):
                          "steps and the 128^3 crystal-plasticity polycrystal under 30 torsion-bending increments")
     ap.add_argument("--arms", default="",
                     help="comma-separated precisions of a --workload scenario (default: per scenario)")
+    ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
+                    help="1: convergence test on the device (default); 0: the host reads the norms every iteration")
     ap.add_argument("--serve", action="store_true",
                     help="serving stream (mixed sizes/BCs/laws, Poisson arrivals): solves/s and p50/p99 latency")
     ap.add_argument("--requests", type=int, default=96, help="requests of the serving stream (--serve)")
@@ -333,6 +335,7 @@ def gpu_arm(args):
                                  lambda0=wl.lambda0, mu0=wl.mu0, precision=precision, tol=wl.tol,
                                  max_iter=wl.max_iter)
         p = F.fftm_problem_create(ctx, desc)
+        F.fftm_set_option(p, F.FFTM_OPT_DEVICE_LOOP, args.device_loop)
         F.fftm_set_load(p, wl.A)
         return p
 
@@ -408,11 +411,16 @@ def gpu_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": workload_name(args.n, args.grains), "precision": args.precision,
+                       "convergence_test": "device" if args.device_loop else "host",
                        "iterations_per_step": iters, "anderson_steps_per_step": last["n_accelerated"],
                        "l2": "inputs larger than L2 (working set several GB; no flush needed)",
                        "parallelism": f"replicas x{dist.world}"},
             "roofline": roofline, "gpu_launches": launches, "clocks": clk,
             "tuning": [t for t in F.fftm_tuning_table().splitlines() if t]}
+
+    # ---- measured FMA rates (the arithmetic roof of the FP64 path) ----
+    line["fma_peak_tflops"] = {"fp64": F.fftm_device_fma_rate(dist.local, True) / 1e12,
+                               "fp32": F.fftm_device_fma_rate(dist.local, False) / 1e12}
 
     # ---- FP64 path beside it (same workload, device-resident) ----
     if args.fp64_steps > 0 and args.precision != "fp64":

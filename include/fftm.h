@@ -264,6 +264,12 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
 enum fftm_option { FFTM_OPT_RESIDUAL_PASSES = 0, FFTM_OPT_RESIDUAL_TILE = 1, FFTM_OPT_DEVICE_LOOP = 2 };
 int fftm_set_option(fftm_problem* p, int option, int value);
 
+/* Measured fused multiply-add throughput of a device (FLOP/s, an FMA counting two), in FP64
+   (fp64 = 1) or FP32 (fp64 = 0): eight independent FMA chains per thread over all SMs, the best
+   of three timed launches.  The denominator of an arithmetic-bound roofline (the FP64 path on
+   this GPU is bound by its FP64 rate, a small fraction of the FP32 one). */
+int fftm_device_fma_rate(int device, int fp64, double* flops_per_s);
+
 /* The launch-shape choices the library has measured in this process, one line per shape
    ("key: choice (times)").  buf (HOST, may be NULL) receives up to len - 1 characters and a
    terminating 0; *needed (may be NULL) the size the whole table needs. */

@@ -1772,6 +1772,18 @@ int fftm_set_option(fftm_problem* p, int option, int value) {
   }
 }
 
+int fftm_device_fma_rate(int device, int fp64, double* flops_per_s) {
+  if (!flops_per_s) return set_err(FFTM_E_INVALID, "null output");
+  int count = 0;
+  CU(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) return set_err(FFTM_E_INVALID, "bad device index");
+  CU(cudaSetDevice(device));
+  const double r = fma_peak_flops(fp64 ? 1 : 0);
+  if (r <= 0.0) return set_err(FFTM_E_CUDA, "FMA probe failed");
+  *flops_per_s = r;
+  return FFTM_OK;
+}
+
 int fftm_tuning_table(char* buf, size_t len, size_t* needed) {
   std::string out;
   {

@@ -271,6 +271,8 @@ cudaError_t launch_mask(T* const f[3], const int lo[3][3], const int hi[3][3], i
                         long long sy, long long sz, cudaStream_t s);
 
 int gram_blocks(long long count);
+// Measured FMA throughput of the current device (FLOP/s, an FMA counting two), FP64 or FP32.
+double fma_peak_flops(int fp64);
 
 // Asynchronous global -> shared copies (cp.async, Ampere and later): the copy
 // is issued without a register round trip, so a thread can keep many loads in

@@ -354,6 +354,54 @@ cudaError_t launch_combine(T* const dst[3], T* const bh[3], T* const bl[3], cons
   return cudaGetLastError();
 }
 
+// ---- arithmetic peak probe --------------------------------------------------------------
+// Eight independent chains of fused multiply-adds per thread (enough to cover the FMA
+// latency), `iters` rounds; the result is written so the chains are not removed.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T* __restrict__ sink, int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = T(threadIdx.x + k) * T(1e-3);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = x[k] * a + b;
+  }
+  T t = T(0);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) t += x[k];
+  if (t == T(-1.2345)) sink[blockIdx.x] = t;  // practically never: keeps the chains live
+}
+
+double fma_peak_flops(int fp64) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -1.0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int blocks = (sms > 0 ? sms : 152) * 8, threads = 256;
+  const int iters = fp64 ? 4096 : 65536;
+  void* sink = nullptr;
+  if (cudaMalloc(&sink, blocks * sizeof(double)) != cudaSuccess) return -1.0;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = -1.0;
+  for (int rep = 0; rep < 4; ++rep) {
+    cudaEventRecord(e0, 0);
+    if (fp64) k_fma_peak<double><<<blocks, threads>>>((double*)sink, iters, 0.999999, 1e-7);
+    else k_fma_peak<float><<<blocks, threads>>>((float*)sink, iters, 0.999999f, 1e-7f);
+    cudaEventRecord(e1, 0);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms > 0.f && rep > 0) {
+      const double flops = 2.0 * 8.0 * (double)iters * blocks * threads / (ms * 1e-3);
+      if (flops > best) best = flops;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  return cudaGetLastError() == cudaSuccess ? best : -1.0;
+}
+
 // Dense [q][z][y][x] <-> pitched component arrays.
 template <typename T>
 __global__ void k_pack(const T* s0, const T* s1, const T* s2, T* d0, T* d1, T* d2, T* dense, int N1, int N2, int N3,

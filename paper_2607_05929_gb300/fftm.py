@@ -39,7 +39,7 @@ EXPORTS = [
     "fftm_last_error", "fftm_version", "fftm_ctx_create", "fftm_ctx_destroy",
     "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
     "fftm_set_phase", "fftm_set_load", "fftm_get_load", "fftm_solve_step", "fftm_field_bytes",
-    "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_set_option", "fftm_tuning_table", "fftm_apply", "fftm_kernel_launches",
+    "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_set_option", "fftm_tuning_table", "fftm_device_fma_rate", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
     "fftm_server_inject_start_failures",
@@ -129,6 +129,7 @@ def load_library(path=LIB_PATH):
         "fftm_field_bytes": ([vp, ctypes.c_int, P(ctypes.c_size_t)], ctypes.c_int),
         "fftm_problem_layout": ([vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int)], ctypes.c_int),
         "fftm_set_option": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "fftm_device_fma_rate": ([ctypes.c_int, ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
         "fftm_tuning_table": ([ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)], ctypes.c_int),
         "fftm_get_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "fftm_set_field": ([vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
@@ -331,6 +332,13 @@ def fftm_problem_layout(p):
 
 def fftm_set_option(p, option, value):
     return _check(load_library().fftm_set_option(p, int(option), int(value)))
+
+
+def fftm_device_fma_rate(device=0, fp64=True):
+    """Measured FMA throughput of the device in FLOP/s (FP64 or FP32)."""
+    r = ctypes.c_double()
+    _check(load_library().fftm_device_fma_rate(int(device), int(bool(fp64)), ctypes.byref(r)))
+    return r.value
 
 
 def fftm_tuning_table():

@@ -615,3 +615,10 @@ def test_tf32_solve_matches_fp64_oracle(name):
         assert rel_l2(sym6(_strain(Gg.reshape(Gg.shape[0], 3, 3, *Gg.shape[2:]))), sym6(_strain(pr.last["G"]))) < 1e-5
     finally:
         gp.close()
+
+
+def test_fma_rate_probe_measures_both_precisions():
+    r64 = F.fftm_device_fma_rate(0, True)
+    r32 = F.fftm_device_fma_rate(0, False)
+    assert 1e11 < r64 < 1e14 and 1e12 < r32 < 1e15
+    assert r32 > r64
