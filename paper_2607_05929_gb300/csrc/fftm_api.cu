@@ -311,6 +311,7 @@ struct fftm_problem {
   // device-decided load steps (every load without a normal-mixed part): the convergence test
   // runs on the device and the host waits once per chunk of iterations
   int dev_loop = 1;                // FFTM_OPT_DEVICE_LOOP
+  int last_iters = -1;             // iterations of the previous device-decided step (chunk sizing)
   int* dctl = nullptr;             // control block of k_check: stop, next iteration, last checked
   double* derr = nullptr;          // per-iteration errors of the step (device)
   int derr_len = 0;
@@ -988,8 +989,12 @@ int device_loop(fftm_problem* p, int cur0, int* m_out, int* stop_out) {
   int stop = 0, mlast = 0;
   p->stop = p->dctl;
   int rc = FFTM_OK;
-  for (int m0 = 0; m0 <= max_iter && !rc; m0 += kDevChunk) {
-    for (int m = m0; m < m0 + kDevChunk && m <= max_iter && !rc; ++m) {
+  // chunks of kDevChunk iterations; near the iteration count of the previous step (a repeated or
+  // similar load) the chunks shrink to one, so a step that stops there enqueues no idle work
+  for (int m0 = 0, K = kDevChunk; m0 <= max_iter && !rc; m0 += K) {
+    K = kDevChunk;
+    if (p->last_iters >= 0 && m0 <= p->last_iters + 1) K = std::max(1, std::min(kDevChunk, p->last_iters - m0));
+    for (int m = m0; m < m0 + K && m <= max_iter && !rc; ++m) {
       p->prof_m = m;
       p->prof_post = 0;
       rc = run_residual<T>(p, (cur0 + m) % NSLOT, false);
@@ -1012,6 +1017,7 @@ int device_loop(fftm_problem* p, int cur0, int* m_out, int* stop_out) {
   p->prof_m = -1;
   p->prof_post = 0;
   if (rc) return rc;
+  p->last_iters = mlast;
   *m_out = mlast;
   *stop_out = stop;
   return FFTM_OK;
