@@ -58,14 +58,18 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--grains", type=int, default=500)
-    ap.add_argument("--precision", choices=["fp32", "fp32_tc", "fp32_tf32", "fp64"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "fp32_tc", "fp32_tf32", "fp64"], default="fp32_tf32",
+                    help="the headline path (default: FP32 fields with TF32 tensor-core transforms, the precision "
+                         "form); the others are timed beside it")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="FP64 path steps timed beside (0 = skip)")
     ap.add_argument("--tc-steps", type=int, default=3,
                     help="tensor-core (FP32_TC) path steps timed beside the FP32 path (0 = skip)")
     ap.add_argument("--tf32-steps", type=int, default=3,
-                    help="TF32 tensor-core (FP32_TF32) path steps timed beside the FP32 path (0 = skip)")
+                    help="TF32 tensor-core (FP32_TF32) path steps timed beside the headline (0 = skip)")
+    ap.add_argument("--fp32-steps", type=int, default=3,
+                    help="FP32 path (FFT transforms) steps timed beside the headline (0 = skip)")
     ap.add_argument("--workload", choices=["polycrystal", "sphere_inclusion", "sphere_bending", "cp_torsion_bending"],
                     default="polycrystal",
                     help="polycrystal: the headline step; the others print one line per precision arm for the "
@@ -422,62 +426,56 @@ def gpu_arm(args):
     line["fma_peak_tflops"] = {"fp64": F.fftm_device_fma_rate(dist.local, True) / 1e12,
                                "fp32": F.fftm_device_fma_rate(dist.local, False) / 1e12}
 
-    # ---- FP64 path beside it (same workload, device-resident) ----
-    if args.fp64_steps > 0 and args.precision != "fp64":
-        F.fftm_problem_destroy(prob)
-        prob = make("fp64")
-        step()  # warm-up
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        u64 = sum(step() for _ in range(args.fp64_steps))
-        e1.record(stream)
-        e1.synchronize()
-        s64 = e0.elapsed_time(e1) / 1000.0
-        line["fp64_path"] = {"value": u64 / s64, "unit": UNIT, "iterations_per_step": last["iterations"],
-                             "steps": args.fp64_steps}
-        F.fftm_problem_destroy(prob)
-        prob = make(args.precision)
+    # ---- the other precisions beside it (same workload, device-resident), and every path's
+    # converged stresses against the FP64 path's (relative L2, computed on the device) ----
+    def stress_dev(pp):
+        prec = F.fftm_problem_layout(pp)[1]
+        nb = F.fftm_field_bytes(pp, F.FFTM_FIELD_STRESS)
+        t = torch.empty(nb // (8 if prec == F.FFTM_FP64 else 4),
+                        dtype=torch.float64 if prec == F.FFTM_FP64 else torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        F.fftm_get_field(pp, F.FFTM_FIELD_STRESS, t)
+        return t.double()
 
-    # ---- tensor-core transforms beside it (the precision form, same workload) ----
-    if args.tc_steps > 0 and args.precision == "fp32":
+    def side(prec, nsteps, note):
+        nonlocal prob
         F.fftm_problem_destroy(prob)
-        prob = make("fp32_tc")
-        step()  # warm-up
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        utc = sum(step() for _ in range(args.tc_steps))
-        e1.record(stream)
-        e1.synchronize()
-        stc = e0.elapsed_time(e1) / 1000.0
-        line["fp32_tc_path"] = {"value": utc / stc, "unit": UNIT, "iterations_per_step": last["iterations"],
-                                "steps": args.tc_steps, "ms_per_step": 1000.0 * stc / args.tc_steps,
-                                "note": "per-axis transforms as tcgen05 BF16 contractions, FP32 fields and residual"}
-        F.fftm_problem_destroy(prob)
-        prob = make(args.precision)
-
-    # ---- TF32 tensor-core transforms beside it (the precision form, same workload) ----
-    if args.tf32_steps > 0 and args.precision == "fp32":
-        F.fftm_problem_destroy(prob)
-        prob = make("fp32_tf32")
+        prob = make(prec)
         step()  # warm-up
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         F.fftm_set_profiling(prob, True)
         e0.record(stream)
-        utf = sum(step() for _ in range(args.tf32_steps))
+        un = sum(step() for _ in range(nsteps))
         e1.record(stream)
         e1.synchronize()
-        stf = e0.elapsed_time(e1) / 1000.0
+        sec = e0.elapsed_time(e1) / 1000.0
         kt = F.fftm_kernel_times(prob)
         F.fftm_set_profiling(prob, False)
-        line["fp32_tf32_path"] = {"value": utf / stf, "unit": UNIT, "iterations_per_step": last["iterations"],
-                                  "steps": args.tf32_steps, "ms_per_step": 1000.0 * stf / args.tf32_steps,
-                                  "ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()},
-                                  "note": "per-axis transforms as tcgen05 TF32 contractions, FP32 fields and residual"}
-        F.fftm_problem_destroy(prob)
-        prob = make(args.precision)
+        rec = {"value": un / sec, "unit": UNIT, "iterations_per_step": last["iterations"], "steps": nsteps,
+               "ms_per_step": 1000.0 * sec / nsteps,
+               "ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kt.items()}, "note": note}
+        return rec, stress_dev(prob)
+
+    notes = {"fp64": "FP64 fields, transforms and residual",
+             "fp32": "FP32 fields (hi + lo displacement) and residual, mixed-radix FFT transforms",
+             "fp32_tf32": "per-axis transforms as tcgen05 TF32 contractions, FP32 fields and residual",
+             "fp32_tc": "per-axis transforms as tcgen05 BF16 contractions, FP32 fields and residual"}
+    keys = {"fp64": "fp64_path", "fp32": "fp32_path", "fp32_tf32": "fp32_tf32_path", "fp32_tc": "fp32_tc_path"}
+    counts = {"fp64": args.fp64_steps, "fp32": args.fp32_steps, "fp32_tf32": args.tf32_steps, "fp32_tc": args.tc_steps}
+    stresses = {args.precision: stress_dev(prob)}
+    for prec in ("fp64", "fp32", "fp32_tf32", "fp32_tc"):
+        if prec == args.precision or counts[prec] <= 0:
+            continue
+        line[keys[prec]], stresses[prec] = side(prec, counts[prec], notes[prec])
+    if "fp64" in stresses:
+        ref = stresses["fp64"]
+        nref = float(torch.linalg.vector_norm(ref))
+        line["stress_rel_l2_vs_fp64"] = {p_: float(torch.linalg.vector_norm(t - ref)) / nref
+                                         for p_, t in stresses.items() if p_ != "fp64"}
+    del stresses
+    F.fftm_problem_destroy(prob)
+    prob = make(args.precision)
 
     # ---- end to end through the C ABI with host buffers ----
     if not args.no_e2e:

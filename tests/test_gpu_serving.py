@@ -34,10 +34,10 @@ def _requests(count, max_side=48):
     return out
 
 
-def _desc(wl):
+def _desc(wl, precision="fp32"):
     mats = [(m.law, m.params, m.quat) for m in wl.materials]
     return F.make_desc(wl.n, wl.phase, mats, wl.bc, scheme=wl.scheme, green=wl.green, lambda0=wl.lambda0,
-                       mu0=wl.mu0, precision="fp32", tol=wl.tol, max_iter=wl.max_iter)
+                       mu0=wl.mu0, precision=precision, tol=wl.tol, max_iter=wl.max_iter)
 
 
 def _u_buffer(wl):
@@ -45,12 +45,12 @@ def _u_buffer(wl):
     return np.zeros((3, N[2], N[1], N[0]), dtype=np.float32)
 
 
-def _run(reqs, slots, one_at_a_time):
+def _run(reqs, slots, one_at_a_time, precision="fp32"):
     srv = F.fftm_server_create(0, 0, slots)
     results, us, keep = {}, {}, []
     try:
         for i, (wl, loads) in enumerate(reqs):
-            desc, kp = _desc(wl)
+            desc, kp = _desc(wl, precision)
             u = _u_buffer(wl)
             keep.append((kp, u))
             rid = F.fftm_server_submit(srv, desc, loads, u_out=u)
@@ -113,7 +113,8 @@ def test_admission_respects_the_memory_budget_and_refuses_oversize():
 
 
 def test_served_results_match_the_fp64_oracle():
-    """Every small served request, solved in the mix on four slots, against the FP64 oracle run
+    """Every small served request, solved in the mix on four slots with the precision form (FP32
+    fields, TF32 tensor-core transforms), against the FP64 oracle run
     through the same load steps: the strain and stress fields of the served u^f (evaluated by the
     oracle's own gradient and law, from its committed state) to 1e-5 relative L2 of the oracle's
     converged fields, the mean stress of the last step to 1e-5, the iteration count within +-2
@@ -121,7 +122,7 @@ def test_served_results_match_the_fp64_oracle():
     from oracle.solver import Problem
 
     reqs = _requests(6, max_side=32)
-    mixed, u_mixed = _run(reqs, 4, False)
+    mixed, u_mixed = _run(reqs, 4, False, precision="fp32_tf32")
     for i, (wl, loads) in enumerate(reqs):
         pr = Problem(wl)
         iters = 0
