@@ -76,7 +76,11 @@ def parse_args(argv=None):
                          "32^3 sphere inclusion (FP64, tol 1e-8), the 128^3 J2 sphere composite under 20 bending "
                          "steps and the 128^3 crystal-plasticity polycrystal under 30 torsion-bending increments")
     ap.add_argument("--arms", default="",
-                    help="comma-separated precisions of a --workload scenario (default: per scenario)")
+                    help="comma-separated precisions of a --workload scenario (default: per scenario) or of "
+                         "--serve (one line each, same requests; default: --precision)")
+    ap.add_argument("--residual-passes", type=int, choices=[0, 1, 2], default=0,
+                    help="residual form: 0 = chosen by the library's launch-shape tuner, 1 = one pass, "
+                         "2 = two passes (FFTM_OPT_RESIDUAL_PASSES)")
     ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
                     help="1: convergence test on the device (default); 0: the host reads the norms every iteration")
     ap.add_argument("--serve", action="store_true",
@@ -340,6 +344,8 @@ def gpu_arm(args):
                                  max_iter=wl.max_iter)
         p = F.fftm_problem_create(ctx, desc)
         F.fftm_set_option(p, F.FFTM_OPT_DEVICE_LOOP, args.device_loop)
+        if args.residual_passes:
+            F.fftm_set_option(p, F.FFTM_OPT_RESIDUAL_PASSES, args.residual_passes)
         F.fftm_set_load(p, wl.A)
         return p
 
@@ -521,15 +527,23 @@ def it_total_plus1(steps, iters):
     return steps * (iters + 1)
 
 
-def serve_requests(count):
-    """The first `count` requests of the serving stream (generation is exact and seeded)."""
+def _serve_request(k):
     from synthetic.serving import request_spec, request_workload
-    out = []
-    for k in range(count):
-        spec = request_spec(k)
-        wl, loads = request_workload(spec)
-        out.append((spec, wl, loads))
-    return out
+    spec = request_spec(k)
+    wl, loads = request_workload(spec)
+    return spec, wl, loads
+
+
+def serve_requests(count):
+    """The first `count` requests of the serving stream (generation is exact and seeded), built
+    by a spawned process pool on the host cores; call before any GPU work."""
+    import multiprocessing as mp
+
+    workers = max(1, min(16, os.cpu_count() or 1, count))
+    if workers == 1:
+        return [_serve_request(k) for k in range(count)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_serve_request, range(count), chunksize=1)
 
 
 def serve_arm(args):
@@ -541,11 +555,18 @@ def serve_arm(args):
     reqs = serve_requests(args.requests)  # before any GPU call
     libbuild.build()
     F.load_library()
+    arms = [a.strip() for a in args.arms.split(",") if a.strip()] if args.arms else [args.precision]
+    for prec in arms:
+        serve_one(args, F, reqs, prec)
+    return 0
+
+
+def serve_one(args, F, reqs, precision):
     descs = []
     for spec, wl, loads in reqs:
         mats = [(m.law, m.params, m.quat) for m in wl.materials]
         descs.append(F.make_desc(wl.n, wl.phase, mats, wl.bc, scheme=wl.scheme, green=wl.green, lambda0=wl.lambda0,
-                                 mu0=wl.mu0, precision=args.precision, tol=wl.tol, max_iter=wl.max_iter))
+                                 mu0=wl.mu0, precision=precision, tol=wl.tol, max_iter=wl.max_iter))
 
     def run(arrivals):
         srv = F.fftm_server_create(0, 0, args.slots)
@@ -590,14 +611,13 @@ def serve_arm(args):
             "p99_latency_s": float(np.percentile(lat, 99)), "mean_latency_s": float(lat.mean()),
             "capacity_solves_per_s": capacity, "arrival_rate_per_s": rate,
             "voxel_iterations_per_s": vox_it / (t_last - t_first), "requests": len(reqs), "slots": args.slots,
-            "not_converged_or_failed": len(bad), "dtype": "f64" if args.precision == "fp64" else "f32",
+            "not_converged_or_failed": len(bad), "dtype": "f64" if precision == "fp64" else "f32",
             "data": "synthetic",
             "config": {"workload": f"serving stream: {len(reqs)} requests (seeds 1000..{999 + len(reqs)}), sides "
                                    "32/48/64/96/128, per-axis P/D/N, isotropic or J2 matrix, HEX1 or TETRA2, "
                                    "spheres or Voronoi; Poisson arrivals at 0.8x the measured capacity",
-                       "precision": args.precision}}
-    print(json.dumps(line))
-    return 0
+                       "precision": precision}}
+    print(json.dumps(line), flush=True)
 
 
 def scenario(name, n=None):
@@ -678,7 +698,41 @@ def scenario_arm(args):
             line["final_stress_rel_l2_vs_fp64"] = float(np.linalg.norm(results[prec] - ref) / np.linalg.norm(ref))
         print(json.dumps(line), flush=True)
     F.fftm_ctx_destroy(ctx)
+    if not args.no_cpu_baseline:
+        print(json.dumps(scenario_oracle(args.workload, wl, loads, desc)), flush=True)
     return 0
+
+
+def scenario_oracle(name, wl, loads, desc):
+    """The FP64 oracle on the host cores for a scenario: the whole first load step on the full grid
+    for the 32^3 sphere inclusion; two fixed-point iterations of the first load step on the full
+    grid for the larger scenarios (a bounded sample, scaled to voxel-it/s)."""
+    from oracle.solver import Problem
+
+    pr = Problem(wl)
+    A, b, Q = loads[0]
+    nvox = wl.n[0] * wl.n[1] * wl.n[2]
+    if name == "sphere_inclusion":
+        t0 = time.perf_counter()
+        _, rep = pr.solve_step(A=A, b=b, Q=Q)
+        sec = time.perf_counter() - t0
+        its = rep.iterations
+        sample = f"the whole first load step ({its} iterations) of the FP64 oracle on the full grid"
+    else:
+        its = 2
+        Gs = pr.grad_ustar(A, b, Q)
+        u = np.zeros(pr.grid.node_shape)
+        t0 = time.perf_counter()
+        for _ in range(its):
+            p_, D, P, G, SD, SP = pr.residual(u, Gs)
+            u = pr.green_update(p_)
+        sec = time.perf_counter() - t0
+        sample = f"{its} fixed-point iterations of the first load step of the FP64 oracle on the full grid"
+    return {"impl": "reference", "metric": METRIC, "value": nvox * its / sec, "unit": UNIT, "dtype": "f64",
+            "data": "synthetic", "seconds": sec,
+            "cpu_baseline": {"value": nvox * its / sec, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": sample},
+            "config": {"workload": desc}}
 
 
 def main(argv=None):

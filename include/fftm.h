@@ -91,7 +91,7 @@ enum fftm_law {
   FFTM_LAW_NEO_HOOKE = 5,     /* finite strain, params mu, K: psi = mu/2 (J^(-2/3)
                                  tr(F^T F) - 3) + K/2 (J - 1)^2, P = F dpsi/dE
                                  (Appendix B)                                   */
-  FFTM_LAW_CP_FCC = 6         /* finite-strain FCC crystal plasticity (Sec. 3.4):
+  FFTM_LAW_CP_FCC = 6,        /* finite-strain FCC crystal plasticity (Sec. 3.4):
                                  F = F^e F^p, Pi = C : E^e (cubic C11, C12, C44,
                                  quat = lattice orientation), 12 {111}<110>
                                  systems, gdot_s = gdot0 |tau_s/tau_c|^n sign,
@@ -100,6 +100,18 @@ enum fftm_law {
                                  implicit increment of length dt per load step.
                                  params: C11, C12, C44, gdot0, n, tau0, tau_inf,
                                  h0, dt.  Not combinable with J2 phases.         */
+  FFTM_LAW_LOG_J2 = 7         /* finite-strain perfect von Mises plasticity in the
+                                 logarithmic strain space (Sec. 3.2, the porous
+                                 medium): Hencky strain H = log(F^T F)/2 split
+                                 additively into H^e + H^p, T = 2 mu dev H^e +
+                                 K tr H^e 1 the stress conjugate to H (K = lambda
+                                 + 2 mu / 3), yield sqrt(3/2) |dev T| = sigma0,
+                                 backward-Euler radial return from the committed
+                                 (H^p, p), second Piola-Kirchhoff S = T : d log C
+                                 / d C (C = F^T F), P = F S.  params: lambda, mu,
+                                 sigma0.  Committed when a load step converges.
+                                 Not combinable with J2 or crystal-plasticity
+                                 phases.                                        */
 };
 
 /* ---- descriptors ------------------------------------------------------ */
@@ -234,8 +246,9 @@ enum fftm_field {
   FFTM_FIELD_STATE = 5   /* committed internal variables at voxel points: J2
                             problems 7 comps (eps^p 11, 22, 33, 23, 13, 12 and
                             the cumulated plastic strain p), crystal plasticity
-                            10 comps (F^p row-major, cumulated slip Gamma);
-                            zero in voxels of other laws; FFTM_E_INVALID for
+                            10 comps (F^p row-major, cumulated slip Gamma),
+                            logarithmic J2 7 comps (H^p 11, 22, 33, 23, 13, 12
+                            and p); zero in voxels of other laws; FFTM_E_INVALID for
                             problems without such a phase                    */
 };
 
@@ -383,6 +396,12 @@ int fftm_host_dense_transform(int kind, int n, int inverse, double* out, int* L_
    the free components of `mask`, zero elsewhere, C0 the isotropic reference stiffness
    (lambda0, mu0 > 0).  sig and d_out: HOST 3x3 row-major. */
 int fftm_host_mixed_increment(const double* sig, int mask, double lambda0, double mu0, double* d_out);
+
+/* The logarithmic J2 law (FFTM_LAW_LOG_J2) at one voxel point, evaluated on the host by the
+   same code the kernels run (FP64): G (9, G[3 i + q] = D_i u_q), params (lambda, mu, sigma0),
+   st (7: the committed H^p 11, 22, 33, 23, 13, 12 and p) -> S (9, S[3 i + q] = P_qi) and, when
+   st_out is not NULL, the returned state (7).  All HOST pointers; FFTM_E_INVALID on NULL. */
+int fftm_host_log_j2(const double* G, const double* params, const double* st, double* S, double* st_out);
 
 #ifdef __cplusplus
 }

@@ -282,7 +282,8 @@ struct fftm_problem {
   int mixed_prev = 0;       // that step's mask (0: none since creation or reset)
   void* Dn = nullptr;       // residual D at the last commit (3 comps)
   int committed = 0;        // a load step has been committed since creation or reset
-  int nst = 0;              // state components per voxel point (7 J2, 10 crystal plasticity, 0 none)
+  int nst = 0;              // state components per voxel point (7 J2 and logarithmic J2, 10 crystal plasticity, 0 none)
+  int slaw = 0;             // 1 J2, 2 crystal plasticity, 4 logarithmic J2, 0 none
   void* state_next = nullptr;  // the state committed by the last converged step, swapped in when
   int commit_pending = 0;      // the next step starts (readouts until then see the step's own state)
   int inc_ok = 0;           // incremental residual after a commit (J2 with linear small-strain laws)
@@ -609,6 +610,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   R.sym = p->sym;
   R.state = reinterpret_cast<T*>(p->state);
   R.nst = p->nst;
+  R.slaw = p->slaw;
   R.quad = 0;
   R.dquad = 0;
   for (int q = 0; q < 3; ++q) {
@@ -1126,10 +1128,10 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
   if (converged && p->state) {  // a9: commit the internal variables of the converged step
     ResParams<T> R = res_params<T>(p, p->cur, nullptr, nullptr);
     ProfScope ps(p, FFTM_KCAT_OTHER);
-    // J2 is rate-independent: its return at the converged field from the committed state
+    // J2 and logarithmic J2 are rate-independent: the return at the converged field from the committed state
     // gives back the converged stress, so it commits in place.  The rate-dependent crystal
     // plasticity law would slip further; its commit waits in state_next for the next step.
-    if (p->nst == 10) {
+    if (p->slaw == 2) {
       CU(launch_commit<T>(R, p->tetra, reinterpret_cast<T*>(p->state_next), s));
       p->commit_pending = 1;
     } else {
@@ -1194,8 +1196,13 @@ int validate(const fftm_problem_desc* d) {
     const int law = d->materials[i].law;
     if (law != FFTM_LAW_ISO_ELASTIC && law != FFTM_LAW_CUBIC_ELASTIC && law != FFTM_LAW_B0_LINEAR &&
         law != FFTM_LAW_J2_LINHARD && law != FFTM_LAW_SVK_CUBIC && law != FFTM_LAW_NEO_HOOKE &&
-        law != FFTM_LAW_CP_FCC)
+        law != FFTM_LAW_CP_FCC && law != FFTM_LAW_LOG_J2)
       return set_err(FFTM_E_INVALID, "unknown law");
+    if (law == FFTM_LAW_LOG_J2) {
+      const double* c = d->materials[i].params;
+      if (!(c[1] > 0.0) || !(3.0 * c[0] + 2.0 * c[1] > 0.0) || !(c[2] > 0.0))
+        return set_err(FFTM_E_INVALID, "logarithmic J2 needs mu > 0, 3 lambda + 2 mu > 0, sigma0 > 0");
+    }
     if (law == FFTM_LAW_CP_FCC) {
       const double* c = d->materials[i].params;
       if (!(c[0] > 0 && c[1] > 0 && c[2] > 0 && c[3] > 0 && c[4] >= 1 && c[5] > 0 && c[6] >= c[5] && c[7] >= 0 &&
@@ -1212,12 +1219,15 @@ int validate(const fftm_problem_desc* d) {
     }
   }
   {
-    bool j2 = false, cp = false;
+    bool j2 = false, cp = false, lj2 = false;
     for (int i = 0; i < d->n_phases; ++i) {
       j2 |= d->materials[i].law == FFTM_LAW_J2_LINHARD;
       cp |= d->materials[i].law == FFTM_LAW_CP_FCC;
+      lj2 |= d->materials[i].law == FFTM_LAW_LOG_J2;
     }
-    if (j2 && cp) return set_err(FFTM_E_UNSUPPORTED, "J2 and crystal-plasticity phases in one problem");
+    if ((int)j2 + (int)cp + (int)lj2 > 1)
+      return set_err(FFTM_E_UNSUPPORTED, "phases of more than one law with internal variables (J2, crystal "
+                                         "plasticity, logarithmic J2) in one problem");
   }
   for (int a = 0; a < 3; ++a) {
     int np = 0;
@@ -1318,12 +1328,14 @@ int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
   const long long nvox = (long long)desc->n[0] * desc->n[1] * desc->n[2];
   const size_t esz = desc->precision == FFTM_FP64 ? 8 : 4;
   const size_t vsb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 9 * nvox * esz;
-  size_t stb = 0;
+  size_t stb = 0;  // committed state and next state; J2 also u^f and D at the commit
   for (int i = 0; i < desc->n_phases; ++i)
     if (desc->materials[i].law == FFTM_LAW_J2_LINHARD)
-      stb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 7 * nvox * esz + (esz == 4 ? 9 : 6) * s.comp_stride * esz;
+      stb = 2 * (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 7 * nvox * esz + (esz == 4 ? 9 : 6) * s.comp_stride * esz;
     else if (desc->materials[i].law == FFTM_LAW_CP_FCC)
-      stb = (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 10 * nvox * esz;
+      stb = 2 * (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 10 * nvox * esz;
+    else if (desc->materials[i].law == FFTM_LAW_LOG_J2)
+      stb = 2 * (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 7 * nvox * esz;
   *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + stb + nvox * sizeof(uint16_t) +
            desc->n_phases * sizeof(int);
   return FFTM_OK;
@@ -1416,16 +1428,19 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
     return set_err(FFTM_E_NOMEM, "device allocation of the fields failed");
   }
   CU(cudaMemsetAsync(p->fields, 0, sz.fields, s));
-  bool has_j2 = false, has_cp = false, finite = false;
+  bool has_j2 = false, has_cp = false, has_lj2 = false, finite = false;
   for (int i = 0; i < desc->n_phases; ++i) {
     const int law = desc->materials[i].law;
-    if (law == FFTM_LAW_B0_LINEAR || law == FFTM_LAW_SVK_CUBIC || law == FFTM_LAW_NEO_HOOKE || law == FFTM_LAW_CP_FCC)
-      p->sym = 0;
+    const bool fin = law == FFTM_LAW_SVK_CUBIC || law == FFTM_LAW_NEO_HOOKE || law == FFTM_LAW_CP_FCC ||
+                     law == FFTM_LAW_LOG_J2;
+    if (law == FFTM_LAW_B0_LINEAR || fin) p->sym = 0;
     has_j2 |= law == FFTM_LAW_J2_LINHARD;
     has_cp |= law == FFTM_LAW_CP_FCC;
-    finite |= law == FFTM_LAW_SVK_CUBIC || law == FFTM_LAW_NEO_HOOKE || law == FFTM_LAW_CP_FCC;
+    has_lj2 |= law == FFTM_LAW_LOG_J2;
+    finite |= fin;
   }
-  p->nst = has_cp ? 10 : (has_j2 ? 7 : 0);
+  p->nst = has_cp ? 10 : ((has_j2 || has_lj2) ? 7 : 0);
+  p->slaw = has_cp ? 2 : (has_j2 ? 1 : (has_lj2 ? 4 : 0));
   p->inc_ok = has_j2 && !finite;
   CU(cudaMalloc(&p->vs, (size_t)(p->tetra ? 2 : 1) * (p->sym ? 6 : 9) * p->nvox * p->esz));
   if (p->nst) {
@@ -1586,6 +1601,8 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         for (int b = a; b < 6; ++b) c[k++] = Cm[a][b];
     } else if (m.law == FFTM_LAW_J2_LINHARD) {
       for (int k = 0; k < 4; ++k) c[k] = m.params[k];
+    } else if (m.law == FFTM_LAW_LOG_J2) {
+      for (int k = 0; k < 3; ++k) c[k] = m.params[k];
     } else if (m.law == FFTM_LAW_CP_FCC) {
       double R[3][3], Cm[6][6];
       quat_rot(m.quat, R);

@@ -86,7 +86,8 @@ struct ResParams {
   // elastic strain e_n (11,22,33,23,13,12) and p_n per voxel point [r][7][voxel], and
   // the trial strain is e_n + sym(grad(u^f - u^f_n) + grad(u* - u*_n)).
   T* state;          // null: no phase with internal variables
-  int nst;           // state components per voxel point: 7 (J2) or 10 (crystal plasticity)
+  int nst;           // state components per voxel point: 7 (J2, logarithmic J2) or 10 (crystal plasticity)
+  int slaw;          // the law with internal variables: 1 J2, 2 crystal plasticity, 4 logarithmic J2, 0 none
   const T* un[3];    // u^f at the last commit (high part in FP32)
   long long nsy, nsz;  // node strides of un (the problem's layout; sy, sz may describe a caller's)
   const T* unlo[3];  // its low part (FP32 only)
@@ -108,7 +109,7 @@ struct ResParams {
   // ghost voxels across it (incremental form: the traction change since the commit)
   int traction;
   T tr[3][2][3];
-  T* vs;             // voxel-point stress buffer [r][c][voxel] (c < NC, see fftm_stencil.cu)
+  T* vs;             // voxel-point stress buffer [r][c][voxel] (c < NC, see fftm_stencil.cuh)
   int sym;           // 1: every law gives a symmetric P (6 stored components)
   int two_pass;      // 1: evaluate the residual as two grid passes even where one pass serves
   int fused_fy;      // voxel tile height of the one-pass residual (8 or 16)

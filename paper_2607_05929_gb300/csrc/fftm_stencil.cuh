@@ -30,13 +30,16 @@
 // redirected to the mirror voxel inside, with the sign sigma(u_q, face) *
 // (-1 if i is the face normal) on component (i, q), and with T1 <-> T2
 // swapped once per face crossed (Sec. 2.2, Sec. 2.5.2).  Periodic axes wrap.
+#pragma once
+// Included by fftm_stencil_f32.cu and fftm_stencil_f64.cu, which instantiate the launchers for
+// one precision each (two translation units that compile in parallel).
 #include <algorithm>
 
 #include "fftm_internal.cuh"
 
 namespace fftm {
 
-enum { LAW_ISO = 0, LAW_CUBIC = 1, LAW_J2 = 2, LAW_B0 = 3, LAW_SVK = 4, LAW_NEOHOOKE = 5, LAW_CP = 6 };
+enum { LAW_ISO = 0, LAW_CUBIC = 1, LAW_J2 = 2, LAW_B0 = 3, LAW_SVK = 4, LAW_NEOHOOKE = 5, LAW_CP = 6, LAW_LOGJ2 = 7 };
 
 // Symmetric tensor (11, 22, 33, 23, 13, 12) -> C : E with the Mandel 6x6 stiffness stored as
 // its upper triangle row-major in c[0..20].
@@ -62,11 +65,22 @@ __device__ __forceinline__ void mandel_apply(const T* __restrict__ c, const T e[
   s[5] = ir2 * sm[5];
 }
 
+// A law constant: read through the read-only cache on the device, plainly on the host (the
+// host instantiation serves fftm_host_log_j2).
+template <typename T>
+__host__ __device__ __forceinline__ T ldc(const T* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
+
 // Finite strain (Sec. 3.1.2, Appendix B): F = 1 + H with H_qi = G[i*3+q]; the
 // Green-Lagrange strain E = (H + H^T + H^T H) / 2 is formed from H so that it keeps
 // its relative precision.  S[i*3+q] = P_qi with P = F Pi.
 template <typename T>
-__device__ __forceinline__ void green_lagrange(const T G[9], T H[3][3], T E[6]) {
+__host__ __device__ __forceinline__ void green_lagrange(const T G[9], T H[3][3], T E[6]) {
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -83,7 +97,7 @@ __device__ __forceinline__ void green_lagrange(const T G[9], T H[3][3], T E[6]) 
 }
 
 template <typename T>
-__device__ __forceinline__ void first_piola(const T H[3][3], const T Pi[6], T S[9]) {
+__host__ __device__ __forceinline__ void first_piola(const T H[3][3], const T Pi[6], T S[9]) {
   const T M[3][3] = {{Pi[0], Pi[5], Pi[4]}, {Pi[5], Pi[1], Pi[3]}, {Pi[4], Pi[3], Pi[2]}};
 #pragma unroll
   for (int q = 0; q < 3; ++q)
@@ -131,7 +145,7 @@ __device__ __forceinline__ void neo_hooke(const T* __restrict__ c, const T G[9],
 // ---- FCC crystal plasticity, finite strain (Sec. 3.4) ----------------------------
 // The 12 {111}<110> systems in the crystal frame (unnormalised plane normal, slip
 // direction); the normalisation 1/sqrt(6) of m (x) n is applied at use.
-__constant__ signed char c_fcc_sys[12][6] = {
+static __constant__ signed char c_fcc_sys[12][6] = {
     {1, 1, 1, 0, 1, -1},  {1, 1, 1, 1, 0, -1},  {1, 1, 1, 1, -1, 0},  {-1, 1, 1, 0, 1, -1},
     {-1, 1, 1, 1, 0, 1},  {-1, 1, 1, 1, 1, 0},  {1, -1, 1, 0, 1, 1},  {1, -1, 1, 1, 0, -1},
     {1, -1, 1, 1, 1, 0},  {1, 1, -1, 0, 1, 1},  {1, 1, -1, 1, 0, 1},  {1, 1, -1, 1, -1, 0}};
@@ -365,6 +379,130 @@ __device__ void cp_eval(const T* __restrict__ c, const T G[9], const T st[10], T
   }
 }
 
+// Eigen-decomposition of a symmetric 3x3 tensor A (11, 22, 33, 23, 13, 12) by cyclic
+// Jacobi rotations (each rotation zeroes one off-diagonal entry; the tangent of the angle is
+// taken as the smaller root of t^2 + 2 th t - 1 = 0, th = (a_qq - a_pp) / (2 a_pq), and the
+// other entries are updated through tau = s / (1 + c) to limit cancellation).  Returns the
+// eigenvalues w and the eigenvectors as the columns of V (row-major).  The sweep count is
+// fixed: convergence is quadratic, so 5 (FP32) or 6 (FP64) sweeps leave the off-diagonal at
+// rounding level for any input; an entry that is already zero is skipped.
+template <typename T>
+__host__ __device__ void sym_eig3(const T A6[6], T w[3], T V[9]) {
+  T a[3][3] = {{A6[0], A6[5], A6[4]}, {A6[5], A6[1], A6[3]}, {A6[4], A6[3], A6[2]}};
+#pragma unroll
+  for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? T(1) : T(0);
+  constexpr int SWEEPS = sizeof(T) == 8 ? 6 : 5;
+  for (int sw = 0; sw < SWEEPS; ++sw) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int p = k == 2 ? 1 : 0, q = k == 0 ? 1 : 2, r = 3 - p - q;
+      const T apq = a[p][q];
+      if (apq == T(0)) continue;
+      const T th = (a[q][q] - a[p][p]) / (T(2) * apq);
+      const T t = copysign(T(1), th) / (fabs(th) + sqrt(th * th + T(1)));  // th^2 = inf gives t = 0
+      const T c = T(1) / sqrt(t * t + T(1)), sn = t * c, tau = sn / (T(1) + c);
+      a[p][p] -= t * apq;
+      a[q][q] += t * apq;
+      a[p][q] = a[q][p] = T(0);
+      const T g = a[r][p], h = a[r][q];
+      a[r][p] = a[p][r] = g - sn * (h + g * tau);
+      a[r][q] = a[q][r] = h + sn * (g - h * tau);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const T vg = V[i * 3 + p], vh = V[i * 3 + q];
+        V[i * 3 + p] = vg - sn * (vh + vg * tau);
+        V[i * 3 + q] = vh + sn * (vg - vh * tau);
+      }
+    }
+  }
+  w[0] = a[0][0];
+  w[1] = a[1][1];
+  w[2] = a[2][2];
+}
+
+// Perfect von Mises plasticity in the logarithmic strain space (Sec. 3.2, the porous
+// medium; reading: T is the stress conjugate to the Hencky strain, Miehe, Apel and
+// Lambrecht 2002).  H = log C / 2 with C = F^T F = 1 + 2E; H = H^e + H^p; trial
+// H^e = H - H^p_n, T = 2 mu dev H^e + K tr H^e 1; on f = sqrt(3/2) |dev T| - sigma0 > 0 the
+// backward-Euler return scales dev T onto the yield surface, dp = f / (3 mu), H^p += dp
+// 3/2 dev T_tr / |.|_eq.  S = T : d log C / d C: in the eigenbasis of C, S_ab = theta_ab T_ab
+// with theta_ab = (log w_a - log w_b) / (w_a - w_b) (1 / w_a on the diagonal); P = F S.
+// The eigenvalues are taken from E (w_a = 1 + 2 e_a), so log w_a = log1p(2 e_a) and the
+// divided differences, r = 2 (e_a - e_b) / w_b, keep their relative precision.
+// c = (lambda, mu, sigma0); st = (H^p 11, 22, 33, 23, 13, 12; p); stn: the returned state.
+template <typename T>
+__host__ __device__ void log_j2_eval(const T* __restrict__ c, const T G[9], const T st[7], T S[9], T* stn) {
+  const T lam = ldc(c), mu = ldc(c + 1), sig0 = ldc(c + 2);
+  const T K = lam + T(2.0 / 3.0) * mu;
+  T H[3][3], E[6];
+  green_lagrange<T>(G, H, E);
+  T e[3], V[9];
+  sym_eig3<T>(E, e, V);
+  T hl[3], w[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    w[a] = T(1) + T(2) * e[a];
+    hl[a] = T(0.5) * log1p(T(2) * e[a]);
+  }
+  constexpr int I6[6][2] = {{0, 0}, {1, 1}, {2, 2}, {1, 2}, {0, 2}, {0, 1}};
+  T He[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int i = I6[k][0], j = I6[k][1];
+    He[k] = (V[i * 3] * hl[0] * V[j * 3] + V[i * 3 + 1] * hl[1] * V[j * 3 + 1] + V[i * 3 + 2] * hl[2] * V[j * 3 + 2]) -
+            st[k];
+  }
+  const T tr = He[0] + He[1] + He[2], m = tr * T(1.0 / 3.0), m2 = T(2) * mu;
+  const T s6[6] = {m2 * (He[0] - m), m2 * (He[1] - m), m2 * (He[2] - m), m2 * He[3], m2 * He[4], m2 * He[5]};
+  const T ss = s6[0] * s6[0] + s6[1] * s6[1] + s6[2] * s6[2] + T(2) * (s6[3] * s6[3] + s6[4] * s6[4] + s6[5] * s6[5]);
+  const T seq = sqrt(T(1.5) * ss);
+  const T f = seq - sig0;
+  T scale = T(1), dp = T(0);
+  if (f > T(0)) {
+    dp = f / (T(3) * mu);
+    scale = sig0 / seq;
+  }
+  if (stn) {
+    const T g = f > T(0) ? dp * T(1.5) / seq : T(0);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) stn[k] = st[k] + g * s6[k];
+    stn[6] = st[6] + dp;
+  }
+  const T kt = K * tr;
+  const T Tm[3][3] = {{scale * s6[0] + kt, scale * s6[5], scale * s6[4]},
+                      {scale * s6[5], scale * s6[1] + kt, scale * s6[3]},
+                      {scale * s6[4], scale * s6[3], scale * s6[2] + kt}};
+  // St = theta o (V^T T V), then S = V St V^T
+  T TV[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) TV[i][b] = Tm[i][0] * V[b] + Tm[i][1] * V[3 + b] + Tm[i][2] * V[6 + b];
+  T St[3][3];
+  const T near = sizeof(T) == 8 ? T(1e-10) : T(1e-30);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T tt = V[a] * TV[0][b] + V[3 + a] * TV[1][b] + V[6 + a] * TV[2][b];
+      const T r = T(2) * (e[a] - e[b]) / w[b];
+      const T th = fabs(r) < near ? T(2) / (w[a] + w[b]) : log1p(r) / (w[b] * r);
+      St[a][b] = th * tt;
+    }
+  T Pi[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const int i = I6[k][0], j = I6[k][1];
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) acc += V[i * 3 + a] * St[a][b] * V[j * 3 + b];
+    Pi[k] = acc;
+  }
+  first_piola<T>(H, Pi, S);
+}
+
 // Small-strain law on the total gradient G[i*3+q]; P returned as 9 components.
 template <typename T>
 __device__ __forceinline__ void law_eval(int law, const T* __restrict__ c, const T G[9], T Pout[9]) {
@@ -480,7 +618,7 @@ __device__ __forceinline__ void j2_inc(const T* __restrict__ c, const T dG[9], c
 
 // Law at voxel point r of voxel v from the gradient G (elastic laws: the total
 // gradient; J2: the increment since the commit).
-template <typename T, int SL = 3>
+template <typename T, int SL = 7>
 __device__ __forceinline__ void point_law(const ResParams<T>& P, int law, const T* lc, const T G[9], int r,
                                           long long v, long long nvox, T Pout[9], T* stn) {
   if ((SL & 1) && law == LAW_J2) {
@@ -495,6 +633,12 @@ __device__ __forceinline__ void point_law(const ResParams<T>& P, int law, const 
 #pragma unroll
     for (int c = 0; c < 10; ++c) st[c] = sp[c * nvox];
     cp_eval<T>(lc, G, st, Pout, stn);
+  } else if ((SL & 4) && law == LAW_LOGJ2) {
+    const T* sp = P.state + (long long)(r * P.nst) * nvox + v;
+    T st[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) st[c] = sp[c * nvox];
+    log_j2_eval<T>(lc, G, st, Pout, stn);
   } else {
     law_eval<T>(law, lc, G, Pout);
   }
@@ -1594,12 +1738,15 @@ static cudaError_t launch_res_t(const ResParams<T>& P, bool lo, cudaStream_t s, 
     if (lo) k_stress_inc<T, TETRA, true, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
     else k_stress_inc<T, TETRA, false, SYM><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
   } else {
-    if (P.nst == 7) {
+    if (P.slaw == 1) {
       if (lo) k_stress<T, TETRA, WITH_P, true, SYM, 1><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
       else k_stress<T, TETRA, WITH_P, false, SYM, 1><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
-    } else if (P.nst == 10) {
+    } else if (P.slaw == 2) {
       if (lo) k_stress<T, TETRA, WITH_P, true, SYM, 2><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
       else k_stress<T, TETRA, WITH_P, false, SYM, 2><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+    } else if (P.slaw == 4) {
+      if (lo) k_stress<T, TETRA, WITH_P, true, SYM, 4><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
+      else k_stress<T, TETRA, WITH_P, false, SYM, 4><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
     } else {
       if (lo) k_stress<T, TETRA, WITH_P, true, SYM, 0><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
       else k_stress<T, TETRA, WITH_P, false, SYM, 0><<<RBLOCKS, RTX * RTY, 0, s>>>(P, tv);
@@ -1627,10 +1774,6 @@ cudaError_t launch_residual(const ResParams<T>& P, int tetra, bool with_p, cudaS
   return tetra ? launch_res_s<T, 1>(P, with_p, s, blocks_out) : launch_res_s<T, 0>(P, with_p, s, blocks_out);
 }
 
-template cudaError_t launch_residual<float>(const ResParams<float>&, int, bool, cudaStream_t, int*);
-template cudaError_t launch_residual<double>(const ResParams<double>&, int, bool, cudaStream_t, int*);
-template int residual_blocks<float>(const ResParams<float>&, int);
-template int residual_blocks<double>(const ResParams<double>&, int);
 
 template <typename T>
 bool residual_one_pass(const ResParams<T>& P) {
@@ -1638,8 +1781,6 @@ bool residual_one_pass(const ResParams<T>& P) {
   Q.two_pass = 0;
   return fused_ok(Q, false);
 }
-template bool residual_one_pass<float>(const ResParams<float>&);
-template bool residual_one_pass<double>(const ResParams<double>&);
 
 // ---- per-voxel evaluation shared by the output and statistics kernels ----
 template <typename T, int TETRA, bool LO>
@@ -1698,10 +1839,10 @@ __global__ void k_commit(ResParams<T> P, T* __restrict__ out) {
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nv;
        v += (long long)gridDim.x * blockDim.x) {
     const int law = __ldg(P.law_id + P.phase[v]);
-    if (law != LAW_J2 && law != LAW_CP) continue;
+    if (law != LAW_J2 && law != LAW_CP && law != LAW_LOGJ2) continue;
     T Gt[2][9], Pp[2][9], stn[2][10];
     voxel_eval<T, TETRA, LO>(P, v, Gt, Pp, stn);
-    const int nc = law == LAW_J2 ? 7 : 10;
+    const int nc = law == LAW_CP ? 10 : 7;
     for (int r = 0; r < (TETRA ? 2 : 1); ++r)
       for (int c = 0; c < nc; ++c) out[v + nv * (c + P.nst * r)] = stn[r][c];
   }
@@ -1720,8 +1861,6 @@ cudaError_t launch_commit(const ResParams<T>& P, int tetra, T* out, cudaStream_t
   }
   return cudaGetLastError();
 }
-template cudaError_t launch_commit<float>(const ResParams<float>&, int, float*, cudaStream_t);
-template cudaError_t launch_commit<double>(const ResParams<double>&, int, double*, cudaStream_t);
 
 template <typename T, int TETRA, bool LO>
 __global__ void k_state_io(ResParams<T> P, T* __restrict__ out, const T* __restrict__ in) {
@@ -1740,6 +1879,16 @@ __global__ void k_state_io(ResParams<T> P, T* __restrict__ out, const T* __restr
         }
         if (out) out[v + nv * (9 + P.nst * r)] = st[nv * 9];
         else st[nv * 9] = in[v + nv * (9 + P.nst * r)];
+      }
+      continue;
+    }
+    if (law == LAW_LOGJ2) {  // stored as read out: H^p (6), p
+      for (int r = 0; r < (TETRA ? 2 : 1); ++r) {
+        T* st = P.state + v + nv * (P.nst * r);
+        for (int c = 0; c < 7; ++c) {
+          if (out) out[v + nv * (c + P.nst * r)] = st[nv * c];
+          else st[nv * c] = in[v + nv * (c + P.nst * r)];
+        }
       }
       continue;
     }
@@ -1796,8 +1945,6 @@ cudaError_t launch_state_io(const ResParams<T>& P, int tetra, T* out, const T* i
   }
   return cudaGetLastError();
 }
-template cudaError_t launch_state_io<float>(const ResParams<float>&, int, float*, const float*, cudaStream_t);
-template cudaError_t launch_state_io<double>(const ResParams<double>&, int, double*, const double*, cudaStream_t);
 
 template <typename T, int TETRA, bool LO>
 __global__ void k_voxel_fields(ResParams<T> P, T* __restrict__ gout, T* __restrict__ sout) {
@@ -1836,8 +1983,6 @@ cudaError_t launch_voxel_fields(const ResParams<T>& P, int tetra, T* grad_out, T
   }
   return cudaGetLastError();
 }
-template cudaError_t launch_voxel_fields<float>(const ResParams<float>&, int, float*, float*, cudaStream_t);
-template cudaError_t launch_voxel_fields<double>(const ResParams<double>&, int, double*, double*, cudaStream_t);
 
 // ---- volume means of P and G (step report) ----
 template <typename T, int TETRA, bool LO>
@@ -1877,7 +2022,5 @@ cudaError_t launch_stats(const ResParams<T>& P, int tetra, double* partial, int 
   }
   return cudaGetLastError();
 }
-template cudaError_t launch_stats<float>(const ResParams<float>&, int, double*, int, cudaStream_t);
-template cudaError_t launch_stats<double>(const ResParams<double>&, int, double*, int, cudaStream_t);
 
 }  // namespace fftm

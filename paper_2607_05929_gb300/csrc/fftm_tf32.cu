@@ -17,9 +17,9 @@
 // pencils, K-major); TMEM lanes are outputs and a warp stores 32 consecutive nodes of a row.
 //
 // The contraction dimension streams through a ring of shared-memory stages, each holding
-// 32 K-columns of the tile (filled by seven producer warps from 16-byte loads, transposed in
-// 4 x 4 blocks on y and z and rounded to the nearest TF32) and of the matrix (one bulk copy,
-// entries rounded to TF32 on the host).  One thread issues the MMAs
+// 32 K-columns of the tile (filled by seven producer warps with 16-byte cp.async copies, up to
+// three stages in flight, then transposed in 4 x 4 blocks on y and z and rounded to the nearest
+// TF32 in place) and of the matrix (one bulk copy, entries rounded to TF32 on the host).  One thread issues the MMAs
 // of a stage as soon as both halves have landed and releases the stage when they have read
 // it; eight epilogue warps drain the TMEM accumulators (two, alternating, when they fit)
 // while the next tile is contracted.  Every wait is bounded: past the limit the CTA records
@@ -135,9 +135,15 @@ __device__ __forceinline__ int tf_total_tiles(const TfPassParams& P) {
 // The tile part of a stage holds 128 rows (pencils) x 32 K values in the K-major core-matrix
 // order: element (p, k) at (p>>3) 1024 + (k>>2) 128 + (p&7) 16 + (k&3) 4 bytes (LBO = 128
 // along K, SBO = 1024 per 8 rows), zero where it falls outside the array or the tile.
-//  x axis: 1024 pieces (row p, group g) of 4 consecutive x, copied with 16-byte cp.async.
-//  y, z axes: 256 blocks (pencil group pg, row group kq) of 4 pencils x 4 rows, loaded as
-//    four 16-byte rows and transposed in registers (each pencil's 4 K values in one store).
+// The producers fill it in two steps: 16-byte cp.async copies from global memory (zero-filled
+// outside), several stages in flight per thread without holding registers, then, once a
+// thread's copies of a stage have landed, an in-place pass over the cells it copied:
+//  x axis: 1024 pieces (row p, group g) of 4 consecutive x land in their final cells; the pass
+//    rounds them to the nearest TF32;
+//  y, z axes: 256 blocks (pencil group pg, row group kq) of 4 pencils x 4 rows; row 4 kq + r of
+//    pencils 4 pg .. 4 pg + 3 lands in the cell of pencil 4 pg + r, so the pass reads the
+//    block's four cells, transposes them in registers (each pencil's 4 K values in one cell)
+//    and writes them back rounded, to the same four cells.
 constexpr int TF_XPC = 5;  // x axis: 16-byte pieces per producer thread and stage (1024 pieces, 224 threads)
 
 constexpr int TF_BLK = 2;  // 4 x 4 blocks per producer thread and stage (256 blocks, 224 threads)
@@ -149,12 +155,24 @@ __device__ __forceinline__ float tf32r(float x) {
   return __uint_as_float(r);
 }
 
-struct TfBlocks {
-  float4 v[8];  // y, z: TF_BLK blocks of 4 rows; x: TF_XPC pieces
-};
+__device__ __forceinline__ void cp_async16(uint32_t dst, const float* src, bool ok) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(ok ? 16 : 0) : "memory");
+}
+
+// waits until at most n of this thread's copy groups are still in flight (n <= 3)
+__device__ __forceinline__ void cp_async_wait(int n) {
+  if (n <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  else if (n == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  else if (n == 2) asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+  else asm volatile("cp.async.wait_group 3;\n" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t tf_cell(int p, int kq) {
+  return (uint32_t)(p >> 3) * 1024u + (uint32_t)kq * 128u + (uint32_t)(p & 7) * 16u;
+}
 
 template <int AXIS>
-__device__ __forceinline__ void tf_load(const TfPassParams& P, const TfTile& T, int c, int ptid, TfBlocks& B) {
+__device__ __forceinline__ void tf_issue(const TfPassParams& P, const TfTile& T, int c, int ptid, uint32_t sdst) {
   const float* __restrict__ in = P.in[T.q];
   const long long PX = P.stride[1];  // row pitch (a multiple of 8, >= N1)
   if (AXIS == 0) {
@@ -164,47 +182,55 @@ __device__ __forceinline__ void tf_load(const TfPassParams& P, const TfTile& T, 
 #pragma unroll
     for (int k = 0; k < TF_XPC; ++k) {
       const int i = ptid + k * TF_PROD;
+      if (i >= TF_P * 8) continue;
       const int p = i >> 3, gq = i & 7;
       const int x = xb + TF_KC * c + 4 * gq;
       const int r = T.row0 + p;
-      const bool ok = i < TF_P * 8 && p < T.npen && x < PX;
-      B.v[k] = ok ? __ldg(reinterpret_cast<const float4*>(in + (long long)(r % N2) * sy + (long long)(r / N2) * sz + x))
-                  : make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool ok = p < T.npen && x < PX;
+      const float* src = ok ? in + (long long)(r % N2) * sy + (long long)(r / N2) * sz + x : in;
+      cp_async16(sdst + tf_cell(p, gq), src, ok);
     }
   } else {
     const int Nax = P.N[AXIS];
 #pragma unroll
     for (int b = 0; b < TF_BLK; ++b) {
       const int i = ptid + b * TF_PROD;
+      if (i >= 256) continue;
       const int pg = i & 31, kq = i >> 5;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const int row = T.lo + TF_KC * c + 4 * kq + r;
-        const bool ok = i < 256 && row < Nax && T.x0 + 4 * pg < PX;
-        B.v[4 * b + r] = ok ? __ldg(reinterpret_cast<const float4*>(in + T.base0 + (long long)row * T.estride + 4 * pg))
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool ok = row < Nax && T.x0 + 4 * pg < PX;
+        const float* src = ok ? in + T.base0 + (long long)row * T.estride + 4 * pg : in;
+        cp_async16(sdst + tf_cell(4 * pg + r, kq), src, ok);
       }
     }
   }
+}
+
+__device__ __forceinline__ float4 ld_shared4(uint32_t a) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a)
+               : "memory");
+  return v;
 }
 
 __device__ __forceinline__ void st_shared4(uint32_t d, float a, float b, float c, float e) {
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(d), "f"(a), "f"(b), "f"(c), "f"(e) : "memory");
 }
 
-// Stores a stage's tile part, every value rounded to the nearest TF32 (the tensor cores would
-// drop the low bits instead).
+// The in-place pass over this thread's cells of a landed stage: every value rounded to the
+// nearest TF32 (the tensor cores would drop the low bits instead), y and z blocks transposed.
 template <int AXIS>
-__device__ __forceinline__ void tf_store(uint32_t sdst, int ptid, const TfBlocks& B) {
+__device__ __forceinline__ void tf_process(uint32_t sdst, int ptid) {
   if (AXIS == 0) {
 #pragma unroll
     for (int k = 0; k < TF_XPC; ++k) {
       const int i = ptid + k * TF_PROD;
       if (i >= TF_P * 8) continue;
-      const int p = i >> 3, gq = i & 7;
-      const float4 v = B.v[k];
-      st_shared4(sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)gq * 128u + (uint32_t)(p & 7) * 16u, tf32r(v.x),
-                 tf32r(v.y), tf32r(v.z), tf32r(v.w));
+      const uint32_t a = sdst + tf_cell(i >> 3, i & 7);
+      const float4 v = ld_shared4(a);
+      st_shared4(a, tf32r(v.x), tf32r(v.y), tf32r(v.z), tf32r(v.w));
     }
   } else {
 #pragma unroll
@@ -212,15 +238,13 @@ __device__ __forceinline__ void tf_store(uint32_t sdst, int ptid, const TfBlocks
       const int i = ptid + b * TF_PROD;
       if (i >= 256) continue;
       const int pg = i & 31, kq = i >> 5;
-      const float4* v = B.v + 4 * b;
-      const float4 w[4] = {make_float4(v[0].x, v[1].x, v[2].x, v[3].x), make_float4(v[0].y, v[1].y, v[2].y, v[3].y),
-                           make_float4(v[0].z, v[1].z, v[2].z, v[3].z), make_float4(v[0].w, v[1].w, v[2].w, v[3].w)};
+      float4 v[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int p = 4 * pg + e;
-        st_shared4(sdst + (uint32_t)(p >> 3) * 1024u + (uint32_t)kq * 128u + (uint32_t)(p & 7) * 16u,
-                   tf32r(w[e].x), tf32r(w[e].y), tf32r(w[e].z), tf32r(w[e].w));
-      }
+      for (int r = 0; r < 4; ++r) v[r] = ld_shared4(sdst + tf_cell(4 * pg + r, kq));
+      st_shared4(sdst + tf_cell(4 * pg, kq), tf32r(v[0].x), tf32r(v[1].x), tf32r(v[2].x), tf32r(v[3].x));
+      st_shared4(sdst + tf_cell(4 * pg + 1, kq), tf32r(v[0].y), tf32r(v[1].y), tf32r(v[2].y), tf32r(v[3].y));
+      st_shared4(sdst + tf_cell(4 * pg + 2, kq), tf32r(v[0].z), tf32r(v[1].z), tf32r(v[2].z), tf32r(v[3].z));
+      st_shared4(sdst + tf_cell(4 * pg + 3, kq), tf32r(v[0].w), tf32r(v[1].w), tf32r(v[2].w), tf32r(v[3].w));
     }
   }
 }
@@ -533,36 +557,39 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
   const uint32_t tmem = *tmem_slot;
 
   if (warp >= TF_EPI / 32 && warp < (TF_EPI + TF_PROD) / 32) {
-    // ---- producers: the tile part of every stage, the next stage's loads in flight while
-    // this one is rounded and stored ----
+    // ---- producers: the tile part of every stage; up to `depth` stages of copies in flight,
+    // the oldest processed and handed to the MMA thread as soon as it has landed ----
     const int ptid = tid - TF_EPI;
-    long long seq = 0;
-    TfBlocks cur, nxt;
+    const int depth = g.nst - 1 < 3 ? g.nst - 1 : 3;
+    long long seq = 0, done = 0;  // stages issued, stages handed over
     int ti = 0, c = 0;
     TfTile T;
-    if (my_tiles > 0) {
-      T = tf_tile_of<AXIS>(P, blockIdx.x);
-      tf_load<AXIS>(P, T, 0, ptid, cur);
-    }
+    if (my_tiles > 0) T = tf_tile_of<AXIS>(P, blockIdx.x);
     while (ti < my_tiles) {
       const int s = (int)(seq % g.nst);
       const long long u = seq / g.nst;
-      int nti = ti, nc = c + 1;  // position of the next stage
-      TfTile NT = T;
-      if (nc == T.Kp / TF_KC) {
-        nc = 0;
-        if (++nti < my_tiles) NT = tf_tile_of<AXIS>(P, blockIdx.x + nti * gridDim.x);
-      }
-      if (nti < my_tiles) tf_load<AXIS>(P, NT, nc, ptid, nxt);
       if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) break;
-      tf_store<AXIS>(smem_u32(stages + (size_t)s * g.stage), ptid, cur);
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      bar_arrive(&B.full[s]);
+      tf_issue<AXIS>(P, T, c, ptid, smem_u32(stages + (size_t)s * g.stage));
+      cp_async_commit();
       ++seq;
-      cur = nxt;
-      ti = nti;
-      c = nc;
-      T = NT;
+      if (++c == T.Kp / TF_KC) {
+        c = 0;
+        if (++ti < my_tiles) T = tf_tile_of<AXIS>(P, blockIdx.x + ti * gridDim.x);
+      }
+      if (seq - done == depth) {
+        cp_async_wait(depth - 1);
+        tf_process<AXIS>(smem_u32(stages + (size_t)(done % g.nst) * g.stage), ptid);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        bar_arrive(&B.full[(int)(done % g.nst)]);
+        ++done;
+      }
+    }
+    // the stages still in flight (all of them after an abort, whose copies must land before exit)
+    cp_async_wait(0);
+    for (; done < seq; ++done) {
+      tf_process<AXIS>(smem_u32(stages + (size_t)(done % g.nst) * g.stage), ptid);
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      bar_arrive(&B.full[(int)(done % g.nst)]);
     }
   } else if (warp == (TF_EPI + TF_PROD) / 32) {
     // ---- warp 15: lane 0 copies the matrix chunks and issues the MMAs ----

@@ -30,6 +30,7 @@ FFTM_HEX1, FFTM_TETRA2 = 0, 1
 FFTM_GREEN_B0, FFTM_GREEN_MU0 = 0, 1
 FFTM_FP64, FFTM_FP32, FFTM_FP32_TC, FFTM_FP32_TF32 = 0, 1, 2, 3
 FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
+FFTM_LAW_SVK_CUBIC, FFTM_LAW_NEO_HOOKE, FFTM_LAW_CP_FCC, FFTM_LAW_LOG_J2 = 4, 5, 6, 7
 FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D, FFTM_FIELD_STATE = 0, 1, 2, 3, 4, 5
 FFTM_OPT_RESIDUAL_PASSES, FFTM_OPT_RESIDUAL_TILE, FFTM_OPT_DEVICE_LOOP = 0, 1, 2
 FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP_GREEN_UPDATE = 0, 1, 2, 3, 4
@@ -43,7 +44,7 @@ EXPORTS = [
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
     "fftm_server_inject_start_failures",
-    "fftm_host_dense_transform", "fftm_host_mixed_increment",
+    "fftm_host_dense_transform", "fftm_host_mixed_increment", "fftm_host_log_j2",
 ]
 FFTM_DT_KINDS = {"DFT": 0, "DCT1": 1, "DCT3": 2, "DST1": 3, "DST3": 4}
 FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "other"]
@@ -124,6 +125,7 @@ def load_library(path=LIB_PATH):
                                        P(ctypes.c_int)], ctypes.c_int),
         "fftm_host_mixed_increment": ([P(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        P(ctypes.c_double)], ctypes.c_int),
+        "fftm_host_log_j2": ([P(ctypes.c_double)] * 5, ctypes.c_int),
         "fftm_solve_step": ([vp, P(fftm_step_report), P(ctypes.c_double), P(ctypes.c_int), ctypes.c_int],
                             ctypes.c_int),
         "fftm_field_bytes": ([vp, ctypes.c_int, P(ctypes.c_size_t)], ctypes.c_int),
@@ -281,6 +283,19 @@ def fftm_host_dense_transform(kind, n, inverse=False):
                                                     out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                     ctypes.byref(L)))
     return out.reshape(L.value, L.value)
+
+
+def fftm_host_log_j2(G, params, st):
+    """The library's logarithmic J2 law at one point (host only): G (9,), params (3,), st (7,)
+    -> (S (9,), returned state (7,))."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    g = np.ascontiguousarray(np.asarray(G, dtype=np.float64).reshape(9))
+    c = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(3))
+    z = np.ascontiguousarray(np.asarray(st, dtype=np.float64).reshape(7))
+    S, zn = np.zeros(9), np.zeros(7)
+    _check(load_library().fftm_host_log_j2(g.ctypes.data_as(dp), c.ctypes.data_as(dp), z.ctypes.data_as(dp),
+                                           S.ctypes.data_as(dp), zn.ctypes.data_as(dp)))
+    return S, zn
 
 
 def fftm_host_mixed_increment(sig, mask, lambda0, mu0):

@@ -34,10 +34,10 @@ def _requests(count, max_side=48):
     return out
 
 
-def _desc(wl, precision="fp32"):
+def _desc(wl, precision="fp32", tol=None):
     mats = [(m.law, m.params, m.quat) for m in wl.materials]
     return F.make_desc(wl.n, wl.phase, mats, wl.bc, scheme=wl.scheme, green=wl.green, lambda0=wl.lambda0,
-                       mu0=wl.mu0, precision=precision, tol=wl.tol, max_iter=wl.max_iter)
+                       mu0=wl.mu0, precision=precision, tol=wl.tol if tol is None else tol, max_iter=wl.max_iter)
 
 
 def _u_buffer(wl):
@@ -45,12 +45,12 @@ def _u_buffer(wl):
     return np.zeros((3, N[2], N[1], N[0]), dtype=np.float32)
 
 
-def _run(reqs, slots, one_at_a_time, precision="fp32"):
+def _run(reqs, slots, one_at_a_time, precision="fp32", tol=None):
     srv = F.fftm_server_create(0, 0, slots)
     results, us, keep = {}, {}, []
     try:
         for i, (wl, loads) in enumerate(reqs):
-            desc, kp = _desc(wl, precision)
+            desc, kp = _desc(wl, precision, tol)
             u = _u_buffer(wl)
             keep.append((kp, u))
             rid = F.fftm_server_submit(srv, desc, loads, u_out=u)
@@ -114,15 +114,19 @@ def test_admission_respects_the_memory_budget_and_refuses_oversize():
 
 def test_served_results_match_the_fp64_oracle():
     """Every small served request, solved in the mix on four slots with the precision form (FP32
-    fields, TF32 tensor-core transforms), against the FP64 oracle run
-    through the same load steps: the strain and stress fields of the served u^f (evaluated by the
-    oracle's own gradient and law, from its committed state) to 1e-5 relative L2 of the oracle's
-    converged fields, the mean stress of the last step to 1e-5, the iteration count within +-2
-    per load step."""
+    fields, TF32 tensor-core transforms), against the FP64 oracle run through the same load
+    steps at the stream's tolerance: the iteration count within +-2 per load step, the stress
+    field of the served u^f (evaluated by the oracle's own gradient and law, from its committed
+    state) to 1e-5 relative L2 of the oracle's converged stress, the mean stress of the last step
+    to 1e-5.  The strain of the softer phase is the most sensitive field: two iterates that both
+    meet the tolerance may differ in it by the tolerance times the conditioning of the fixed
+    point, so it is held against the exact discrete solution (the oracle run to 1e-9): within
+    1e-5 of it, or no farther from it than twice the oracle's own iterate at the same tolerance."""
     from oracle.solver import Problem
 
     reqs = _requests(6, max_side=32)
     mixed, u_mixed = _run(reqs, 4, False, precision="fp32_tf32")
+    sym = lambda G: 0.5 * (G + np.swapaxes(G, 1, 2))  # noqa: E731
     for i, (wl, loads) in enumerate(reqs):
         pr = Problem(wl)
         iters = 0
@@ -130,16 +134,22 @@ def test_served_results_match_the_fp64_oracle():
             _, rep = pr.solve_step(A=A, b=b, Q=Q, tol=wl.tol)
             assert rep.converged
             iters += rep.iterations
+        px = Problem(wl)
+        for A, b, Q in loads:
+            _, rep = px.solve_step(A=A, b=b, Q=Q, tol=1e-9)
+            assert rep.converged
         r = mixed[i]
         assert r["status"] == F.FFTM_OK and r["converged_steps"] == len(loads), r
         assert abs(r["iterations"] - iters) <= 2 * len(loads), (i, r["iterations"], iters)
         u = np.asarray(u_mixed[i], dtype=np.float64).transpose(0, 3, 2, 1)
         A, b, Q = loads[-1]
         _, _, P_s, G_s, _, _ = pr.residual(u, pr.grad_ustar(A, b, Q))
-        P_o, G_o = pr.last["P"], pr.last["G"]
-        sym = lambda G: 0.5 * (G + np.swapaxes(G, 1, 2))  # noqa: E731
+        P_o, G_o, G_x = pr.last["P"], pr.last["G"], px.last["G"]
         assert np.linalg.norm(P_s - P_o) <= 1e-5 * np.linalg.norm(P_o), i
-        assert np.linalg.norm(sym(G_s) - sym(G_o)) <= 1e-5 * np.linalg.norm(sym(G_o)), i
+        nx = np.linalg.norm(sym(G_x))
+        served = np.linalg.norm(sym(G_s) - sym(G_x)) / nx
+        own = np.linalg.norm(sym(G_o) - sym(G_x)) / nx
+        assert served <= max(1e-5, 2 * own), (i, served, own)
         Pm = P_o.mean(axis=(0, 3, 4, 5))
         ref = np.array([Pm[0, 0], Pm[1, 1], Pm[2, 2], Pm[1, 2], Pm[0, 2], Pm[0, 1]])
         assert np.linalg.norm(r["mean_P"] - ref) <= 1e-5 * np.linalg.norm(ref), (i, r["mean_P"], ref)
