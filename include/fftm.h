@@ -63,7 +63,14 @@ extern "C" {
 /* ---- enumerations ----------------------------------------------------- */
 enum fftm_bc { FFTM_BC_PERIODIC = 0, FFTM_BC_DIRICHLET = 1, FFTM_BC_NEUMANN = 2 };
 enum fftm_scheme { FFTM_HEX1 = 0, FFTM_TETRA2 = 1 };
-enum fftm_green { FFTM_GREEN_B0 = 0, FFTM_GREEN_MU0 = 1 };
+/* FFTM_GREEN_C0: the reference stiffness C0 : grad u = 2 mu0 grad u + lambda0 tr(grad u) 1
+   (Sec. 2.6.1, Eq. TF_C0_behavior), whose discrete Green operator couples the three
+   components at each frequency (Eq. FourierSGO_HEX1).  Valid for normal-mixed BCs (Eq.
+   SGO_BCs); this library builds it for HEX1 with every axis non-periodic, the same symmetry
+   on both faces of an axis per component, and on each axis the normal component's symmetry
+   opposite to the tangential ones' (normal Dirichlet and tangential Neumann, or the converse);
+   FFTM_E_UNSUPPORTED otherwise. */
+enum fftm_green { FFTM_GREEN_B0 = 0, FFTM_GREEN_MU0 = 1, FFTM_GREEN_C0 = 2 };
 /* FFTM_FP32_TC: FP32 fields and residual (as FFTM_FP32), per-axis transforms
    as dense matrix contractions on the tensor cores (tcgen05) with BF16 operands
    and FP32 accumulation (transform lengths up to 288 node positions along x, the
@@ -135,7 +142,7 @@ typedef struct fftm_problem_desc {
                                 Dirichlet -> u^f_q anti-symmetric, Neumann ->
                                 symmetric (Eq. GeneralBCtobesolved).          */
   int scheme;                /* enum fftm_scheme (Sec. 2.5)                  */
-  int green;                 /* enum fftm_green (Sec. 2.6.2 / 2.6.3)         */
+  int green;                 /* enum fftm_green (Sec. 2.6.1 / 2.6.2 / 2.6.3) */
   double lambda0, mu0;       /* reference material; lambda0 ignored for MU0  */
   int precision;             /* enum fftm_precision                          */
   double tol;                /* equilibrium tolerance epsilon, > 0           */

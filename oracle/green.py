@@ -1,4 +1,4 @@
-"""B0 and 2mu0 discrete Green operators (Sec. 2.6.2, Sec. 2.6.3).
+"""B0, 2mu0 and C0 discrete Green operators (Sec. 2.6.1, Sec. 2.6.2, Sec. 2.6.3).
 
 Per component i (no summation), Eq. NSGO2_HEX1 / NSGO2_TETRA2:
 
@@ -58,3 +58,76 @@ def operator_symbol(grid, q, scheme, lambda0, mu0):
     """Symbol of div(B0 : grad u)_q on component q's frequency grid: -(2mu0 ||xi||^2 + lambda0 |xi_q|^2)."""
     sq = squared_symbols(grid.kind[q], grid.n, grid.h, scheme)
     return -(2.0 * mu0 * (sq[0] + sq[1] + sq[2]) + lambda0 * sq[q])
+
+
+# ---- the C0 discrete Green operator (Sec. 2.6.1), HEX1, normal-mixed BCs -------------------
+# R0 : grad u = C0 : grad u = 2 mu0 grad u + lambda0 tr(grad u) 1 (Eq. TF_C0_behavior), so
+# div(R0 : grad u) = 2 mu0 div grad u + lambda0 div grad^T u (Eq. FourierSGO), which couples the
+# three components.  With HEX1 the symbol is -(2 mu0 |xi_H|^2 I + lambda0 xi_H (x) xi_H) and its
+# inverse is Eq. FourierSGO_HEX1 (a rank-one correction of the diagonal part).
+#
+# Reading (the paper states it in the Fourier space of the extended fields): on the real
+# DCT-I / DST-I coefficients the library and this oracle use, a derivative along axis a maps
+# the cosine series of a symmetric component to the sine series of the opposite parity and
+# back, with the factor -(2/h_a) sin(xi_a/2) (cosine -> sine) or +(2/h_a) sin(xi_a/2) (sine ->
+# cosine), and the averages of the HEX1 stencil give the cos(xi_b/2) factors; for normal-mixed
+# BCs (Eq. SGO_BCs) the coupling term lambda0 D_q D_i u_i lands on u_q's own series at the same
+# node position, so the symbol on the real coefficients is -(2 mu0 |xi_H|^2 I + lambda0 v (x) v)
+# with v_q = tau_q (xi_H)_q, tau_q = -1 when u_q is symmetric about the faces normal to q
+# (DCT-I along q) and +1 when it is anti-symmetric (DST-I).  The real-space operator pins this
+# (tests/test_oracle_c0.py).  Supported here: HEX1; every axis non-periodic with the same
+# symmetries on both faces (no quarter-wave kinds); on each axis the normal component's symmetry
+# opposite to the tangential ones'.
+
+def c0_unsupported(grid, scheme):
+    """None if the C0 operator below applies to this grid, else the reason."""
+    if scheme != "HEX1":
+        return "the C0 operator is built for HEX1 only"
+    for a in range(3):
+        for q in range(3):
+            k = grid.kind[q][a]
+            if k not in ("DCT1", "DST1"):
+                return "C0 needs non-periodic axes with the same symmetry on both faces"
+        normal = grid.kind[a][a]
+        for q in range(3):
+            if q != a and grid.kind[q][a] == normal:
+                return "C0 needs normal-mixed BCs (Eq. SGO_BCs): normal and tangential symmetries opposite"
+    return None
+
+
+def c0_vectors(grid):
+    """(v[3], |xi_H|^2) on the node positions m (xi_a = pi m_a / n_a for DCT-I and DST-I alike)."""
+    s, c = [], []
+    for a in range(3):
+        sa, ca = half_angles("DCT1", grid.n[a])  # positions 0..n, exact zeros at both ends
+        shape = [1, 1, 1]
+        shape[a] = sa.size
+        s.append(sa.reshape(shape))
+        c.append(ca.reshape(shape))
+    xi = []
+    for a in range(3):
+        b, d = [x for x in range(3) if x != a]
+        xi.append((2.0 / grid.h[a]) * s[a] * c[b] * c[d])
+    shape = np.broadcast_shapes(*[x.shape for x in xi])
+    xi = [np.broadcast_to(x, shape) for x in xi]
+    xx = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    tau = [-1.0 if grid.kind[q][q] == "DCT1" else 1.0 for q in range(3)]
+    return [tau[q] * xi[q] for q in range(3)], xx
+
+
+def c0_symbol_apply(grid, lambda0, mu0, uhat):
+    """p_hat = -(2 mu0 |xi|^2 u_hat + lambda0 (v . u_hat) v) on node positions (3 arrays)."""
+    v, xx = c0_vectors(grid)
+    vu = sum(v[q] * uhat[q] for q in range(3))
+    return [-(2.0 * mu0 * xx * uhat[q] + lambda0 * vu * v[q]) for q in range(3)]
+
+
+def c0_green_apply(grid, lambda0, mu0, phat):
+    """Eq. FourierSGO_HEX1 on the real coefficients: u_hat = -(p_hat - lambda0 / (2 mu0 + lambda0)
+    (v . p_hat) v / |xi|^2) / (2 mu0 |xi|^2), zero where |xi|^2 = 0 (the null rule of Sec. 2.6)."""
+    v, xx = c0_vectors(grid)
+    vp = sum(v[q] * phat[q] for q in range(3))
+    nz = xx > 0.0
+    safe = np.where(nz, xx, 1.0)
+    beta = lambda0 / (2.0 * mu0 + lambda0)
+    return [np.where(nz, -(phat[q] - beta * vp * v[q] / safe) / (2.0 * mu0 * safe), 0.0) for q in range(3)]

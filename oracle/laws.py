@@ -205,6 +205,15 @@ def stress(G, materials, groups, state=None):
     return P, new_state
 
 
+def c0_apply(G, lambda0, mu0):
+    """R0 : G for the C0 preconditioner, 2 mu0 G + lambda0 tr(G) 1 (Eq. TF_C0_behavior)."""
+    out = 2.0 * mu0 * G
+    tr = G[:, 0, 0] + G[:, 1, 1] + G[:, 2, 2]
+    for i in range(3):
+        out[:, i, i] += lambda0 * tr
+    return out
+
+
 def b0_apply(G, lambda0, mu0):
     """R0 : G for the B0 preconditioner, 2 mu0 G + lambda0 G (.) I (Sec. 2.6.3)."""
     out = 2.0 * mu0 * G

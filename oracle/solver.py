@@ -24,8 +24,8 @@ import numpy as np
 from . import anderson as anderson_mod
 from . import mixed as mixed_mod
 from .bc import Grid
-from .green import green_factor
-from .laws import b0_apply, phase_groups, stress
+from .green import c0_green_apply, c0_unsupported, green_factor
+from .laws import b0_apply, c0_apply, phase_groups, stress
 from .stencils import div, full_nodes, grad, grad_full, n_points
 from .transforms import dt3d_forward, dt3d_inverse
 
@@ -55,6 +55,11 @@ class Problem:
         self.groups = phase_groups(wl.phase, len(wl.materials))
         self.fast = fast
         self.masks = [self.grid.dof_mask(q) for q in range(3)]
+        self.c0 = wl.green == "C0"
+        if self.c0:
+            why = c0_unsupported(self.grid, wl.scheme)
+            if why:
+                raise ValueError(why)
         self.factors = [green_factor(self.grid, q, wl.scheme, self.lambda0, self.mu0) for q in range(3)]
         self.state = None
         shp = (self.npp,) + self.grid.n
@@ -104,7 +109,8 @@ class Problem:
             D[q][~self.masks[q]] = 0.0
         S_D = float(np.sum(D * D))
         S_P = float(np.sum(P * P)) / self.npp
-        p = div(b0_apply(Gf, self.lambda0, self.mu0), self.grid, self.scheme) - D
+        r0 = c0_apply if self.c0 else b0_apply
+        p = div(r0(Gf, self.lambda0, self.mu0), self.grid, self.scheme) - D
         for q in range(3):
             p[q][~self.masks[q]] = 0.0
         return p, D, P, G, S_D, S_P
@@ -118,6 +124,16 @@ class Problem:
         """a6-a8: u^f = iDT(DGO(DT(q)))."""
         g = self.grid
         out = np.zeros(g.node_shape)
+        if self.c0:  # the three components couple at each node position (green.c0_green_apply)
+            ph = []
+            for q in range(3):
+                full = np.zeros(g.N)
+                full[g.dof_slices(q)] = dt3d_forward(q_field[q], g.kind[q], g.n, fast=self.fast)
+                ph.append(full)
+            uh = c0_green_apply(g, self.lambda0, self.mu0, ph)
+            for q in range(3):
+                out[q] = dt3d_inverse(uh[q][g.dof_slices(q)], g.kind[q], g.n, g.N, fast=self.fast)
+            return out
         for q in range(3):
             spec = dt3d_forward(q_field[q], g.kind[q], g.n, fast=self.fast)
             spec = spec * self.factors[q]

@@ -284,6 +284,8 @@ struct fftm_problem {
   int committed = 0;        // a load step has been committed since creation or reset
   int nst = 0;              // state components per voxel point (7 J2 and logarithmic J2, 10 crystal plasticity, 0 none)
   int slaw = 0;             // 1 J2, 2 crystal plasticity, 4 logarithmic J2, 0 none
+  int c0 = 0;               // the C0 Green operator (three components coupled per frequency)
+  void* c0tab = nullptr;    // its sin / cos tables per axis over the node positions
   void* state_next = nullptr;  // the state committed by the last converged step, swapped in when
   int commit_pending = 0;      // the next step starts (readouts until then see the step's own state)
   int inc_ok = 0;           // incremental residual after a commit (J2 with linear small-strain laws)
@@ -611,6 +613,7 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
   R.state = reinterpret_cast<T*>(p->state);
   R.nst = p->nst;
   R.slaw = p->slaw;
+  R.c0 = p->c0;
   R.quad = 0;
   R.dquad = 0;
   for (int q = 0; q < 3; ++q) {
@@ -801,9 +804,99 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
 // first pass reads `in_set`, the rest work in place on WORK; the z pass runs
 // forward z, the Green factor and inverse z in one kernel.
 template <typename T>
+C0Params<T> c0_params(fftm_problem* p, bool normalised_inverse, bool negate) {
+  C0Params<T> G;
+  std::memset(&G, 0, sizeof(G));
+  const T* tab = reinterpret_cast<const T*>(p->c0tab);
+  size_t at = 0;
+  for (int a = 0; a < 3; ++a) {
+    G.N[a] = p->N[a];
+    G.s[a] = tab + at;
+    G.c[a] = tab + at + p->N[a];
+    at += 2 * (size_t)p->N[a];
+    G.hf[a] = T(2.0 / p->h[a]);
+  }
+  for (int q = 0; q < 3; ++q) {
+    G.f[q] = field_ptr<T>(p, SET_WORK, q);
+    for (int a = 0; a < 3; ++a) {
+      G.lo[q][a] = p->plans[q][a].lo;
+      G.hi[q][a] = p->plans[q][a].lo + p->plans[q][a].L;
+    }
+    G.tau[q] = p->kind[q][q] == K_DCT1 ? T(-1) : T(1);
+    // the FFT inverse passes are unnormalised (the factor goes here); the tensor-core inverse
+    // matrices carry it
+    const double nrm = normalised_inverse ? 1.0 : axis_norm(p, q, 0) * axis_norm(p, q, 1) * axis_norm(p, q, 2);
+    G.gscale[q] = T((negate ? -1.0 : 1.0) / nrm);
+  }
+  G.sy = p->sy;
+  G.sz = p->sz;
+  G.two_mu0 = T(2.0 * p->desc.mu0);
+  G.beta = T(p->desc.lambda0 / (2.0 * p->desc.mu0 + p->desc.lambda0));
+  G.stop = p->stop;
+  return G;
+}
+
+// a6-a8 with the C0 operator: the three forward passes, the coupled Green operator at every
+// node position, the three inverse passes (the last one forms base - Gamma(in))
+template <typename T>
+int green_apply_c0(fftm_problem* p, int in_set, int base_set, int base_lo_set, int out_set, int out_lo_set,
+                   bool negate) {
+  int rc;
+  const cudaStream_t s = p->ctx->stream;
+  const bool tens = p->tf || p->tc;
+  for (int a = 0; a < 3; ++a) {
+    const int in = a == 0 ? in_set : SET_WORK;
+    rc = p->tf ? launch_tf(p, tf_params(p, a, 0, 0, in, SET_WORK))
+         : p->tc ? launch_tc(p, tc_params(p, a, 0, 0, in, SET_WORK))
+                 : run_pass<T>(p, a, 0, 0, in, SET_WORK, false);
+    if (rc) return rc;
+  }
+  {
+    ProfScope ps(p, FFTM_KCAT_PASS_Z);
+    CU(launch_green_c0<T>(c0_params<T>(p, tens, negate), s));
+    p->launches++;
+  }
+  for (int a = 2; a >= 1; --a) {
+    rc = p->tf ? launch_tf(p, tf_params(p, a, 1, 0, SET_WORK, SET_WORK))
+         : p->tc ? launch_tc(p, tc_params(p, a, 1, 0, SET_WORK, SET_WORK))
+                 : run_pass<T>(p, a, 1, 0, SET_WORK, SET_WORK, false);
+    if (rc) return rc;
+  }
+  if (p->tf) {
+    TfPassParams P = tf_params(p, 0, 1, base_set >= 0 ? 1 : 0, SET_WORK, out_set);
+    if (base_set >= 0)
+      for (int q = 0; q < 3; ++q) {
+        P.base[q] = field_ptr<float>(p, base_set, q);
+        P.base_lo[q] = base_lo_set >= 0 ? field_ptr<float>(p, base_lo_set, q) : nullptr;
+        P.out_lo[q] = out_lo_set >= 0 ? field_ptr<float>(p, out_lo_set, q) : nullptr;
+      }
+    return launch_tf(p, P);
+  }
+  if (p->tc) {
+    TcPassParams P = tc_params(p, 0, 1, 0, SET_WORK, out_set);
+    if (base_set >= 0)
+      for (int q = 0; q < 3; ++q) {
+        P.base[q] = field_ptr<float>(p, base_set, q);
+        P.base_lo[q] = base_lo_set >= 0 ? field_ptr<float>(p, base_lo_set, q) : nullptr;
+        P.out_lo[q] = out_lo_set >= 0 ? field_ptr<float>(p, out_lo_set, q) : nullptr;
+      }
+    return launch_tc(p, P);
+  }
+  PassParams<T> P = pass_params<T>(p, 0, 1, 0, SET_WORK, out_set);
+  if (base_set >= 0)
+    for (int q = 0; q < 3; ++q) {
+      P.base[q] = field_ptr<T>(p, base_set, q);
+      P.base_lo[q] = base_lo_set >= 0 ? field_ptr<T>(p, base_lo_set, q) : nullptr;
+      P.out_lo[q] = out_lo_set >= 0 ? field_ptr<T>(p, out_lo_set, q) : nullptr;
+    }
+  return launch_pp<T>(p, P, 0);
+}
+
+template <typename T>
 int green_apply(fftm_problem* p, int in_set, int base_set, int base_lo_set, int out_set, int out_lo_set,
                 bool negate) {
   int rc;
+  if (p->c0) return green_apply_c0<T>(p, in_set, base_set, base_lo_set, out_set, out_lo_set, negate);
   if (p->tf) {
     if ((rc = launch_tf(p, tf_params(p, 0, 0, 0, in_set, SET_WORK)))) return rc;
     if ((rc = launch_tf(p, tf_params(p, 1, 0, 0, SET_WORK, SET_WORK)))) return rc;
@@ -1242,7 +1335,22 @@ int validate(const fftm_problem_desc* d) {
       return set_err(FFTM_E_INVALID, "a periodic axis must be periodic on both faces for every component");
   }
   if (d->scheme != FFTM_HEX1 && d->scheme != FFTM_TETRA2) return set_err(FFTM_E_INVALID, "bad scheme");
-  if (d->green != FFTM_GREEN_B0 && d->green != FFTM_GREEN_MU0) return set_err(FFTM_E_INVALID, "bad green");
+  if (d->green != FFTM_GREEN_B0 && d->green != FFTM_GREEN_MU0 && d->green != FFTM_GREEN_C0)
+    return set_err(FFTM_E_INVALID, "bad green");
+  if (d->green == FFTM_GREEN_C0) {  // Sec. 2.6.1: normal-mixed BCs (Eq. SGO_BCs), as built here
+    if (d->scheme != FFTM_HEX1) return set_err(FFTM_E_UNSUPPORTED, "the C0 Green operator is built for HEX1 only");
+    for (int a = 0; a < 3; ++a)
+      for (int q = 0; q < 3; ++q) {
+        const int b0 = d->bc[a][0][q], b1 = d->bc[a][1][q];
+        if (b0 == FFTM_BC_PERIODIC || b0 != b1)
+          return set_err(FFTM_E_UNSUPPORTED, "the C0 Green operator needs non-periodic axes with the same "
+                                             "condition on both faces");
+        if (q != a && b0 == d->bc[a][0][a])
+          return set_err(FFTM_E_UNSUPPORTED, "the C0 Green operator needs normal-mixed conditions: on each axis "
+                                             "the normal component Dirichlet and the tangential ones Neumann, "
+                                             "or the converse");
+      }
+  }
   if (!(d->mu0 > 0.0) || !(d->lambda0 >= 0.0)) return set_err(FFTM_E_INVALID, "need mu0 > 0, lambda0 >= 0");
   if (d->precision != FFTM_FP64 && d->precision != FFTM_FP32 && d->precision != FFTM_FP32_TC &&
       d->precision != FFTM_FP32_TF32)
@@ -1336,7 +1444,8 @@ int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
       stb = 2 * (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 10 * nvox * esz;
     else if (desc->materials[i].law == FFTM_LAW_LOG_J2)
       stb = 2 * (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 7 * nvox * esz;
-  *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + stb + nvox * sizeof(uint16_t) +
+  const size_t c0b = desc->green == FFTM_GREEN_C0 ? 2 * (size_t)(desc->n[0] + desc->n[1] + desc->n[2] + 3) * esz : 0;
+  *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + stb + c0b + nvox * sizeof(uint16_t) +
            desc->n_phases * sizeof(int);
   return FFTM_OK;
 }
@@ -1365,6 +1474,7 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->Dn);
   cudaFree(p->tcmat);
   cudaFree(p->tc_err);
+  cudaFree(p->c0tab);
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -1658,6 +1768,25 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
   } else {
     std::vector<float> lf(lc.begin(), lc.end());
     CU(cudaMemcpy(p->law_c, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
+  }
+  if (desc->green == FFTM_GREEN_C0) {
+    // sin and cos of xi / 2 at the node positions m = 0 .. n of each axis (xi = pi m / n, the
+    // DCT-I / DST-I frequency of position m), with the exact zeros sin = 0 at m = 0 and cos = 0
+    // at m = n (the null rule is decided on them)
+    p->c0 = 1;
+    std::vector<double> t;
+    for (int a = 0; a < 3; ++a) {
+      const int n = p->n[a];
+      for (int m = 0; m < p->N[a]; ++m) t.push_back(m == 0 ? 0.0 : std::sin(0.5 * kPi * m / n));
+      for (int m = 0; m < p->N[a]; ++m) t.push_back(m == n ? 0.0 : std::cos(0.5 * kPi * m / n));
+    }
+    CU(cudaMalloc(&p->c0tab, t.size() * p->esz));
+    if (p->esz == 8) {
+      CU(cudaMemcpy(p->c0tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> tf(t.begin(), t.end());
+      CU(cudaMemcpy(p->c0tab, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice));
+    }
   }
   CU(cudaStreamSynchronize(s));
   *out = p.release();
@@ -1988,6 +2117,12 @@ static int apply_t(fftm_problem* p, int op, double* norms) {
                      : run_pass<T>(p, a, 1, 0, SET_WORK, SET_WORK, true);
       break;
     case FFTM_OP_GREEN: {
+      if (p->c0) {  // the coupled operator on the coefficients in WORK, no normalisation
+        C0Params<T> G = c0_params<T>(p, true, false);
+        CU(launch_green_c0<T>(G, s));
+        p->launches++;
+        break;
+      }
       PassParams<T> P = pass_params<T>(p, 2, 0, 0, SET_WORK, SET_WORK);
       GreenParams<T> G;
       std::memset(&G, 0, sizeof(G));

@@ -88,6 +88,7 @@ struct ResParams {
   T* state;          // null: no phase with internal variables
   int nst;           // state components per voxel point: 7 (J2, logarithmic J2) or 10 (crystal plasticity)
   int slaw;          // the law with internal variables: 1 J2, 2 crystal plasticity, 4 logarithmic J2, 0 none
+  int c0;            // the reference stiffness of tau is C0 (lambda0 tr(G) 1) instead of B0 (lambda0 G_ii)
   const T* un[3];    // u^f at the last commit (high part in FP32)
   long long nsy, nsz;  // node strides of un (the problem's layout; sy, sz may describe a caller's)
   const T* unlo[3];  // its low part (FP32 only)
@@ -210,9 +211,28 @@ struct GreenParams {
   T gscale[3];
 };
 
+// The C0 Green operator at every node position (fftm_c0.cu): the three components' DCT-I /
+// DST-I coefficients of one position couple through v (v_q = tau_q (xi_H)_q).
+template <typename T>
+struct C0Params {
+  T* f[3];                  // in place: p_hat in, u_hat out
+  int N[3];
+  long long sy, sz;
+  int lo[3][3], hi[3][3];   // node-position range [lo, hi) of component q along axis a
+  const T* s[3];            // sin(xi_a / 2) at node positions 0 .. N_a - 1 (xi = pi m / n_a)
+  const T* c[3];            // cos(xi_a / 2), exact zero at m = n_a
+  T hf[3];                  // 2 / h_a
+  T tau[3];                 // -1: u_q symmetric about the faces normal to q (DCT-I), +1: anti-symmetric
+  T two_mu0, beta;          // beta = lambda0 / (2 mu0 + lambda0)
+  T gscale[3];              // normalisation of the transforms (and the sign of the update)
+  const int* stop;
+};
+
 // ---- launchers (return cudaError_t of the launch) ----
 template <typename T>
 cudaError_t launch_pass(const PassParams<T>& P, int maxM, int maxL, int maxn, cudaStream_t s);
+template <typename T>
+cudaError_t launch_green_c0(const C0Params<T>& P, cudaStream_t s);
 template <typename T>
 cudaError_t launch_residual(const ResParams<T>& P, int tetra, bool with_p, cudaStream_t s, int* blocks_out);
 template <typename T>

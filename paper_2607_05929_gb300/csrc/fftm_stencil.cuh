@@ -4,7 +4,7 @@
 // Two passes over the grid.  k_stress (one thread per voxel) evaluates the
 // gradient at the voxel point(s) (HEX1: Eqs. D1HG-D3HG; TETRA2: Eqs.
 // D1T1T2G-D3T1T2G) and the law, and stores P (for the test variant also
-// tau = R0 : grad u^f - P with B0 = 2 mu0 G + lambda0 G (.) I, Sec. 2.6.3).
+// tau = R0 : grad u^f - P with B0 = 2 mu0 G + lambda0 G (.) I, Sec. 2.6.3, or C0 = 2 mu0 G + lambda0 tr(G) I, Sec. 2.6.1).
 // k_div (one thread per node) applies Remark 1 -- node m reads the voxels
 // m + o - 1 with the same signs -- to get D = div P (and p = div tau), written
 // for the transformed node components (dismissed ones get 0).  FP64 block
@@ -875,7 +875,7 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress(ResParams<T> P, TileIdx ti
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
               T tq = P.two_mu0 * Gf[i * 3 + q] - Pp[i * 3 + q];
-              if (i == q) tq += P.lam0 * Gf[i * 3 + i];
+              if (i == q) tq += P.lam0 * (P.c0 ? Gf[0] + Gf[4] + Gf[8] : Gf[i * 3 + i]);
               base[(size_t)(NC + i * 3 + q) * nvox] = tq;
             }
         }

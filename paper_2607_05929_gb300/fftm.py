@@ -27,7 +27,7 @@ FFTM_E_TIMEOUT = -6
 # enums
 FFTM_BC_PERIODIC, FFTM_BC_DIRICHLET, FFTM_BC_NEUMANN = 0, 1, 2
 FFTM_HEX1, FFTM_TETRA2 = 0, 1
-FFTM_GREEN_B0, FFTM_GREEN_MU0 = 0, 1
+FFTM_GREEN_B0, FFTM_GREEN_MU0, FFTM_GREEN_C0 = 0, 1, 2
 FFTM_FP64, FFTM_FP32, FFTM_FP32_TC, FFTM_FP32_TF32 = 0, 1, 2, 3
 FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
 FFTM_LAW_SVK_CUBIC, FFTM_LAW_NEO_HOOKE, FFTM_LAW_CP_FCC, FFTM_LAW_LOG_J2 = 4, 5, 6, 7
@@ -213,7 +213,7 @@ def make_desc(n, phase, materials, bc, scheme="HEX1", green="B0", lambda0=0.0, m
             for q in range(3):
                 d.bc[a][f][q] = code[bc[a][f][q]]
     d.scheme = FFTM_TETRA2 if scheme == "TETRA2" else FFTM_HEX1
-    d.green = FFTM_GREEN_MU0 if green == "MU0" else FFTM_GREEN_B0
+    d.green = {"B0": FFTM_GREEN_B0, "MU0": FFTM_GREEN_MU0, "C0": FFTM_GREEN_C0}[green]
     d.lambda0 = float(lambda0)
     d.mu0 = float(mu0)
     d.precision = {"fp64": FFTM_FP64, "fp32": FFTM_FP32, "float32": FFTM_FP32,

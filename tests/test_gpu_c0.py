@@ -1,0 +1,138 @@
+"""The C0 discrete Green operator (Sec. 2.6.1, Eq. FourierSGO_HEX1) on the GPU against the
+oracle, through the C ABI, for normal-mixed BCs (Eq. SGO_BCs) with HEX1:
+
+* the coupled operator on random coefficients (FFTM_OP_GREEN) equals green.c0_green_apply;
+* the whole Green update (forward transforms, operator, inverse transforms) equals the
+  oracle's green_update, FP64, FP32 with FFT transforms and FP32 with TF32 contractions;
+* the residual's polarisation p = div(C0 : grad u^f) - D equals the oracle's;
+* whole load steps on a two-phase sphere composite: FP64 with the oracle's iteration count,
+  Anderson steps and stresses to 1e-9; FP32 (FFT and TF32 transforms) within +-2 iterations
+  and 1e-5.
+"""
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from abi_helpers import GpuProblem, rel_l2
+from oracle.bc import Grid
+from oracle.green import c0_green_apply
+from oracle.solver import Problem
+from paper_2607_05929_gb300 import build
+from paper_2607_05929_gb300 import fftm as F
+from synthetic.workloads import ISO_ELASTIC, Material, Workload
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-11, "fp32": 2e-5, "fp32_tf32": 2e-3}
+CHOICES = [("D", "N", "N"), ("N", "D", "N"), ("D", "D", "N")]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    F.load_library()
+
+
+def _bc(choice):
+    other = {"D": "N", "N": "D"}
+    return [[[choice[a] if q == a else other[choice[a]] for q in range(3)] for _ in range(2)] for a in range(3)]
+
+
+def _wl(choice, n=(16, 12, 8), tol=1e-8):
+    ph = syn.random_spheres(n, 0.2, 1.5, 2.5, 11)
+    E, nu = 1.0, 0.3
+    lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
+    mats = [Material(ISO_ELASTIC, (lam, mu)), Material(ISO_ELASTIC, (5 * lam, 5 * mu))]
+    A = np.zeros((3, 3))
+    A[0, 0] = 1e-3
+    if choice[0] == "N":  # x faces: normal Neumann, so load through a tangential component
+        A[0, 0] = 0.0
+        A[1, 0] = 1e-3
+    return Workload("c0_spheres", n, ph, mats, _bc(choice), scheme="HEX1", green="C0", lambda0=3 * lam,
+                    mu0=3 * mu, tol=tol, A=A, max_iter=2000)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("choice", CHOICES)
+def test_green_operator_matches_the_oracle(precision, choice):
+    wl = _wl(choice)
+    g = Grid(wl.n, wl.bc, wl.h)
+    gp = GpuProblem(wl, precision)
+    try:
+        x = np.random.default_rng(5).standard_normal(g.node_shape)
+        for q in range(3):
+            x[q][~g.dof_mask(q)] = 0.0
+        gp.set_node(F.FFTM_FIELD_WORK, x)
+        F.fftm_apply(gp.p, F.FFTM_OP_GREEN)
+        got = gp.get_node(F.FFTM_FIELD_WORK)
+        ref = c0_green_apply(g, wl.lambda0, wl.mu0, [x[q] for q in range(3)])
+        for q in range(3):
+            ref[q][~g.dof_mask(q)] = 0.0
+        assert rel_l2(got, np.stack(ref)) < (1e-12 if precision == "fp64" else 1e-6)
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tf32"])
+@pytest.mark.parametrize("choice", CHOICES)
+def test_green_update_matches_the_oracle(precision, choice):
+    wl = _wl(choice)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, precision)
+    try:
+        p = np.random.default_rng(7).standard_normal(pr.grid.node_shape)
+        for q in range(3):
+            p[q][~pr.grid.dof_mask(q)] = 0.0
+        gp.set_node(F.FFTM_FIELD_WORK, p)
+        F.fftm_apply(gp.p, F.FFTM_OP_GREEN_UPDATE)
+        u = gp.get_node(F.FFTM_FIELD_U)
+        ref = pr.green_update(p)
+        # random input: the transforms' rounding is amplified by the spread of the operator
+        tol = TOL[precision] if precision != "fp32" else 1e-4
+        assert rel_l2(u, ref) < tol
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_residual_polarisation_matches_the_oracle(precision):
+    wl = _wl(("D", "N", "N"))
+    pr = Problem(wl)
+    gp = GpuProblem(wl, precision)
+    try:
+        u = 1e-3 * np.random.default_rng(9).standard_normal(pr.grid.node_shape)
+        for q in range(3):
+            u[q][~pr.grid.dof_mask(q)] = 0.0
+        gp.set_node(F.FFTM_FIELD_U, u)
+        F.fftm_apply(gp.p, F.FFTM_OP_RESIDUAL)
+        p_ref, D_ref, *_ = pr.residual(u, pr.grad_ustar())
+        assert rel_l2(gp.get_node(F.FFTM_FIELD_WORK), p_ref) < (1e-11 if precision == "fp64" else 2e-5)
+        assert rel_l2(gp.get_node(F.FFTM_FIELD_D), D_ref) < (1e-11 if precision == "fp64" else 2e-5)
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tf32"])
+@pytest.mark.parametrize("choice", CHOICES)
+def test_solve_step_matches_the_oracle(precision, choice):
+    wl = _wl(choice, tol=1e-8 if precision == "fp64" else 1e-6)
+    pr = Problem(wl)
+    _, rep = pr.solve_step()
+    assert rep.converged
+    gp = GpuProblem(wl, precision)
+    try:
+        st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+        assert r["converged"], r
+        Sg = gp.get_voxel(F.FFTM_FIELD_STRESS)
+        P = pr.last["P"]
+        ref = np.stack([P[:, 0, 0], P[:, 1, 1], P[:, 2, 2], P[:, 1, 2], P[:, 0, 2], P[:, 0, 1]], axis=1)
+        if precision == "fp64":
+            assert r["iterations"] == rep.iterations, (r["iterations"], rep.iterations)
+            assert [i for i, a in enumerate(ah) if a] == rep.accelerated
+            assert rel_l2(Sg, ref) < 1e-9
+        else:
+            assert abs(r["iterations"] - rep.iterations) <= 2, (r["iterations"], rep.iterations)
+            assert rel_l2(Sg, ref) < 1e-5
+    finally:
+        gp.close()

@@ -81,3 +81,32 @@ def test_the_library_law_matches_the_oracle_pointwise(seed):
         H1 = Hp_o[0, :, :, 0]
         st_ref = [H1[0, 0], H1[1, 1], H1[2, 2], H1[1, 2], H1[0, 2], H1[0, 1], p_o[0, 0]]
         assert np.abs(stn - st_ref).max() <= 1e-12 * (np.abs(st_ref).max() + 1e-3), (scale, stn, st_ref)
+
+
+@pytest.mark.parametrize("case", ["tetra", "periodic", "not_normal_mixed", "faces_differ"])
+def test_c0_green_outside_its_conditions_is_refused(case):
+    n = (6, 4, 4)
+    ph = np.zeros(n, np.uint16)
+    bc = [[["D", "N", "N"]] * 2, [["D", "N", "D"]] * 2, [["N", "N", "D"]] * 2]  # normal-mixed
+    scheme = "HEX1"
+    if case == "tetra":
+        scheme = "TETRA2"
+    elif case == "periodic":
+        bc[2] = [["P"] * 3] * 2
+    elif case == "not_normal_mixed":
+        bc[1] = [["D"] * 3] * 2
+    else:
+        bc[0] = [["D", "N", "N"], ["N", "D", "D"]]
+    desc, keep = F.make_desc(n, ph, [(ISO_ELASTIC, (LAM, MU), Q1)], bc, scheme=scheme, green="C0",
+                             lambda0=LAM, mu0=MU, tol=1e-8, max_iter=100)
+    with pytest.raises(F.FFTMError) as e:
+        F.fftm_problem_workspace_bytes(desc)
+    assert e.value.status == F.FFTM_E_UNSUPPORTED
+
+
+def test_c0_green_within_its_conditions_is_accepted():
+    n = (6, 4, 4)
+    bc = [[["D", "N", "N"]] * 2, [["D", "N", "D"]] * 2, [["N", "N", "D"]] * 2]
+    desc, keep = F.make_desc(n, np.zeros(n, np.uint16), [(ISO_ELASTIC, (LAM, MU), Q1)], bc, green="C0",
+                             lambda0=LAM, mu0=MU, tol=1e-8, max_iter=100)
+    assert F.fftm_problem_workspace_bytes(desc) > 0
