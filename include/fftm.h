@@ -226,6 +226,19 @@ int fftm_set_phase(fftm_problem* p, const uint16_t* phase);
 /* Set the prescribed displacement of the next load steps (Algorithm 1,
    "update the desired loading"). */
 int fftm_set_load(fftm_problem* p, const fftm_load* load);
+
+/* Non-uniform Neumann tractions on one face (Sec. 2.2; the uniform part is fftm_load.T, and
+   the two add): t holds 3 x n_c x n_b values of the problem's precision, component-major,
+   t[(q * n_c + c) * n_b + b] at the centre of face voxel (b, c), where b < c are the two
+   in-plane axes (axis 0: (y, z); axis 1: (x, z); axis 2: (x, y)); outward normal convention
+   (traction_q = P_iq n_i).  Imposed through P* = 2 t at the mirror voxel centres across the
+   face (ghost voxels beyond the face's edges take the value of the face voxel they mirror).
+   t is a HOST (t_is_device = 0) or device pointer, copied before the call returns; bytes must
+   be 3 n_b n_c times the element size.  A component that is not Neumann on that face must be
+   zero (FFTM_E_INVALID); so must the call for a periodic axis.  t = NULL removes the field.
+   Takes effect at the next load step (or residual). */
+int fftm_set_face_traction(fftm_problem* p, int axis, int face, const void* t, int t_is_device, size_t bytes);
+
 /* The current load (HOST out): as set, with the free components of a mixed load
    at their latest adjusted values. */
 int fftm_get_load(const fftm_problem* p, fftm_load* out);

@@ -98,13 +98,13 @@ class Problem:
         return grad_full(self.ustar_full(A, b, Q), self.grid, self.scheme)
 
     # --- pieces of one iteration ------------------------------------------------------
-    def residual(self, uf, Gs, T=None):
+    def residual(self, uf, Gs, T=None, Tf=None):
         """a1-a4 and p: returns (p, D, P, G, S_D, S_P); T: uniform Neumann tractions
         T[axis][face][component] (D = div P + D*, the ghosts of P* = 2 t)."""
         Gf = grad(uf, self.grid, self.scheme)
         G = Gf + Gs
         P, _ = stress(G, self.wl.materials, self.groups, self.state)
-        D = div(P, self.grid, self.scheme, T)
+        D = div(P, self.grid, self.scheme, T, Tf)
         for q in range(3):
             D[q][~self.masks[q]] = 0.0
         S_D = float(np.sum(D * D))
@@ -142,12 +142,13 @@ class Problem:
 
     # --- Algorithm 1, one load step -----------------------------------------------------
     def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True, Q=None, mixed=0,
-                   T=None):
+                   T=None, Tf=None):
         """One load step.  mixed: bit mask of the symmetric strain components (Voigt order
         11, 22, 33, 23, 13, 12) of u* that are adjusted so that the mean stress vanishes in
         them (normal-mixed loading, mixed.py); the other components of A are imposed.
         T: uniform tractions T[axis][face][component] on the faces where that component is
-        Neumann (stencils.add_traction_ghosts), or None for traction-free faces."""
+        Neumann (stencils.add_traction_ghosts), or None for traction-free faces; Tf: per-face
+        traction fields {(axis, face): t (3, n_b, n_c)} added to T."""
         wl = self.wl
         tol = wl.tol if tol is None else tol
         max_iter = wl.max_iter if max_iter is None else max_iter
@@ -162,7 +163,7 @@ class Problem:
         mixer = anderson_mod.Mixer(wl.anderson_depth, wl.anderson_period, enabled=anderson)
         rep = Report(iterations=0, converged=False)
         for m in range(max_iter + 1):
-            p, D, P, G, S_D, S_P = self.residual(uf, Gs, T)
+            p, D, P, G, S_D, S_P = self.residual(uf, Gs, T, Tf)
             err = self.error(S_D, S_P)
             rep.err.append(err)
             rep.iterations = m

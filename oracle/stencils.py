@@ -142,40 +142,70 @@ def _div_one(Ei, tab, grid, scale):
     return out
 
 
-def add_traction_ghosts(E, grid, T):
+def _face_axes(a):
+    return [b for b in range(3) if b != a]
+
+
+def face_field_ghost(t, grid, a):
+    """A traction field over the voxel centres of a face normal to a, t (3, n_b, n_c) with b < c
+    the in-plane axes, spread over the face's whole ghost layer (extended in-plane indices
+    0 .. n + 1): a ghost outside the face takes the value at the voxel it mirrors (the nearest
+    face voxel on a non-periodic axis, the wrapped one on a periodic axis)."""
+    b, c = _face_axes(a)
+    idx = []
+    for ax in (b, c):
+        e = np.arange(grid.n[ax] + 2) - 1
+        if grid.periodic[ax]:
+            e = e % grid.n[ax]
+        else:
+            e = np.clip(e, 0, grid.n[ax] - 1)
+        idx.append(e)
+    return np.asarray(t)[:, idx[0][:, None], idx[1][None, :]]
+
+
+def add_traction_ghosts(E, grid, T, Tf=None):
     """The imposed stress of non-zero Neumann tractions (Sec. 2.2, the construction of the
     Neumann-BC figure): P = P^f + P*, with P* zero inside the cell and P*_aq = 2 t_q at the
     mirror voxel centres across a face normal to axis a whose u_q is Neumann, t_q =
     (-1)^(alpha+1) T[a][alpha][q] the face value of P_aq for the traction T (outward normal
     convention, traction_q = P_iq n_i), so that P* interpolated at the face is t.  Reading:
     P* covers the whole ghost layer of the face, its edges and corners included, and is
-    added after the symmetry reflections (uniform T only)."""
+    added after the symmetry reflections.  T: uniform tractions (or None); Tf: non-uniform
+    ones, a dict {(axis, face): t (3, n_b, n_c)} over the face's voxel centres (b < c the
+    in-plane axes), spread over the ghost layer by face_field_ghost and added to T."""
     n = grid.n
     for a in range(3):
         if grid.periodic[a]:
             continue
         for side in range(2):
+            field = None
+            if Tf is not None and (a, side) in Tf:
+                field = face_field_ghost(Tf[(a, side)], grid, a)
             for q in range(3):
-                t = T[a][side][q]
-                if t == 0.0 or grid.sym[q][a][side] != "S":
+                t = 0.0 if T is None else T[a][side][q]
+                if grid.sym[q][a][side] != "S" or (t == 0.0 and field is None):
                     continue
                 idx = [slice(None)] * 6
                 idx[1] = a
                 idx[2] = q
                 idx[3 + a] = 0 if side == 0 else n[a] + 1
-                E[tuple(idx)] += 2.0 * (1.0 if side == 1 else -1.0) * t
+                val = t if field is None else t + field[q]
+                # the ghost layer slice has the two in-plane axes in order (b, c)
+                E[tuple(idx)] += 2.0 * (1.0 if side == 1 else -1.0) * (val if np.ndim(val) == 0
+                                                                        else val[None])
     return E
 
 
-def div(S, grid, scheme, T=None):
+def div(S, grid, scheme, T=None, Tf=None):
     """Divergence at the nodes of a voxel tensor S (npp, 3, 3, n1, n2, n3); T: uniform
-    Neumann tractions T[axis][face][component] (add_traction_ghosts) or None.
+    Neumann tractions T[axis][face][component] (add_traction_ghosts) or None; Tf: per-face
+    traction fields {(axis, face): t (3, n_b, n_c)} or None.
 
     HEX1: D_q = sum_i D_i^H S_iq.  TETRA2: 1/2 (div_{T2} S^{(T1)} + div_{T1} S^{(T2)}).
     """
     E = ghost_extend(S, grid, scheme)
-    if T is not None:
-        E = add_traction_ghosts(E, grid, T)
+    if T is not None or Tf:
+        E = add_traction_ghosts(E, grid, T, Tf)
     if scheme == "HEX1":
         return _div_one(E[0], HEX1, grid, HEX1_SCALE)
     return 0.5 * (_div_one(E[0], T2, grid, T_SCALE) + _div_one(E[1], T1, grid, T_SCALE))

@@ -285,6 +285,8 @@ struct fftm_problem {
   int nst = 0;              // state components per voxel point (7 J2 and logarithmic J2, 10 crystal plasticity, 0 none)
   int slaw = 0;             // 1 J2, 2 crystal plasticity, 4 logarithmic J2, 0 none
   int c0 = 0;               // the C0 Green operator (three components coupled per frequency)
+  void* tface[3][2] = {};   // non-uniform tractions per face (fftm_set_face_traction), or null
+  void* tface_n[3][2] = {}; // the fields at the last commit (J2's incremental residual)
   void* c0tab = nullptr;    // its sin / cos tables per axis over the node positions
   void* state_next = nullptr;  // the state committed by the last converged step, swapped in when
   int commit_pending = 0;      // the next step starts (readouts until then see the step's own state)
@@ -637,6 +639,12 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
         R.tr[a][f][q] = T(p->load.T[a][f][q]);
         R.traction |= p->load.T[a][f][q] != 0.0;
       }
+  for (int a = 0; a < 3; ++a)
+    for (int f = 0; f < 2; ++f) {
+      R.tface[a][f] = reinterpret_cast<const T*>(p->tface[a][f]);
+      R.tface_n[a][f] = nullptr;
+      R.traction |= p->tface[a][f] != nullptr;
+    }
   return R;
 }
 
@@ -787,6 +795,11 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
           R.tr[a][f][q] = T(dt);
           R.traction |= dt != 0.0;
         }
+    for (int a = 0; a < 3; ++a)
+      for (int f = 0; f < 2; ++f) {
+        R.tface_n[a][f] = reinterpret_cast<const T*>(p->tface_n[a][f]);
+        R.traction |= p->tface[a][f] != nullptr || p->tface_n[a][f] != nullptr;
+      }
   }
   int blocks = 0;
   ProfScope ps(p, test_outputs ? FFTM_KCAT_OTHER : FFTM_KCAT_RESIDUAL);
@@ -1242,6 +1255,17 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
                            cudaMemcpyDeviceToDevice, s));
     }
     p->load_n = p->load;
+    for (int a = 0; a < 3; ++a)  // the face traction fields at the commit
+      for (int f = 0; f < 2; ++f) {
+        if (!p->tface[a][f]) {
+          cudaFree(p->tface_n[a][f]);
+          p->tface_n[a][f] = nullptr;
+          continue;
+        }
+        const size_t nb = (size_t)3 * p->n[a == 0 ? 1 : 0] * p->n[a == 2 ? 1 : 2] * sizeof(T);
+        if (!p->tface_n[a][f]) CU(cudaMalloc(&p->tface_n[a][f], nb));
+        CU(cudaMemcpyAsync(p->tface_n[a][f], p->tface[a][f], nb, cudaMemcpyDeviceToDevice, s));
+      }
     p->committed = 1;
     // D_n = div P_n evaluated afresh (plain form) so that rounding does not accumulate
     // from step to step through the incremental form
@@ -1475,6 +1499,11 @@ int fftm_problem_destroy(fftm_problem* p) {
   cudaFree(p->tcmat);
   cudaFree(p->tc_err);
   cudaFree(p->c0tab);
+  for (int a = 0; a < 3; ++a)
+    for (int f = 0; f < 2; ++f) {
+      cudaFree(p->tface[a][f]);
+      cudaFree(p->tface_n[a][f]);
+    }
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -1866,6 +1895,40 @@ int fftm_host_mixed_increment(const double* sig, int mask, double lambda0, doubl
   mixed_increment(s3, mask, lambda0, mu0, d);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) d_out[i * 3 + j] = d[i][j];
+  return FFTM_OK;
+}
+
+int fftm_set_face_traction(fftm_problem* p, int axis, int face, const void* t, int t_is_device, size_t bytes) {
+  if (!p) return set_err(FFTM_E_INVALID, "null problem");
+  if (axis < 0 || axis > 2 || face < 0 || face > 1) return set_err(FFTM_E_INVALID, "bad axis or face");
+  if (p->periodic[axis]) return set_err(FFTM_E_INVALID, "a periodic axis has no faces to load");
+  CU(cudaSetDevice(p->ctx->device));
+  const int nb = p->n[axis == 0 ? 1 : 0], nc = p->n[axis == 2 ? 1 : 2];
+  const size_t cnt = (size_t)3 * nb * nc, need = cnt * p->esz;
+  if (!t) {
+    CU(cudaStreamSynchronize(p->ctx->stream));
+    cudaFree(p->tface[axis][face]);
+    p->tface[axis][face] = nullptr;
+    return FFTM_OK;
+  }
+  if (bytes != need) return set_err(FFTM_E_INVALID, "byte count does not match 3 x the face's voxels");
+  std::vector<unsigned char> h(need);
+  if (t_is_device) {
+    CU(cudaMemcpy(h.data(), t, need, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(h.data(), t, need);
+  }
+  for (int q = 0; q < 3; ++q) {
+    if (p->desc.bc[axis][face][q] == FFTM_BC_NEUMANN) continue;
+    for (size_t k = 0; k < (size_t)nb * nc; ++k) {
+      const double v = p->esz == 8 ? reinterpret_cast<const double*>(h.data())[q * (size_t)nb * nc + k]
+                                   : reinterpret_cast<const float*>(h.data())[q * (size_t)nb * nc + k];
+      if (v != 0.0) return set_err(FFTM_E_INVALID, "a traction on a face where that component is not Neumann");
+    }
+  }
+  CU(cudaStreamSynchronize(p->ctx->stream));
+  if (!p->tface[axis][face]) CU(cudaMalloc(&p->tface[axis][face], need));
+  CU(cudaMemcpy(p->tface[axis][face], h.data(), need, cudaMemcpyHostToDevice));
   return FFTM_OK;
 }
 

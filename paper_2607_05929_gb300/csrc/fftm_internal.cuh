@@ -110,6 +110,11 @@ struct ResParams {
   // ghost voxels across it (incremental form: the traction change since the commit)
   int traction;
   T tr[3][2][3];
+  // Non-uniform tractions per face (null: none): tface[a][f][q * nb * nc + vb + nb * vc] over
+  // the face's voxel centres (b < c the in-plane axes); the incremental form subtracts the
+  // committed field tface_n
+  const T* tface[3][2];
+  const T* tface_n[3][2];
   T* vs;             // voxel-point stress buffer [r][c][voxel] (c < NC, see fftm_stencil.cuh)
   int sym;           // 1: every law gives a symmetric P (6 stored components)
   int two_pass;      // 1: evaluate the residual as two grid passes even where one pass serves

@@ -1038,18 +1038,36 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
       T s = T(0), st = T(0);
       // imposed stress of a traction on the face normal to i that this node lies on: every
       // pair along i has its ghost corner there (Sec. 2.2, P* = 2 t at the mirror centres)
-      T ps = T(0);
+      // side 0: - (2 (-1) t) at corner o; side 1: + (2 t) at corner o1 -- both add 2 t
+      int side = -1;
       if (P.traction && !P.periodic[i]) {
         const int m_i = i == 0 ? mx : (i == 1 ? my : mz);
-        if (m_i == 0 && P.sgn[q][i][0] > 0) ps += T(2) * P.tr[i][0][q];         // - (2 (-1) t) at corner o
-        if (m_i == P.n[i] && P.sgn[q][i][1] > 0) ps += T(2) * P.tr[i][1][q];  // + (2 t) at corner o1
+        if (m_i == 0 && P.sgn[q][i][0] > 0) side = 0;
+        else if (m_i == P.n[i] && P.sgn[q][i][1] > 0) side = 1;
       }
+      const T* tfc = side >= 0 ? P.tface[i][side] : nullptr;
+      const T* tfn = side >= 0 ? P.tface_n[i][side] : nullptr;
+      const T ps_u = side >= 0 ? T(2) * P.tr[i][side][q] : T(0);
       for (int o = 0; o < 8; ++o) {
         if ((o >> i) & 1) continue;
         const int o1 = o | (1 << i);
         T f0, f1;
         const long long a0 = corner(o, i, q, &f0);
         const long long a1 = corner(o1, i, q, &f1);
+        T ps = ps_u;
+        if (tfc || tfn) {  // the field at the face voxel that this pair's ghost corner mirrors
+          const int b = i == 0 ? 1 : 0, cc = i == 2 ? 1 : 2;
+          const int mb = b == 0 ? mx : my, mc = cc == 1 ? my : mz;
+          const int nb = P.n[b], nc = P.n[cc];
+          int vb = mb + ((o >> b) & 1) - 1, vc = mc + ((o >> cc) & 1) - 1;
+          if (vb < 0) vb = P.periodic[b] ? nb - 1 : 0;
+          if (vb >= nb) vb = P.periodic[b] ? 0 : nb - 1;
+          if (vc < 0) vc = P.periodic[cc] ? nc - 1 : 0;
+          if (vc >= nc) vc = P.periodic[cc] ? 0 : nc - 1;
+          const long long at = (long long)q * nb * nc + vb + (long long)nb * vc;
+          if (tfc) ps += T(2) * tfc[at];
+          if (tfn) ps -= T(2) * tfn[at];
+        }
         s += f1 * P.vs[a1 + c * nvox] - f0 * P.vs[a0 + c * nvox] + ps;
         if (WITH_P) st += f1 * P.vs[a1 + (NC + i * 3 + q) * nvox] - f0 * P.vs[a0 + (NC + i * 3 + q) * nvox];
       }

@@ -8,7 +8,12 @@
 * A J2 matrix loaded by traction over two steps (the second past yield) goes through the
   incremental residual, which takes only the traction's change since the commit: FP64
   matches the oracle's iterations and stresses at both steps.
-* A traction on a component that is not Neumann on that face is refused.
+* Non-uniform tractions on a face (a smooth field plus noise over the face's voxels, on two
+  components) reproduce the oracle's stencils.add_traction_ghosts construction: FP64 with
+  its iteration count and stresses to 1e-9, FP32 within +-2 iterations and 1e-5; the field
+  on a J2 matrix over two steps goes through the incremental residual (its change since the
+  commit) with the oracle's iterations.
+* A traction on a component that is not Neumann on that face is refused, uniform or field.
 """
 
 import numpy as np
@@ -157,5 +162,73 @@ def test_traction_on_a_dirichlet_component_is_refused():
         T[0, 0, 0] = 1e-3  # component 1 is Dirichlet on the x = 0 face
         with pytest.raises(F.FFTMError):
             gp.set_load(np.zeros((3, 3)), np.zeros(3), np.zeros((3, 6)), T=T)
+    finally:
+        gp.close()
+
+
+def _face_field(n, seed, scale):
+    """(3, n_y, n_z) field over the x = L face (oracle order [q][b][c] with b = y, c = z) and its
+    ABI array (3, n_z, n_y); component 1 loaded smoothly, component 2 with noise, component 3 zero."""
+    rng = np.random.default_rng(seed)
+    y = (np.arange(n[1]) + 0.5) / n[1]
+    z = (np.arange(n[2]) + 0.5) / n[2]
+    t = np.zeros((3, n[1], n[2]))
+    t[0] = scale * (1.0 + 0.5 * np.outer(np.sin(np.pi * y), np.cos(np.pi * z)))
+    t[1] = 0.2 * scale * rng.standard_normal((n[1], n[2]))
+    return t, np.ascontiguousarray(t.transpose(0, 2, 1))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_face_traction_field_matches_the_oracle(scheme, precision):
+    wl = _two_phase(scheme, 1e-10 if precision == "fp64" else 1e-6)
+    t, t_abi = _face_field(wl.n, 13, 1e-3)
+    pr = Problem(wl)
+    uf, rep = pr.solve_step(Tf={(0, 1): t})
+    assert rep.converged
+    gp = GpuProblem(wl, precision)
+    try:
+        F.fftm_set_face_traction(gp.p, 0, 1, t_abi.astype(gp.dtype))
+        st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+        assert r["converged"], r
+        S = gp.get_voxel(F.FFTM_FIELD_STRESS)
+        if precision == "fp64":
+            assert r["iterations"] == rep.iterations, (r["iterations"], rep.iterations)
+            assert rel_l2(S, sym6(pr.last["P"])) < 1e-9
+        else:
+            assert abs(r["iterations"] - rep.iterations) <= 2, (r["iterations"], rep.iterations)
+            assert rel_l2(S, sym6(pr.last["P"])) < 1e-5
+    finally:
+        gp.close()
+
+
+def test_face_traction_field_j2_two_steps_through_the_incremental_residual():
+    wl = _two_phase("HEX1", 1e-10, law=J2_LINHARD)
+    pr = Problem(wl)
+    gp = GpuProblem(wl, "fp64")
+    try:
+        for k, scale in enumerate((3e-4, 6e-4)):
+            t, t_abi = _face_field(wl.n, 14, scale)
+            _, rep = pr.solve_step(Tf={(0, 1): t})
+            assert rep.converged
+            F.fftm_set_face_traction(gp.p, 0, 1, t_abi)
+            st, r, _, _ = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+            assert st == F.FFTM_OK and r["converged"]
+            assert r["iterations"] == rep.iterations, (k, r["iterations"], rep.iterations)
+            assert rel_l2(gp.get_voxel(F.FFTM_FIELD_STRESS), sym6(pr.last["P"])) < 1e-9
+    finally:
+        gp.close()
+
+
+def test_face_traction_field_on_a_dirichlet_component_is_refused():
+    wl = _two_phase("HEX1", 1e-8)
+    gp = GpuProblem(wl, "fp64")
+    try:
+        bad = np.zeros((3, wl.n[1], wl.n[2]))
+        bad[0] = 1e-3  # component 1 is Dirichlet on the x = 0 face
+        with pytest.raises(F.FFTMError):
+            F.fftm_set_face_traction(gp.p, 0, 0, bad)
+        with pytest.raises(F.FFTMError):
+            F.fftm_set_face_traction(gp.p, 0, 1, np.zeros((3, 2, 2)))  # wrong size
     finally:
         gp.close()

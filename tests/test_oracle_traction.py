@@ -17,7 +17,7 @@ import synthetic as syn
 from oracle.bc import Grid
 from oracle.solver import Problem
 from oracle.stencils import div
-from synthetic.workloads import ISO_ELASTIC, Material, Workload
+from synthetic.workloads import ISO_ELASTIC, Material, Workload, axis_bc
 
 
 def _bar_bc():
@@ -60,3 +60,37 @@ def test_end_loaded_bar_is_in_uniaxial_stress(scheme):
     assert np.abs(eps - expect[None, :, :, None, None, None]).max() < 1e-10 * sig / E
     P = pr.last["P"]
     assert np.abs(P - np.diag([sig, 0.0, 0.0])[None, :, :, None, None, None]).max() < 1e-10 * sig
+
+
+def test_face_field_gives_the_hand_derived_nodal_forces():
+    """Non-uniform tractions t(v_b, v_c) on one face: with the stress itself zero, the HEX1
+    divergence at a node (m_b, m_c) of the face is the average over its four face voxels of
+    2 t / h_a (the uniform case's 2 t / h_a, voxel by voxel), the voxels beyond the face's
+    edges taking the value of the face voxel they mirror; the other faces' nodes get nothing."""
+    n = (6, 5, 4)
+    h = (1.0, 0.8, 1.3)
+    bc = axis_bc("D", "N", "N")
+    g = Grid(n, bc, h)
+    rng = np.random.default_rng(3)
+    t = rng.standard_normal((3, n[0], n[2]))  # face y = L2 (axis 1, face 1): in-plane axes x, z
+    D = div(np.zeros((1, 3, 3) + n), g, "HEX1", Tf={(1, 1): t})
+    for q in range(3):
+        for mb in range(n[0] + 1):
+            for mc in range(n[2] + 1):
+                vals = [t[q, min(max(mb + ob - 1, 0), n[0] - 1), min(max(mc + oc - 1, 0), n[2] - 1)]
+                        for ob in (0, 1) for oc in (0, 1)]
+                assert abs(D[q, mb, n[1], mc] - 2.0 / h[1] * np.mean(vals)) < 1e-12
+    assert np.abs(D[:, :, : n[1], :]).max() < 1e-12
+
+
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_uniform_face_field_equals_the_uniform_traction(scheme):
+    n = (6, 5, 4)
+    g = Grid(n, axis_bc("D", "N", "N"), (1.0, 0.8, 1.3))
+    S = np.random.default_rng(4).standard_normal((2 if scheme == "TETRA2" else 1, 3, 3) + n)
+    T = np.zeros((3, 2, 3))
+    T[2, 0] = [0.3, -0.2, 0.5]
+    field = np.broadcast_to(np.array(T[2, 0])[:, None, None], (3, n[0], n[1])).copy()
+    a = div(S, g, scheme, T=T)
+    b = div(S, g, scheme, Tf={(2, 0): field})
+    assert np.abs(a - b).max() < 1e-12
