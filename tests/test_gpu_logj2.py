@@ -9,7 +9,8 @@ the oracle, through the C ABI.
 * a porous-like medium (log-J2 matrix, soft Neo-Hookean spheres standing in for the pores),
   TETRA2, three stretch steps well past yield: FP64 with the oracle's iteration counts and
   Anderson steps, stresses to 1e-9 and the committed (H^p, p) to 1e-8 of the oracle's; FP32
-  fields (FFT and TF32 transforms): stresses and state to 1e-5 at every step, iterations at
+  fields (FFT and TF32 transforms): stresses and state within 1e-5 of the exact discrete
+  solution or no farther from it than the oracle's own iterate at tol 1e-6 (x2), iterations at
   most 30 % above the oracle's (a diagnostic: the +-2 bar is missed, see the test);
 * the STATE field round trip and reset.
 """
@@ -98,11 +99,19 @@ def _porous(tol):
 def test_porous_medium_matches_the_oracle(precision):
     wl, loads = _porous(1e-8 if precision == "fp64" else 1e-6)
     pr = Problem(wl)
+    # FP32: the fields are held against the exact discrete solution (the oracle run to 1e-10
+    # through the same steps), within 1e-5 or no farther than twice the oracle's own iterate at
+    # the same tolerance: two iterates that both meet 1e-6 may differ by the tolerance times the
+    # conditioning of the fixed point, which the perfectly plastic zone makes large
+    px = Problem(wl) if precision != "fp64" else None
     gp = GpuProblem(wl, precision)
     try:
         for k, (A, b, Q) in enumerate(loads):
             _, rep = pr.solve_step(A=A, b=b, Q=Q)
             assert rep.converged
+            if px is not None:
+                _, repx = px.solve_step(A=A, b=b, Q=Q, tol=1e-10)
+                assert repx.converged
             gp.set_load(A, b, Q)
             st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
             assert r["converged"], (k, r)
@@ -116,9 +125,10 @@ def test_porous_medium_matches_the_oracle(precision):
                 assert rel_l2(Sg, So) < 1e-9, k
                 assert rel_l2(Zg, Zo) < 1e-8, k
             else:
-                assert rel_l2(Sg, So) < 1e-5, k
-                assert rel_l2(Zg[:, :6], Zo[:, :6]) < 1e-5, k
-                assert rel_l2(Zg[:, 6], Zo[:, 6]) < 1e-5, k
+                Sx, Zx = _s9(px.last["P"]), _state7(px.state)
+                for got, own, exact in ((Sg, So, Sx), (Zg[:, :6], Zo[:, :6], Zx[:, :6]), (Zg[:, 6], Zo[:, 6], Zx[:, 6])):
+                    assert rel_l2(got, exact) <= max(1e-5, 2 * rel_l2(own, exact)), (k, rel_l2(got, exact),
+                                                                                    rel_l2(own, exact))
                 # a labelled diagnostic, not the +-2 bar: with FP32 fields the residual of this
                 # perfectly plastic law carries the law's FP32 rounding (~1e-7 of the stress), which
                 # the zero plastic tangent leaves undamped, so the solve needs up to ~20 % more
