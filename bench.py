@@ -81,6 +81,8 @@ def parse_args(argv=None):
     ap.add_argument("--residual-passes", type=int, choices=[0, 1, 2], default=0,
                     help="residual form: 0 = chosen by the library's launch-shape tuner, 1 = one pass, "
                          "2 = two passes (FFTM_OPT_RESIDUAL_PASSES)")
+    ap.add_argument("--graph", type=int, choices=[0, 1], default=0,
+                    help="1: device-decided steps replayed from CUDA graphs (FFTM_OPT_CUDA_GRAPH)")
     ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
                     help="1: convergence test on the device (default); 0: the host reads the norms every iteration")
     ap.add_argument("--serve", action="store_true",
@@ -344,6 +346,7 @@ def gpu_arm(args):
                                  max_iter=wl.max_iter)
         p = F.fftm_problem_create(ctx, desc)
         F.fftm_set_option(p, F.FFTM_OPT_DEVICE_LOOP, args.device_loop)
+        F.fftm_set_option(p, F.FFTM_OPT_CUDA_GRAPH, args.graph)
         if args.residual_passes:
             F.fftm_set_option(p, F.FFTM_OPT_RESIDUAL_PASSES, args.residual_passes)
         F.fftm_set_load(p, wl.A)
@@ -577,6 +580,7 @@ def serve_one(args, F, reqs, precision):
 
     def run(arrivals):
         srv = F.fftm_server_create(0, 0, args.slots)
+        F.fftm_server_set_option(srv, F.FFTM_OPT_CUDA_GRAPH, args.graph)
         done = {}
         t0 = time.monotonic()
         ids = {}
@@ -623,7 +627,7 @@ def serve_one(args, F, reqs, precision):
             "config": {"workload": f"serving stream: {len(reqs)} requests (seeds 1000..{999 + len(reqs)}), sides "
                                    "32/48/64/96/128, per-axis P/D/N, isotropic or J2 matrix, HEX1 or TETRA2, "
                                    "spheres or Voronoi; Poisson arrivals at 0.8x the measured capacity",
-                       "precision": precision}}
+                       "precision": precision, "cuda_graph": args.graph}}
     print(json.dumps(line), flush=True)
 
 

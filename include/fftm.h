@@ -284,6 +284,15 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
                              for this grid shape on this GPU (timed once per shape and process;
                              fftm_tuning_table lists the choices).  Both forms give the same D;
                              problems with other laws always take two passes.
+   FFTM_OPT_CUDA_GRAPH       1: a device-decided step (FFTM_OPT_DEVICE_LOOP 1, no normal-mixed
+                             load, profiling off) captures its iterations into two CUDA graphs
+                             per load step (the first lcm(5, anderson_period) iterations and the
+                             next as many, which repeat) and replays the second until the
+                             convergence flag is set, one host wait per replay; results are
+                             bit-identical to 0 (the default: iterations enqueued one by one).
+                             Launch counts then include the kernels replayed past the stop,
+                             which return at once.  A stream that cannot be captured falls back
+                             to 0.
    FFTM_OPT_RESIDUAL_TILE    the one-pass form's voxel tile height: 8 or 16 rows of 32
                              voxels per thread block, or 0 (default) = measured, as above.
    FFTM_OPT_DEVICE_LOOP      1 (default): the convergence test of each iteration (Eq.
@@ -294,7 +303,12 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes);
                              host reads the norms after every residual.  Loads with a
                              normal-mixed part always take the host path (their free strain
                              components are updated on the host).  Both give the same iterates. */
-enum fftm_option { FFTM_OPT_RESIDUAL_PASSES = 0, FFTM_OPT_RESIDUAL_TILE = 1, FFTM_OPT_DEVICE_LOOP = 2 };
+enum fftm_option {
+  FFTM_OPT_RESIDUAL_PASSES = 0,
+  FFTM_OPT_RESIDUAL_TILE = 1,
+  FFTM_OPT_DEVICE_LOOP = 2,
+  FFTM_OPT_CUDA_GRAPH = 3
+};
 int fftm_set_option(fftm_problem* p, int option, int value);
 
 /* Measured fused multiply-add throughput of a device (FLOP/s, an FMA counting two), in FP64

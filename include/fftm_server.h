@@ -74,6 +74,11 @@ int fftm_server_poll(fftm_server* s, fftm_result* out, int max_results, int wait
 /* Requests queued, solves resident, device bytes reserved by resident solves. */
 int fftm_server_pending(fftm_server* s, int* queued, int* active, size_t* bytes_in_use);
 
+/* An fftm_set_option call (include/fftm.h, enum fftm_option) that every request submitted
+   afterwards gets on its problem, e.g. FFTM_OPT_CUDA_GRAPH 1; a value the problem refuses
+   fails that request with the option's status.  FFTM_E_INVALID for an unknown option. */
+int fftm_server_set_option(fftm_server* s, int option, int value);
+
 /* Finish every queued request, join the threads, free the server. */
 int fftm_server_destroy(fftm_server* s);
 

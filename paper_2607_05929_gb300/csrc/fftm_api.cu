@@ -316,6 +316,7 @@ struct fftm_problem {
   // device-decided load steps (every load without a normal-mixed part): the convergence test
   // runs on the device and the host waits once per chunk of iterations
   int dev_loop = 1;                // FFTM_OPT_DEVICE_LOOP
+  int graph = 0;                   // FFTM_OPT_CUDA_GRAPH: device-decided steps replay captured iterations
   int last_iters = -1;             // iterations of the previous device-decided step (chunk sizing)
   int* dctl = nullptr;             // control block of k_check: stop, next iteration, last checked
   double* derr = nullptr;          // per-iteration errors of the step (device)
@@ -1077,6 +1078,70 @@ int update_after(fftm_problem* p, int m, int cur0) {
 // Returns the last checked iteration in *m_out and the stop code in *stop_out.
 constexpr int kDevChunk = 4;
 
+// Device-decided steps replayed from CUDA graphs.  The launches of iteration m depend on m only
+// through the slot ring (m mod NSLOT) and the Anderson gate (m mod period, and whether `depth`
+// couples exist yet), so iterations [G, 2G) with G = lcm(NSLOT, period) repeat for every later
+// block of G.  Two graphs are captured per load step (their kernel arguments hold the load):
+// iterations [0, G) and [G, 2G); the second is replayed until the stop flag is set.  Kernels
+// replayed past the stop return at once.  FFTM_E_UNSUPPORTED: the capture failed (the caller
+// falls back to enqueueing the iterations one by one).
+template <typename T>
+int graph_loop(fftm_problem* p, int cur0, int* stop_out, int* mlast_out) {
+  cudaStream_t s = p->ctx->stream;
+  const int max_iter = p->desc.max_iter;
+  const int depth = p->desc.anderson_depth, period = std::max(1, p->desc.anderson_period);
+  int G = NSLOT;
+  if (depth > 0) {
+    int a = NSLOT, b = period;
+    while (b) { const int t = a % b; a = b; b = t; }
+    G = NSLOT / a * period;
+    while (G < depth) G += NSLOT / a * period;
+  }
+  cudaGraphExec_t ex[2] = {nullptr, nullptr};
+  long long ncap[2] = {0, 0};
+  int rc = FFTM_OK;
+  for (int k = 0; k < 2 && !rc; ++k) {
+    const long long before = p->launches;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      rc = FFTM_E_UNSUPPORTED;
+      break;
+    }
+    int irc = FFTM_OK;
+    for (int m = k * G; m < (k + 1) * G && !irc; ++m) {
+      irc = run_residual<T>(p, (cur0 + m) % NSLOT, false);
+      if (!irc) irc = update_after<T>(p, m, cur0);
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    ncap[k] = p->launches - before;
+    p->launches = before;
+    if (irc || e != cudaSuccess || !g || cudaGraphInstantiate(&ex[k], g, 0) != cudaSuccess) rc = FFTM_E_UNSUPPORTED;
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+  }
+  int stop = 0, mlast = 0;
+  int* hctl = reinterpret_cast<int*>(p->hpin + 40);
+  for (int m0 = 0; !rc && m0 <= max_iter; m0 += G) {
+    const int k = m0 == 0 ? 0 : 1;
+    if (cudaGraphLaunch(ex[k], s) != cudaSuccess ||
+        cudaMemcpyAsync(hctl, p->dctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = set_err(FFTM_E_CUDA, std::string("graph replay: ") + cudaGetErrorString(cudaGetLastError()));
+      break;
+    }
+    p->launches += ncap[k];
+    stop = hctl[0];
+    mlast = hctl[2];
+    if (stop) break;
+  }
+  for (int k = 0; k < 2; ++k)
+    if (ex[k]) cudaGraphExecDestroy(ex[k]);
+  *stop_out = stop;
+  *mlast_out = mlast;
+  return rc;
+}
+
 template <typename T>
 int device_loop(fftm_problem* p, int cur0, int* m_out, int* stop_out) {
   cudaStream_t s = p->ctx->stream;
@@ -1097,6 +1162,18 @@ int device_loop(fftm_problem* p, int cur0, int* m_out, int* stop_out) {
   int stop = 0, mlast = 0;
   p->stop = p->dctl;
   int rc = FFTM_OK;
+  if (p->graph && !p->prof) {
+    const int grc = graph_loop<T>(p, cur0, &stop, &mlast);
+    if (grc != FFTM_E_UNSUPPORTED) {  // else: the stream could not be captured, enqueue as usual
+      p->stop = nullptr;
+      if (grc) return grc;
+      p->last_iters = mlast;
+      *m_out = mlast;
+      *stop_out = stop;
+      return FFTM_OK;
+    }
+    CU(cudaMemsetAsync(p->dctl, 0, 4 * sizeof(int), s));
+  }
   // chunks of kDevChunk iterations; near the iteration count of the previous step (a repeated or
   // similar load) the chunks shrink to one, so a step that stops there enqueues no idle work
   for (int m0 = 0, K = kDevChunk; m0 <= max_iter && !rc; m0 += K) {
@@ -1976,6 +2053,10 @@ int fftm_set_option(fftm_problem* p, int option, int value) {
     case FFTM_OPT_DEVICE_LOOP:
       if (value != 0 && value != 1) return set_err(FFTM_E_INVALID, "device loop: 0 or 1");
       p->dev_loop = value;
+      return FFTM_OK;
+    case FFTM_OPT_CUDA_GRAPH:
+      if (value != 0 && value != 1) return set_err(FFTM_E_INVALID, "CUDA graph: 0 or 1");
+      p->graph = value;
       return FFTM_OK;
     case FFTM_OPT_RESIDUAL_TILE:
       if (value != 0 && value != 8 && value != 16) return set_err(FFTM_E_INVALID, "residual tile: 0 (tuned), 8 or 16");

@@ -45,6 +45,7 @@ struct Request {
   size_t u_out_bytes = 0;
   size_t need = 0;        // workspace bytes
   double t_submit = 0.0;
+  std::vector<std::pair<int, int>> options;  // fftm_set_option calls for the request's problem
 };
 
 }  // namespace
@@ -65,6 +66,7 @@ struct fftm_server {
   std::condition_variable cv_start;
   std::vector<std::thread> workers;
   std::string error;
+  std::vector<std::pair<int, int>> options;  // applied to the problems of requests submitted later
 };
 
 namespace {
@@ -89,6 +91,7 @@ void run_request(fftm_ctx* ctx, Request& q, fftm_result& r) {
   q.desc.phase = q.phase.data();
   q.desc.materials = q.mats.data();
   int st = fftm_problem_create(ctx, &q.desc, &p);
+  for (size_t k = 0; st == FFTM_OK && k < q.options.size(); ++k) st = fftm_set_option(p, q.options[k].first, q.options[k].second);
   if (st == FFTM_OK) {
     for (size_t k = 0; k < q.loads.size() && st >= 0; ++k) {
       st = fftm_set_load(p, &q.loads[k]);
@@ -249,6 +252,10 @@ int fftm_server_submit(fftm_server* s, const fftm_request* req, long long* id) {
   q->loads.assign(req->loads, req->loads + req->n_loads);
   q->u_out = req->u_out;
   q->u_out_bytes = req->u_out_bytes;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    q->options = s->options;
+  }
   q->need = need;
   q->t_submit = now_s();
   {
@@ -305,3 +312,18 @@ int fftm_server_inject_start_failures(int count) {
 }
 
 }  // extern "C"
+
+extern "C" int fftm_server_set_option(fftm_server* s, int option, int value) {
+  if (!s) return FFTM_E_INVALID;
+  if (option != FFTM_OPT_RESIDUAL_PASSES && option != FFTM_OPT_RESIDUAL_TILE && option != FFTM_OPT_DEVICE_LOOP &&
+      option != FFTM_OPT_CUDA_GRAPH)
+    return FFTM_E_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto& o : s->options)
+    if (o.first == option) {
+      o.second = value;
+      return FFTM_OK;
+    }
+  s->options.emplace_back(option, value);
+  return FFTM_OK;
+}

@@ -1673,7 +1673,7 @@ __global__ void __launch_bounds__(256) k_face_div(ResParams<T> P, FaceIdx fi) {
   }
 }
 
-constexpr int kFaceBlocks = 152 * 2;
+constexpr int kFaceBlocks = 152 * 8;  // one face node per thread at 256^3 (the work per node is a long chain of gathers)
 
 template <typename T>
 static size_t fused_smem(int tetra, int fy) {

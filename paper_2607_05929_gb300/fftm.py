@@ -32,7 +32,7 @@ FFTM_FP64, FFTM_FP32, FFTM_FP32_TC, FFTM_FP32_TF32 = 0, 1, 2, 3
 FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
 FFTM_LAW_SVK_CUBIC, FFTM_LAW_NEO_HOOKE, FFTM_LAW_CP_FCC, FFTM_LAW_LOG_J2 = 4, 5, 6, 7
 FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D, FFTM_FIELD_STATE = 0, 1, 2, 3, 4, 5
-FFTM_OPT_RESIDUAL_PASSES, FFTM_OPT_RESIDUAL_TILE, FFTM_OPT_DEVICE_LOOP = 0, 1, 2
+FFTM_OPT_RESIDUAL_PASSES, FFTM_OPT_RESIDUAL_TILE, FFTM_OPT_DEVICE_LOOP, FFTM_OPT_CUDA_GRAPH = 0, 1, 2, 3
 FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP_GREEN_UPDATE = 0, 1, 2, 3, 4
 
 # every symbol include/fftm.h declares
@@ -43,7 +43,7 @@ EXPORTS = [
     "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_set_option", "fftm_tuning_table", "fftm_device_fma_rate", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
-    "fftm_server_inject_start_failures",
+    "fftm_server_inject_start_failures", "fftm_server_set_option",
     "fftm_host_dense_transform", "fftm_host_mixed_increment", "fftm_host_log_j2",
 ]
 FFTM_DT_KINDS = {"DFT": 0, "DCT1": 1, "DCT3": 2, "DST1": 3, "DST3": 4}
@@ -148,6 +148,7 @@ def load_library(path=LIB_PATH):
         "fftm_server_pending": ([vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_size_t)], ctypes.c_int),
         "fftm_server_destroy": ([vp], ctypes.c_int),
         "fftm_server_inject_start_failures": ([ctypes.c_int], ctypes.c_int),
+        "fftm_server_set_option": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -520,6 +521,10 @@ def fftm_server_pending(s):
 
 def fftm_server_destroy(s):
     return _check(load_library().fftm_server_destroy(s))
+
+
+def fftm_server_set_option(srv, option, value):
+    return _check(load_library().fftm_server_set_option(srv, int(option), int(value)))
 
 
 def fftm_server_inject_start_failures(count):

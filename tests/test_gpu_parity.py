@@ -375,6 +375,47 @@ def test_device_decided_step_equals_the_host_loop(precision, name):
     assert np.array_equal(r1["mean_P"], r2["mean_P"])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tf32"])
+@pytest.mark.parametrize("name", ["sphere16_hex", "voronoi_tet"])
+def test_graph_replayed_step_equals_the_enqueued_one(precision, name):
+    """Device-decided steps replayed from CUDA graphs (FFTM_OPT_CUDA_GRAPH) give the iterates of
+    the steps whose iterations are enqueued one by one, bit for bit, over two load steps (the
+    second starting from the first's field, so the graphs are captured again with the new
+    load)."""
+    wl = SOLVE_CASES[name]()
+    wl.tol = 1e-8 if precision == "fp64" else 1e-6
+    runs = []
+    for graph in (1, 0):
+        gp = GpuProblem(wl, precision)
+        try:
+            F.fftm_set_option(gp.p, F.FFTM_OPT_CUDA_GRAPH, graph)
+            out = []
+            for scale in (1.0, 1.5):
+                gp.set_load(scale * np.asarray(wl.A), np.asarray(wl.b), np.asarray(getattr(wl, "Q", np.zeros((3, 6)))))
+                st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=wl.max_iter + 1)
+                out.append((st, r, eh, ah, gp.get_node(F.FFTM_FIELD_U)))
+            runs.append(out)
+        finally:
+            gp.close()
+    for (s1, r1, e1, a1, u1), (s2, r2, e2, a2, u2) in zip(*runs):
+        assert s1 == s2 == F.FFTM_OK and r1["converged"] and r2["converged"]
+        assert r1["iterations"] == r2["iterations"] and list(a1) == list(a2)
+        assert np.array_equal(e1, e2) and np.array_equal(u1, u2)
+        assert np.array_equal(r1["mean_P"], r2["mean_P"])
+
+
+def test_graph_replayed_step_stops_at_the_iteration_limit():
+    wl = SOLVE_CASES["sphere16_hex"]()
+    gp = GpuProblem(wl, "fp64", max_iter=7)
+    try:
+        F.fftm_set_option(gp.p, F.FFTM_OPT_CUDA_GRAPH, 1)
+        st, r, eh, ah = F.fftm_solve_step(gp.p, history_len=9)
+        assert st == F.FFTM_NOT_CONVERGED and not r["converged"] and r["iterations"] == 7
+        assert len(eh) == 8 and np.all(np.isfinite(eh))
+    finally:
+        gp.close()
+
+
 def test_device_decided_step_stops_at_the_iteration_limit():
     wl = SOLVE_CASES["sphere16_hex"]()
     gp = GpuProblem(wl, "fp64", max_iter=6)
