@@ -239,6 +239,17 @@ int fftm_set_load(fftm_problem* p, const fftm_load* load);
    Takes effect at the next load step (or residual). */
 int fftm_set_face_traction(fftm_problem* p, int axis, int face, const void* t, int t_is_device, size_t bytes);
 
+/* A prescribed displacement given as a node field (Sec. 2.2: u* is any field carrying the
+   Dirichlet values), added to the closed-form u* of fftm_set_load: 3 components in the dense
+   node layout of the file header (problem precision), HOST (is_device = 0) or device pointer,
+   copied before the call returns; bytes must be 3 N1 N2 N3 times the element size.  Its
+   gradient at the voxel points is the scheme's stencil on its node values (Eqs. D1HG-D3HG,
+   D1T1T2G-D3T1T2G); on a periodic axis the stored nodes make it periodic.  Its values at the
+   Dirichlet nodes are the displacement imposed there (u^f vanishes at them).  NULL removes it.
+   Not combinable with a normal-mixed load (FFTM_E_INVALID).  Takes effect at the next load
+   step; a J2 problem's incremental residual takes its change since the last commit. */
+int fftm_set_load_field(fftm_problem* p, const void* ustar, int is_device, size_t bytes);
+
 /* The current load (HOST out): as set, with the free components of a mixed load
    at their latest adjusted values. */
 int fftm_get_load(const fftm_problem* p, fftm_load* out);

@@ -93,9 +93,14 @@ class Problem:
         return np.stack([A[q, 0] * X[0] + A[q, 1] * X[1] + A[q, 2] * X[2] + b[q]
                          + sum(Q[q][k] * mono[k] for k in range(6)) for q in range(3)])
 
-    def grad_ustar(self, A=None, b=None, Q=None):
-        """Discrete gradient of u* at the voxel points (the scheme's stencil on the node values)."""
-        return grad_full(self.ustar_full(A, b, Q), self.grid, self.scheme)
+    def grad_ustar(self, A=None, b=None, Q=None, Us=None):
+        """Discrete gradient of u* at the voxel points (the scheme's stencil on the node values);
+        Us: a node field (3, N1, N2, N3) on the stored node grid added to the closed-form u*
+        (Sec. 2.2: u* is any field carrying the Dirichlet values)."""
+        u = self.ustar_full(A, b, Q)
+        if Us is not None:
+            u = u + full_nodes(np.asarray(Us, dtype=np.float64), self.grid)
+        return grad_full(u, self.grid, self.scheme)
 
     # --- pieces of one iteration ------------------------------------------------------
     def residual(self, uf, Gs, T=None, Tf=None):
@@ -142,13 +147,14 @@ class Problem:
 
     # --- Algorithm 1, one load step -----------------------------------------------------
     def solve_step(self, A=None, b=None, uf0=None, max_iter=None, tol=None, anderson=True, Q=None, mixed=0,
-                   T=None, Tf=None):
+                   T=None, Tf=None, Us=None):
         """One load step.  mixed: bit mask of the symmetric strain components (Voigt order
         11, 22, 33, 23, 13, 12) of u* that are adjusted so that the mean stress vanishes in
         them (normal-mixed loading, mixed.py); the other components of A are imposed.
         T: uniform tractions T[axis][face][component] on the faces where that component is
         Neumann (stencils.add_traction_ghosts), or None for traction-free faces; Tf: per-face
-        traction fields {(axis, face): t (3, n_b, n_c)} added to T."""
+        traction fields {(axis, face): t (3, n_b, n_c)} added to T; Us: u* as a node field on
+        the stored node grid, added to the closed-form u*."""
         wl = self.wl
         tol = wl.tol if tol is None else tol
         max_iter = wl.max_iter if max_iter is None else max_iter
@@ -158,7 +164,7 @@ class Problem:
                 i, j = mixed_mod.VOIGT[k]
                 A[i, j] = self.mixed_A[i, j]
                 A[j, i] = self.mixed_A[j, i]
-        Gs = self.grad_ustar(A, b, Q)
+        Gs = self.grad_ustar(A, b, Q, Us)
         uf = self.uf.copy() if uf0 is None else np.array(uf0, dtype=np.float64)
         mixer = anderson_mod.Mixer(wl.anderson_depth, wl.anderson_period, enabled=anderson)
         rep = Report(iterations=0, converged=False)
@@ -185,7 +191,7 @@ class Problem:
             uf = self.green_update(q)
             if mixed:  # the free strain components of u* for the next iteration
                 A = A + mixed_mod.mixed_increment(mean_sig, mixed, float(wl.lambda0), float(wl.mu0))
-                Gs = self.grad_ustar(A, b, Q)
+                Gs = self.grad_ustar(A, b, Q, Us)
         self.uf = uf
         if mixed:
             self.mixed_A = A.copy()

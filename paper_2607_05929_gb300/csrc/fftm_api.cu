@@ -287,6 +287,8 @@ struct fftm_problem {
   int c0 = 0;               // the C0 Green operator (three components coupled per frequency)
   void* tface[3][2] = {};   // non-uniform tractions per face (fftm_set_face_traction), or null
   void* tface_n[3][2] = {}; // the fields at the last commit (J2's incremental residual)
+  void* ustar = nullptr;    // u* as a node field (fftm_set_load_field), 3 components, or null
+  void* ustar_n = nullptr;  // that field at the last commit (J2's incremental residual)
   void* c0tab = nullptr;    // its sin / cos tables per axis over the node positions
   void* state_next = nullptr;  // the state committed by the last converged step, swapped in when
   int commit_pending = 0;      // the next step starts (readouts until then see the step's own state)
@@ -646,6 +648,10 @@ ResParams<T> res_params(fftm_problem* p, int slot, T* D_base, T* p_base) {
       R.tface_n[a][f] = nullptr;
       R.traction |= p->tface[a][f] != nullptr;
     }
+  for (int q = 0; q < 3; ++q) {
+    R.us[q] = p->ustar ? reinterpret_cast<const T*>(p->ustar) + q * p->comp_stride : nullptr;
+    R.us_n[q] = p->ustar_n ? reinterpret_cast<const T*>(p->ustar_n) + q * p->comp_stride : nullptr;
+  }
   return R;
 }
 
@@ -1332,6 +1338,13 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
                            cudaMemcpyDeviceToDevice, s));
     }
     p->load_n = p->load;
+    if (p->ustar) {  // the u* field at the commit
+      const size_t ub = 3 * (size_t)p->comp_stride * sizeof(T);
+      if (!p->ustar_n) CU(cudaMalloc(&p->ustar_n, ub));
+      CU(cudaMemcpyAsync(p->ustar_n, p->ustar, ub, cudaMemcpyDeviceToDevice, s));
+    } else if (p->ustar_n) {
+      CU(cudaMemsetAsync(p->ustar_n, 0, 3 * (size_t)p->comp_stride * sizeof(T), s));
+    }
     for (int a = 0; a < 3; ++a)  // the face traction fields at the commit
       for (int f = 0; f < 2; ++f) {
         if (!p->tface[a][f]) {
@@ -1506,6 +1519,33 @@ Sizes sizes_of(const fftm_problem_desc* d) {
 
 // ======================================================================================
 extern "C" {
+static int ensure_scratch(fftm_problem* p, size_t bytes);
+}
+
+template <typename T>
+static int set_load_field_t(fftm_problem* p, const void* u, int is_device, size_t bytes) {
+  cudaStream_t s = p->ctx->stream;
+  const void* from = u;
+  if (!is_device) {
+    int rc = ensure_scratch(p, bytes);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(p->scratch, u, bytes, cudaMemcpyHostToDevice, s));
+    from = p->scratch;
+  }
+  if (!p->ustar) {
+    CU(cudaMalloc(&p->ustar, 3 * (size_t)p->comp_stride * sizeof(T)));
+    CU(cudaMemsetAsync(p->ustar, 0, 3 * (size_t)p->comp_stride * sizeof(T), s));
+  }
+  T* dst[3];
+  for (int q = 0; q < 3; ++q) dst[q] = reinterpret_cast<T*>(p->ustar) + q * p->comp_stride;
+  CU(launch_pack<T>((const T* const*)dst, const_cast<T*>(reinterpret_cast<const T*>(from)), p->N[0], p->N[1],
+                    p->N[2], p->sy, p->sz, 1, s));
+  CU(cudaStreamSynchronize(s));
+  p->launches++;
+  return FFTM_OK;
+}
+
+extern "C" {
 
 const char* fftm_last_error(void) { return g_last_error.c_str(); }
 int fftm_version(void) { return 1; }
@@ -1581,6 +1621,8 @@ int fftm_problem_destroy(fftm_problem* p) {
       cudaFree(p->tface[a][f]);
       cudaFree(p->tface_n[a][f]);
     }
+  cudaFree(p->ustar);
+  cudaFree(p->ustar_n);
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
@@ -1973,6 +2015,22 @@ int fftm_host_mixed_increment(const double* sig, int mask, double lambda0, doubl
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) d_out[i * 3 + j] = d[i][j];
   return FFTM_OK;
+}
+
+int fftm_set_load_field(fftm_problem* p, const void* ustar, int is_device, size_t bytes) {
+  if (!p) return set_err(FFTM_E_INVALID, "null problem");
+  CU(cudaSetDevice(p->ctx->device));
+  if (!ustar) {
+    CU(cudaStreamSynchronize(p->ctx->stream));
+    cudaFree(p->ustar);
+    p->ustar = nullptr;
+    return FFTM_OK;
+  }
+  if (p->load.mixed) return set_err(FFTM_E_INVALID, "a u* field with a normal-mixed load");
+  const size_t need = 3 * (size_t)p->N[0] * p->N[1] * p->N[2] * p->esz;
+  if (bytes != need) return set_err(FFTM_E_INVALID, "byte count does not match the node field");
+  if (p->esz == 8) return set_load_field_t<double>(p, ustar, is_device, bytes);
+  return set_load_field_t<float>(p, ustar, is_device, bytes);
 }
 
 int fftm_set_face_traction(fftm_problem* p, int axis, int face, const void* t, int t_is_device, size_t bytes) {

@@ -2,6 +2,7 @@
 // blocks and the launchers each .cu file provides.  Not part of the ABI.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the TMA descriptor type; no driver call is made through it here)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -80,6 +81,10 @@ struct ResParams {
   long long vy, vz;  // voxel strides
   T Gs[9];           // uniform gradient of the affine part of u*
   int quad;          // 1 if u* has quadratic terms
+  // u* given as a node field (fftm_set_load_field, the problem's node layout nsy / nsz), added
+  // to the closed-form part; us_n: the field at the last commit (J2 increments), or null
+  const T* us[3];
+  const T* us_n[3];
   T Qc[3][6];        // their coefficients: x1^2, x2^2, x3^2, x2 x3, x1 x3, x1 x2
   T hh[3];           // voxel sizes
   // J2 phases are evaluated incrementally from the last commit: the state holds the
@@ -176,6 +181,9 @@ int pass_tc_rows(int Kp, int axis);
 // unevaluated hi + lo pair when out_lo is set; mode 2 (z axis): the forward result times the
 // B0 / 2 mu0 Green factor -gscale / den (0 where den is null).
 struct TfPassParams {
+  // x axis: each input component as a 2D tensor {row pitch, N2 * N3 rows}, 32 x 128 boxes with
+  // the 128-byte swizzle (filled by launch_pass_tf32)
+  CUtensorMap xmap[3];
   const float* in[3];
   float* out[3];
   const float* base[3];

@@ -701,6 +701,29 @@ __device__ __forceinline__ void law_grad(const ResParams<T>& P, bool j2, const T
     for (int i = 0; i < 9; ++i) Gt[i] = Gf[i] + P.Gs[i];
     if (P.quad) add_quad<T, TETRA>(P.hh, P.Qc, r, vx, vy, vz, Gt);
   }
+  if (P.us[0]) {  // u* as a node field: the scheme's stencil on its corner values (its change
+                  // since the commit for a J2 increment)
+    T sh[3][8], sl[3][8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+      int gx = vx + (o & 1), gy = vy + ((o >> 1) & 1), gz = vz + (o >> 2);
+      if (P.periodic[0] && gx == P.n[0]) gx = 0;
+      if (P.periodic[1] && gy == P.n[1]) gy = 0;
+      if (P.periodic[2] && gz == P.n[2]) gz = 0;
+      const long long at = gx + gy * P.nsy + gz * P.nsz;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T v = P.us[c][at];
+        if (j2 && P.us_n[0]) v -= P.us_n[c][at];
+        sh[c][o] = v;
+        sl[c][o] = T(0);
+      }
+    }
+    T Gu[9];
+    point_grad<T, TETRA, false>(sh, sl, r, P.wgrad, Gu);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Gt[i] += Gu[i];
+  }
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -1695,7 +1718,7 @@ static cudaError_t launch_fused_kernel(const ResParams<T>& P, const FusedGeom& g
 // plain (non-incremental) form without the test outputs.
 template <typename T>
 static bool fused_ok(const ResParams<T>& P, bool with_p) {
-  return !with_p && !P.inc && P.nst == 0 && P.sym && P.state == nullptr && !P.two_pass;
+  return !with_p && !P.inc && P.nst == 0 && P.sym && P.state == nullptr && !P.two_pass && P.us[0] == nullptr;
 }
 
 template <typename T>

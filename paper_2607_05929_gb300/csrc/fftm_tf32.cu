@@ -24,6 +24,8 @@
 // it; eight epilogue warps drain the TMEM accumulators (two, alternating, when they fit)
 // while the next tile is contracted.  Every wait is bounded: past the limit the CTA records
 // an error in P.err, lets its copies and MMAs finish, frees its TMEM and returns.
+#include <cudaTypedefs.h>
+
 #include "fftm_internal.cuh"
 #include "fftm_umma.cuh"
 
@@ -42,6 +44,26 @@ constexpr uint32_t TF_TILE_BYTES = TF_P * TF_KC * 4;
 // N >> 3, M >> 4.
 __device__ __forceinline__ uint32_t tf_idesc(int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TF_P >> 4) << 24);
+}
+
+// K-major operand with the 128-byte swizzle (rows of 128 bytes, 8-row atoms of 1024 bytes, the
+// 16-byte chunks of row r at chunk ^ (r & 7)): the layout a TMA box of 32 FP32 x rows writes with
+// CU_TENSOR_MAP_SWIZZLE_128B.  A k-step of 8 elements advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  return smem_desc(saddr, 16, 1024) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
 }
 
 __device__ __forceinline__ void tf_mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
@@ -256,6 +278,7 @@ struct TfBars {
   uint64_t* acc_full;   // [2]   1 (MMA commit): the tile's contraction is done
   uint64_t* acc_empty;  // [2]   TF_EPI arrivals: the accumulator has been drained
   uint64_t* done;       // 1     (MMA commit): every MMA of the CTA has completed
+  uint64_t* land;       // [nst] x axis: 1 (the TMA issuer) + the tile's transaction bytes
 };
 
 // ---- the MMA thread (warp 15, lane 0): matrix copies ahead, MMAs as stages land -----------
@@ -312,7 +335,7 @@ __device__ void tf_mma_thread(const TfPassParams& P, const TfGeom& g, unsigned c
           if (AXIS == 0) {
             // D[m][p] += T[m][k] S[p][k]: A = matrix (K-major, blocks of 128 rows), B = tile
             // (K-major, N = 128): a k-step of 8 is two core matrices along K
-            const uint64_t db = smem_desc(st + (uint32_t)ks * 256u, 128, 1024);
+            const uint64_t db = smem_desc_sw128(st + (uint32_t)ks * 32u);
             for (int mb = 0; mb < cg.mp / 128; ++mb) {
               const uint64_t da = smem_desc(sm + (uint32_t)mb * 16u * 1024u + (uint32_t)ks * 256u, 128, 1024);
               tf_mma(acc + mb * 128, da, db, tf_idesc(TF_P), accum);
@@ -525,10 +548,17 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
   B.acc_full = bars + 2 * TF_MAXST;
   B.acc_empty = bars + 2 * TF_MAXST + 2;
   B.done = bars + 2 * TF_MAXST + 4;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TF_MAXST + 5);
+  B.land = bars + 2 * TF_MAXST + 5;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TF_MAXST + 5);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   unsigned char* stages = smem + 2048;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // the x tiles use the 128-byte swizzle, whose pattern the MMA descriptor takes from 1024-byte
+  // aligned stages (every stage size is a multiple of 1024): refuse a misaligned window
+  if (AXIS == 0 && (smem_u32(stages) & 1023u)) {
+    if (tid == 0) atomicExch(P.err, 1);
+    return;
+  }
   const int ntiles = tf_total_tiles<AXIS>(P);
   const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int nacc = 2 * g.acc_cols <= TF_TMEM_COLS ? 2 : 1;
@@ -542,6 +572,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
     for (int s = 0; s < TF_MAXST; ++s) {
       bar_init(&B.full[s], TF_PROD + 1);
       bar_init(&B.empty[s], 1);
+      bar_init(&B.land[s], 1);
     }
     for (int i = 0; i < 2; ++i) {
       bar_init(&B.acc_full[i], 1);
@@ -560,6 +591,51 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
     // ---- producers: the tile part of every stage; up to `depth` stages of copies in flight,
     // the oldest processed and handed to the MMA thread as soon as it has landed ----
     const int ptid = tid - TF_EPI;
+    if (AXIS == 0) {
+      // x: one thread issues a TMA box per stage (32 x values of 128 consecutive rows, written in
+      // the 128-byte-swizzled K-major layout); once it has landed every producer rounds its share
+      // of the 16 KB to the nearest TF32 in place
+      const int depth = g.nst - 1 < 3 ? g.nst - 1 : 3;
+      long long seq = 0, done = 0;
+      int ti = 0, c = 0;
+      TfTile T;
+      if (my_tiles > 0) T = tf_tile_of<AXIS>(P, blockIdx.x);
+      auto process = [&](long long k) {
+        const int s = (int)(k % g.nst);
+        if (!bar_wait(&B.land[s], (uint32_t)((k / g.nst) & 1), abort)) return false;
+        const uint32_t base = smem_u32(stages + (size_t)s * g.stage);
+#pragma unroll
+        for (int j = 0; j < TF_XPC; ++j) {
+          const int i = ptid + j * TF_PROD;
+          if (i >= TF_P * 8) continue;
+          const float4 v = ld_shared4(base + (uint32_t)i * 16u);
+          st_shared4(base + (uint32_t)i * 16u, tf32r(v.x), tf32r(v.y), tf32r(v.z), tf32r(v.w));
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        bar_arrive(&B.full[s]);
+        return true;
+      };
+      bool live = true;
+      while (ti < my_tiles && live) {
+        const int s = (int)(seq % g.nst);
+        const long long u = seq / g.nst;
+        if (ptid == 0) {
+          if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) break;
+          expect_tx(&B.land[s], TF_TILE_BYTES);
+          tma_load_2d(smem_u32(stages + (size_t)s * g.stage), &P.xmap[T.q], (T.lo & ~3) + TF_KC * c, T.row0,
+                      &B.land[s]);
+        }
+        ++seq;
+        if (++c == T.Kp / TF_KC) {
+          c = 0;
+          if (++ti < my_tiles) T = tf_tile_of<AXIS>(P, blockIdx.x + ti * gridDim.x);
+        }
+        if (seq - done == depth) live = process(done++);
+      }
+      // the stages still in flight (thread 0 may have issued one more than the others counted
+      // after an abort: every thread drains what it counted, thread 0 its own count)
+      while (done < seq && live) live = process(done++);
+    } else {
     const int depth = g.nst - 1 < 3 ? g.nst - 1 : 3;
     long long seq = 0, done = 0;  // stages issued, stages handed over
     int ti = 0, c = 0;
@@ -590,6 +666,7 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
       tf_process<AXIS>(smem_u32(stages + (size_t)(done % g.nst) * g.stage), ptid);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       bar_arrive(&B.full[(int)(done % g.nst)]);
+    }
     }
   } else if (warp == (TF_EPI + TF_PROD) / 32) {
     // ---- warp 15: lane 0 copies the matrix chunks and issues the MMAs ----
@@ -630,7 +707,48 @@ static cudaError_t launch_tf32_one(const TfPassParams& P, int maxKp, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass_tf32(const TfPassParams& P, cudaStream_t s) {
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the library links the
+// runtime only)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// x axis: component q's input as {row pitch (x), N2 * N3 rows}, boxes of 32 x 128 with the
+// 128-byte swizzle; coordinates past the extents read zeros
+static cudaError_t encode_x_maps(TfPassParams& P) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  for (int q = 0; q < 3; ++q) {
+    const cuuint64_t dims[2] = {(cuuint64_t)P.stride[1], (cuuint64_t)P.N[1] * (cuuint64_t)P.N[2]};
+    const cuuint64_t strides[1] = {(cuuint64_t)P.stride[1] * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)TF_KC, (cuuint32_t)TF_P};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(&P.xmap[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P.in[q]), dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_pass_tf32(const TfPassParams& P0, cudaStream_t s) {
+  TfPassParams P = P0;
+  if (P.axis == 0) {
+    const cudaError_t e = encode_x_maps(P);
+    if (e != cudaSuccess) return e;
+  }
   int maxKp = 0;
   for (int q = 0; q < 3; ++q) {
     if (!pass_tf32_fits(P.Kp[q], P.axis)) return cudaErrorInvalidValue;

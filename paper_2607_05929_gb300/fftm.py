@@ -39,7 +39,7 @@ FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP
 EXPORTS = [
     "fftm_last_error", "fftm_version", "fftm_ctx_create", "fftm_ctx_destroy",
     "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
-    "fftm_set_phase", "fftm_set_load", "fftm_set_face_traction", "fftm_get_load", "fftm_solve_step", "fftm_field_bytes",
+    "fftm_set_phase", "fftm_set_load", "fftm_set_face_traction", "fftm_set_load_field", "fftm_get_load", "fftm_solve_step", "fftm_field_bytes",
     "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_set_option", "fftm_tuning_table", "fftm_device_fma_rate", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
@@ -122,6 +122,7 @@ def load_library(path=LIB_PATH):
         "fftm_set_load": ([vp, P(fftm_load)], ctypes.c_int),
         "fftm_get_load": ([vp, P(fftm_load)], ctypes.c_int),
         "fftm_set_face_traction": ([vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
+        "fftm_set_load_field": ([vp, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "fftm_host_dense_transform": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                                        P(ctypes.c_int)], ctypes.c_int),
         "fftm_host_mixed_increment": ([P(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -385,6 +386,15 @@ def fftm_set_face_traction(p, axis, face, t):
         return _check(load_library().fftm_set_face_traction(p, int(axis), int(face), None, 0, 0))
     ptr, dev, nb = _ptr_of(t)
     return _check(load_library().fftm_set_face_traction(p, int(axis), int(face), ctypes.c_void_p(ptr), dev, nb))
+
+
+def fftm_set_load_field(p, ustar):
+    """u* as a node field (numpy array or torch tensor of the problem's precision, the dense
+    layout (3, N3, N2, N1)), or None to remove it."""
+    if ustar is None:
+        return _check(load_library().fftm_set_load_field(p, None, 0, 0))
+    ptr, dev, nb = _ptr_of(ustar)
+    return _check(load_library().fftm_set_load_field(p, ctypes.c_void_p(ptr), dev, nb))
 
 
 def fftm_get_field(p, field, out):
