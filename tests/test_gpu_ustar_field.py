@@ -30,7 +30,7 @@ def _lib():
 
 
 def _wl(scheme, tol, law=ISO_ELASTIC):
-    n = (12, 10, 8)
+    n = (12, 9, 8)
     lam1, mu1 = syn.iso_lame(1.0, 0.3)
     lam2, mu2 = syn.iso_lame(4.0, 0.25)
     ph = syn.random_spheres(n, 0.2, 1.5, 2.0, 9)
