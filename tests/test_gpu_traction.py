@@ -8,8 +8,8 @@
 * A J2 matrix loaded by traction over two steps (the second past yield) goes through the
   incremental residual, which takes only the traction's change since the commit: FP64
   matches the oracle's iterations and stresses at both steps.
-* Non-uniform tractions on a face (a smooth field plus noise over the face's voxels, on two
-  components) reproduce the oracle's stencils.add_traction_ghosts construction: FP64 with
+* Non-uniform tractions on a face (smooth normal and shear fields over the face's voxels)
+  reproduce the oracle's stencils.add_traction_ghosts construction: FP64 with
   its iteration count and stresses to 1e-9, FP32 within +-2 iterations and 1e-5; the field
   on a J2 matrix over two steps goes through the incremental residual (its change since the
   commit) with the oracle's iterations.
@@ -168,13 +168,15 @@ def test_traction_on_a_dirichlet_component_is_refused():
 
 def _face_field(n, seed, scale):
     """(3, n_y, n_z) field over the x = L face (oracle order [q][b][c] with b = y, c = z) and its
-    ABI array (3, n_z, n_y); component 1 loaded smoothly, component 2 with noise, component 3 zero."""
+    ABI array (3, n_z, n_y): a normal load and a shear load, both varying over the face (phases
+    drawn from the seed), component 3 zero."""
     rng = np.random.default_rng(seed)
     y = (np.arange(n[1]) + 0.5) / n[1]
     z = (np.arange(n[2]) + 0.5) / n[2]
+    ph = rng.uniform(0.0, np.pi, 2)
     t = np.zeros((3, n[1], n[2]))
-    t[0] = scale * (1.0 + 0.5 * np.outer(np.sin(np.pi * y), np.cos(np.pi * z)))
-    t[1] = 0.2 * scale * rng.standard_normal((n[1], n[2]))
+    t[0] = scale * (1.0 + 0.5 * np.outer(np.sin(np.pi * y + ph[0]), np.cos(np.pi * z)))
+    t[1] = 0.2 * scale * np.outer(np.cos(2 * np.pi * y + ph[1]), np.sin(np.pi * z))
     return t, np.ascontiguousarray(t.transpose(0, 2, 1))
 
 
