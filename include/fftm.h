@@ -209,9 +209,22 @@ int fftm_version(void);
 int fftm_ctx_create(fftm_ctx** out, int device, void* cuda_stream);
 int fftm_ctx_destroy(fftm_ctx* ctx);
 
-/* Device bytes a problem with this descriptor allocates (fields, Anderson
-   history, transform tables, law tables). */
+/* Device bytes a problem with this descriptor allocates to solve (fields, Anderson
+   history, transform tables and matrices, law tables, internal variables, the staging
+   buffer of host transfers, the device-decided step's history), an upper bound that
+   includes the alignment of every allocation. */
 int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes);
+
+/* fftm_problem_create with every device allocation of the problem carved from a caller's
+   device buffer (e.g. a torch tensor, so that the framework owns the memory): `workspace`
+   (DEVICE pointer on the context's device, 256-byte aligned) of `bytes` >=
+   fftm_problem_workspace_bytes(desc) (FFTM_E_NOMEM otherwise); the caller keeps ownership
+   and must keep it alive until fftm_problem_destroy.  Allocations made after creation by
+   optional features (fftm_set_load_field, fftm_set_face_traction, the test variant of
+   FFTM_OP_RESIDUAL) are carved from what is left and return FFTM_E_NOMEM when it does not
+   suffice, so pass more than the minimum when they are used. */
+int fftm_problem_create_in(fftm_ctx* ctx, const fftm_problem_desc* desc, void* workspace, size_t bytes,
+                           fftm_problem** out);
 
 /* Validate the descriptor, derive per-component per-axis transform kinds and
    node ranges (Table 1; Sec. 2.7.2 "dismissed" points), build the frequency

@@ -33,6 +33,15 @@ static int set_err(int code, const std::string& msg) {
       return set_err(FFTM_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));            \
   } while (0)
 
+// a device allocation: FFTM_E_NOMEM when the device or the caller's workspace has no room
+#define DEVALLOC(call)                                                                            \
+  do {                                                                                            \
+    if ((call) != cudaSuccess) {                                                                  \
+      cudaGetLastError();                                                                         \
+      return set_err(FFTM_E_NOMEM, std::string("device allocation failed: ") + #call);            \
+    }                                                                                             \
+  } while (0)
+
 struct fftm_ctx {
   int device;
   cudaStream_t stream;
@@ -287,6 +296,8 @@ struct fftm_problem {
   int c0 = 0;               // the C0 Green operator (three components coupled per frequency)
   void* tface[3][2] = {};   // non-uniform tractions per face (fftm_set_face_traction), or null
   void* tface_n[3][2] = {}; // the fields at the last commit (J2's incremental residual)
+  char* arena = nullptr;    // caller-provided device workspace (fftm_problem_create_in), or null
+  size_t arena_size = 0, arena_used = 0;
   void* ustar = nullptr;    // u* as a node field (fftm_set_load_field), 3 components, or null
   void* ustar_n = nullptr;  // that field at the last commit (J2's incremental residual)
   void* c0tab = nullptr;    // its sin / cos tables per axis over the node positions
@@ -361,6 +372,27 @@ int ev_get(fftm_problem* p) {
 }
 
 // Brackets the launches of one category with two events when profiling is on.
+// Device allocations of a problem: from the caller's workspace when it gave one (a bump
+// allocator, 256-byte aligned; FFTM_E_NOMEM when it is exhausted), else cudaMalloc.  Memory of
+// the workspace is released with the problem, never piecewise.
+static cudaError_t dev_alloc(fftm_problem* p, void** ptr, size_t bytes) {
+  if (!p->arena) return cudaMalloc(ptr, bytes);
+  const size_t at = (p->arena_used + 255) & ~(size_t)255;
+  if (at > p->arena_size || bytes > p->arena_size - at) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  *ptr = p->arena + at;
+  p->arena_used = at + bytes;
+  return cudaSuccess;
+}
+
+static void dev_free(fftm_problem* p, void* ptr) {
+  if (!ptr) return;
+  if (p->arena && static_cast<char*>(ptr) >= p->arena && static_cast<char*>(ptr) < p->arena + p->arena_size) return;
+  cudaFree(ptr);
+}
+
 struct ProfScope {
   fftm_problem* p;
   int cat, a = -1;
@@ -779,14 +811,14 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
   T* pp = nullptr;
   if (test_outputs) {
     if (!p->Dbuf) {
-      CU(cudaMalloc(&p->Dbuf, 3 * p->comp_stride * sizeof(T)));
+      DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->Dbuf), 3 * p->comp_stride * sizeof(T)));
       CU(cudaMemsetAsync(p->Dbuf, 0, 3 * p->comp_stride * sizeof(T), p->ctx->stream));
     }
     D = reinterpret_cast<T*>(p->Dbuf);
     pp = field_ptr<T>(p, SET_WORK, 0);
     if (!p->vs_test) {
       const size_t b = (size_t)(p->tetra ? 2 : 1) * ((p->sym ? 6 : 9) + 9) * p->nvox * sizeof(T);
-      CU(cudaMalloc(&p->vs_test, b));
+      DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->vs_test), b));
     }
   }
   ResParams<T> R = res_params<T>(p, slot, D, pp);
@@ -1153,12 +1185,12 @@ int device_loop(fftm_problem* p, int cur0, int* m_out, int* stop_out) {
   cudaStream_t s = p->ctx->stream;
   const int max_iter = p->desc.max_iter;
   if (p->derr_len < max_iter + 1) {
-    if (p->derr) cudaFree(p->derr);
+    if (p->derr) dev_free(p, p->derr);
     p->derr = nullptr;
-    CU(cudaMalloc(&p->derr, (max_iter + 1) * sizeof(double)));
+    DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->derr), (max_iter + 1) * sizeof(double)));
     p->derr_len = max_iter + 1;
   }
-  if (!p->dctl) CU(cudaMalloc(&p->dctl, 4 * sizeof(int)));
+  if (!p->dctl) DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->dctl), 4 * sizeof(int)));
   CU(cudaMemsetAsync(p->dctl, 0, 4 * sizeof(int), s));
   if (p->res_two_pass < 0) {  // the residual's form is measured before anything is enqueued
     int rc = resolve_residual_form<T>(p, cur0 % NSLOT);
@@ -1227,9 +1259,9 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
   const int max_iter = p->desc.max_iter;
   const long long cnt = p->comp_stride;
   if (p->dint_len < max_iter + 1) {
-    if (p->dint) cudaFree(p->dint);
+    if (p->dint) dev_free(p, p->dint);
     p->dint = nullptr;
-    CU(cudaMalloc(&p->dint, (max_iter + 1) * sizeof(int)));
+    DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->dint), (max_iter + 1) * sizeof(int)));
     p->dint_len = max_iter + 1;
   }
   CU(cudaMemsetAsync(p->dint, 0, (max_iter + 1) * sizeof(int), s));
@@ -1340,7 +1372,7 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     p->load_n = p->load;
     if (p->ustar) {  // the u* field at the commit
       const size_t ub = 3 * (size_t)p->comp_stride * sizeof(T);
-      if (!p->ustar_n) CU(cudaMalloc(&p->ustar_n, ub));
+      if (!p->ustar_n) DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->ustar_n), ub));
       CU(cudaMemcpyAsync(p->ustar_n, p->ustar, ub, cudaMemcpyDeviceToDevice, s));
     } else if (p->ustar_n) {
       CU(cudaMemsetAsync(p->ustar_n, 0, 3 * (size_t)p->comp_stride * sizeof(T), s));
@@ -1348,12 +1380,12 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
     for (int a = 0; a < 3; ++a)  // the face traction fields at the commit
       for (int f = 0; f < 2; ++f) {
         if (!p->tface[a][f]) {
-          cudaFree(p->tface_n[a][f]);
+          dev_free(p, p->tface_n[a][f]);
           p->tface_n[a][f] = nullptr;
           continue;
         }
         const size_t nb = (size_t)3 * p->n[a == 0 ? 1 : 0] * p->n[a == 2 ? 1 : 2] * sizeof(T);
-        if (!p->tface_n[a][f]) CU(cudaMalloc(&p->tface_n[a][f], nb));
+        if (!p->tface_n[a][f]) DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->tface_n[a][f]), nb));
         CU(cudaMemcpyAsync(p->tface_n[a][f], p->tface[a][f], nb, cudaMemcpyDeviceToDevice, s));
       }
     p->committed = 1;
@@ -1495,6 +1527,20 @@ struct Sizes {
   size_t fields, tables, lawc, partial;
 };
 
+// what a problem allocates besides its fields and tables, counted for a caller's workspace: the
+// staging buffer of host transfers (the largest field), the device-decided step's history and
+// control block, the one-pass law table, the norm scalars, and the 256-byte alignment of every
+// allocation
+size_t step_extra_bytes(const fftm_problem_desc* d) {
+  const size_t esz = d->precision == FFTM_FP64 ? 8 : 4;
+  const size_t nvox = (size_t)d->n[0] * d->n[1] * d->n[2], npp = d->scheme == FFTM_TETRA2 ? 2 : 1;
+  size_t nodes = 1;
+  for (int a = 0; a < 3; ++a) nodes *= (size_t)(d->bc[a][0][0] == FFTM_BC_PERIODIC ? d->n[a] : d->n[a] + 1);
+  const size_t scratch = std::max(3 * nodes, 10 * npp * nvox) * esz;
+  const size_t hist = (size_t)(d->max_iter + 1) * (sizeof(double) + sizeof(int)) + 4 * sizeof(int);
+  return scratch + hist + (size_t)d->n_phases * 36 * esz + 64 * sizeof(double) + sizeof(int) + 64 * 256;
+}
+
 Sizes sizes_of(const fftm_problem_desc* d) {
   Sizes s;
   const size_t esz = d->precision == FFTM_FP64 ? 8 : 4;
@@ -1533,7 +1579,7 @@ static int set_load_field_t(fftm_problem* p, const void* u, int is_device, size_
     from = p->scratch;
   }
   if (!p->ustar) {
-    CU(cudaMalloc(&p->ustar, 3 * (size_t)p->comp_stride * sizeof(T)));
+    DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->ustar), 3 * (size_t)p->comp_stride * sizeof(T)));
     CU(cudaMemsetAsync(p->ustar, 0, 3 * (size_t)p->comp_stride * sizeof(T), s));
   }
   T* dst[3];
@@ -1586,56 +1632,83 @@ int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
     else if (desc->materials[i].law == FFTM_LAW_LOG_J2)
       stb = 2 * (size_t)(desc->scheme == FFTM_TETRA2 ? 2 : 1) * 7 * nvox * esz;
   const size_t c0b = desc->green == FFTM_GREEN_C0 ? 2 * (size_t)(desc->n[0] + desc->n[1] + desc->n[2] + 3) * esz : 0;
+  size_t tcb = 0;  // tensor-core transform matrices: forward and inverse per component and axis
+  if (desc->precision == FFTM_FP32_TC || desc->precision == FFTM_FP32_TF32)
+    for (int a = 0; a < 3; ++a) {
+      const size_t Kp = (size_t)(desc->n[a] + 4 + 31) / 32 * 32, R = (Kp + 127) / 128 * 128;
+      tcb += 3 * 2 * R * Kp * (desc->precision == FFTM_FP32_TC ? 2 : 4);
+    }
   *bytes = s.fields + s.tables + s.lawc + s.partial + vsb + stb + c0b + nvox * sizeof(uint16_t) +
-           desc->n_phases * sizeof(int);
+           desc->n_phases * sizeof(int) + step_extra_bytes(desc) + tcb;
   return FFTM_OK;
 }
 
 int fftm_problem_destroy(fftm_problem* p) {
   if (!p) return FFTM_OK;
   if (p->ctx) cudaSetDevice(p->ctx->device);
-  cudaFree(p->fields);
-  cudaFree(p->Dbuf);
-  cudaFree(p->tables);
-  cudaFree(p->phase);
-  cudaFree(p->law_id);
-  cudaFree(p->law_c);
-  cudaFree(p->law_m);
-  cudaFree(p->partial);
-  cudaFree(p->dscal);
-  cudaFree(p->dint);
-  cudaFree(p->dctl);
-  cudaFree(p->derr);
-  cudaFree(p->scratch);
-  cudaFree(p->vs);
-  cudaFree(p->vs_test);
-  cudaFree(p->state);
-  cudaFree(p->state_next);
-  cudaFree(p->un);
-  cudaFree(p->Dn);
-  cudaFree(p->tcmat);
-  cudaFree(p->tc_err);
-  cudaFree(p->c0tab);
+  dev_free(p, p->fields);
+  dev_free(p, p->Dbuf);
+  dev_free(p, p->tables);
+  dev_free(p, p->phase);
+  dev_free(p, p->law_id);
+  dev_free(p, p->law_c);
+  dev_free(p, p->law_m);
+  dev_free(p, p->partial);
+  dev_free(p, p->dscal);
+  dev_free(p, p->dint);
+  dev_free(p, p->dctl);
+  dev_free(p, p->derr);
+  dev_free(p, p->scratch);
+  dev_free(p, p->vs);
+  dev_free(p, p->vs_test);
+  dev_free(p, p->state);
+  dev_free(p, p->state_next);
+  dev_free(p, p->un);
+  dev_free(p, p->Dn);
+  dev_free(p, p->tcmat);
+  dev_free(p, p->tc_err);
+  dev_free(p, p->c0tab);
   for (int a = 0; a < 3; ++a)
     for (int f = 0; f < 2; ++f) {
-      cudaFree(p->tface[a][f]);
-      cudaFree(p->tface_n[a][f]);
+      dev_free(p, p->tface[a][f]);
+      dev_free(p, p->tface_n[a][f]);
     }
-  cudaFree(p->ustar);
-  cudaFree(p->ustar_n);
+  dev_free(p, p->ustar);
+  dev_free(p, p->ustar_n);
   if (p->hpin) cudaFreeHost(p->hpin);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   delete p;
   return FFTM_OK;
 }
 
+static int problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, void* workspace, size_t ws_bytes,
+                          fftm_problem** out);
+
 int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_problem** out) {
+  return problem_create(ctx, desc, nullptr, 0, out);
+}
+
+int fftm_problem_create_in(fftm_ctx* ctx, const fftm_problem_desc* desc, void* workspace, size_t bytes,
+                           fftm_problem** out) {
+  if (!workspace) return set_err(FFTM_E_INVALID, "null workspace");
+  if (reinterpret_cast<uintptr_t>(workspace) % 256) return set_err(FFTM_E_INVALID, "workspace must be 256-byte aligned");
+  size_t need = 0;
+  int rc = fftm_problem_workspace_bytes(desc, &need);
+  if (rc) return rc;
+  if (bytes < need) return set_err(FFTM_E_NOMEM, "workspace smaller than fftm_problem_workspace_bytes");
+  return problem_create(ctx, desc, workspace, bytes, out);
+}
+
+static int problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, void* workspace, size_t ws_bytes,
+                          fftm_problem** out) {
   if (!ctx || !out) return set_err(FFTM_E_INVALID, "null ctx or out");
   int rc = validate(desc);
   if (rc) return rc;
   CU(cudaSetDevice(ctx->device));
   std::unique_ptr<fftm_problem> p(new (std::nothrow) fftm_problem);
   if (!p) return set_err(FFTM_E_NOMEM, "host allocation");
+  p->arena = static_cast<char*>(workspace);
+  p->arena_size = workspace ? ws_bytes : 0;
   p->ctx = ctx;
   p->desc = *desc;
   p->mats.assign(desc->materials, desc->materials + desc->n_phases);
@@ -1681,7 +1754,7 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
   }
   // ---- device allocations ----
   const cudaStream_t s = ctx->stream;
-  if (cudaMalloc(&p->fields, sz.fields) != cudaSuccess) {
+  if (dev_alloc(p.get(), reinterpret_cast<void**>(&p->fields), sz.fields) != cudaSuccess) {
     cudaGetLastError();
     return set_err(FFTM_E_NOMEM, "device allocation of the fields failed");
   }
@@ -1700,28 +1773,28 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
   p->nst = has_cp ? 10 : ((has_j2 || has_lj2) ? 7 : 0);
   p->slaw = has_cp ? 2 : (has_j2 ? 1 : (has_lj2 ? 4 : 0));
   p->inc_ok = has_j2 && !finite;
-  CU(cudaMalloc(&p->vs, (size_t)(p->tetra ? 2 : 1) * (p->sym ? 6 : 9) * p->nvox * p->esz));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->vs), (size_t)(p->tetra ? 2 : 1) * (p->sym ? 6 : 9) * p->nvox * p->esz));
   if (p->nst) {
     const size_t sb = (size_t)(p->tetra ? 2 : 1) * p->nst * p->nvox * p->esz;
-    CU(cudaMalloc(&p->state, sb));
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->state), sb));
     CU(cudaMemsetAsync(p->state, 0, sb, s));  // J2: e = 0, p = 0; crystal plasticity: F^p - 1 = 0, Gamma = 0
-    CU(cudaMalloc(&p->state_next, sb));
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->state_next), sb));
     CU(cudaMemsetAsync(p->state_next, 0, sb, s));
   }
   if (p->inc_ok) {
     {
       const size_t ub = (size_t)(p->esz == 4 ? 6 : 3) * p->comp_stride * p->esz;
-      CU(cudaMalloc(&p->un, ub));
+      DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->un), ub));
       CU(cudaMemsetAsync(p->un, 0, ub, s));
-      CU(cudaMalloc(&p->Dn, 3 * p->comp_stride * p->esz));
+      DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->Dn), 3 * p->comp_stride * p->esz));
       CU(cudaMemsetAsync(p->Dn, 0, 3 * p->comp_stride * p->esz, s));
     }
   }
-  CU(cudaMalloc(&p->phase, p->nvox * sizeof(uint16_t)));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->phase), p->nvox * sizeof(uint16_t)));
   CU(cudaMemcpyAsync(p->phase, desc->phase, p->nvox * sizeof(uint16_t), cudaMemcpyHostToDevice, s));
-  CU(cudaMalloc(&p->partial, sz.partial));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->partial), sz.partial));
   p->partial_len = sz.partial / sizeof(double);
-  CU(cudaMalloc(&p->dscal, 64 * sizeof(double)));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->dscal), 64 * sizeof(double)));
   CU(cudaMemsetAsync(p->dscal, 0, 64 * sizeof(double), s));
   CU(cudaMallocHost(&p->hpin, 64 * sizeof(double)));
   // ---- tables: plans and Green half-angle tables ----
@@ -1759,7 +1832,7 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         p->off_C2[q][a] = put(c2f.data(), c2f.size() * 4);
       }
     }
-  CU(cudaMalloc(&p->tables, tab.size()));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->tables), tab.size()));
   CU(cudaMemcpy(p->tables, tab.data(), tab.size(), cudaMemcpyHostToDevice));
   if (desc->precision == FFTM_FP32_TC) {
     p->tc = 1;
@@ -1799,9 +1872,9 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         p->off_tcf[q][a] = put_mat(F, L, Kp, R, col0);
         p->off_tci[q][a] = put_mat(I, L, Kp, R, col0);
       }
-    CU(cudaMalloc(&p->tcmat, mats.size() * sizeof(uint16_t)));
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->tcmat), mats.size() * sizeof(uint16_t)));
     CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-    CU(cudaMalloc(&p->tc_err, sizeof(int)));
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->tc_err), sizeof(int)));
     CU(cudaMemset(p->tc_err, 0, sizeof(int)));
   }
   if (desc->precision == FFTM_FP32_TF32) {
@@ -1838,9 +1911,9 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         p->off_tcf[q][a] = put_mat(F, L, Kp, R, col0);
         p->off_tci[q][a] = put_mat(I, L, Kp, R, col0);
       }
-    CU(cudaMalloc(&p->tcmat, mats.size() * sizeof(float)));
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->tcmat), mats.size() * sizeof(float)));
     CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(float), cudaMemcpyHostToDevice));
-    CU(cudaMalloc(&p->tc_err, sizeof(int)));
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->tc_err), sizeof(int)));
     CU(cudaMemset(p->tc_err, 0, sizeof(int)));
   }
   // ---- law tables ----
@@ -1901,16 +1974,16 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
         f[3] = Cm[2 * rp + 1][2 * bp + 1];
       }
   }
-  CU(cudaMalloc(&p->law_m, lm.size() * p->esz));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->law_m), lm.size() * p->esz));
   if (p->esz == 8) {
     CU(cudaMemcpy(p->law_m, lm.data(), lm.size() * 8, cudaMemcpyHostToDevice));
   } else {
     std::vector<float> lf(lm.begin(), lm.end());
     CU(cudaMemcpy(p->law_m, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
   }
-  CU(cudaMalloc(&p->law_id, lid.size() * sizeof(int)));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->law_id), lid.size() * sizeof(int)));
   CU(cudaMemcpy(p->law_id, lid.data(), lid.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CU(cudaMalloc(&p->law_c, lc.size() * p->esz));
+  DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->law_c), lc.size() * p->esz));
   if (p->esz == 8) {
     CU(cudaMemcpy(p->law_c, lc.data(), lc.size() * 8, cudaMemcpyHostToDevice));
   } else {
@@ -1928,13 +2001,24 @@ int fftm_problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, fftm_probl
       for (int m = 0; m < p->N[a]; ++m) t.push_back(m == 0 ? 0.0 : std::sin(0.5 * kPi * m / n));
       for (int m = 0; m < p->N[a]; ++m) t.push_back(m == n ? 0.0 : std::cos(0.5 * kPi * m / n));
     }
-    CU(cudaMalloc(&p->c0tab, t.size() * p->esz));
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->c0tab), t.size() * p->esz));
     if (p->esz == 8) {
       CU(cudaMemcpy(p->c0tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice));
     } else {
       std::vector<float> tf(t.begin(), t.end());
       CU(cudaMemcpy(p->c0tab, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice));
     }
+  }
+  if (p->arena) {  // everything the solve allocates later comes from the workspace now
+    const size_t nodes3 = (size_t)3 * p->N[0] * p->N[1] * p->N[2];
+    const size_t pts10 = (size_t)10 * (p->tetra ? 2 : 1) * (size_t)p->nvox;
+    int rc2 = ensure_scratch(p.get(), (nodes3 > pts10 ? nodes3 : pts10) * p->esz);
+    if (rc2) return rc2;
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->derr), (desc->max_iter + 1) * sizeof(double)));
+    p->derr_len = desc->max_iter + 1;
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->dint), (desc->max_iter + 1) * sizeof(int)));
+    p->dint_len = desc->max_iter + 1;
+    DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->dctl), 4 * sizeof(int)));
   }
   CU(cudaStreamSynchronize(s));
   *out = p.release();
@@ -2022,7 +2106,7 @@ int fftm_set_load_field(fftm_problem* p, const void* ustar, int is_device, size_
   CU(cudaSetDevice(p->ctx->device));
   if (!ustar) {
     CU(cudaStreamSynchronize(p->ctx->stream));
-    cudaFree(p->ustar);
+    dev_free(p, p->ustar);
     p->ustar = nullptr;
     return FFTM_OK;
   }
@@ -2042,7 +2126,7 @@ int fftm_set_face_traction(fftm_problem* p, int axis, int face, const void* t, i
   const size_t cnt = (size_t)3 * nb * nc, need = cnt * p->esz;
   if (!t) {
     CU(cudaStreamSynchronize(p->ctx->stream));
-    cudaFree(p->tface[axis][face]);
+    dev_free(p, p->tface[axis][face]);
     p->tface[axis][face] = nullptr;
     return FFTM_OK;
   }
@@ -2062,7 +2146,7 @@ int fftm_set_face_traction(fftm_problem* p, int axis, int face, const void* t, i
     }
   }
   CU(cudaStreamSynchronize(p->ctx->stream));
-  if (!p->tface[axis][face]) CU(cudaMalloc(&p->tface[axis][face], need));
+  if (!p->tface[axis][face]) DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->tface[axis][face]), need));
   CU(cudaMemcpy(p->tface[axis][face], h.data(), need, cudaMemcpyHostToDevice));
   return FFTM_OK;
 }
@@ -2164,10 +2248,10 @@ int fftm_problem_layout(const fftm_problem* p, int N[3], int* precision, int* de
 
 static int ensure_scratch(fftm_problem* p, size_t bytes) {
   if (p->scratch_bytes >= bytes) return FFTM_OK;
-  cudaFree(p->scratch);
+  dev_free(p, p->scratch);
   p->scratch = nullptr;
   p->scratch_bytes = 0;
-  if (cudaMalloc(&p->scratch, bytes) != cudaSuccess) {
+  if (dev_alloc(p, reinterpret_cast<void**>(&p->scratch), bytes) != cudaSuccess) {
     cudaGetLastError();
     return set_err(FFTM_E_NOMEM, "scratch allocation failed");
   }

@@ -181,9 +181,10 @@ int pass_tc_rows(int Kp, int axis);
 // unevaluated hi + lo pair when out_lo is set; mode 2 (z axis): the forward result times the
 // B0 / 2 mu0 Green factor -gscale / den (0 where den is null).
 struct TfPassParams {
-  // x axis: each input component as a 2D tensor {row pitch, N2 * N3 rows}, 32 x 128 boxes with
-  // the 128-byte swizzle (filled by launch_pass_tf32)
-  CUtensorMap xmap[3];
+  // TMA descriptors of the input components (filled by launch_pass_tf32): x axis a 2D tensor
+  // {row pitch, N2 * N3 rows} in 32 x 128 boxes with the 128-byte swizzle; y and z axes a 3D
+  // tensor {row pitch, N2, N3} in boxes of 128 x values by 32 rows along the axis
+  CUtensorMap tmap[3];
   const float* in[3];
   float* out[3];
   const float* base[3];

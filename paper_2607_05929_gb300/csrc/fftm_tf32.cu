@@ -60,6 +60,13 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
                "r"(bytes)
@@ -77,19 +84,26 @@ __device__ __forceinline__ void tf_mma(uint32_t tmem, uint64_t da, uint64_t db, 
 // Shared-memory geometry for a padded transform length Kp (a multiple of 32).
 struct TfGeom {
   int mp;            // matrix rows (x: Kp rounded up to 128; y, z: Kp)
-  uint32_t stage;    // bytes of one stage: tile part, then matrix part (mp x 32 FP32)
+  uint32_t stage;    // bytes of one stage: tile part, matrix part (mp x 32 FP32), raw part
   int nst;           // stages
   int acc_cols;      // TMEM columns of one accumulator
+  int raw;           // y, z: the tile arrives by TMA in a raw part (rows of 128 pencils) and is
+                     // transposed from there (when three stages still fit); else per-thread copies
   __host__ __device__ static TfGeom make(int Kp, int axis) {
     TfGeom g;
     g.mp = axis == 0 ? (Kp + 127) / 128 * 128 : Kp;
-    g.stage = (TF_TILE_BYTES + (uint32_t)g.mp * TF_KC * 4 + 1023u) & ~1023u;
-    const long long room = (long long)kMaxDynSmem - 2048;
-    g.nst = (int)(room / g.stage);
-    if (g.nst > TF_MAXST) g.nst = TF_MAXST;
     g.acc_cols = axis == 0 ? g.mp : Kp;
+    const long long room = (long long)kMaxDynSmem - 2048;
+    for (g.raw = axis == 0 ? 0 : 1; g.raw >= 0; --g.raw) {
+      g.stage = (TF_TILE_BYTES * (1u + (uint32_t)g.raw) + (uint32_t)g.mp * TF_KC * 4 + 1023u) & ~1023u;
+      g.nst = (int)(room / g.stage);
+      if (g.nst >= 3) break;
+    }
+    if (g.raw < 0) g.raw = 0;
+    if (g.nst > TF_MAXST) g.nst = TF_MAXST;
     return g;
   }
+  __host__ __device__ uint32_t raw_off() const { return TF_TILE_BYTES + (uint32_t)mp * TF_KC * 4; }
   __host__ __device__ size_t smem() const { return 2048 + (size_t)nst * stage; }
 };
 
@@ -591,10 +605,12 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
     // ---- producers: the tile part of every stage; up to `depth` stages of copies in flight,
     // the oldest processed and handed to the MMA thread as soon as it has landed ----
     const int ptid = tid - TF_EPI;
-    if (AXIS == 0) {
-      // x: one thread issues a TMA box per stage (32 x values of 128 consecutive rows, written in
-      // the 128-byte-swizzled K-major layout); once it has landed every producer rounds its share
-      // of the 16 KB to the nearest TF32 in place
+    if (AXIS == 0 || g.raw) {
+      // one thread issues a TMA box per stage.  x: 32 x values of 128 consecutive rows, written in
+      // the 128-byte-swizzled K-major layout; once it has landed every producer rounds its share of
+      // the 16 KB to the nearest TF32 in place.  y, z: 32 rows along the axis of 128 consecutive
+      // pencils, into the stage's raw part; every producer transposes its 4 x 4 blocks from there
+      // into the K-major tile, rounded
       const int depth = g.nst - 1 < 3 ? g.nst - 1 : 3;
       long long seq = 0, done = 0;
       int ti = 0, c = 0;
@@ -604,12 +620,29 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
         const int s = (int)(k % g.nst);
         if (!bar_wait(&B.land[s], (uint32_t)((k / g.nst) & 1), abort)) return false;
         const uint32_t base = smem_u32(stages + (size_t)s * g.stage);
+        if (AXIS == 0) {
 #pragma unroll
-        for (int j = 0; j < TF_XPC; ++j) {
-          const int i = ptid + j * TF_PROD;
-          if (i >= TF_P * 8) continue;
-          const float4 v = ld_shared4(base + (uint32_t)i * 16u);
-          st_shared4(base + (uint32_t)i * 16u, tf32r(v.x), tf32r(v.y), tf32r(v.z), tf32r(v.w));
+          for (int j = 0; j < TF_XPC; ++j) {
+            const int i = ptid + j * TF_PROD;
+            if (i >= TF_P * 8) continue;
+            const float4 v = ld_shared4(base + (uint32_t)i * 16u);
+            st_shared4(base + (uint32_t)i * 16u, tf32r(v.x), tf32r(v.y), tf32r(v.z), tf32r(v.w));
+          }
+        } else {
+          const uint32_t raw = base + g.raw_off();
+#pragma unroll
+          for (int b = 0; b < TF_BLK; ++b) {
+            const int i = ptid + b * TF_PROD;
+            if (i >= 256) continue;
+            const int pg = i & 31, kq = i >> 5;
+            float4 v[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) v[r] = ld_shared4(raw + (uint32_t)((4 * kq + r) * TF_P + 4 * pg) * 4u);
+            st_shared4(base + tf_cell(4 * pg, kq), tf32r(v[0].x), tf32r(v[1].x), tf32r(v[2].x), tf32r(v[3].x));
+            st_shared4(base + tf_cell(4 * pg + 1, kq), tf32r(v[0].y), tf32r(v[1].y), tf32r(v[2].y), tf32r(v[3].y));
+            st_shared4(base + tf_cell(4 * pg + 2, kq), tf32r(v[0].z), tf32r(v[1].z), tf32r(v[2].z), tf32r(v[3].z));
+            st_shared4(base + tf_cell(4 * pg + 3, kq), tf32r(v[0].w), tf32r(v[1].w), tf32r(v[2].w), tf32r(v[3].w));
+          }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         bar_arrive(&B.full[s]);
@@ -622,8 +655,13 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
         if (ptid == 0) {
           if (u > 0 && !bar_wait(&B.empty[s], (uint32_t)((u - 1) & 1), abort)) break;
           expect_tx(&B.land[s], TF_TILE_BYTES);
-          tma_load_2d(smem_u32(stages + (size_t)s * g.stage), &P.xmap[T.q], (T.lo & ~3) + TF_KC * c, T.row0,
-                      &B.land[s]);
+          const uint32_t dst = smem_u32(stages + (size_t)s * g.stage);
+          if (AXIS == 0)
+            tma_load_2d(dst, &P.tmap[T.q], (T.lo & ~3) + TF_KC * c, T.row0, &B.land[s]);
+          else if (AXIS == 1)
+            tma_load_3d(dst + g.raw_off(), &P.tmap[T.q], T.x0, T.lo + TF_KC * c, T.other, &B.land[s]);
+          else
+            tma_load_3d(dst + g.raw_off(), &P.tmap[T.q], T.x0, T.other, T.lo + TF_KC * c, &B.land[s]);
         }
         ++seq;
         if (++c == T.Kp / TF_KC) {
@@ -727,17 +765,30 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 // x axis: component q's input as {row pitch (x), N2 * N3 rows}, boxes of 32 x 128 with the
 // 128-byte swizzle; coordinates past the extents read zeros
-static cudaError_t encode_x_maps(TfPassParams& P) {
+// y, z axes: component q's input as {row pitch, N2, N3}, boxes of 128 x values by 32 rows along
+// the pass axis, no swizzle (the rows land one after the other in the stage's raw part)
+static cudaError_t encode_maps(TfPassParams& P) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   for (int q = 0; q < 3; ++q) {
-    const cuuint64_t dims[2] = {(cuuint64_t)P.stride[1], (cuuint64_t)P.N[1] * (cuuint64_t)P.N[2]};
-    const cuuint64_t strides[1] = {(cuuint64_t)P.stride[1] * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)TF_KC, (cuuint32_t)TF_P};
-    const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = enc(&P.xmap[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P.in[q]), dims, strides,
-                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r;
+    if (P.axis == 0) {
+      const cuuint64_t dims[2] = {(cuuint64_t)P.stride[1], (cuuint64_t)P.N[1] * (cuuint64_t)P.N[2]};
+      const cuuint64_t strides[1] = {(cuuint64_t)P.stride[1] * sizeof(float)};
+      const cuuint32_t box[2] = {(cuuint32_t)TF_KC, (cuuint32_t)TF_P};
+      const cuuint32_t estr[2] = {1, 1};
+      r = enc(&P.tmap[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(P.in[q]), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      const cuuint64_t dims[3] = {(cuuint64_t)P.stride[1], (cuuint64_t)P.N[1], (cuuint64_t)P.N[2]};
+      const cuuint64_t strides[2] = {(cuuint64_t)P.stride[1] * sizeof(float), (cuuint64_t)P.stride[2] * sizeof(float)};
+      const cuuint32_t box[3] = {(cuuint32_t)TF_P, P.axis == 1 ? (cuuint32_t)TF_KC : 1u, P.axis == 2 ? (cuuint32_t)TF_KC : 1u};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      r = enc(&P.tmap[q], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(P.in[q]), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
   return cudaSuccess;
@@ -745,8 +796,8 @@ static cudaError_t encode_x_maps(TfPassParams& P) {
 
 cudaError_t launch_pass_tf32(const TfPassParams& P0, cudaStream_t s) {
   TfPassParams P = P0;
-  if (P.axis == 0) {
-    const cudaError_t e = encode_x_maps(P);
+  {
+    const cudaError_t e = encode_maps(P);
     if (e != cudaSuccess) return e;
   }
   int maxKp = 0;

@@ -38,7 +38,7 @@ FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP
 # every symbol include/fftm.h declares
 EXPORTS = [
     "fftm_last_error", "fftm_version", "fftm_ctx_create", "fftm_ctx_destroy",
-    "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_destroy",
+    "fftm_problem_workspace_bytes", "fftm_problem_create", "fftm_problem_create_in", "fftm_problem_destroy",
     "fftm_set_phase", "fftm_set_load", "fftm_set_face_traction", "fftm_set_load_field", "fftm_get_load", "fftm_solve_step", "fftm_field_bytes",
     "fftm_get_field", "fftm_set_field", "fftm_problem_layout", "fftm_set_option", "fftm_tuning_table", "fftm_device_fma_rate", "fftm_apply", "fftm_kernel_launches",
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
@@ -117,6 +117,7 @@ def load_library(path=LIB_PATH):
         "fftm_ctx_destroy": ([vp], ctypes.c_int),
         "fftm_problem_workspace_bytes": ([P(fftm_problem_desc), P(ctypes.c_size_t)], ctypes.c_int),
         "fftm_problem_create": ([vp, P(fftm_problem_desc), P(vp)], ctypes.c_int),
+        "fftm_problem_create_in": ([vp, P(fftm_problem_desc), vp, ctypes.c_size_t, P(vp)], ctypes.c_int),
         "fftm_problem_destroy": ([vp], ctypes.c_int),
         "fftm_set_phase": ([vp, P(ctypes.c_uint16)], ctypes.c_int),
         "fftm_set_load": ([vp, P(fftm_load)], ctypes.c_int),
@@ -232,6 +233,17 @@ def fftm_problem_workspace_bytes(desc):
     b = ctypes.c_size_t()
     _check(load_library().fftm_problem_workspace_bytes(ctypes.byref(desc), ctypes.byref(b)))
     return b.value
+
+
+def fftm_problem_create_in(ctx, desc, workspace):
+    """fftm_problem_create inside a caller's device buffer (a contiguous CUDA tensor; keep it alive
+    until fftm_problem_destroy)."""
+    ptr, dev, nb = _ptr_of(workspace)
+    if not dev:
+        raise ValueError("the workspace must be device memory")
+    p = ctypes.c_void_p()
+    _check(load_library().fftm_problem_create_in(ctx, ctypes.byref(desc), ctypes.c_void_p(ptr), nb, ctypes.byref(p)))
+    return p
 
 
 def fftm_problem_create(ctx, desc):
