@@ -65,11 +65,11 @@ enum fftm_bc { FFTM_BC_PERIODIC = 0, FFTM_BC_DIRICHLET = 1, FFTM_BC_NEUMANN = 2 
 enum fftm_scheme { FFTM_HEX1 = 0, FFTM_TETRA2 = 1 };
 /* FFTM_GREEN_C0: the reference stiffness C0 : grad u = 2 mu0 grad u + lambda0 tr(grad u) 1
    (Sec. 2.6.1, Eq. TF_C0_behavior), whose discrete Green operator couples the three
-   components at each frequency (Eq. FourierSGO_HEX1).  Valid for normal-mixed BCs (Eq.
-   SGO_BCs); this library builds it for HEX1 with every axis non-periodic, the same symmetry
-   on both faces of an axis per component, and on each axis the normal component's symmetry
-   opposite to the tangential ones' (normal Dirichlet and tangential Neumann, or the converse);
-   FFTM_E_UNSUPPORTED otherwise. */
+   components at each frequency (Eq. FourierSGO_HEX1; TETRA2: Eqs. FourierSGO_TETRA2_1/2, a
+   2 x 2 system per frequency).  Valid for normal-mixed BCs (Eq. SGO_BCs); this library builds
+   it with every axis non-periodic, the same symmetry on both faces of an axis per component,
+   and on each axis the normal component's symmetry opposite to the tangential ones' (normal
+   Dirichlet and tangential Neumann, or the converse); FFTM_E_UNSUPPORTED otherwise. */
 enum fftm_green { FFTM_GREEN_B0 = 0, FFTM_GREEN_MU0 = 1, FFTM_GREEN_C0 = 2 };
 /* FFTM_FP32_TC: FP32 fields and residual (as FFTM_FP32), per-axis transforms
    as dense matrix contractions on the tensor cores (tcgen05) with BF16 operands

@@ -75,14 +75,26 @@ def operator_symbol(grid, q, scheme, lambda0, mu0):
 # node position, so the symbol on the real coefficients is -(2 mu0 |xi_H|^2 I + lambda0 v (x) v)
 # with v_q = tau_q (xi_H)_q, tau_q = -1 when u_q is symmetric about the faces normal to q
 # (DCT-I along q) and +1 when it is anti-symmetric (DST-I).  The real-space operator pins this
-# (tests/test_oracle_c0.py).  Supported here: HEX1; every axis non-periodic with the same
-# symmetries on both faces (no quarter-wave kinds); on each axis the normal component's symmetry
-# opposite to the tangential ones'.
+# (tests/test_oracle_c0.py).
+#
+# TETRA2 (Eqs. p_u_tetra2, FourierSGO_TETRA2_1/2): with xi_T2 = xi_H + i xi' (Eq. freq_TETRA2) the
+# symbol is -(2 mu0 |xi_T2|^2 I + lambda0/2 [xi_T2 (x) conj(xi_T2) + conj(xi_T2) (x) xi_T2]), on the
+# real coefficients -(2 mu0 |z|^2 I + lambda0/2 [z (x) conj(z) + conj(z) (x) z]) with z = v + i w,
+# w_q = tau_q xi'_q (the same signs; the real-space operator pins it).  Its inverse follows the
+# paper's steps: the dot products of p with z and conj(z), the 2 x 2 system for u . z and
+# u . conj(z) obtained by dotting the operator with z and conj(z), then back-substitution.  Reading
+# (R27): the diagonal coefficient of that system is taken from the operator itself,
+# 2 mu0 + lambda0 / 2 = (4 mu0 + lambda0) / 2 times |z|^2 -- the printed (2 mu0 + lambda0) / 2 would
+# not reduce to Eq. FourierSGO_HEX1 when xi' = 0, while this one does.
+#
+# Supported here: every axis non-periodic with the same symmetries on both faces (no
+# quarter-wave kinds); on each axis the normal component's symmetry opposite to the tangential
+# ones'.
 
 def c0_unsupported(grid, scheme):
     """None if the C0 operator below applies to this grid, else the reason."""
-    if scheme != "HEX1":
-        return "the C0 operator is built for HEX1 only"
+    if scheme not in ("HEX1", "TETRA2"):
+        return "unknown scheme"
     for a in range(3):
         for q in range(3):
             k = grid.kind[q][a]
@@ -95,8 +107,9 @@ def c0_unsupported(grid, scheme):
     return None
 
 
-def c0_vectors(grid):
-    """(v[3], |xi_H|^2) on the node positions m (xi_a = pi m_a / n_a for DCT-I and DST-I alike)."""
+def c0_vectors(grid, scheme="HEX1"):
+    """(v[3], w[3], |xi|^2) on the node positions m (xi_a = pi m_a / n_a for DCT-I and DST-I
+    alike); w = 0 for HEX1, |xi|^2 = |xi_H|^2 + |xi'|^2 for TETRA2."""
     s, c = [], []
     for a in range(3):
         sa, ca = half_angles("DCT1", grid.n[a])  # positions 0..n, exact zeros at both ends
@@ -104,30 +117,53 @@ def c0_vectors(grid):
         shape[a] = sa.size
         s.append(sa.reshape(shape))
         c.append(ca.reshape(shape))
-    xi = []
+    xi, xp = [], []
     for a in range(3):
         b, d = [x for x in range(3) if x != a]
         xi.append((2.0 / grid.h[a]) * s[a] * c[b] * c[d])
-    shape = np.broadcast_shapes(*[x.shape for x in xi])
+        xp.append((2.0 / grid.h[a]) * c[a] * s[b] * s[d] if scheme == "TETRA2" else 0.0 * s[a])
+    shape = np.broadcast_shapes(*[x.shape for x in xi + xp])
     xi = [np.broadcast_to(x, shape) for x in xi]
-    xx = xi[0] ** 2 + xi[1] ** 2 + xi[2] ** 2
+    xp = [np.broadcast_to(x, shape) for x in xp]
+    xx = sum(xi[q] ** 2 + xp[q] ** 2 for q in range(3))
     tau = [-1.0 if grid.kind[q][q] == "DCT1" else 1.0 for q in range(3)]
-    return [tau[q] * xi[q] for q in range(3)], xx
+    return [tau[q] * xi[q] for q in range(3)], [tau[q] * xp[q] for q in range(3)], xx
 
 
-def c0_symbol_apply(grid, lambda0, mu0, uhat):
-    """p_hat = -(2 mu0 |xi|^2 u_hat + lambda0 (v . u_hat) v) on node positions (3 arrays)."""
-    v, xx = c0_vectors(grid)
+def c0_symbol_apply(grid, lambda0, mu0, uhat, scheme="HEX1"):
+    """p_hat = -(2 mu0 |xi|^2 u_hat + lambda0 [(v . u_hat) v + (w . u_hat) w]) on node positions."""
+    v, w, xx = c0_vectors(grid, scheme)
     vu = sum(v[q] * uhat[q] for q in range(3))
-    return [-(2.0 * mu0 * xx * uhat[q] + lambda0 * vu * v[q]) for q in range(3)]
+    wu = sum(w[q] * uhat[q] for q in range(3))
+    return [-(2.0 * mu0 * xx * uhat[q] + lambda0 * (vu * v[q] + wu * w[q])) for q in range(3)]
 
 
-def c0_green_apply(grid, lambda0, mu0, phat):
-    """Eq. FourierSGO_HEX1 on the real coefficients: u_hat = -(p_hat - lambda0 / (2 mu0 + lambda0)
-    (v . p_hat) v / |xi|^2) / (2 mu0 |xi|^2), zero where |xi|^2 = 0 (the null rule of Sec. 2.6)."""
-    v, xx = c0_vectors(grid)
-    vp = sum(v[q] * phat[q] for q in range(3))
+def c0_green_apply(grid, lambda0, mu0, phat, scheme="HEX1"):
+    """The C0 discrete Green operator on the real coefficients, zero where |xi|^2 = 0 (the null
+    rule of Sec. 2.6).  HEX1, Eq. FourierSGO_HEX1: u_hat = -(p_hat - lambda0 / (2 mu0 + lambda0)
+    (v . p_hat) v / |xi|^2) / (2 mu0 |xi|^2).  TETRA2, Eqs. FourierSGO_TETRA2_1/2 with z = v + i w
+    and the reading R27 above."""
+    v, w, xx = c0_vectors(grid, scheme)
     nz = xx > 0.0
     safe = np.where(nz, xx, 1.0)
-    beta = lambda0 / (2.0 * mu0 + lambda0)
-    return [np.where(nz, -(phat[q] - beta * vp * v[q] / safe) / (2.0 * mu0 * safe), 0.0) for q in range(3)]
+    if scheme == "HEX1":
+        vp = sum(v[q] * phat[q] for q in range(3))
+        beta = lambda0 / (2.0 * mu0 + lambda0)
+        return [np.where(nz, -(phat[q] - beta * vp * v[q] / safe) / (2.0 * mu0 * safe), 0.0) for q in range(3)]
+    z = [v[q] + 1j * w[q] for q in range(3)]
+    zc = [np.conj(zq) for zq in z]
+    pz = sum(phat[q] * z[q] for q in range(3))      # p . z
+    pzc = sum(phat[q] * zc[q] for q in range(3))    # p . conj(z)
+    zz = sum(zq * zq for zq in z)                   # z . z
+    zzc = np.conj(zz)                               # conj(z) . conj(z)
+    d = (2.0 * mu0 + 0.5 * lambda0) * safe          # the diagonal coefficient (R27) times |z|^2
+    Ds = d * d - (0.5 * lambda0) ** 2 * np.abs(zz) ** 2
+    Ds = np.where(nz, Ds, 1.0)
+    # u . z and u . conj(z) from  -p.z = d (u.z) + lambda0/2 (z.z) (u.conj z)  and its conjugate pair
+    p_int1 = (-d * pz + 0.5 * lambda0 * zz * pzc) / Ds   # = u . z
+    p_int2 = (0.5 * lambda0 * zzc * pz - d * pzc) / Ds   # = u . conj(z)
+    out = []
+    for q in range(3):
+        uq = -(phat[q] + 0.5 * lambda0 * (p_int2 * z[q] + p_int1 * zc[q])) / (2.0 * mu0 * safe)
+        out.append(np.where(nz, np.real(uq), 0.0))
+    return out

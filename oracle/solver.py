@@ -135,7 +135,7 @@ class Problem:
                 full = np.zeros(g.N)
                 full[g.dof_slices(q)] = dt3d_forward(q_field[q], g.kind[q], g.n, fast=self.fast)
                 ph.append(full)
-            uh = c0_green_apply(g, self.lambda0, self.mu0, ph)
+            uh = c0_green_apply(g, self.lambda0, self.mu0, ph, self.scheme)
             for q in range(3):
                 out[q] = dt3d_inverse(uh[q][g.dof_slices(q)], g.kind[q], g.n, g.N, fast=self.fast)
             return out

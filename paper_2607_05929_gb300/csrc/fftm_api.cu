@@ -884,6 +884,8 @@ C0Params<T> c0_params(fftm_problem* p, bool normalised_inverse, bool negate) {
   G.sz = p->sz;
   G.two_mu0 = T(2.0 * p->desc.mu0);
   G.beta = T(p->desc.lambda0 / (2.0 * p->desc.mu0 + p->desc.lambda0));
+  G.lam0 = T(p->desc.lambda0);
+  G.tetra = p->tetra;
   G.stop = p->stop;
   return G;
 }
@@ -1484,7 +1486,6 @@ int validate(const fftm_problem_desc* d) {
   if (d->green != FFTM_GREEN_B0 && d->green != FFTM_GREEN_MU0 && d->green != FFTM_GREEN_C0)
     return set_err(FFTM_E_INVALID, "bad green");
   if (d->green == FFTM_GREEN_C0) {  // Sec. 2.6.1: normal-mixed BCs (Eq. SGO_BCs), as built here
-    if (d->scheme != FFTM_HEX1) return set_err(FFTM_E_UNSUPPORTED, "the C0 Green operator is built for HEX1 only");
     for (int a = 0; a < 3; ++a)
       for (int q = 0; q < 3; ++q) {
         const int b0 = d->bc[a][0][q], b1 = d->bc[a][1][q];

@@ -238,6 +238,8 @@ struct C0Params {
   T hf[3];                  // 2 / h_a
   T tau[3];                 // -1: u_q symmetric about the faces normal to q (DCT-I), +1: anti-symmetric
   T two_mu0, beta;          // beta = lambda0 / (2 mu0 + lambda0)
+  T lam0;
+  int tetra;                // TETRA2: the second coupling vector w (w_q = tau_q xi'_q)
   T gscale[3];              // normalisation of the transforms (and the sign of the update)
   const int* stop;
 };

@@ -1,5 +1,5 @@
-"""The C0 discrete Green operator (Sec. 2.6.1, Eq. FourierSGO_HEX1) on the GPU against the
-oracle, through the C ABI, for normal-mixed BCs (Eq. SGO_BCs) with HEX1:
+"""The C0 discrete Green operator (Sec. 2.6.1, Eqs. FourierSGO_HEX1, FourierSGO_TETRA2_1/2) on
+the GPU against the oracle, through the C ABI, for normal-mixed BCs (Eq. SGO_BCs), both schemes:
 
 * the coupled operator on random coefficients (FFTM_OP_GREEN) equals green.c0_green_apply;
 * the whole Green update (forward transforms, operator, inverse transforms) equals the
@@ -39,7 +39,7 @@ def _bc(choice):
     return [[[choice[a] if q == a else other[choice[a]] for q in range(3)] for _ in range(2)] for a in range(3)]
 
 
-def _wl(choice, n=(16, 12, 8), tol=1e-8):
+def _wl(choice, n=(16, 12, 8), tol=1e-8, scheme="HEX1"):
     ph = syn.random_spheres(n, 0.2, 1.5, 2.5, 11)
     E, nu = 1.0, 0.3
     lam, mu = E * nu / ((1 + nu) * (1 - 2 * nu)), E / (2 * (1 + nu))
@@ -49,14 +49,15 @@ def _wl(choice, n=(16, 12, 8), tol=1e-8):
     if choice[0] == "N":  # x faces: normal Neumann, so load through a tangential component
         A[0, 0] = 0.0
         A[1, 0] = 1e-3
-    return Workload("c0_spheres", n, ph, mats, _bc(choice), scheme="HEX1", green="C0", lambda0=3 * lam,
+    return Workload("c0_spheres", n, ph, mats, _bc(choice), scheme=scheme, green="C0", lambda0=3 * lam,
                     mu0=3 * mu, tol=tol, A=A, max_iter=2000)
 
 
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("choice", CHOICES)
-def test_green_operator_matches_the_oracle(precision, choice):
-    wl = _wl(choice)
+def test_green_operator_matches_the_oracle(precision, choice, scheme):
+    wl = _wl(choice, scheme=scheme)
     g = Grid(wl.n, wl.bc, wl.h)
     gp = GpuProblem(wl, precision)
     try:
@@ -66,7 +67,7 @@ def test_green_operator_matches_the_oracle(precision, choice):
         gp.set_node(F.FFTM_FIELD_WORK, x)
         F.fftm_apply(gp.p, F.FFTM_OP_GREEN)
         got = gp.get_node(F.FFTM_FIELD_WORK)
-        ref = c0_green_apply(g, wl.lambda0, wl.mu0, [x[q] for q in range(3)])
+        ref = c0_green_apply(g, wl.lambda0, wl.mu0, [x[q] for q in range(3)], scheme)
         for q in range(3):
             ref[q][~g.dof_mask(q)] = 0.0
         assert rel_l2(got, np.stack(ref)) < (1e-12 if precision == "fp64" else 1e-6)
@@ -74,10 +75,11 @@ def test_green_operator_matches_the_oracle(precision, choice):
         gp.close()
 
 
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tf32"])
 @pytest.mark.parametrize("choice", CHOICES)
-def test_green_update_matches_the_oracle(precision, choice):
-    wl = _wl(choice)
+def test_green_update_matches_the_oracle(precision, choice, scheme):
+    wl = _wl(choice, scheme=scheme)
     pr = Problem(wl)
     gp = GpuProblem(wl, precision)
     try:
@@ -95,9 +97,10 @@ def test_green_update_matches_the_oracle(precision, choice):
         gp.close()
 
 
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_residual_polarisation_matches_the_oracle(precision):
-    wl = _wl(("D", "N", "N"))
+def test_residual_polarisation_matches_the_oracle(precision, scheme):
+    wl = _wl(("D", "N", "N"), scheme=scheme)
     pr = Problem(wl)
     gp = GpuProblem(wl, precision)
     try:
@@ -113,10 +116,11 @@ def test_residual_polarisation_matches_the_oracle(precision):
         gp.close()
 
 
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_tf32"])
 @pytest.mark.parametrize("choice", CHOICES)
-def test_solve_step_matches_the_oracle(precision, choice):
-    wl = _wl(choice, tol=1e-8 if precision == "fp64" else 1e-6)
+def test_solve_step_matches_the_oracle(precision, choice, scheme):
+    wl = _wl(choice, tol=1e-8 if precision == "fp64" else 1e-6, scheme=scheme)
     pr = Problem(wl)
     _, rep = pr.solve_step()
     assert rep.converged

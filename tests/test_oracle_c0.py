@@ -2,7 +2,8 @@
 FourierSGO_HEX1), pinned by its real-space definition.
 
 * For every normal-mixed BC combination of Eq. SGO_BCs on non-periodic axes (per axis: normal
-  component Dirichlet and tangential ones Neumann, or the converse), HEX1, anisotropic voxels:
+  component Dirichlet and tangential ones Neumann, or the converse), HEX1 and TETRA2,
+  anisotropic voxels:
   the DCT/DST coefficients of div(C0 : grad u) computed in real space with the ghost rules
   (stencils.div) equal the symbol -(2 mu0 |xi|^2 u + lambda0 (v . u) v) on the coefficients of
   u, for random u.  A sign slip in v (one component's tau flipped) must break the identity.
@@ -10,7 +11,8 @@ FourierSGO_HEX1), pinned by its real-space definition.
 * A fixed point preconditioned with C0 converges to the solution the B0-preconditioned one
   reaches (a different preconditioner, the same discrete problem), in fewer iterations on a
   nearly incompressible-free isotropic composite.
-* Unsupported cases are refused: TETRA2, a periodic axis, BCs that are not normal-mixed.
+* Both schemes (TETRA2: Eqs. FourierSGO_TETRA2_1/2, a 2 x 2 system per frequency).
+* Unsupported cases are refused: a periodic axis, BCs that are not normal-mixed.
 """
 
 import itertools
@@ -55,37 +57,41 @@ def _random_u(g, seed):
     return u
 
 
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
 @pytest.mark.parametrize("choice", list(itertools.product("DN", repeat=3)))
-def test_real_space_operator_equals_the_symbol(choice):
+def test_real_space_operator_equals_the_symbol(choice, scheme):
     g = Grid((6, 5, 4), _bc(choice), h=(1.0, 0.8, 1.3))
-    assert c0_unsupported(g, "HEX1") is None
+    assert c0_unsupported(g, scheme) is None
     u = _random_u(g, 3)
-    p = div(c0_apply(grad(u, g, "HEX1"), LAM0, MU0), g, "HEX1")
+    p = div(c0_apply(grad(u, g, scheme), LAM0, MU0), g, scheme)
     for q in range(3):
         p[q][~g.dof_mask(q)] = 0.0
     ph = _coeffs(p, g)
     uh = _coeffs(u, g)
-    sym = c0_symbol_apply(g, LAM0, MU0, uh)
+    sym = c0_symbol_apply(g, LAM0, MU0, uh, scheme)
     for q in range(3):
         m = np.zeros(g.N, dtype=bool)
         m[g.dof_slices(q)] = True
         ref = np.abs(ph[q][m]).max()
         assert np.abs(sym[q][m] - ph[q][m]).max() <= 1e-12 * ref, (choice, q)
-    # a planted sign slip in v: the identity must fail
-    v, xx = c0_vectors(g)
+    # a planted sign slip in v (and in w for TETRA2): the identity must fail
+    v, w, xx = c0_vectors(g, scheme)
     v[0] = -v[0]
+    w[1] = -w[1]
     vu = sum(v[q] * uh[q] for q in range(3))
-    bad = [-(2.0 * MU0 * xx * uh[q] + LAM0 * vu * v[q]) for q in range(3)]
+    wu = sum(w[q] * uh[q] for q in range(3))
+    bad = [-(2.0 * MU0 * xx * uh[q] + LAM0 * (vu * v[q] + wu * w[q])) for q in range(3)]
     worst = max(np.abs(bad[q] - ph[q]).max() / np.abs(ph[q]).max() for q in range(3))
     assert worst > 1e-3
 
 
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
 @pytest.mark.parametrize("choice", [("D", "N", "D"), ("N", "D", "N")])
-def test_green_inverts_the_symbol(choice):
+def test_green_inverts_the_symbol(choice, scheme):
     g = Grid((6, 5, 4), _bc(choice), h=(1.0, 0.8, 1.3))
     uh = _coeffs(_random_u(g, 5), g)
-    back = c0_green_apply(g, LAM0, MU0, c0_symbol_apply(g, LAM0, MU0, uh))
-    v, xx = c0_vectors(g)
+    back = c0_green_apply(g, LAM0, MU0, c0_symbol_apply(g, LAM0, MU0, uh, scheme), scheme)
+    v, w, xx = c0_vectors(g, scheme)
     for q in range(3):
         m = np.zeros(g.N, dtype=bool)
         m[g.dof_slices(q)] = True
@@ -93,7 +99,8 @@ def test_green_inverts_the_symbol(choice):
         assert np.abs(back[q][m] - uh[q][m]).max() <= 1e-12 * np.abs(uh[q][m]).max()
 
 
-def test_c0_and_b0_fixed_points_agree():
+@pytest.mark.parametrize("scheme", ["HEX1", "TETRA2"])
+def test_c0_and_b0_fixed_points_agree(scheme):
     import synthetic as syn
     from synthetic.workloads import ISO_ELASTIC, Material, Workload
 
@@ -106,7 +113,7 @@ def test_c0_and_b0_fixed_points_agree():
     A[0, 0] = 1e-3
     out = {}
     for green in ("B0", "C0"):
-        wl = Workload("c0_vs_b0", n, ph, mats, _bc(("D", "N", "N")), scheme="HEX1", green=green,
+        wl = Workload("c0_vs_b0", n, ph, mats, _bc(("D", "N", "N")), scheme=scheme, green=green,
                       lambda0=3 * lam, mu0=3 * mu, tol=1e-11, A=A, max_iter=2000)
         pr = Problem(wl)
         _, rep = pr.solve_step()
@@ -119,8 +126,6 @@ def test_c0_and_b0_fixed_points_agree():
 
 
 def test_unsupported_cases_are_refused():
-    g = Grid((6, 5, 4), _bc(("D", "N", "D")))
-    assert c0_unsupported(g, "TETRA2") is not None
     bc = _bc(("D", "N", "D"))
     bc[2] = [["P"] * 3, ["P"] * 3]
     assert c0_unsupported(Grid((6, 5, 4), bc), "HEX1") is not None
