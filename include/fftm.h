@@ -280,20 +280,24 @@ int fftm_solve_step(fftm_problem* p, fftm_step_report* report, double* err_histo
 
 /* ---- fields ----------------------------------------------------------- */
 enum fftm_field {
-  FFTM_FIELD_U = 0,      /* u^f, node field (3 comps)                           */
+  FFTM_FIELD_U = 0,      /* u^f, node field (3 comps; FP32: the high part)       */
   FFTM_FIELD_WORK = 1,   /* the p / spectral work field, node layout (3 comps)   */
   FFTM_FIELD_GRAD = 2,   /* total gradient G at voxel points (9 comps)           */
   FFTM_FIELD_STRESS = 3, /* stress at voxel points (6 comps, or 9 for problems
                             with non-symmetric stresses, see the layout above)  */
   FFTM_FIELD_D = 4,      /* residual D = div P at the nodes (3 comps), dismissed
                             node components 0; written by FFTM_OP_RESIDUAL       */
-  FFTM_FIELD_STATE = 5   /* committed internal variables at voxel points: J2
+  FFTM_FIELD_STATE = 5,  /* committed internal variables at voxel points: J2
                             problems 7 comps (eps^p 11, 22, 33, 23, 13, 12 and
                             the cumulated plastic strain p), crystal plasticity
                             10 comps (F^p row-major, cumulated slip Gamma),
                             logarithmic J2 7 comps (H^p 11, 22, 33, 23, 13, 12
                             and p); zero in voxels of other laws; FFTM_E_INVALID for
                             problems without such a phase                    */
+  FFTM_FIELD_U_LO = 6    /* FP32 problems carry u^f as an unevaluated sum hi + lo of
+                            two floats: FFTM_FIELD_U reads and writes the high part,
+                            this the low part (read only; FFTM_FIELD_U's write sets
+                            it to zero); zeros for FP64 problems; node layout      */
 };
 
 /* Bytes of a field (dense layout above, problem precision). */

@@ -2172,6 +2172,7 @@ int fftm_field_bytes(const fftm_problem* p, int field, size_t* bytes) {
   const size_t npp = p->tetra ? 2 : 1;
   switch (field) {
     case FFTM_FIELD_U:
+    case FFTM_FIELD_U_LO:
     case FFTM_FIELD_WORK:
     case FFTM_FIELD_D: *bytes = 3 * nodes * p->esz; return FFTM_OK;
     case FFTM_FIELD_GRAD: *bytes = 9 * npp * p->nvox * p->esz; return FFTM_OK;
@@ -2278,10 +2279,14 @@ static int get_field_t(fftm_problem* p, int field, void* dst, int dst_is_device,
     CU(cudaStreamSynchronize(s));
     return FFTM_OK;
   }
-  if (field == FFTM_FIELD_U || field == FFTM_FIELD_WORK || field == FFTM_FIELD_D) {
+  if (field == FFTM_FIELD_U_LO && p->esz == 8) {  // FP64: no low part
+    CU(cudaMemsetAsync(target, 0, bytes, s));
+  } else if (field == FFTM_FIELD_U || field == FFTM_FIELD_U_LO || field == FFTM_FIELD_WORK || field == FFTM_FIELD_D) {
     const T* src[3];
     for (int q = 0; q < 3; ++q) {
-      if (field == FFTM_FIELD_D) {
+      if (field == FFTM_FIELD_U_LO) {
+        src[q] = field_ptr<T>(p, SET_UL + p->cur, q);
+      } else if (field == FFTM_FIELD_D) {
         if (!p->Dbuf) return set_err(FFTM_E_INVALID, "D is written by FFTM_OP_RESIDUAL first");
         src[q] = reinterpret_cast<const T*>(p->Dbuf) + q * p->comp_stride;
       } else {

@@ -32,6 +32,7 @@ FFTM_FP64, FFTM_FP32, FFTM_FP32_TC, FFTM_FP32_TF32 = 0, 1, 2, 3
 FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_LINEAR = 0, 1, 2, 3
 FFTM_LAW_SVK_CUBIC, FFTM_LAW_NEO_HOOKE, FFTM_LAW_CP_FCC, FFTM_LAW_LOG_J2 = 4, 5, 6, 7
 FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D, FFTM_FIELD_STATE = 0, 1, 2, 3, 4, 5
+FFTM_FIELD_U_LO = 6
 FFTM_OPT_RESIDUAL_PASSES, FFTM_OPT_RESIDUAL_TILE, FFTM_OPT_DEVICE_LOOP, FFTM_OPT_CUDA_GRAPH = 0, 1, 2, 3
 FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP_GREEN_UPDATE = 0, 1, 2, 3, 4
 
