@@ -782,9 +782,10 @@ struct FaceIdx {
   int org[3][3];  // origin along each axis in segment a
   __device__ __forceinline__ bool at(int t, int n_face[3], int* m) const {
     for (int a = 0; a < 3; ++a) {
-      if (t < seg[a]) {
-        const int side = t & 1;
-        int r = t >> 1;
+      if (t < seg[a]) {  // side 0's nodes, then side 1's (a warp stays on one face)
+        const int half = seg[a] >> 1;
+        const int side = t >= half;
+        int r = side ? t - half : t;
         for (int b = 0; b < 3; ++b) {
           if (b == a) {
             m[b] = side ? n_face[a] : 0;
@@ -1014,7 +1015,8 @@ __global__ void __launch_bounds__(RTX * RTY) k_stress_inc(ResParams<T> P, TileId
 
 // General divergence at node (mx, my, mz), with the ghost rules on face nodes.
 template <typename T, int TETRA, bool WITH_P, bool SYM>
-__device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, int my, int mz, T Dq[3], T pq[3]) {
+__device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, int my, int mz, T Dq[3], T pq[3],
+                                                 int qmask = 7) {
   constexpr int NC = SYM ? 6 : 9;
   constexpr int NCT = WITH_P ? NC + 9 : NC;
   const int n1 = P.n[0], n2 = P.n[1], n3 = P.n[2];
@@ -1057,6 +1059,7 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
   };
   for (int i = 0; i < 3; ++i) {
     for (int q = 0; q < 3; ++q) {
+      if (!((qmask >> q) & 1)) continue;  // a component without a dof at this node stays zero
       const int c = SYM ? sym_index(i, q) : i * 3 + q;
       T s = T(0), st = T(0);
       // imposed stress of a traction on the face normal to i that this node lies on: every
@@ -1071,6 +1074,7 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
       const T* tfc = side >= 0 ? P.tface[i][side] : nullptr;
       const T* tfn = side >= 0 ? P.tface_n[i][side] : nullptr;
       const T ps_u = side >= 0 ? T(2) * P.tr[i][side][q] : T(0);
+#pragma unroll
       for (int o = 0; o < 8; ++o) {
         if ((o >> i) & 1) continue;
         const int o1 = o | (1 << i);
@@ -1234,11 +1238,12 @@ static void interior_and_faces(const ResParams<T>& P, TileIdx* ti, FaceIdx* fi) 
 // ---- the residual as one pass (small-strain elastic laws) -----------------------
 // k_residual_fused: a block marches a tile of FX x FY voxels (x, y) through a chunk of z
 // planes.  Per z step it (1) stores the next node plane of u^f (FX+1 x FY+1 nodes, hi and
-// lo parts) in shared memory, (2) evaluates the gradient and the law of its voxel layer
-// from the two node planes around it (the lower plane's corners stay in registers from the
-// previous step) and keeps the voxel-point stresses in shared memory, and (3) forms D at
-// the node plane between this voxel layer and the previous one, from the 8 voxels around
-// each node, as the same sums of neighbour differences as k_div (Remark 1).  The block's
+// lo parts) in shared memory, then, after the step's one barrier, (2) forms D at the node
+// plane below the previous voxel layer, from the 8 voxels around each node, as the same sums
+// of neighbour differences as k_div (Remark 1), and (3) evaluates the gradient and the law of
+// its voxel layer from the two node planes around it (the lower plane's corners stay in
+// registers from the previous step), keeping the voxel-point stresses in shared memory: a
+// ring of three layers, so that the layer being written is never one that (2) reads.  The block's
 // voxel tile overlaps its neighbours' by one voxel in x and y so that the (FX-1) x (FY-1)
 // nodes it owns see all their voxels; the stresses never leave the SM.  Nodes on
 // non-periodic faces take the ghost rules in k_face_div, which reads the stresses of the
@@ -1264,6 +1269,8 @@ struct FusedGeom {
   int ntx, nty, nzc, zc;
   int items;
   int faces;  // 1 if some axis is non-periodic: boundary voxel layers go to the stress buffer
+  int fdof[3];  // the faces normal to axis a hold a dof of some component: their voxel layers
+                // go to the stress buffer (the face kernel reads no other)
 };
 
 template <typename T>
@@ -1287,6 +1294,12 @@ static FusedGeom fused_geom(const ResParams<T>& P) {
   g.nzc = nz > 0 ? (nz + g.zc - 1) / g.zc : 0;
   g.items = (int)(cols * g.nzc);
   g.faces = !(P.periodic[0] && P.periodic[1] && P.periodic[2]);
+  for (int a = 0; a < 3; ++a) {
+    g.fdof[a] = 0;
+    if (P.periodic[a]) continue;
+    for (int q = 0; q < 3; ++q)
+      if (P.lo[q][a] == 0 || P.hi[q][a] > P.n[a]) g.fdof[a] = 1;
+  }
   return g;
 }
 
@@ -1426,7 +1439,7 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
   constexpr int SL = FY * FX;      // one stress pair of one point of one voxel layer
   extern __shared__ __align__(16) unsigned char fsm[];
   NV* su = reinterpret_cast<NV*>(fsm);                      // [2][3][FNY][FNX] node planes
-  T2* ss = reinterpret_cast<T2*>(su + 2 * 3 * PL);          // [2][NPP][3][FY][FX] stress pairs
+  T2* ss = reinterpret_cast<T2*>(su + 2 * 3 * PL);          // [3][NPP][3][FY][FX] stress pairs
   __shared__ double red[32];
 
   const int tx = threadIdx.x % FX, ty = threadIdx.x / FX;
@@ -1452,7 +1465,7 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
   const int ox_lo = X0 - ((ix == 0 && !P.periodic[0]) ? 1 : 0);
   const int oy_lo = Y0 - ((iy == 0 && !P.periodic[1]) ? 1 : 0);
   const bool own_xy = vin && mx >= ox_lo && mx < Xend && my >= oy_lo && my < Yend;
-  const bool xy_face = (!P.periodic[0] && (vx == 0 || vx == n1 - 1)) || (!P.periodic[1] && (vy == 0 || vy == n2 - 1));
+  const bool xy_face = (g.fdof[0] && (vx == 0 || vx == n1 - 1)) || (g.fdof[1] && (vy == 0 || vy == n2 - 1));
   const int phase_xy = vx + vy * (int)P.vy;
   const int own_z0 = Z0 - (iz == 0 && !P.periodic[2] ? 1 : 0);
   const long long node_xy = node_out ? mx + my * sy : 0;
@@ -1519,8 +1532,7 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
   T2* const ss_me = ss + ty * FX + tx;
   // voxel layer vz from the corner planes L (lower) and U (upper): stresses into stress
   // buffer b, S_P, boundary layers to the stress buffer of the face kernel
-  auto voxel_layer = [&](auto par, int vz, int ph, const NV (&L)[3][4], const NV (&U)[3][4]) {
-    constexpr int b = decltype(par)::value;
+  auto voxel_layer = [&](int b, int vz, int ph, const NV (&L)[3][4], const NV (&U)[3][4]) {
     const bool zin = vz >= 0 && vz < n3;
     const int vzz = vz < 0 ? vz + n3 : vz;
     T Ps[NPP][6];
@@ -1561,7 +1573,7 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
           spv += Ps[r][0] * Ps[r][0] + Ps[r][1] * Ps[r][1] + Ps[r][2] * Ps[r][2] +
                  T(2) * (Ps[r][3] * Ps[r][3] + Ps[r][4] * Ps[r][4] + Ps[r][5] * Ps[r][5]);
         sp += spv;
-        if (g.faces && (xy_face || (!P.periodic[2] && (vzz == 0 || vzz == n3 - 1)))) {
+        if (g.faces && (xy_face || (g.fdof[2] && (vzz == 0 || vzz == n3 - 1)))) {
           const long long v = phase_xy + (long long)vzz * P.vz;
 #pragma unroll
           for (int r = 0; r < NPP; ++r) {
@@ -1584,9 +1596,8 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
     }
   };
   const T2* const ss_nb = ss + (ty > 0 ? ty - 1 : 0) * FX + (tx > 0 ? tx - 1 : 0);
-  // D at node plane z from the voxel layers below (stress buffer bl) and above (bu)
-  auto node_div = [&](auto parl, int z) {
-    constexpr int bl = decltype(parl)::value, bu = 1 - bl;
+  // D at node plane z from the voxel layers below (stress slot bl) and above (bu)
+  auto node_div = [&](int bl, int bu, int z) {
     T val[8][6];
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -1620,10 +1631,14 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
     }
   };
 
-  // one z step: node plane z + 1 into node buffer B, voxel layer z from (Lo, Up) into
-  // stress buffer 1 - B, D at node plane z (stress buffers B below, 1 - B above)
+  // one z step: node plane z + 1 into node buffer B; after the barrier, D at node plane z - 1
+  // (voxel layers z - 2 and z - 1, published by this barrier) and voxel layer z from (Lo, Up)
+  // into stress slot sz_cur.  Voxel layer l sits in slot (l - Z0 + 1) % 3: it is written in
+  // step l and read in steps l + 1 and l + 2, and its slot is written again in step l + 3,
+  // after the barrier that ends step l + 2.
   NV cA[3][4], cB[3][4];
   int ph_next = 0;
+  int s_lo = 0, s_mid = 0, s_cur = 1;  // slots of layers z - 2, z - 1 and z
   auto step = [&](auto par, int z, const NV (&Lo)[3][4], NV (&Up)[3][4]) {
     constexpr int B = decltype(par)::value;
     store_plane(Par<B>{});
@@ -1631,10 +1646,12 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
     if (z + 2 <= Z1) fetch_plane(z + 2);  // in flight during this layer
     const int ph = ph_next;
     if (z + 1 < Z1) ph_next = phase_at(z + 1);
+    if (z > Z0 && node_out) node_div(s_lo, s_mid, z - 1);
     read4(Par<B>{}, Up);
-    voxel_layer(Par<1 - B>{}, z, ph, Lo, Up);
-    __syncthreads();
-    if (node_out) node_div(Par<B>{}, z);
+    voxel_layer(s_cur, z, ph, Lo, Up);
+    s_lo = s_mid;
+    s_mid = s_cur;
+    s_cur = s_cur == 2 ? 0 : s_cur + 1;
     if (++run == 16) {
       SP += (double)sp;
       SD += (double)sd;
@@ -1643,7 +1660,7 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
     }
   };
 
-  // prologue: node planes Z0 - 1 (buffer 0) and Z0 (buffer 1), voxel layer Z0 - 1 (stress 0)
+  // prologue: node planes Z0 - 1 (buffer 0) and Z0 (buffer 1), voxel layer Z0 - 1 (slot 0)
   ph_next = phase_at(Z0 - 1);
   fetch_plane(Z0 - 1);
   store_plane(Par<0>{});
@@ -1656,14 +1673,18 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
   {
     const int ph = ph_next;
     ph_next = phase_at(Z0);
-    voxel_layer(Par<0>{}, Z0 - 1, ph, cB, cA);
+    voxel_layer(0, Z0 - 1, ph, cB, cA);
+    s_mid = 0;
   }
   if (Z0 + 1 <= Z1) fetch_plane(Z0 + 1);
-  // steps alternate buffers; the corners of plane z stay in registers (cA, cB in turn)
+  // steps alternate node buffers; the corners of plane z stay in registers (cA, cB in turn)
   for (int z = Z0; z < Z1; z += 2) {
     step(Par<0>{}, z, cA, cB);
     if (z + 1 < Z1) step(Par<1>{}, z + 1, cB, cA);
   }
+  // the last node plane: voxel layers Z1 - 2 and Z1 - 1
+  __syncthreads();
+  if (Z1 > Z0 && node_out) node_div(s_lo, s_mid, Z1 - 1);
   SP += (double)sp;
   SD += (double)sd;
   const double tsp = block_sum(SP, red);
@@ -1675,19 +1696,29 @@ __global__ void __launch_bounds__(FX * FY, 16 / FY) k_residual_fused(ResParams<T
 }
 
 // Nodes on non-periodic faces (each once), with the ghost rules, from the boundary voxel
-// layers that k_residual_fused stored; one S_D partial per block (S_P slot zero).
+// layers that k_residual_fused stored; one S_D partial per block (S_P slot zero).  A thread
+// takes one component of one node (component-major, so that a warp walks one face): the
+// gathers of a node's three components run in parallel, and a component without a dof there
+// (every component of a fully Dirichlet face) writes its zero without any gather.
 template <typename T, int TETRA>
-__global__ void __launch_bounds__(256) k_face_div(ResParams<T> P, FaceIdx fi) {
+__global__ void __launch_bounds__(256, 2) k_face_div(ResParams<T> P, FaceIdx fi) {
   if (P.stop && *P.stop) return;
   __shared__ double red[32];
   double SD = 0.0;
   int nface[3] = {P.n[0], P.n[1], P.n[2]};
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < fi.count; t += gridDim.x * blockDim.x) {
+  const long long total = 3LL * fi.count;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(t / fi.count), k = (int)(t - (long long)q * fi.count);
     int m[3];
-    if (!fi.at(t, nface, m)) continue;
+    if (!fi.at(k, nface, m)) continue;
+    const bool dof = m[0] >= P.lo[q][0] && m[0] < P.hi[q][0] && m[1] >= P.lo[q][1] && m[1] < P.hi[q][1] &&
+                     m[2] >= P.lo[q][2] && m[2] < P.hi[q][2];
     T Dq[3] = {T(0), T(0), T(0)}, pq[3] = {T(0), T(0), T(0)};
-    node_div_general<T, TETRA, false, true>(P, m[0], m[1], m[2], Dq, pq);
-    SD += (double)store_node<T, false, false>(P, m[0], m[1], m[2], Dq, pq);
+    if (dof) node_div_general<T, TETRA, false, true>(P, m[0], m[1], m[2], Dq, pq, 1 << q);
+    const long long off = m[0] + m[1] * P.sy + m[2] * P.sz;
+    P.D[q][off] = dof ? Dq[q] : T(0);
+    if (dof) SD += (double)(Dq[q] * Dq[q]);
   }
   const double tot = block_sum(SD, red);
   if (threadIdx.x == 0) {
@@ -1696,12 +1727,12 @@ __global__ void __launch_bounds__(256) k_face_div(ResParams<T> P, FaceIdx fi) {
   }
 }
 
-constexpr int kFaceBlocks = 152 * 8;  // one face node per thread at 256^3 (the work per node is a long chain of gathers)
+constexpr int kFaceBlocks = 152 * 8;  // a few node components per thread at 256^3 (each a chain of gathers)
 
 template <typename T>
 static size_t fused_smem(int tetra, int fy) {
   using NVs = typename NodeV<T, true>::t;  // same size as the FP64 node value
-  return (size_t)2 * 3 * (fy + 1) * FNX * sizeof(NVs) + (size_t)2 * (tetra ? 2 : 1) * 3 * fy * FX * 2 * sizeof(T);
+  return (size_t)2 * 3 * (fy + 1) * FNX * sizeof(NVs) + (size_t)3 * (tetra ? 2 : 1) * 3 * fy * FX * 2 * sizeof(T);
 }
 
 template <typename T, int TETRA, bool LO, int FY>

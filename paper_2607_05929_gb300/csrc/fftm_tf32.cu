@@ -433,9 +433,36 @@ __device__ __forceinline__ TfGreenLine tf_green_line(const TfPassParams& P, int 
 // ---- the epilogue (warps 0-7) --------------------------------------------------------------
 // Warp w reads TMEM lanes 32 (w % 4) .. + 31 and takes half h = w / 4 of the accumulator's
 // columns (x: of its M blocks).
+// The Green factor's per-tile inputs, fetched by each epilogue warp before it waits for the
+// accumulator (their latency hides behind the wait): the (kx, ky) line coefficients and, when a
+// warp's half of the z outputs spans at most TF_ZCH chunks of 16, that half's sin^2 / cos^2
+// factors, chunk j in register r[j] (lane i < 16: sin^2 of output 16 j + i; lane 16 + i: cos^2).
+constexpr int TF_ZCH = 8;
+struct TfZPre {
+  TfGreenLine G;
+  bool gl, reg;
+  float r[TF_ZCH];
+};
+
+__device__ __forceinline__ TfZPre tf_z_prefetch(const TfPassParams& P, const TfTile& T, int warp, int lane) {
+  TfZPre Z;
+  const int q = T.q, p = (warp & 3) * 32 + lane, h = warp >> 2, half = T.Kp / 2;
+  const int kx = T.x0 + p - P.flo[q][0], ky = T.other - P.flo[q][1];
+  Z.gl = p < T.npen && kx >= 0 && kx < P.fL[q][0] && ky >= 0 && ky < P.fL[q][1];
+  Z.G = tf_green_line(P, q, Z.gl ? kx : 0, Z.gl ? ky : 0);
+  Z.reg = half <= 16 * TF_ZCH;
+  const float* __restrict__ src = lane < 16 ? P.S2[q][2] : P.C2[q][2];
+#pragma unroll
+  for (int j = 0; j < TF_ZCH; ++j) {
+    const int k = min(h * half + 16 * j + (lane & 15), T.L - 1);
+    Z.r[j] = (Z.reg && 16 * j < half) ? __ldg(src + k) : 0.f;
+  }
+  return Z;
+}
+
 template <int AXIS>
 __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTile& T, uint32_t acc, int warp,
-                                              int lane) {
+                                              int lane, const TfZPre& Z) {
   const int q = T.q, L = T.L, Kp = T.Kp, npen = T.npen;
   float* __restrict__ out = P.out[q];
   const float sc = P.scale[q];
@@ -512,18 +539,29 @@ __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTil
     const bool live = p < npen;
     const long long rowbase = T.base0 + p + (long long)T.lo * T.estride;
     const bool green = AXIS == 2 && P.mode == 2;
-    TfGreenLine G;
-    G.alpha = G.beta = 0.f;
-    G.g = 0.f;
-    bool gl = false;
-    if (green) {
-      const int kx = T.x0 + p - P.flo[q][0], ky = T.other - P.flo[q][1];
-      gl = live && kx >= 0 && kx < P.fL[q][0] && ky >= 0 && ky < P.fL[q][1];
-      G = tf_green_line(P, q, gl ? kx : 0, gl ? ky : 0);
+    const int half = Kp / 2;  // a multiple of 16
+    if (green && Z.reg) {
+      // the z factors come from the prefetched registers, one shuffle per factor
+#pragma unroll
+      for (int j = 0; j < TF_ZCH; ++j) {
+        if (16 * j >= half) break;
+        const int c0 = h * half + 16 * j;
+        float v[16];
+        tmem_ld16(acc + lane_base + (uint32_t)c0, v);  // warp-collective: every lane takes part
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float zs = __shfl_sync(0xffffffffu, Z.r[j], i);
+          const float zc = __shfl_sync(0xffffffffu, Z.r[j], 16 + i);
+          const int k = c0 + i;
+          if (live && k < L) out[rowbase + (long long)k * T.estride] = Z.gl ? sc * v[i] * Z.G.at(zs, zc) : 0.f;
+        }
+      }
+      return;
     }
+    const TfGreenLine& G = Z.G;
+    const bool gl = Z.gl;
     const float* __restrict__ Sz = P.S2[q][2];
     const float* __restrict__ Cz = P.C2[q][2];
-    const int half = Kp / 2;  // a multiple of 16
     for (int c0 = h * half; c0 < (h + 1) * half; c0 += 16) {
       float zs[16], zc[16];
       if (green) {  // the z factors of these 16 outputs, loaded before the TMEM read
@@ -717,10 +755,14 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
       const int a = i % nacc;
       const uint32_t acc = tmem + (uint32_t)(a * 256);
       const TfTile T = tf_tile_of<AXIS>(P, blockIdx.x + i * gridDim.x);
+      TfZPre Z;
+      Z.gl = Z.reg = false;
+      Z.G.alpha = Z.G.beta = Z.G.g = 0.f;
+      if (AXIS == 2 && P.mode == 2) Z = tf_z_prefetch(P, T, warp, lane);
       if (!bar_wait(&B.acc_full[a], acc_uses[a] & 1, abort)) break;
       ++acc_uses[a];
       asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      tf_store_tile<AXIS>(P, T, acc, warp, lane);
+      tf_store_tile<AXIS>(P, T, acc, warp, lane, Z);
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       bar_arrive(&B.acc_empty[a]);
     }

@@ -2,8 +2,12 @@
 transform contractions, the launch configuration of the bench), checked by the FP64 oracle at full
 size: the oracle's own residual of the GPU's converged displacement (u^f read as its high and low
 parts) meets the load step's tolerance, the GPU's equilibrium error and mean stress agree with the
-oracle's evaluation of the same field, and the GPU's residual field D matches the oracle's on that
-field.  The oracle evaluates one residual of the whole grid (about a minute on the host cores)."""
+oracle's evaluation of the same field, and the GPU's residual field D differs from the oracle's by
+no more than FP32 rounding accounts for.  At convergence D is about 1e-6 of the stress scale, so the
+FP32 evaluation of the stresses (rounding of a few units of 2^-24 on each entry, summed with
+cancellation by the divergence) is a visible fraction of D: the bound is stated against the
+divergence of the oracle's stress rounded once to FP32, times the number of roundings a stress entry
+and a node's sum go through on the GPU.  The oracle evaluates one residual of the whole grid."""
 
 import numpy as np
 import pytest
@@ -11,6 +15,7 @@ import pytest
 import bench
 from abi_helpers import node_from_abi, rel_l2
 from oracle.solver import Problem
+from oracle.stencils import div
 from paper_2607_05929_gb300 import build
 from paper_2607_05929_gb300 import fftm as F
 
@@ -50,11 +55,21 @@ def test_full_size_tf32_solve_is_an_equilibrium_of_the_oracle():
     p_ref, D_ref, P_ref, G_ref, SD, SP = pr.residual(u, pr.grad_ustar())
     err = pr.error(SD, SP)
     # the GPU stopped at its FP32 evaluation of err < tol; the FP64 evaluation of the same field
-    # agrees with it to the FP32 residual's rounding (a few 1e-8 of the stress scale, i.e. a few
-    # per cent of D when err is 1e-6)
+    # agrees with it to the FP32 residual's rounding, which adds in quadrature to D
     assert err < 1.1 * wl.tol, (err, r["err"])
     assert abs(err - r["err"]) <= 0.1 * err, (err, r["err"])
-    assert rel_l2(node_from_abi(Dg.astype(np.float64)), D_ref) < 0.1
+    # rounding model: the divergence of one FP32 rounding of every stress entry; the GPU rounds the
+    # gradient, each term of the law and each partial sum of a node's divergence, so its deviation
+    # is a small multiple of the model (16 bounds the gradient + law + sum chain with margin)
+    dP = P_ref.astype(np.float32).astype(np.float64) - P_ref
+    D_round = div(dP, pr.grid, pr.scheme)
+    for q in range(3):
+        D_round[q][~pr.masks[q]] = 0.0
+    dev = float(np.linalg.norm(node_from_abi(Dg.astype(np.float64)) - D_ref))
+    model = float(np.linalg.norm(D_round))
+    print(f"|D_gpu - D_ref| = {dev:.3e}, one-rounding model {model:.3e}, ratio {dev / model:.2f}, "
+          f"|D_ref| = {np.linalg.norm(D_ref):.3e}")
+    assert dev <= 16.0 * model, (dev, model)
     Pm = P_ref.mean(axis=(0, 3, 4, 5))
     ref = np.array([Pm[0, 0], Pm[1, 1], Pm[2, 2], Pm[1, 2], Pm[0, 2], Pm[0, 1]])
     assert np.linalg.norm(r["mean_P"] - ref) <= 1e-5 * np.linalg.norm(ref)
