@@ -81,6 +81,8 @@ def parse_args(argv=None):
     ap.add_argument("--residual-passes", type=int, choices=[0, 1, 2], default=0,
                     help="residual form: 0 = chosen by the library's launch-shape tuner, 1 = one pass, "
                          "2 = two passes (FFTM_OPT_RESIDUAL_PASSES)")
+    ap.add_argument("--residual-tile", type=int, choices=[0, 8, 16], default=0,
+                    help="one-pass residual tile height: 0 = tuned, 8 or 16 voxel rows (FFTM_OPT_RESIDUAL_TILE)")
     ap.add_argument("--graph", type=int, choices=[0, 1], default=0,
                     help="1: device-decided steps replayed from CUDA graphs (FFTM_OPT_CUDA_GRAPH)")
     ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
@@ -349,6 +351,8 @@ def gpu_arm(args):
         F.fftm_set_option(p, F.FFTM_OPT_CUDA_GRAPH, args.graph)
         if args.residual_passes:
             F.fftm_set_option(p, F.FFTM_OPT_RESIDUAL_PASSES, args.residual_passes)
+        if args.residual_tile:
+            F.fftm_set_option(p, F.FFTM_OPT_RESIDUAL_TILE, args.residual_tile)
         F.fftm_set_load(p, wl.A)
         return p
 

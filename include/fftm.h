@@ -369,7 +369,11 @@ int fftm_set_field(fftm_problem* p, int field, const void* src, int src_is_devic
 /* ---- single steps of one iteration (each a row of the hot path) -------- */
 enum fftm_op {
   FFTM_OP_RESIDUAL = 0,     /* u^f -> WORK = p (Eq. div_pol), D, and norms:
-                               norms[0] = S_D, norms[1] = S_P, norms[2] = err  */
+                               norms[0] = S_D, norms[1] = S_P, norms[2] = err.
+                               With FFTM_OPT_RESIDUAL_PASSES 1 and a tile height
+                               set, D and the norms come from the solver's
+                               one-pass kernels (u^f as hi + lo) and WORK is
+                               left as it was                                   */
   FFTM_OP_DT_FORWARD = 1,   /* WORK -> WORK, 3D forward DT (x, y, z; Table 1);
                                DCT/DST coefficient k of an axis sits at node
                                position lo + k; a periodic axis is stored in

@@ -800,21 +800,25 @@ int resolve_residual_form(fftm_problem* p, int slot) {
   return FFTM_OK;
 }
 
-// a1-a4: D (into the D slot of `slot`, or the test buffers) and the two norms.
+// a1-a4: D (into the D slot of `slot`, or the test buffers) and the two norms.  solver_form:
+// the solver's residual kernels (one pass where the form allows it, no p), D into the test
+// buffer, no convergence test (FFTM_OP_RESIDUAL with the one-pass form forced).
 template <typename T>
-int run_residual(fftm_problem* p, int slot, bool test_outputs) {
+int run_residual(fftm_problem* p, int slot, bool test_outputs, bool solver_form = false) {
   if (!test_outputs && p->res_two_pass < 0) {
     int rc = resolve_residual_form<T>(p, slot);
     if (rc) return rc;
   }
   T* D = nullptr;
   T* pp = nullptr;
-  if (test_outputs) {
+  if (test_outputs || solver_form) {
     if (!p->Dbuf) {
       DEVALLOC(dev_alloc(p, reinterpret_cast<void**>(&p->Dbuf), 3 * p->comp_stride * sizeof(T)));
       CU(cudaMemsetAsync(p->Dbuf, 0, 3 * p->comp_stride * sizeof(T), p->ctx->stream));
     }
     D = reinterpret_cast<T*>(p->Dbuf);
+  }
+  if (test_outputs) {
     pp = field_ptr<T>(p, SET_WORK, 0);
     if (!p->vs_test) {
       const size_t b = (size_t)(p->tetra ? 2 : 1) * ((p->sym ? 6 : 9) + 9) * p->nvox * sizeof(T);
@@ -845,7 +849,7 @@ int run_residual(fftm_problem* p, int slot, bool test_outputs) {
   CU(launch_residual<T>(R, p->tetra, test_outputs, p->ctx->stream, &blocks));
   CU(launch_reduce_norms(p->partial, blocks, 2, p->dscal, p->ctx->stream, p->stop));
   p->launches += 2;
-  if (p->stop && !test_outputs) {  // the convergence test on the device
+  if (p->stop && !test_outputs && !solver_form) {  // the convergence test on the device
     CU(launch_check(p->dscal, p->dctl, p->derr, p->desc.tol, p->desc.max_iter, p->h[0], p->ctx->stream));
     p->launches += 1;
   }
@@ -2385,7 +2389,10 @@ static int apply_t(fftm_problem* p, int op, double* norms) {
   int rc = FFTM_OK;
   switch (op) {
     case FFTM_OP_RESIDUAL: {
-      rc = run_residual<T>(p, p->cur, true);
+      // the one-pass form forced (passes 1 and a tile height): D and the norms from the
+      // solver's own kernels on u^f (hi + lo), p not formed
+      const bool solver_form = p->res_passes == 1 && p->res_two_pass == 0;
+      rc = solver_form ? run_residual<T>(p, p->cur, false, true) : run_residual<T>(p, p->cur, true);
       if (rc) return rc;
       CU(cudaMemcpyAsync(p->hpin, p->dscal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
       CU(cudaStreamSynchronize(s));
