@@ -541,20 +541,29 @@ __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTil
     const bool green = AXIS == 2 && P.mode == 2;
     const int half = Kp / 2;  // a multiple of 16
     if (green && Z.reg) {
-      // the z factors come from the prefetched registers, one shuffle per factor
-#pragma unroll
-      for (int j = 0; j < TF_ZCH; ++j) {
-        if (16 * j >= half) break;
-        const int c0 = h * half + 16 * j;
+      // the z factors come from the prefetched registers, one shuffle per factor.  The chunk
+      // loop stays rolled: a compact body, since the epilogue shares the instruction cache
+      // with the producers and the MMA thread
+      const float gs = Z.gl ? Z.G.g * sc : 0.f;  // the scale folded into the factor's numerator
+      const float al = Z.G.alpha, be = Z.G.beta;
+      const long long es = T.estride;
+      const int nch = half / 16;
+      float* o = out + rowbase + (long long)(h * half) * es;
+#pragma unroll 1
+      for (int j = 0; j < nch; ++j) {
+        const int kb = h * half + 16 * j;
+        const float zr = Z.r[j];
         float v[16];
-        tmem_ld16(acc + lane_base + (uint32_t)c0, v);  // warp-collective: every lane takes part
+        tmem_ld16(acc + lane_base + (uint32_t)kb, v);  // warp-collective: every lane takes part
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-          const float zs = __shfl_sync(0xffffffffu, Z.r[j], i);
-          const float zc = __shfl_sync(0xffffffffu, Z.r[j], 16 + i);
-          const int k = c0 + i;
-          if (live && k < L) out[rowbase + (long long)k * T.estride] = Z.gl ? sc * v[i] * Z.G.at(zs, zc) : 0.f;
+          const float zs = __shfl_sync(0xffffffffu, zr, i);
+          const float zc = __shfl_sync(0xffffffffu, zr, 16 + i);
+          const float den = fmaf(al, zc, be * zs);
+          const float f = den > 0.f ? __fdividef(gs, den) : 0.f;
+          if (live && kb + i < L) o[(long long)i * es] = v[i] * f;
         }
+        o += 16 * es;
       }
       return;
     }
