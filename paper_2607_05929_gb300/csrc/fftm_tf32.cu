@@ -480,54 +480,54 @@ __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTil
     for (int mb = h; mb < mp / 128; mb += 2) {
       const int x = xb + mb * 128 + gq * 32 + lane;
       const bool ok = x >= T.lo && x < T.lo + L;
-      for (int p0 = 0; p0 < npen; p0 += 32) {
-        float v[32];
-        tmem_ld32(acc + lane_base + (uint32_t)(mb * 128 + p0), v);
+      // 16 rows per round, the loop rolled (a compact body: the epilogue shares the
+      // instruction cache with the producers and the MMA thread)
+      const bool acc_mode = P.mode == 1 && bh != nullptr;
+      const int wr = (int)wrap, syi = (int)sy;
+#pragma unroll 1
+      for (int p0 = 0; p0 < npen; p0 += 16) {
+        float v[16];
+        tmem_ld16(acc + lane_base + (uint32_t)(mb * 128 + p0), v);  // warp-collective
         if (!ok) continue;
         // row r = row0 + p0 + u of the grid's (y, z) rows: its offset advances by sy, or
         // wraps to the next z plane
         int y = (T.row0 + p0) % N2;
-        int row = y * (int)sy + ((T.row0 + p0) / N2) * (int)P.stride[2];  // within one component array
-        const int wr = (int)wrap, syi = (int)sy;
-        int at[32];
+        int row = y * syi + ((T.row0 + p0) / N2) * (int)P.stride[2];  // within one component array
+        int at[16];
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
+        for (int u = 0; u < 16; ++u) {
           at[u] = row + x;
           row += (++y == N2) ? wr : syi;
           if (y == N2) y = 0;
         }
-        const bool acc_mode = P.mode == 1 && bh != nullptr;
         if (!acc_mode) {
 #pragma unroll
-          for (int u = 0; u < 32; ++u)
+          for (int u = 0; u < 16; ++u)
             if (p0 + u < npen) out[at[u]] = sc * v[u];
         } else {
+          // the base values of the 16 rows are loaded before the first sum (loads in flight together)
+          float a[16], b[16];
 #pragma unroll
-          for (int h16 = 0; h16 < 32; h16 += 16) {
-            // the base values of 16 rows are loaded before the first sum (loads in flight together)
-            float a[16], b[16];
+          for (int u = 0; u < 16; ++u) {
+            const bool live = p0 + u < npen;
+            a[u] = live ? bh[at[u]] : 0.f;
+            b[u] = (live && ol) ? bl[at[u]] : 0.f;
+          }
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              const bool live = p0 + h16 + u < npen;
-              a[u] = live ? bh[at[h16 + u]] : 0.f;
-              b[u] = (live && ol) ? bl[at[h16 + u]] : 0.f;
-            }
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-              if (p0 + h16 + u >= npen) continue;
-              const int o = at[h16 + u];
-              const float val = sc * v[h16 + u];
-              if (ol == nullptr) {
-                out[o] = a[u] + val;
-              } else {  // (hi, lo) = (bh, bl) + val with an error-free sum of the high parts
-                const float s1 = a[u] + val;
-                const float bs = s1 - a[u];
-                const float er = (a[u] - (s1 - bs)) + (val - bs);
-                const float tt = b[u] + er;
-                const float hsum = s1 + tt;
-                out[o] = hsum;
-                ol[o] = tt - (hsum - s1);
-              }
+          for (int u = 0; u < 16; ++u) {
+            if (p0 + u >= npen) continue;
+            const int o = at[u];
+            const float val = sc * v[u];
+            if (ol == nullptr) {
+              out[o] = a[u] + val;
+            } else {  // (hi, lo) = (bh, bl) + val with an error-free sum of the high parts
+              const float s1 = a[u] + val;
+              const float bs = s1 - a[u];
+              const float er = (a[u] - (s1 - bs)) + (val - bs);
+              const float tt = b[u] + er;
+              const float hsum = s1 + tt;
+              out[o] = hsum;
+              ol[o] = tt - (hsum - s1);
             }
           }
         }
