@@ -1057,9 +1057,12 @@ __device__ __forceinline__ void node_div_general(const ResParams<T>& P, int mx, 
     *f = T(sgn);
     return (long long)(r * NCT) * nvox + vx + vy * P.vy + (long long)vz * P.vz;
   };
-  for (int i = 0; i < 3; ++i) {
-    for (int q = 0; q < 3; ++q) {
-      if (!((qmask >> q) & 1)) continue;  // a component without a dof at this node stays zero
+  // component outermost, the three directions unrolled: a component's 24 gathers are
+  // independent and in flight together (the sums over i keep their order)
+  for (int q = 0; q < 3; ++q) {
+    if (!((qmask >> q) & 1)) continue;  // a component without a dof at this node stays zero
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
       const int c = SYM ? sym_index(i, q) : i * 3 + q;
       T s = T(0), st = T(0);
       // imposed stress of a traction on the face normal to i that this node lies on: every
