@@ -311,6 +311,9 @@ struct fftm_problem {
   int* tc_err = nullptr;  // timeout flag of the tensor-core passes
   size_t off_tcf[3][3], off_tci[3][3];
   int tcKp[3][3];
+  int tcKn[3][3];                        // TF32: outputs on the tensor cores (tcKp, or 256)
+  size_t off_tcxf[3][3], off_tcxi[3][3];  // TF32 y, z with 257 outputs: output 256's row
+  int tcx[3][3];
   // device table offsets (bytes) inside `tables`
   size_t off_perm[3][3], off_tw[3][3], off_qw[3][3], off_S2[3][3], off_C2[3][3];
   int maxM[3], maxL[3];
@@ -566,6 +569,10 @@ TfPassParams tf_params(fftm_problem* p, int axis, int inverse, int mode, int in_
     P.lo[q] = p->plans[q][axis].lo;
     P.L[q] = p->plans[q][axis].L;
     P.Kp[q] = p->tcKp[q][axis];
+    P.Kn[q] = p->tcKn[q][axis];
+    P.xrow[q] = p->tcx[q][axis]
+                    ? reinterpret_cast<const float*>(base + (inverse ? p->off_tcxi[q][axis] : p->off_tcxf[q][axis]))
+                    : nullptr;
     P.A[q] = reinterpret_cast<const float*>(base + (inverse ? p->off_tci[q][axis] : p->off_tcf[q][axis]));
     P.scale[q] = 1.f;
     for (int a = 0; a < 3; ++a) {
@@ -1895,6 +1902,7 @@ static int problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, void* wo
       for (int r0 = 0; r0 < L; ++r0)
         for (int c0 = 0; c0 < L; ++c0) {
           const int m = r0 + sh, c = c0 + sh;
+          if (m >= R) continue;  // output 256 of a 257-output y / z transform: its own row
           const int ch = c / 32, jj = c % 32;
           const size_t at = (size_t)ch * R * 32 + (size_t)(m >> 3) * 256 + (jj >> 2) * 32 + (m & 7) * 4 + (jj & 3);
           mats[off + at] = to_tf32(M[(size_t)r0 * L + c0]);
@@ -1909,12 +1917,27 @@ static int problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, void* wo
         dense_inverse(p->kind[q][a], p->n[a], &I);
         const int col0 = a == 0 ? (p->plans[q][a].lo & 3) : 0;
         const int Kp = (L + col0 + 31) / 32 * 32;
-        if (!pass_tf32_fits(Kp, a))
+        // y, z with 257 outputs (DCT-I over 256 intervals): 256 on the tensor cores, so that two
+        // accumulators fit TMEM, and output 256 as an FP32 dot product in the producers
+        const bool xt = a != 0 && L == 257 && pass_tf32_fits(256, a, 1);
+        const int Kn = xt ? 256 : Kp;
+        if (!pass_tf32_fits(Kn, a, xt ? 1 : 0))
           return set_err(FFTM_E_UNSUPPORTED, "TF32 tensor-core transforms need lengths up to 384 per axis");
         p->tcKp[q][a] = Kp;
-        const int R = pass_tf32_rows(Kp, a);
+        p->tcKn[q][a] = Kn;
+        p->tcx[q][a] = xt ? 1 : 0;
+        const int R = pass_tf32_rows(Kn, a);
         p->off_tcf[q][a] = put_mat(F, L, Kp, R, col0);
         p->off_tci[q][a] = put_mat(I, L, Kp, R, col0);
+        if (xt) {  // row 256 over the K positions, FP32, zero-padded to Kp
+          for (int inv = 0; inv < 2; ++inv) {
+            const std::vector<double>& M = inv ? I : F;
+            const size_t off = (mats.size() + 31) & ~(size_t)31;
+            mats.resize(off + (size_t)Kp, 0.f);
+            for (int c0 = 0; c0 < L; ++c0) mats[off + c0] = (float)M[(size_t)256 * L + c0];
+            (inv ? p->off_tcxi : p->off_tcxf)[q][a] = off * sizeof(float);
+          }
+        }
       }
     DEVALLOC(dev_alloc(p.get(), reinterpret_cast<void**>(&p->tcmat), mats.size() * sizeof(float)));
     CU(cudaMemcpy(p->tcmat, mats.data(), mats.size() * sizeof(float), cudaMemcpyHostToDevice));

@@ -179,7 +179,10 @@ int pass_tc_rows(int Kp, int axis);
 // FP32 elements: element (m, jj) of chunk c at c R 32 + (m>>3) 256 + (jj>>2) 32 + (m&7) 4
 // + (jj&3).  mode 0: out = scale T in; mode 1 (x axis): out = base + scale T in, as an
 // unevaluated hi + lo pair when out_lo is set; mode 2 (z axis): the forward result times the
-// B0 / 2 mu0 Green factor -gscale / den (0 where den is null).
+// B0 / 2 mu0 Green factor -gscale / den (0 where den is null).  On y and z a transform of
+// 257 outputs (DCT-I over 256 intervals) runs the first Kn = 256 on the tensor cores (R = 256
+// rows, two accumulators fit TMEM) and the last as a dot product of the FP32 tile with the
+// matrix row xrow (K positions, FP32) in the producers.
 struct TfPassParams {
   // TMA descriptors of the input components (filled by launch_pass_tf32): x axis a 2D tensor
   // {row pitch, N2 * N3 rows} in 32 x 128 boxes with the 128-byte swizzle; y and z axes a 3D
@@ -194,6 +197,8 @@ struct TfPassParams {
   int N[3];
   long long stride[3];
   int lo[3], L[3], Kp[3];
+  int Kn[3];             // outputs contracted on the tensor cores (Kp, or 256 with xrow)
+  const float* xrow[3];  // y, z: the matrix row of output 256 when L = 257 (else null)
   const float* A[3];
   float scale[3];
   const float* S2[3][3];
@@ -207,7 +212,7 @@ struct TfPassParams {
   const int* stop;  // device flag: nonzero once the load step has stopped (the launch does nothing)
 };
 cudaError_t launch_pass_tf32(const TfPassParams& P, cudaStream_t s);
-bool pass_tf32_fits(int Kp, int axis);
+bool pass_tf32_fits(int Kp, int axis, int xtra = 0);
 int pass_tf32_rows(int Kp, int axis);
 
 // Green factor on a spectral field (standalone step).

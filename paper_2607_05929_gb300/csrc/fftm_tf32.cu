@@ -81,19 +81,24 @@ __device__ __forceinline__ void tf_mma(uint32_t tmem, uint64_t da, uint64_t db, 
 }
 
 
-// Shared-memory geometry for a padded transform length Kp (a multiple of 32).
+// Shared-memory geometry for Kn outputs on the tensor cores (a multiple of 32).  xtra: room for
+// the partial sums of the one output that the producers contract (y, z, 257 outputs).
+constexpr uint32_t TF_XBYTES = 2u * 8u * TF_P * 4u;  // two tiles x eight row groups x 128 pencils
+
 struct TfGeom {
-  int mp;            // matrix rows (x: Kp rounded up to 128; y, z: Kp)
+  int mp;            // matrix rows (x: Kn rounded up to 128; y, z: Kn)
   uint32_t stage;    // bytes of one stage: tile part, matrix part (mp x 32 FP32), raw part
   int nst;           // stages
   int acc_cols;      // TMEM columns of one accumulator
   int raw;           // y, z: the tile arrives by TMA in a raw part (rows of 128 pencils) and is
                      // transposed from there (when three stages still fit); else per-thread copies
-  __host__ __device__ static TfGeom make(int Kp, int axis) {
+  int xtra;          // the partial-sum area follows the stages
+  __host__ __device__ static TfGeom make(int Kn, int axis, int xtra = 0) {
     TfGeom g;
-    g.mp = axis == 0 ? (Kp + 127) / 128 * 128 : Kp;
-    g.acc_cols = axis == 0 ? g.mp : Kp;
-    const long long room = (long long)kMaxDynSmem - 2048;
+    g.mp = axis == 0 ? (Kn + 127) / 128 * 128 : Kn;
+    g.acc_cols = axis == 0 ? g.mp : Kn;
+    g.xtra = xtra ? 1 : 0;
+    const long long room = (long long)kMaxDynSmem - 2048 - (xtra ? (long long)TF_XBYTES : 0);
     for (g.raw = axis == 0 ? 0 : 1; g.raw >= 0; --g.raw) {
       g.stage = (TF_TILE_BYTES * (1u + (uint32_t)g.raw) + (uint32_t)g.mp * TF_KC * 4 + 1023u) & ~1023u;
       g.nst = (int)(room / g.stage);
@@ -104,7 +109,8 @@ struct TfGeom {
     return g;
   }
   __host__ __device__ uint32_t raw_off() const { return TF_TILE_BYTES + (uint32_t)mp * TF_KC * 4; }
-  __host__ __device__ size_t smem() const { return 2048 + (size_t)nst * stage; }
+  __host__ __device__ uint32_t xoff() const { return (uint32_t)nst * stage; }  // from the first stage
+  __host__ __device__ size_t smem() const { return 2048 + (size_t)nst * stage + (xtra ? TF_XBYTES : 0); }
 };
 
 // ---- tiles ------------------------------------------------------------------------------
@@ -112,7 +118,8 @@ struct TfGeom {
 // pencils along x within the component's x node range (from a multiple of 8), for every z
 // (y pass) or for every y of the component's y range (z passes).
 struct TfTile {
-  int q, L, lo, Kp, npen, row0, x0, other;
+  int q, L, lo, Kp, Kn, npen, row0, x0, other;
+  int xt;  // the producers contract output 256 (Kn = 256, L = 257)
   long long base0, estride;
 };
 
@@ -142,6 +149,8 @@ __device__ __forceinline__ TfTile tf_tile_of(const TfPassParams& P, int t) {
   T.L = P.L[q];
   T.lo = P.lo[q];
   T.Kp = P.Kp[q];
+  T.Kn = P.Kn[q];
+  T.xt = AXIS != 0 && P.xrow[q] != nullptr;
   T.row0 = T.x0 = T.other = 0;
   T.base0 = 0;
   T.estride = 1;
@@ -293,6 +302,8 @@ struct TfBars {
   uint64_t* acc_empty;  // [2]   TF_EPI arrivals: the accumulator has been drained
   uint64_t* done;       // 1     (MMA commit): every MMA of the CTA has completed
   uint64_t* land;       // [nst] x axis: 1 (the TMA issuer) + the tile's transaction bytes
+  uint64_t* xready;     // [2]   TF_PROD arrivals: a tile's partial sums of output 256 are written
+  uint64_t* xfree;      // [2]   TF_EPI arrivals: the epilogue has read them
 };
 
 // ---- the MMA thread (warp 15, lane 0): matrix copies ahead, MMAs as stages land -----------
@@ -315,7 +326,7 @@ __device__ void tf_mma_thread(const TfPassParams& P, const TfGeom& g, unsigned c
       const int s = (int)(nl % g.nst);
       const long long u = nl / g.nst;
       if (u == 0 || bar_test(&B.empty[s], (uint32_t)((u - 1) & 1))) {
-        const TfGeom tg = TfGeom::make(LT.Kp, AXIS);
+        const TfGeom tg = TfGeom::make(LT.Kn, AXIS);
         const uint32_t mbytes = (uint32_t)tg.mp * TF_KC * 4;
         bulk_load(stages + (size_t)s * g.stage + TF_TILE_BYTES,
                   reinterpret_cast<const unsigned char*>(P.A[LT.q]) + (size_t)lc * mbytes, mbytes, &B.full[s]);
@@ -339,7 +350,7 @@ __device__ void tf_mma_thread(const TfPassParams& P, const TfGeom& g, unsigned c
       const int s = (int)(nc % g.nst);
       if (bar_test(&B.full[s], (uint32_t)((nc / g.nst) & 1))) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        const TfGeom cg = TfGeom::make(CT.Kp, AXIS);
+        const TfGeom cg = TfGeom::make(CT.Kn, AXIS);
         const uint32_t acc = tmem + (uint32_t)(a * 256);
         const uint32_t st = smem_u32(stages + (size_t)s * g.stage);
         const uint32_t sm = st + TF_TILE_BYTES;
@@ -358,8 +369,8 @@ __device__ void tf_mma_thread(const TfPassParams& P, const TfGeom& g, unsigned c
             // D[p][k] += S[p][j] T[k][j]: A = tile (K-major, M = 128 pencils), B = matrix
             // (K-major, N = outputs in blocks of up to 256)
             const uint64_t da = smem_desc(st + (uint32_t)ks * 256u, 128, 1024);
-            for (int n0 = 0; n0 < CT.Kp; n0 += 256) {
-              const int nn = CT.Kp - n0 < 256 ? CT.Kp - n0 : 256;
+            for (int n0 = 0; n0 < CT.Kn; n0 += 256) {
+              const int nn = CT.Kn - n0 < 256 ? CT.Kn - n0 : 256;
               const uint64_t db = smem_desc(sm + (uint32_t)(n0 / 8) * 1024u + (uint32_t)ks * 256u, 128, 1024);
               tf_mma(acc + n0, da, db, tf_idesc(nn), accum);
             }
@@ -446,7 +457,7 @@ struct TfZPre {
 
 __device__ __forceinline__ TfZPre tf_z_prefetch(const TfPassParams& P, const TfTile& T, int warp, int lane) {
   TfZPre Z;
-  const int q = T.q, p = (warp & 3) * 32 + lane, h = warp >> 2, half = T.Kp / 2;
+  const int q = T.q, p = (warp & 3) * 32 + lane, h = warp >> 2, half = T.Kn / 2;
   const int kx = T.x0 + p - P.flo[q][0], ky = T.other - P.flo[q][1];
   Z.gl = p < T.npen && kx >= 0 && kx < P.fL[q][0] && ky >= 0 && ky < P.fL[q][1];
   Z.G = tf_green_line(P, q, Z.gl ? kx : 0, Z.gl ? ky : 0);
@@ -463,7 +474,7 @@ __device__ __forceinline__ TfZPre tf_z_prefetch(const TfPassParams& P, const TfT
 template <int AXIS>
 __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTile& T, uint32_t acc, int warp,
                                               int lane, const TfZPre& Z) {
-  const int q = T.q, L = T.L, Kp = T.Kp, npen = T.npen;
+  const int q = T.q, L = T.L, Kp = T.Kn, npen = T.npen;  // Kp: the outputs in TMEM
   float* __restrict__ out = P.out[q];
   const float sc = P.scale[q];
   const int gq = warp & 3, h = warp >> 2;
@@ -597,10 +608,11 @@ __device__ __forceinline__ void tf_store_tile(const TfPassParams& P, const TfTil
 }
 
 template <int AXIS>
-__global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_constant__ TfPassParams P, int maxKp) {
+__global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_constant__ TfPassParams P, int maxKn,
+                                                              int xtra) {
   if (P.stop && *P.stop) return;  // before any TMEM allocation or barrier
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TfGeom g = TfGeom::make(maxKp, AXIS);
+  const TfGeom g = TfGeom::make(maxKn, AXIS, xtra);
   // fixed region (2 KB): barriers, TMEM slot, abort flag; the stages follow
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
   TfBars B;
@@ -610,7 +622,9 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
   B.acc_empty = bars + 2 * TF_MAXST + 2;
   B.done = bars + 2 * TF_MAXST + 4;
   B.land = bars + 2 * TF_MAXST + 5;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TF_MAXST + 5);
+  B.xready = bars + 3 * TF_MAXST + 5;
+  B.xfree = bars + 3 * TF_MAXST + 7;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * TF_MAXST + 9);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
   unsigned char* stages = smem + 2048;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -638,6 +652,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
     for (int i = 0; i < 2; ++i) {
       bar_init(&B.acc_full[i], 1);
       bar_init(&B.acc_empty[i], TF_EPI);
+      bar_init(&B.xready[i], TF_PROD);
+      bar_init(&B.xfree[i], TF_EPI);
     }
     bar_init(B.done, 1);
     *abort = 0;
@@ -663,6 +679,18 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
       int ti = 0, c = 0;
       TfTile T;
       if (my_tiles > 0) T = tf_tile_of<AXIS>(P, blockIdx.x);
+      // output 256 of a 257-output transform (y, z): each producer keeps the partial dot products
+      // of its two 4 x 4 blocks (row group kq, pencils 4 pg ..) over the tile's chunks and stores
+      // them, per row group, in one of two slot sets; the epilogue adds the eight row groups in order
+      TfTile PT;  // the tile being processed, its chunk and its rank among the tiles with xt
+      int pc = 0, pti = 0, pxi = 0;
+      if (my_tiles > 0) PT = T;
+      float xacc[TF_BLK][4];
+#pragma unroll
+      for (int b = 0; b < TF_BLK; ++b)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) xacc[b][j] = 0.f;
+      float* const xpart = reinterpret_cast<float*>(stages + g.xoff());
       auto process = [&](long long k) {
         const int s = (int)(k % g.nst);
         if (!bar_wait(&B.land[s], (uint32_t)((k / g.nst) & 1), abort)) return false;
@@ -685,6 +713,17 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
             float4 v[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) v[r] = ld_shared4(raw + (uint32_t)((4 * kq + r) * TF_P + 4 * pg) * 4u);
+            if (AXIS != 0 && PT.xt) {  // FP32 tile values, FP32 matrix row
+              const float* xr = P.xrow[PT.q] + TF_KC * pc + 4 * kq;
+#pragma unroll
+              for (int r = 0; r < 4; ++r) {
+                const float w = __ldg(xr + r);
+                xacc[b][0] = fmaf(w, v[r].x, xacc[b][0]);
+                xacc[b][1] = fmaf(w, v[r].y, xacc[b][1]);
+                xacc[b][2] = fmaf(w, v[r].z, xacc[b][2]);
+                xacc[b][3] = fmaf(w, v[r].w, xacc[b][3]);
+              }
+            }
             st_shared4(base + tf_cell(4 * pg, kq), tf32r(v[0].x), tf32r(v[1].x), tf32r(v[2].x), tf32r(v[3].x));
             st_shared4(base + tf_cell(4 * pg + 1, kq), tf32r(v[0].y), tf32r(v[1].y), tf32r(v[2].y), tf32r(v[3].y));
             st_shared4(base + tf_cell(4 * pg + 2, kq), tf32r(v[0].z), tf32r(v[1].z), tf32r(v[2].z), tf32r(v[3].z));
@@ -693,6 +732,28 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         bar_arrive(&B.full[s]);
+        if (AXIS != 0 && ++pc == PT.Kp / TF_KC) {  // the tile's last chunk
+          if (PT.xt) {
+            const int par = pxi & 1;
+            // the slot set was last read for the tile with xt two before this one
+            if (pxi >= 2 && !bar_wait(&B.xfree[par], (uint32_t)(((pxi >> 1) - 1) & 1), abort)) return false;
+#pragma unroll
+            for (int b = 0; b < TF_BLK; ++b) {
+              const int i = ptid + b * TF_PROD;
+              if (i < 256) {
+                const int pg = i & 31, kq = i >> 5;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) xpart[(par * 8 + kq) * TF_P + 4 * pg + j] = xacc[b][j];
+              }
+#pragma unroll
+              for (int j = 0; j < 4; ++j) xacc[b][j] = 0.f;
+            }
+            bar_arrive(&B.xready[par]);
+            ++pxi;
+          }
+          pc = 0;
+          if (++pti < my_tiles) PT = tf_tile_of<AXIS>(P, blockIdx.x + pti * gridDim.x);
+        }
         return true;
       };
       bool live = true;
@@ -760,6 +821,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
   } else {
     // ---- epilogue warps 0-7 ----
     uint32_t acc_uses[2] = {0u, 0u};
+    int xi = 0;  // rank of the tile among those whose output 256 the producers contract
+    const float* const xpart = reinterpret_cast<const float*>(stages + g.xoff());
     for (int i = 0; i < my_tiles; ++i) {
       const int a = i % nacc;
       const uint32_t acc = tmem + (uint32_t)(a * 256);
@@ -774,6 +837,25 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
       tf_store_tile<AXIS>(P, T, acc, warp, lane, Z);
       asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
       bar_arrive(&B.acc_empty[a]);
+      if (AXIS != 0 && T.xt) {  // output 256: the producers' partial sums, row groups in order
+        const int par = xi & 1;
+        if (!bar_wait(&B.xready[par], (uint32_t)((xi >> 1) & 1), abort)) break;
+        const int p = (warp & 3) * 32 + lane;
+        if ((warp >> 2) == 0 && p < T.npen && 256 < T.L) {
+          float sum = 0.f;
+#pragma unroll
+          for (int kq = 0; kq < 8; ++kq) sum += xpart[(par * 8 + kq) * TF_P + p];
+          float val = P.scale[T.q] * sum;
+          if (AXIS == 2 && P.mode == 2) {  // the Green factor at frequency 256 of this (kx, ky) line
+            const float gs = Z.gl ? Z.G.g * P.scale[T.q] : 0.f;
+            const float den = fmaf(Z.G.alpha, __ldg(P.C2[T.q][2] + 256), Z.G.beta * __ldg(P.S2[T.q][2] + 256));
+            val = sum * (den > 0.f ? __fdividef(gs, den) : 0.f);
+          }
+          P.out[T.q][T.base0 + p + (long long)(T.lo + 256) * T.estride] = val;
+        }
+        bar_arrive(&B.xfree[par]);
+        ++xi;
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -783,8 +865,8 @@ __global__ void __launch_bounds__(TF_THREADS, 1) k_pass_tf32(const __grid_consta
 }
 
 template <int AXIS>
-static cudaError_t launch_tf32_one(const TfPassParams& P, int maxKp, cudaStream_t s) {
-  const size_t smem = TfGeom::make(maxKp, AXIS).smem();
+static cudaError_t launch_tf32_one(const TfPassParams& P, int maxKn, int xtra, cudaStream_t s) {
+  const size_t smem = TfGeom::make(maxKn, AXIS, xtra).smem();
   auto kern = k_pass_tf32<AXIS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmem);
   if (e != cudaSuccess) return e;
@@ -792,7 +874,7 @@ static cudaError_t launch_tf32_one(const TfPassParams& P, int maxKp, cudaStream_
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // one persistent CTA per SM (each holds all 512 TMEM columns)
-  kern<<<dim3((unsigned)(sms > 0 ? sms : 152)), TF_THREADS, smem, s>>>(P, maxKp);
+  kern<<<dim3((unsigned)(sms > 0 ? sms : 152)), TF_THREADS, smem, s>>>(P, maxKn, xtra);
   return cudaGetLastError();
 }
 
@@ -851,22 +933,28 @@ cudaError_t launch_pass_tf32(const TfPassParams& P0, cudaStream_t s) {
     const cudaError_t e = encode_maps(P);
     if (e != cudaSuccess) return e;
   }
-  int maxKp = 0;
+  int maxKn = 0, xtra = 0;
   for (int q = 0; q < 3; ++q) {
-    if (!pass_tf32_fits(P.Kp[q], P.axis)) return cudaErrorInvalidValue;
-    maxKp = maxKp > P.Kp[q] ? maxKp : P.Kp[q];
+    // output 256 in the producers: y, z only, 257 outputs, 256 of them on the tensor cores
+    if (P.xrow[q] && (P.axis == 0 || P.Kn[q] != 256 || P.L[q] != 257)) return cudaErrorInvalidValue;
+    xtra |= P.xrow[q] != nullptr;
+    if (!P.xrow[q] && P.Kn[q] != P.Kp[q]) return cudaErrorInvalidValue;
+    maxKn = maxKn > P.Kn[q] ? maxKn : P.Kn[q];
   }
+  for (int q = 0; q < 3; ++q)
+    if (!pass_tf32_fits(P.Kn[q], P.axis, xtra)) return cudaErrorInvalidValue;
+  if (xtra && !TfGeom::make(maxKn, P.axis, 1).raw) return cudaErrorInvalidValue;  // TMA producers only
   if (P.mode == 1 && P.axis != 0) return cudaErrorInvalidValue;
   if (P.mode == 2 && P.axis != 2) return cudaErrorInvalidValue;
-  if (P.axis == 0) return launch_tf32_one<0>(P, maxKp, s);
-  if (P.axis == 1) return launch_tf32_one<1>(P, maxKp, s);
-  return launch_tf32_one<2>(P, maxKp, s);
+  if (P.axis == 0) return launch_tf32_one<0>(P, maxKn, xtra, s);
+  if (P.axis == 1) return launch_tf32_one<1>(P, maxKn, xtra, s);
+  return launch_tf32_one<2>(P, maxKn, xtra, s);
 }
 
-bool pass_tf32_fits(int Kp, int axis) {
-  if (Kp < TF_KC || Kp % TF_KC != 0) return false;
-  const TfGeom g = TfGeom::make(Kp, axis);
-  // the accumulator fits TMEM (x: Mp / 128 blocks of 128 columns; y, z: Kp columns) and the
+bool pass_tf32_fits(int Kn, int axis, int xtra) {
+  if (Kn < TF_KC || Kn % TF_KC != 0) return false;
+  const TfGeom g = TfGeom::make(Kn, axis, xtra);
+  // the accumulator fits TMEM (x: Mp / 128 blocks of 128 columns; y, z: Kn columns) and the
   // ring has at least three stages
   return g.acc_cols <= TF_TMEM_COLS && g.nst >= 3 && g.smem() <= (size_t)kMaxDynSmem;
 }

@@ -638,9 +638,19 @@ TF32_TOL = 2e-3  # one 3D transform with TF32 products (11-bit significands), FP
 TF32_RT_TOL = 5e-3  # forward and inverse: six axis passes
 
 
-@pytest.mark.parametrize("case", range(len(TC_DT_CASES)))
+# 257 outputs on y or z (DCT-I over 256 intervals): 256 of them on the tensor cores, output 256
+# contracted by the producers; with mixed pairs the other components of that axis have 256 or
+# 255 outputs, so tiles with and without the producers' output share one launch
+TF32_DT_CASES = TC_DT_CASES + [
+    ((6, 256, 8), ("P", "DCT1", "DST1")),
+    ((8, 6, 256), ("DST1", "P", "DCT1")),
+    ((4, 256, 256), ("DCT3", "DCT1", "DCT1")),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TF32_DT_CASES)))
 def test_tf32_dt_forward_and_round_trip(case):
-    n, kinds = TC_DT_CASES[case]
+    n, kinds = TF32_DT_CASES[case]
     wl = _wl(n, _bc_for(*kinds, mix=True))
     g = Grid(wl.n, wl.bc)
     gp = GpuProblem(wl, "fp32_tf32")
@@ -673,6 +683,30 @@ def test_tf32_green_update(case):
         u = np.zeros(pr.grid.node_shape)
         for q in range(3):
             u[q] = rng.standard_normal() * np.sin(np.linspace(0, np.pi, pr.grid.N[0]))[:, None, None]
+            u[q][~pr.grid.dof_mask(q)] = 0.0
+        p = pr.residual(u, 0 * pr.grad_ustar())[0]
+        gp.set_node(F.FFTM_FIELD_WORK, p)
+        F.fftm_apply(gp.p, F.FFTM_OP_GREEN_UPDATE)
+        got = gp.get_node(F.FFTM_FIELD_U)
+        assert rel_l2(got, pr.green_update(p)) < 3 * TF32_TOL
+    finally:
+        gp.close()
+
+
+@pytest.mark.parametrize("n,kinds", [((8, 6, 256), ("DST1", "P", "DCT1")), ((8, 256, 6), ("DST1", "DCT1", "P"))])
+def test_tf32_green_update_257_outputs(n, kinds):
+    """The Green update on an axis of 257 outputs (the z pass with the Green factor, or the y
+    passes): output 256 from the producers' FP32 dot product, the rest on the tensor cores.
+    A Dirichlet x axis keeps the smallest non-null Green denominator away from zero (with
+    Neumann or periodic conditions on every axis, random input leaves the step conditioned so
+    that even the FP32-FFT path is 2e-5 away from the oracle)."""
+    wl = _cubic_wl(n, _bc_for(*kinds), "TETRA2")
+    pr = Problem(wl)
+    gp = GpuProblem(wl, "fp32_tf32")
+    try:
+        rng = np.random.default_rng(sum(n))
+        u = 1e-3 * rng.standard_normal(pr.grid.node_shape)
+        for q in range(3):
             u[q][~pr.grid.dof_mask(q)] = 0.0
         p = pr.residual(u, 0 * pr.grad_ustar())[0]
         gp.set_node(F.FFTM_FIELD_WORK, p)
