@@ -458,6 +458,17 @@ enum fftm_dt_kind { FFTM_DT_DFT = 0, FFTM_DT_DCT1 = 1, FFTM_DT_DCT3 = 2, FFTM_DT
    argument. */
 int fftm_host_dense_transform(int kind, int n, int inverse, double* out, int* L_out);
 
+/* Test export: the 1D transform of Table 1 of `kind` over an axis of n voxels (inverse 1:
+   its normalised inverse), computed on GPU `device` by the library's FP64 transform pass
+   (the kernels FFTM_OP_DT_FORWARD and FFTM_OP_DT_INVERSE run): a temporary problem of
+   n x 2 x 2 voxels, periodic along y and z, carries the data as a constant along them.
+   in, out: HOST arrays of L doubles (L as for fftm_host_dense_transform), node position
+   lo + c of the kind's range at index c, the coefficients in the library's storage (DCT/DST
+   coefficient k at k, the DFT in halfcomplex order).  The 3D form is FFTM_OP_DT_FORWARD on
+   a problem's WORK field.  FFTM_E_INVALID on a bad argument; the errors of problem creation
+   otherwise. */
+int fftm_dt1d(int device, int kind, int n, int inverse, const double* in, double* out);
+
 /* The normal-mixed strain increment (see fftm_load.mixed): d = -(C0_FF)^-1 <sigma>_F on
    the free components of `mask`, zero elsewhere, C0 the isotropic reference stiffness
    (lambda0, mu0 > 0).  sig and d_out: HOST 3x3 row-major. */

@@ -2117,6 +2117,70 @@ int fftm_host_dense_transform(int kind, int n, int inverse, double* out, int* L_
   return FFTM_OK;
 }
 
+int fftm_dt1d(int device, int kind, int n, int inverse, const double* in, double* out) {
+  if (kind < K_DFT || kind > K_DST3 || n < 2 || n > 4096 || (inverse != 0 && inverse != 1) || !in || !out)
+    return set_err(FFTM_E_INVALID, "bad transform kind, length or array");
+  int lo = 0, L = 0;
+  kind_range(kind, n, &lo, &L);
+  // an n x 2 x 2 problem, periodic along y and z, the kind's face pair on x for every component
+  static const int pair[5][2] = {{FFTM_BC_PERIODIC, FFTM_BC_PERIODIC}, {FFTM_BC_NEUMANN, FFTM_BC_NEUMANN},
+                                 {FFTM_BC_NEUMANN, FFTM_BC_DIRICHLET}, {FFTM_BC_DIRICHLET, FFTM_BC_DIRICHLET},
+                                 {FFTM_BC_DIRICHLET, FFTM_BC_NEUMANN}};
+  std::vector<uint16_t> phase((size_t)n * 4, 0);
+  fftm_material mat;
+  std::memset(&mat, 0, sizeof(mat));
+  mat.law = FFTM_LAW_ISO_ELASTIC;
+  mat.params[0] = 1.0;
+  mat.params[1] = 1.0;
+  mat.quat[0] = 1.0;
+  fftm_problem_desc d;
+  std::memset(&d, 0, sizeof(d));
+  d.n[0] = n;
+  d.n[1] = d.n[2] = 2;
+  d.h[0] = d.h[1] = d.h[2] = 1.0;
+  d.phase = phase.data();
+  d.n_phases = 1;
+  d.materials = &mat;
+  for (int f = 0; f < 2; ++f)
+    for (int q = 0; q < 3; ++q) {
+      d.bc[0][f][q] = pair[kind][f];
+      d.bc[1][f][q] = d.bc[2][f][q] = FFTM_BC_PERIODIC;
+    }
+  d.scheme = FFTM_HEX1;
+  d.green = FFTM_GREEN_B0;
+  d.lambda0 = d.mu0 = 1.0;
+  d.precision = FFTM_FP64;
+  d.tol = 1.0;
+  d.max_iter = 1;
+  d.anderson_depth = 0;
+  d.anderson_period = 3;
+  fftm_ctx* ctx = nullptr;
+  int rc = fftm_ctx_create(&ctx, device, nullptr);
+  if (rc) return rc;
+  fftm_problem* p = nullptr;
+  rc = fftm_problem_create(ctx, &d, &p);
+  if (rc) {
+    fftm_ctx_destroy(ctx);
+    return rc;
+  }
+  // component 0: forward, the input on all four (y, z) lines (the y and z DFTs of a constant
+  // put 4 x the x transform on line (0, 0)); inverse, 4 x the input on line (0, 0) alone (the
+  // normalised y and z inverses spread it to every line)
+  const int N0 = p->N[0];
+  const size_t line = (size_t)N0, count = 3 * 4 * line;
+  std::vector<double> f(count, 0.0);
+  for (int l = 0; l < (inverse ? 1 : 4); ++l)
+    for (int c = 0; c < L; ++c) f[l * line + lo + c] = inverse ? 4.0 * in[c] : in[c];
+  rc = fftm_set_field(p, FFTM_FIELD_WORK, f.data(), 0, count * sizeof(double));
+  if (!rc) rc = fftm_apply(p, inverse ? FFTM_OP_DT_INVERSE : FFTM_OP_DT_FORWARD, nullptr);
+  if (!rc) rc = fftm_get_field(p, FFTM_FIELD_WORK, f.data(), 0, count * sizeof(double));
+  if (!rc)
+    for (int c = 0; c < L; ++c) out[c] = inverse ? f[lo + c] : 0.25 * f[lo + c];
+  fftm_problem_destroy(p);
+  fftm_ctx_destroy(ctx);
+  return rc;
+}
+
 int fftm_host_mixed_increment(const double* sig, int mask, double lambda0, double mu0, double* d_out) {
   if (!sig || !d_out || (mask & ~0x3F) || !(mu0 > 0.0) || !(lambda0 >= 0.0))
     return set_err(FFTM_E_INVALID, "bad mixed increment arguments");

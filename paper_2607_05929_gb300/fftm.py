@@ -45,7 +45,7 @@ EXPORTS = [
     "fftm_reset_state", "fftm_set_profiling", "fftm_kernel_times", "fftm_residual_noalloc",
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
     "fftm_server_inject_start_failures", "fftm_server_set_option",
-    "fftm_host_dense_transform", "fftm_host_mixed_increment", "fftm_host_log_j2",
+    "fftm_host_dense_transform", "fftm_host_mixed_increment", "fftm_host_log_j2", "fftm_dt1d",
 ]
 FFTM_DT_KINDS = {"DFT": 0, "DCT1": 1, "DCT3": 2, "DST1": 3, "DST3": 4}
 FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "other"]
@@ -127,6 +127,8 @@ def load_library(path=LIB_PATH):
         "fftm_set_load_field": ([vp, vp, ctypes.c_int, ctypes.c_size_t], ctypes.c_int),
         "fftm_host_dense_transform": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                                        P(ctypes.c_int)], ctypes.c_int),
+        "fftm_dt1d": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
+                       P(ctypes.c_double)], ctypes.c_int),
         "fftm_host_mixed_increment": ([P(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        P(ctypes.c_double)], ctypes.c_int),
         "fftm_host_log_j2": ([P(ctypes.c_double)] * 5, ctypes.c_int),
@@ -287,6 +289,18 @@ def fftm_set_load(p, A, b=(0.0, 0.0, 0.0), Q=None, mixed=0, T=None):
                     ld.T[a][f][q] = float(T[a][f][q])
     ld.mixed = int(mixed)
     return _check(load_library().fftm_set_load(p, ctypes.byref(ld)))
+
+
+def fftm_dt1d(kind, n, x, inverse=False, device=0):
+    """The 1D transform of Table 1 (or its inverse) of the L values x, on the GPU by the
+    library's FP64 transform pass; returns the L outputs."""
+    k = FFTM_DT_KINDS[kind] if isinstance(kind, str) else int(kind)
+    xin = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros_like(xin)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load_library().fftm_dt1d(int(device), k, int(n), int(bool(inverse)), xin.ctypes.data_as(dp),
+                                    out.ctypes.data_as(dp)))
+    return out
 
 
 def fftm_host_dense_transform(kind, n, inverse=False):
