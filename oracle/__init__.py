@@ -21,11 +21,13 @@ Modules and what they restate:
 * ``solver``      Algorithm 1, one load step (with Neumann tractions through ``stencils``)
 * ``direct``      the same discrete problem assembled as a sparse matrix and solved directly
 
-Parity status of each part is stated in the module headers; Anderson's
-acceleration step has no closed form to pin it against beyond its own
-definition (parity unpinned beyond self-consistency: its decisions are fixed
-by the stated rule and the fixed point it reaches is pinned by the direct
-solve and the laminate closed forms).  The crystal-plasticity law is pinned by its
+Parity status of each part is stated in the module headers.  Anderson's
+combination is pinned by identities of affine maps (the mix of dim + 1 couples
+lands on the fixed point, its residual is M r_min, a 3-free-DOF solve reaches
+the solution right after its first mix); the accelerated iterates of a general
+problem have no closed form (parity unpinned beyond self-consistency: the skip
+decisions are fixed by the stated rule, and the fixed point reached is pinned
+by the direct solve and the laminate closed forms).  The crystal-plasticity law is pinned by its
 single-slip recursion; its full-field polycrystal response is parity unpinned beyond
 the oracle itself (no closed form).
 """
