@@ -28,6 +28,7 @@ the solution right after its first mix); the accelerated iterates of a general
 problem have no closed form (parity unpinned beyond self-consistency: the skip
 decisions are fixed by the stated rule, and the fixed point reached is pinned
 by the direct solve and the laminate closed forms).  The crystal-plasticity law is pinned by its
-single-slip recursion; its full-field polycrystal response is parity unpinned beyond
-the oracle itself (no closed form).
+single-slip recursion and the full-field solve by a two-crystal laminate past yield
+(traction continuity solved independently); its full-field polycrystal response is
+parity unpinned beyond that (no closed form).
 """

@@ -20,8 +20,10 @@ stress (div P)_q = d P_qi / d x_i.
   Pi = C : (A - 1)/2 - sum_s dgamma_s C : sym(A P_s), A = F^p_n^{-T} F^T F F^p_n^{-1},
   tau_s = Pi : P_s (the Mandel stress with C^e ~ 1 in the resolved shear), tau_c at the
   committed Gamma_n.  params = (C11, C12, C44, gdot0, n, tau0, tau_inf, h0, dt).
-  Pinned by the single-slip recursion under simple shear; the full-field polycrystal
-  response is parity unpinned beyond the oracle itself.
+  Pinned by the single-slip recursion under simple shear; the full-field solve through
+  this law by a two-crystal laminate past yield (traction continuity solved independently,
+  tests/test_oracle_cp_laminate.py); the full-field polycrystal response is parity
+  unpinned beyond that.
 * LOG_J2: perfect von Mises plasticity in the logarithmic framework the paper uses for the
   porous medium (Sec. 3.2, after Miehe, Apel and Lambrecht): Hencky strain H = log(F^T F)/2
   split additively, H = H^e + H^p; the stress conjugate to H is T = 2 mu dev H^e + K tr H^e 1
