@@ -83,7 +83,7 @@ def operator_symbol(grid, q, scheme, lambda0, mu0):
 # w_q = tau_q xi'_q (the same signs; the real-space operator pins it).  Its inverse follows the
 # paper's steps: the dot products of p with z and conj(z), the 2 x 2 system for u . z and
 # u . conj(z) obtained by dotting the operator with z and conj(z), then back-substitution.  Reading
-# (R27): the diagonal coefficient of that system is taken from the operator itself,
+# taken: the diagonal coefficient of that system is taken from the operator itself,
 # 2 mu0 + lambda0 / 2 = (4 mu0 + lambda0) / 2 times |z|^2 -- the printed (2 mu0 + lambda0) / 2 would
 # not reduce to Eq. FourierSGO_HEX1 when xi' = 0, while this one does.
 #
@@ -142,7 +142,7 @@ def c0_green_apply(grid, lambda0, mu0, phat, scheme="HEX1"):
     """The C0 discrete Green operator on the real coefficients, zero where |xi|^2 = 0 (the null
     rule of Sec. 2.6).  HEX1, Eq. FourierSGO_HEX1: u_hat = -(p_hat - lambda0 / (2 mu0 + lambda0)
     (v . p_hat) v / |xi|^2) / (2 mu0 |xi|^2).  TETRA2, Eqs. FourierSGO_TETRA2_1/2 with z = v + i w
-    and the reading R27 above."""
+    and the reading of its diagonal coefficient stated above."""
     v, w, xx = c0_vectors(grid, scheme)
     nz = xx > 0.0
     safe = np.where(nz, xx, 1.0)
@@ -156,7 +156,7 @@ def c0_green_apply(grid, lambda0, mu0, phat, scheme="HEX1"):
     pzc = sum(phat[q] * zc[q] for q in range(3))    # p . conj(z)
     zz = sum(zq * zq for zq in z)                   # z . z
     zzc = np.conj(zz)                               # conj(z) . conj(z)
-    d = (2.0 * mu0 + 0.5 * lambda0) * safe          # the diagonal coefficient (R27) times |z|^2
+    d = (2.0 * mu0 + 0.5 * lambda0) * safe          # the diagonal coefficient (read above) times |z|^2
     Ds = d * d - (0.5 * lambda0) ** 2 * np.abs(zz) ** 2
     Ds = np.where(nz, Ds, 1.0)
     # u . z and u . conj(z) from  -p.z = d (u.z) + lambda0/2 (z.z) (u.conj z)  and its conjugate pair

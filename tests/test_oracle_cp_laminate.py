@@ -10,7 +10,8 @@ continuous, S_A[0, :] = S_B[0, :] (Eq. GeneralBCtobesolved with the stencils of 
 test solves those three equations for g_A by its own Newton iteration, with the oracle's
 pointwise law (`oracle.finite.cp_fcc`, pinned separately by the single-slip recursion) from the
 virgin state, and compares with Algorithm 1 run by the oracle on the full grid: one implicit
-increment past yield (Sec. 3.4 law of R18)."""
+increment past yield (power-law slip with Voce hardening, the crystal law of Sec. 3.4 as the
+oracle states it)."""
 
 import numpy as np
 
