@@ -73,3 +73,13 @@ def test_bad_host_arguments_are_refused(F):
         F.fftm_host_mixed_increment(np.eye(3), 1 << 6, 1.0, 1.0)
     with pytest.raises(F.FFTMError):
         F.fftm_host_mixed_increment(np.eye(3), 1, 1.0, 0.0)
+
+
+def test_dt1d_refuses_bad_arguments_before_any_device_work(F):
+    """fftm_dt1d checks its kind, length and arrays before it touches a device."""
+    with pytest.raises(F.FFTMError):
+        F.fftm_dt1d(7, 8, np.zeros(8))
+    with pytest.raises(F.FFTMError):
+        F.fftm_dt1d("DCT1", 1, np.zeros(2))
+    with pytest.raises(F.FFTMError):
+        F.fftm_dt1d("DST1", 5000, np.zeros(4999))
