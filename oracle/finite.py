@@ -22,7 +22,7 @@ stress (div P)_q = d P_qi / d x_i.
   committed Gamma_n.  params = (C11, C12, C44, gdot0, n, tau0, tau_inf, h0, dt).
   Pinned by the single-slip recursion under simple shear; the full-field solve through
   this law by a two-crystal laminate past yield (traction continuity solved independently,
-  tests/test_oracle_cp_laminate.py); the full-field polycrystal response is parity
+  tests/test_oracle_laminate_nonlinear.py); the full-field polycrystal response is parity
   unpinned beyond that.
 * LOG_J2: perfect von Mises plasticity in the logarithmic framework the paper uses for the
   porous medium (Sec. 3.2, after Miehe, Apel and Lambrecht): Hencky strain H = log(F^T F)/2
