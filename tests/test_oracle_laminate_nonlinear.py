@@ -191,3 +191,79 @@ def test_laminate_solve_matches_the_traction_continuity_solution(name, scheme):
         for r in range(G.shape[0]):
             assert np.abs(G[r][:, :, sel] - GL[:, :, None]).max() <= 1e-7 * np.abs(GL).max()
             assert np.abs(P[r][:, :, sel] - SL[:, :, None]).max() <= 1e-6 * np.abs(SL).max()
+
+
+def _virgin_state(law):
+    assert law == J2_LINHARD
+    return {"ep": np.zeros((1, 3, 3, 1, 1, 1)), "p": np.zeros((1, 1, 1, 1))}
+
+
+def _point_law(G, mat, st):
+    P, new = stress(G.reshape(1, 3, 3, 1, 1, 1), [mat], [np.array([0])], st)
+    return P.reshape(3, 3), new
+
+
+@pytest.mark.parametrize("name", ["j2"])
+def test_laminate_two_steps_carry_the_committed_state(name):
+    """Load past yield, then reverse part of the load: the second step's fields are the
+    traction-continuity solution from each layer's state committed at the end of the first
+    (J2 with hardening; a reversed crystal-plasticity increment takes the oracle minutes)."""
+    n = (12, 2, 2)
+    phase = syn.laminate(n, 0, 3)
+    lam, mu = iso_lame(200.0, 0.3)
+    mats = [Material(J2_LINHARD, (lam, mu, 0.15, 1.0)), Material(J2_LINHARD, (lam, mu, 0.3, 2.0))]
+    loads = [np.array([3e-3, 2e-3, -1e-3]), np.array([1e-3, -1e-3, 0.5e-3])]
+    lam0, mu0 = lam, mu
+    A = np.zeros((3, 3))
+    A[:, 0] = loads[0]
+    wl = Workload(name="laminate2_" + name, n=n, phase=phase, materials=mats, bc=axis_bc("D", "P", "P"),
+                  scheme="HEX1", green="B0", lambda0=lam0, mu0=mu0, tol=1e-11, A=A, max_iter=3000)
+    pr = Problem(wl)
+    nA = int(np.sum(phase[:, 0, 0] == 0))
+    nB = n[0] - nA
+    states = [_virgin_state(m.law) for m in mats]
+    for step, a in enumerate(loads):
+        A = np.zeros((3, 3))
+        A[:, 0] = a
+        _, rep = pr.solve_step(A=A)
+        assert rep.converged, step
+        Gs = np.zeros((3, 3))
+        Gs[0, :] = a
+
+        def layers(g):
+            GA, GB = Gs.copy(), Gs.copy()
+            GA[0, :] += g
+            GB[0, :] -= (nA / nB) * g
+            return GA, GB
+
+        def resid(g):
+            GA, GB = layers(g)
+            return _point_law(GA, mats[0], states[0])[0][0, :] - _point_law(GB, mats[1], states[1])[0][0, :]
+
+        g = np.zeros(3)
+        scale = np.abs(_point_law(Gs, mats[0], states[0])[0]).max()
+        for _ in range(60):
+            r = resid(g)
+            if np.linalg.norm(r) < 1e-14 * scale:
+                break
+            J = np.zeros((3, 3))
+            for k in range(3):
+                dg = np.zeros(3)
+                dg[k] = 1e-7
+                J[:, k] = (resid(g + dg) - resid(g - dg)) / 2e-7
+            g = g - np.linalg.solve(J, r)
+        assert np.linalg.norm(resid(g)) < 1e-12 * scale
+        G = pr.last["G"][0]
+        P = pr.last["P"][0]
+        new_states = []
+        for ph, GL in enumerate(layers(g)):
+            SL, st = _point_law(GL, mats[ph], states[ph])
+            sel = phase == ph
+            assert np.abs(G[:, :, sel] - GL[:, :, None]).max() <= 1e-7 * np.abs(GL).max(), (step, ph)
+            assert np.abs(P[:, :, sel] - SL[:, :, None]).max() <= 1e-6 * np.abs(SL).max(), (step, ph)
+            new_states.append(st)
+        states = new_states  # committed at the end of the step, as the solver does
+    # the history mattered: the second step's stress differs from a virgin response
+    SA_virgin = _point_law(layers(g)[0], mats[0], _virgin_state(mats[0].law))[0]
+    SA = _point_law(layers(g)[0], mats[0], states[0])[0]
+    assert np.linalg.norm(P[:, :, phase == 0][:, :, 0] - SA_virgin) > 1e-3 * np.abs(SA_virgin).max()
