@@ -82,6 +82,10 @@ enum fftm_green { FFTM_GREEN_B0 = 0, FFTM_GREEN_MU0 = 1, FFTM_GREEN_C0 = 2 };
    FP32 accumulation), lengths up to 384 node positions per axis (FFTM_E_UNSUPPORTED
    beyond). */
 enum fftm_precision { FFTM_FP64 = 0, FFTM_FP32 = 1, FFTM_FP32_TC = 2, FFTM_FP32_TF32 = 3 };
+
+/* fftm_problem_desc.lambda0 / mu0: take the reference medium from the phases (Sec. 2.6, the
+   paper's choice of half the sum of the extreme values of each Lame coefficient). */
+#define FFTM_REF_AUTO (-1.0)
 enum fftm_law {
   FFTM_LAW_ISO_ELASTIC = 0,   /* params: lambda, mu                          */
   FFTM_LAW_CUBIC_ELASTIC = 1, /* params: C11, C12, C44; quat = orientation     */
@@ -143,7 +147,10 @@ typedef struct fftm_problem_desc {
                                 symmetric (Eq. GeneralBCtobesolved).          */
   int scheme;                /* enum fftm_scheme (Sec. 2.5)                  */
   int green;                 /* enum fftm_green (Sec. 2.6.1 / 2.6.2 / 2.6.3) */
-  double lambda0, mu0;       /* reference material; lambda0 ignored for MU0  */
+  double lambda0, mu0;       /* reference material; lambda0 ignored for MU0;
+                                FFTM_REF_AUTO for either: half the sum of the
+                                largest and smallest value over the phases
+                                (fftm_host_reference_medium)                   */
   int precision;             /* enum fftm_precision                          */
   double tol;                /* equilibrium tolerance epsilon, > 0           */
   int max_iter;              /* I_max, >= 1                                  */
@@ -468,6 +475,14 @@ int fftm_host_dense_transform(int kind, int n, int inverse, double* out, int* L_
    a problem's WORK field.  FFTM_E_INVALID on a bad argument; the errors of problem creation
    otherwise. */
 int fftm_dt1d(int device, int kind, int n, int inverse, const double* in, double* out);
+
+/* The reference medium a descriptor asks for: lambda0 and mu0 as given, or, for the one set to
+   FFTM_REF_AUTO, (max + min) / 2 over the phases of their Lame pair: lambda, mu for the
+   isotropic, J2, B0-linear and logarithmic J2 laws; lambda = C12, mu = (C44 + (C11 - C12) / 2)
+   / 2 for the cubic ones (elastic, St-Venant-Kirchhoff, crystal plasticity); lambda = K -
+   2 mu / 3 for Neo-Hooke.  d: HOST pointer; FFTM_E_INVALID on NULL arguments or an AUTO value
+   without materials.  fftm_problem_create applies it before validating the descriptor. */
+int fftm_host_reference_medium(const fftm_problem_desc* d, double* lambda0, double* mu0);
 
 /* The normal-mixed strain increment (see fftm_load.mixed): d = -(C0_FF)^-1 <sigma>_F on
    the free components of `mask`, zero elsewhere, C0 the isotropic reference stiffness

@@ -1435,6 +1435,33 @@ int solve_step_t(fftm_problem* p, fftm_step_report* rep, double* err_hist, int* 
   return converged ? FFTM_OK : FFTM_NOT_CONVERGED;
 }
 
+// The Lame pair a phase contributes to an automatic reference medium.
+void phase_lame(const fftm_material& m, double* lam, double* mu) {
+  const double* c = m.params;
+  switch (m.law) {
+    case FFTM_LAW_CUBIC_ELASTIC:
+    case FFTM_LAW_SVK_CUBIC:
+    case FFTM_LAW_CP_FCC:
+      *lam = c[1];
+      *mu = 0.5 * (c[2] + 0.5 * (c[0] - c[1]));
+      return;
+    case FFTM_LAW_NEO_HOOKE:
+      *lam = c[1] - 2.0 * c[0] / 3.0;
+      *mu = c[0];
+      return;
+    default:  // isotropic, J2, B0-linear, logarithmic J2: (lambda, mu) first
+      *lam = c[0];
+      *mu = c[1];
+  }
+}
+
+// a copy of the descriptor with the reference medium resolved (FFTM_REF_AUTO)
+int resolved_desc(const fftm_problem_desc* in, fftm_problem_desc* out) {
+  if (!in) return set_err(FFTM_E_INVALID, "null descriptor");
+  *out = *in;
+  return fftm_host_reference_medium(in, &out->lambda0, &out->mu0);
+}
+
 int validate(const fftm_problem_desc* d) {
   if (!d) return set_err(FFTM_E_INVALID, "null descriptor");
   for (int a = 0; a < 3; ++a) {
@@ -1627,8 +1654,12 @@ int fftm_ctx_destroy(fftm_ctx* ctx) {
   return FFTM_OK;
 }
 
-int fftm_problem_workspace_bytes(const fftm_problem_desc* desc, size_t* bytes) {
-  int rc = validate(desc);
+int fftm_problem_workspace_bytes(const fftm_problem_desc* desc0, size_t* bytes) {
+  fftm_problem_desc dres;
+  int rc = resolved_desc(desc0, &dres);
+  if (rc) return rc;
+  const fftm_problem_desc* desc = &dres;
+  rc = validate(desc);
   if (rc) return rc;
   if (!bytes) return set_err(FFTM_E_INVALID, "null bytes");
   Sizes s = sizes_of(desc);
@@ -1711,10 +1742,14 @@ int fftm_problem_create_in(fftm_ctx* ctx, const fftm_problem_desc* desc, void* w
   return problem_create(ctx, desc, workspace, bytes, out);
 }
 
-static int problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc, void* workspace, size_t ws_bytes,
+static int problem_create(fftm_ctx* ctx, const fftm_problem_desc* desc0, void* workspace, size_t ws_bytes,
                           fftm_problem** out) {
   if (!ctx || !out) return set_err(FFTM_E_INVALID, "null ctx or out");
-  int rc = validate(desc);
+  fftm_problem_desc dres;
+  int rc = resolved_desc(desc0, &dres);
+  if (rc) return rc;
+  const fftm_problem_desc* desc = &dres;
+  rc = validate(desc);
   if (rc) return rc;
   CU(cudaSetDevice(ctx->device));
   std::unique_ptr<fftm_problem> p(new (std::nothrow) fftm_problem);
@@ -2179,6 +2214,28 @@ int fftm_dt1d(int device, int kind, int n, int inverse, const double* in, double
   fftm_problem_destroy(p);
   fftm_ctx_destroy(ctx);
   return rc;
+}
+
+int fftm_host_reference_medium(const fftm_problem_desc* d, double* lambda0, double* mu0) {
+  if (!d || !lambda0 || !mu0) return set_err(FFTM_E_INVALID, "null argument");
+  double l0 = d->lambda0, m0 = d->mu0;
+  if (l0 == FFTM_REF_AUTO || m0 == FFTM_REF_AUTO) {
+    if (!d->materials || d->n_phases < 1) return set_err(FFTM_E_INVALID, "FFTM_REF_AUTO needs the materials");
+    double lmin = 0.0, lmax = 0.0, mmin = 0.0, mmax = 0.0;
+    for (int i = 0; i < d->n_phases; ++i) {
+      double l, m;
+      phase_lame(d->materials[i], &l, &m);
+      lmin = (i == 0 || l < lmin) ? l : lmin;
+      lmax = (i == 0 || l > lmax) ? l : lmax;
+      mmin = (i == 0 || m < mmin) ? m : mmin;
+      mmax = (i == 0 || m > mmax) ? m : mmax;
+    }
+    if (l0 == FFTM_REF_AUTO) l0 = 0.5 * (lmin + lmax);
+    if (m0 == FFTM_REF_AUTO) m0 = 0.5 * (mmin + mmax);
+  }
+  *lambda0 = l0;
+  *mu0 = m0;
+  return FFTM_OK;
 }
 
 int fftm_host_mixed_increment(const double* sig, int mask, double lambda0, double mu0, double* d_out) {

@@ -33,6 +33,7 @@ FFTM_LAW_ISO_ELASTIC, FFTM_LAW_CUBIC_ELASTIC, FFTM_LAW_J2_LINHARD, FFTM_LAW_B0_L
 FFTM_LAW_SVK_CUBIC, FFTM_LAW_NEO_HOOKE, FFTM_LAW_CP_FCC, FFTM_LAW_LOG_J2 = 4, 5, 6, 7
 FFTM_FIELD_U, FFTM_FIELD_WORK, FFTM_FIELD_GRAD, FFTM_FIELD_STRESS, FFTM_FIELD_D, FFTM_FIELD_STATE = 0, 1, 2, 3, 4, 5
 FFTM_FIELD_U_LO = 6
+FFTM_REF_AUTO = -1.0  # fftm_problem_desc.lambda0 / mu0: the reference medium from the phases
 FFTM_OPT_RESIDUAL_PASSES, FFTM_OPT_RESIDUAL_TILE, FFTM_OPT_DEVICE_LOOP, FFTM_OPT_CUDA_GRAPH = 0, 1, 2, 3
 FFTM_OP_RESIDUAL, FFTM_OP_DT_FORWARD, FFTM_OP_GREEN, FFTM_OP_DT_INVERSE, FFTM_OP_GREEN_UPDATE = 0, 1, 2, 3, 4
 
@@ -46,6 +47,7 @@ EXPORTS = [
     "fftm_server_create", "fftm_server_submit", "fftm_server_poll", "fftm_server_pending", "fftm_server_destroy",
     "fftm_server_inject_start_failures", "fftm_server_set_option",
     "fftm_host_dense_transform", "fftm_host_mixed_increment", "fftm_host_log_j2", "fftm_dt1d",
+    "fftm_host_reference_medium",
 ]
 FFTM_DT_KINDS = {"DFT": 0, "DCT1": 1, "DCT3": 2, "DST1": 3, "DST3": 4}
 FFTM_KCAT_NAMES = ["residual", "pass_x", "pass_y", "pass_z_fused", "anderson", "other"]
@@ -129,6 +131,8 @@ def load_library(path=LIB_PATH):
                                        P(ctypes.c_int)], ctypes.c_int),
         "fftm_dt1d": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P(ctypes.c_double),
                        P(ctypes.c_double)], ctypes.c_int),
+        "fftm_host_reference_medium": ([P(fftm_problem_desc), P(ctypes.c_double), P(ctypes.c_double)],
+                                       ctypes.c_int),
         "fftm_host_mixed_increment": ([P(ctypes.c_double), ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        P(ctypes.c_double)], ctypes.c_int),
         "fftm_host_log_j2": ([P(ctypes.c_double)] * 5, ctypes.c_int),
@@ -301,6 +305,13 @@ def fftm_dt1d(kind, n, x, inverse=False, device=0):
     _check(load_library().fftm_dt1d(int(device), k, int(n), int(bool(inverse)), xin.ctypes.data_as(dp),
                                     out.ctypes.data_as(dp)))
     return out
+
+
+def fftm_host_reference_medium(desc):
+    """(lambda0, mu0) a descriptor asks for, FFTM_REF_AUTO resolved from its phases (host only)."""
+    l0, m0 = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().fftm_host_reference_medium(ctypes.byref(desc), ctypes.byref(l0), ctypes.byref(m0)))
+    return l0.value, m0.value
 
 
 def fftm_host_dense_transform(kind, n, inverse=False):

@@ -83,3 +83,29 @@ def test_dt1d_refuses_bad_arguments_before_any_device_work(F):
         F.fftm_dt1d("DCT1", 1, np.zeros(2))
     with pytest.raises(F.FFTMError):
         F.fftm_dt1d("DST1", 5000, np.zeros(4999))
+
+
+def test_reference_medium_auto_is_half_the_extremes_over_the_phases(F):
+    """FFTM_REF_AUTO: (max + min) / 2 of each Lame coefficient over the phases' pairs (isotropic,
+    J2: lambda, mu; cubic: C12 and the mid-range shear modulus; Neo-Hooke: K - 2 mu / 3, mu)."""
+    q = (1.0, 0.0, 0.0, 0.0)
+    mats = [(F.FFTM_LAW_ISO_ELASTIC, (1.0, 2.0), q), (F.FFTM_LAW_CUBIC_ELASTIC, (168.0, 121.0, 75.0), q),
+            (F.FFTM_LAW_NEO_HOOKE, (4.0, 10.0), q), (F.FFTM_LAW_J2_LINHARD, (3.0, 0.5, 0.1, 1.0), q)]
+    lams = [1.0, 121.0, 10.0 - 8.0 / 3.0, 3.0]
+    mus = [2.0, 0.5 * (75.0 + 0.5 * (168.0 - 121.0)), 4.0, 0.5]
+    n = (4, 4, 4)
+    bc = [[["D"] * 3] * 2, [["P"] * 3] * 2, [["P"] * 3] * 2]
+    phase = np.zeros(n, dtype=np.uint16)
+    desc, keep = F.make_desc(n, phase, mats, bc, lambda0=F.FFTM_REF_AUTO, mu0=F.FFTM_REF_AUTO)
+    l0, m0 = F.fftm_host_reference_medium(desc)
+    assert l0 == 0.5 * (max(lams) + min(lams)) and m0 == 0.5 * (max(mus) + min(mus))
+    desc, keep = F.make_desc(n, phase, mats, bc, lambda0=7.0, mu0=F.FFTM_REF_AUTO)
+    assert F.fftm_host_reference_medium(desc) == (7.0, 0.5 * (max(mus) + min(mus)))
+    desc, keep = F.make_desc(n, phase, mats, bc, lambda0=7.0, mu0=3.0)
+    assert F.fftm_host_reference_medium(desc) == (7.0, 3.0)
+    # the descriptor checks see the resolved values: AUTO is accepted, another negative is not
+    desc, keep = F.make_desc(n, phase, mats[:1], bc, lambda0=F.FFTM_REF_AUTO, mu0=F.FFTM_REF_AUTO)
+    assert F.fftm_problem_workspace_bytes(desc) > 0
+    desc, keep = F.make_desc(n, phase, mats[:1], bc, lambda0=1.0, mu0=-2.0)
+    with pytest.raises(F.FFTMError):
+        F.fftm_problem_workspace_bytes(desc)
